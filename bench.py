@@ -1,0 +1,429 @@
+"""Benchmark: Image Domain Gridding, grid + degrid throughput on one GB300.
+
+One step = one pass of the whole hot path over the workload: idg_grid (plan's
+subgrid images, taper and A-terms, subgrid FFT, adder into a zeroed grid)
+followed by idg_degrid (splitter, subgrid IFFT, taper and A-terms, degridder)
+from a model grid.  value = visibilities / (time of grid + degrid) in MVis/s,
+with inputs resident in device memory.  e2e = the same metric through the
+host-buffer C-ABI calls (idg_grid_host, idg_degrid_host) with the copies from
+and to page-locked host memory inside the timed region.
+
+Default workload: the LOFAR-like configuration (48 stations, 1128 baselines,
+4096 x 1 s, 16 channels 130-146 MHz, 73.9 M visibilities, subgrid 32, grid
+4096^2 x 4, A-terms every 128 timesteps).  Visibilities (2.37 GB) and grid
+(0.54 GB) exceed the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic issue slots per visibility-pixel of the gridder and degridder:
+# 16 FFMA (4 complex multiply-adds), 2 FFMA for the phase a*X + (b*Y + c*n'),
+# and 2 SFU ops (sin, cos).  Every SM dispatches 4 x 32 of these per cycle.
+ISSUE_PER_VISPIX = 20
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="lofar", choices=["lofar", "tiny"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "gb300" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_workload(name):
+    from paper_1909_07226_gb300 import synthetic as syn
+    if name == "tiny":
+        return syn.make_tiny()
+    return syn.make_lofar(with_vis=True)
+
+
+def workload_config(wl, name):
+    return {
+        "workload": ("LOFAR-like plain: 48 stations (1128 baselines), 4096 x 1 s, 16 ch 130-146 MHz, "
+                     "subgrid 32, grid 4096^2 x 4 c64, A-terms every 128 t"
+                     if name == "lofar" else
+                     "Tiny plain: 8 stations, 64 x 10 s, 8 ch 140-148 MHz, subgrid 24, grid 512^2 x 4 c64"),
+        "n_vis": int(wl.n_vis), "n_baselines": int(wl.n_bl), "n_timesteps": int(wl.n_t),
+        "n_channels": int(wl.n_chan), "subgrid_size": int(wl.subgrid_size), "grid_size": int(wl.grid_size),
+        "kernel_size": float(wl.kernel_size), "max_timesteps_per_subgrid": int(wl.max_timesteps),
+        "aterm_slots": int(wl.n_slots), "w_step": float(wl.w_step),
+        "l2": "inputs larger than L2 (visibilities and grid), no flush",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.sel = []
+        try:
+            import torch
+            props = torch.cuda.get_device_properties(device_index)
+            uuid = str(getattr(props, "uuid", "") or "")
+            if uuid:
+                self.sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            self.sel = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", *self.sel], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+
+
+def oracle_sample(wl, op, target_s: float, seed: int = 0):
+    """Time the FP64 oracle's grid + degrid on a deterministic sample of the
+    workload's subgrids sized to about target_s seconds.  Returns (MVis/s,
+    description, seconds)."""
+    from oracle import oracle as O
+    from paper_1909_07226_gb300 import synthetic as syn
+    n = op.n_sub
+    L = wl.subgrid_size
+    model = syn.random_grid(np.random.default_rng(seed), 1, 2 * L)   # local model patch source
+    kp = op.desc[:, O.D_KP].astype(np.int64)
+
+    def run(ids):
+        sub_desc = op.desc[ids].copy()
+        # place the sampled subgrids on a private small grid so the oracle's
+        # adder and splitter stay O(L^2) per subgrid
+        sub_desc[:, O.D_Q0] = 0
+        sub_desc[:, O.D_R0] = 0
+        sub_desc[:, O.D_LAYER] = 0
+        p_s = O.OraclePlan(sub_desc, 0, 1, op.k_min)
+        wl_s = _SubWorkload(wl, grid_size=2 * L)
+        t0 = time.perf_counter()
+        img = O.subgrid_images(wl, O.OraclePlan(op.desc, 0, op.n_w, op.k_min), ids)
+        uv = O.dft2(img, -1)
+        O.add(wl_s, p_s, uv)
+        t1 = time.perf_counter()
+        sp = O.split(wl_s, p_s, model)
+        im = O.dft2(sp, +1)
+        O.degrid_images(wl, O.OraclePlan(op.desc, 0, op.n_w, op.k_min), im, ids)
+        t2 = time.perf_counter()
+        return t2 - t0
+
+    # calibrate on a few subgrids, then size the sample
+    rng = np.random.default_rng(seed)
+    cal = np.sort(rng.choice(n, size=min(n, 4), replace=False)).astype(np.int32)
+    tc = run(cal)
+    per_vis = tc / max(1, int(kp[cal].sum()))
+    want_vis = target_s / max(per_vis, 1e-12)
+    mean_kp = float(kp.mean())
+    m = int(min(n, max(4, want_vis / mean_kp)))
+    ids = np.sort(rng.choice(n, size=m, replace=False)).astype(np.int32)
+    dt = run(ids)
+    nvis = int(kp[ids].sum())
+    desc = (f"{m} of {n} subgrids drawn uniformly (seed {seed}), {nvis} visibilities, "
+            f"grid + degrid in FP64 on all host cores")
+    return nvis / dt / 1e6, desc, dt
+
+
+class _SubWorkload:
+    """View of a workload with a different grid size (for the oracle sample)."""
+
+    def __init__(self, wl, grid_size):
+        self._wl = wl
+        self.grid_size = grid_size
+
+    def __getattr__(self, k):
+        return getattr(self._wl, k)
+
+
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    wl = make_workload(args.config)
+    op = O.plan(wl)
+    cfg = workload_config(wl, args.config)
+    for _ in range(args.warmup):
+        oracle_sample(wl, op, min(args.cpu_seconds, 2.0), seed=1)
+    vals, secs, descs = [], [], []
+    for k in range(args.steps):
+        v, d, s = oracle_sample(wl, op, args.cpu_seconds, seed=100 + k)
+        vals.append(v)
+        secs.append(s)
+        descs.append(d)
+    value = float(np.mean(vals))
+    cores = os.cpu_count()
+    rec = {
+        "impl": "reference", "metric": "grid+degrid MVis/s", "value": value, "unit": "MVis/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "MVis/s", "cores": cores, "kind": "oracle",
+                         "sample": descs[0] + " (one sample per step)"},
+        "e2e": {"value": value, "unit": "MVis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(rec))
+
+
+def run_gb300(args, world, rank, local):
+    import torch
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    wl = make_workload(args.config)
+    t0 = time.perf_counter()
+    plan = idg.plan_from_workload(wl)
+    plan_s = time.perf_counter() - t0
+    dev = torch.device("cuda", local)
+    vis = torch.from_numpy(wl.vis).to(dev)
+    aterms = torch.from_numpy(wl.aterms).to(dev)
+    taper = torch.from_numpy(wl.taper).to(dev)
+    flags = None if wl.flags is None else torch.from_numpy(wl.flags).to(dev)
+    model_h = syn.random_grid(np.random.default_rng(7), plan.n_w_layers, wl.grid_size)
+    model = torch.from_numpy(model_h).to(dev)
+    grid = torch.empty((plan.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
+    vis_out = torch.empty_like(vis)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        grid.zero_()                       # Algorithm 1 starts from V = 0
+        idg.grid(plan, vis, flags, aterms, taper, grid, stream)
+        idg.degrid(plan, model, flags, aterms, taper, vis_out, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    idg.profile_enable(True)
+    idg.profile_read(reset=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    idg.profile_enable(False)
+    prof = idg.profile_read(reset=True)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(world, ms_total)
+    ms_step = ms_total / args.steps
+    total_vis = sum_over_ranks(world, float(wl.n_vis) * args.steps)
+    value = total_vis / (ms_total * 1e-3) / 1e6
+
+    # kernels: achieved against their rooflines
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    f_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    alu_peak = n_sm * LANES_PER_SM * f_max_mhz * 1e6 / ISSUE_PER_VISPIX / 1e9     # G vis-pix / s
+    kernels = {}
+    for k, d in prof.items():
+        if d["launches"] == 0:
+            continue
+        ent = {"launches": d["launches"] // args.steps, "ms_per_step": d["ms"] / args.steps,
+               "share": d["ms"] / ms_total if ms_total > 0 else None}
+        if k in ("gridder", "degridder"):
+            ach = d["work"] / (d["ms"] * 1e-3) / 1e9
+            ent.update(bound="alu", achieved=ach, peak=alu_peak, unit="Gvispix/s", frac=ach / alu_peak)
+        elif k in ("adder", "splitter"):
+            ach = d["work"] / (d["ms"] * 1e-3) / 1e9
+            ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
+        kernels[k] = ent
+    dom = max(("gridder", "degridder"), key=lambda k: prof[k]["ms"])
+    roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["achieved"], "peak": alu_peak,
+            "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": None,
+            "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} lanes x {f_max_mhz:.0f} MHz / {ISSUE_PER_VISPIX} issue slots "
+                          f"per visibility-pixel", "hbm_peak_basis": hbm_src}
+    gpu_launches = int(sum(d["launches"] for d in prof.values()))
+
+    # end to end through the host-buffer C-ABI calls
+    vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+    vis_h.copy_(torch.from_numpy(wl.vis))
+    model_p = torch.empty(model.shape, dtype=torch.complex64, pin_memory=True)
+    model_p.copy_(torch.from_numpy(model_h))
+    grid_h = torch.empty(grid.shape, dtype=torch.complex64, pin_memory=True)
+    visout_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+    aterms_h = torch.from_numpy(wl.aterms)
+    taper_h = torch.from_numpy(wl.taper)
+    flags_h = None if wl.flags is None else torch.from_numpy(wl.flags)
+
+    def e2e_step():
+        idg.grid_host(plan, vis_h, flags_h, aterms_h, taper_h, grid_h, stream)
+        idg.degrid_host(plan, model_p, flags_h, aterms_h, taper_h, visout_h, stream)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+    e2e_value = sum_over_ranks(world, float(wl.n_vis) * args.e2e_steps) / e2e_s / 1e6
+    nvis = wl.n_vis
+    fl = 0 if wl.flags is None else wl.flags.nbytes
+    # grid_host: visibilities, flags, A-terms, taper in, grid out;
+    # degrid_host: model grid, flags, A-terms, taper in, visibilities out
+    h2d = (nvis * 32 + fl + wl.aterms.nbytes + wl.taper.nbytes) + (model_h.nbytes + fl + wl.aterms.nbytes + wl.taper.nbytes)
+    d2h = grid_h.numel() * 8 + nvis * 32
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        op = O.plan(wl)
+        v, desc, secs = oracle_sample(wl, op, args.cpu_seconds)
+        cpu = {"value": v, "unit": "MVis/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    if rank == 0:
+        rec = {
+            "metric": "grid+degrid MVis/s", "value": value, "unit": "MVis/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(wl, args.config),
+            "roofline": roof, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+            "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu,
+            "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        }
+        print(json.dumps(rec))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_gb300(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * idg.h -- C ABI of a single-GPU (sm_103a) implementation of Image Domain
+ * Gridding (van der Tol, Veenboer & Offringa, "Image Domain Gridding: a fast
+ * method for convolutional resampling of visibilities", A&A 2018).
+ *
+ * The library implements the data-parallel part of the method: the partition
+ * of the visibilities into subgrids (Sect. 3.2), the per-subgrid gridder and
+ * degridder (Algorithms 1 and 2, inner loops; Eq. ShiftedDirectImaging), the
+ * image-domain kernel of taper and per-station 2x2 A-terms (Sect. 3.4), the
+ * batched subgrid transform ("FFT"/"IFFT" of Algorithms 1 and 2) and the adder
+ * and splitter that move subgrids to and from the master uv grid.
+ *
+ * Conventions (all arrays C-contiguous, little-endian):
+ *   visibility   complex64 (8 B: re, im float32) [n_bl][n_t][n_chan][4], pol
+ *                order XX, XY, YX, YY = the 2x2 matrix [[XX, XY], [YX, YY]];
+ *   uvw          float64 [n_bl][n_t][3], metres (uvw = x_q - x_p of baseline (p,q));
+ *   frequency    float64 [n_chan], Hz (channel centres);
+ *   baselines    int32 [n_bl][2], station pair (p, q);
+ *   A-terms      complex64 [n_slots][n_stations][L][L][4], the Jones matrix of a
+ *                station sampled at subgrid pixel (y, x); slot a covers the
+ *                timesteps [aterm_offsets[a], aterm_offsets[a+1]);
+ *   taper        float32 [L][L], real, centre pixel (L/2, L/2) normally 1;
+ *   grid         complex64 [n_w][N][N][4], row index v, column index u;
+ *                pixel q of an axis has uv coordinate (q - N/2)/S, S = N * cell;
+ *   subgrid      complex64 [L][L][4] (uv or image domain).
+ * Subgrid image pixel (y, x) sits at l = (x - L/2) S / L, m = (y - L/2) S / L,
+ * n' = sqrt(1 - l^2 - m^2) - 1 (Sect. 2, pixel positions; Alg. 1/2 use n').
+ *
+ * Gridding (Alg. 1, without the final full-grid FFT and taper division):
+ *   I_p[y][x] = sum_k V_k exp(+2 pi i ((u_k - u0) l + (v_k - v0) m + (w_k - w0) n'))
+ *   I_p <- taper * A_p^H I_p A_q                     (per pixel, 2x2 products)
+ *   V_p[i][j] = L^-2 sum_{y,x} I_p[y][x] exp(-2 pi i ((j-L/2)(x-L/2) + (i-L/2)(y-L/2)) / L)
+ *   grid[layer][r0 + i][q0 + j] += V_p[i][j]
+ * Degridding (Alg. 2, after the full-image steps) is its exact adjoint:
+ *   V_p = grid[layer][r0..][q0..];  I_p = L^-2 sum V_p exp(+2 pi i ...);
+ *   I_p <- taper * A_p I_p A_q^H;  y_k = sum_{y,x} I_p exp(-2 pi i (...)).
+ *
+ * Ownership: the caller owns every data buffer; device pointers are plain CUDA
+ * device (or managed) addresses, host pointers plain host memory.  A plan owns
+ * its own host and device metadata and is immutable after creation; it may be
+ * used from several host threads and streams at once.  Device calls are
+ * asynchronous and stream-ordered on the stream given (NULL = legacy default
+ * stream); a call returns after enqueueing.  Host-buffer variants synchronise.
+ *
+ * Errors: every entry point returns an idg_status; nothing crosses the ABI as
+ * an exception.  idg_last_error() returns a thread-local description of the
+ * last failure on the calling thread.  Invalid arguments are rejected before
+ * any work is enqueued.  No entry point aborts the process.
+ */
+#ifndef IDG_GB300_IDG_H
+#define IDG_GB300_IDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idg_plan idg_plan;
+typedef struct CUstream_st *idg_stream;   /* the same type as cudaStream_t */
+
+typedef enum {
+    IDG_OK = 0,
+    IDG_ERR_INVALID_ARG = 1,    /* a size, pointer or value is out of range        */
+    IDG_ERR_NO_MEMORY = 2,      /* host or device allocation failed                */
+    IDG_ERR_CUDA = 3,           /* a CUDA runtime call or launch failed            */
+    IDG_ERR_TIMEOUT = 4,        /* a bounded device wait gave up                   */
+    IDG_ERR_DEVICE_CHECK = 5,   /* a device-side consistency check failed          */
+    IDG_ERR_UNSUPPORTED = 6     /* valid, but not built into this library (e.g. L) */
+} idg_status;
+
+/* Plan options.  Fill with idg_plan_options_default() and change fields. */
+typedef struct {
+    double kernel_size;              /* beta: main-lobe width of the uv kernel in
+                                        pixels; allowed shift from the subgrid
+                                        centre is (L - beta + 1)/2 (Sect. 4.3).
+                                        Default 7 (Sect. 5.3, Table 1).          */
+    int max_timesteps_per_subgrid;   /* T_max, default 128                        */
+    int precision_mode;              /* IDG_PHASOR_* (see below)                  */
+    int fft_mode;                    /* IDG_FFT_*                                  */
+    int adder_mode;                  /* IDG_ADDER_*                                */
+    int n_host_threads;              /* planner threads, 0 = hardware concurrency */
+} idg_plan_options;
+
+enum { IDG_PHASOR_SINCOS = 0,      /* FP32 sin/cos of every phase                  */
+       IDG_PHASOR_RECURRENCE = 1 };/* channel recurrence, re-anchored periodically  */
+enum { IDG_FFT_FP32 = 0 };
+enum { IDG_ADDER_ATOMIC = 0 };
+
+typedef struct {
+    int64_t n_subgrids;       /* P, number of blocks                              */
+    int64_t n_vis_planned;    /* sum of K_p (flags are not known to the plan)     */
+    int64_t n_vis_dropped;    /* visibilities whose support is off the grid       */
+    int64_t max_kp;           /* largest K_p                                      */
+    int32_t n_w_layers;       /* layers of the grid (1 without W-layers)          */
+    int32_t w_layer_min;      /* k of layer 0: w0(layer) = (layer + min) * w_step */
+    int32_t subgrid_size;     /* L                                                */
+    int32_t grid_size;        /* N                                                */
+    int32_t n_bl, n_t, n_chan, n_stations, n_slots;
+    int32_t device;           /* CUDA device holding the plan's metadata          */
+} idg_plan_stats;
+
+/* Number of int32 fields per exported subgrid descriptor, and their order. */
+#define IDG_DESC_FIELDS 10
+enum { IDG_DESC_BASELINE = 0, IDG_DESC_SLOT, IDG_DESC_T0, IDG_DESC_NT, IDG_DESC_C0,
+       IDG_DESC_NC, IDG_DESC_Q0, IDG_DESC_R0, IDG_DESC_LAYER, IDG_DESC_KP };
+
+void idg_plan_options_default(idg_plan_options *opts);
+
+/*
+ * Partition the visibilities into subgrids (Sect. 3.2, Fig. 2) and upload the
+ * plan's metadata (descriptors, uvw, channel scales) to the current device.
+ *
+ * Block rule (deterministic): per baseline (input order), per A-term slot, the
+ * smallest number G of contiguous channel groups (the first n_chan mod G groups
+ * one channel larger) such that every single timestep of every group fits by
+ * size; then, per group, timesteps are added in order while the block still
+ * fits and has at most T_max timesteps.  A block fits when every sample's grid
+ * pixel position pu = u/lambda * S + N/2 (and pv) lies within (L - beta + 1)/2
+ * of the centre Cu = floor((min + max)/2 + 1/2), the box [Cu - L/2, Cu + L/2)
+ * lies inside [0, N) on both axes, and (with w_step > 0) its w spread is at
+ * most w_step.  A lone timestep that does not fit is dropped and counted.
+ * Layers: k = floor(mid_w / w_step + 1/2), w0 = k * w_step; w_step = 0 means
+ * a single layer with w0 = 0.  Descriptors are ordered (baseline, slot, group,
+ * first timestep).  The plan is bit-identical on every host (FP64, no fused
+ * multiply-add).
+ *
+ * uvw_m          [n_bl][n_t][3] float64, host, metres, finite
+ * freqs_hz       [n_chan] float64, host, > 0, finite
+ * baselines      [n_bl][2] int32, host, station indices in [0, n_stations)
+ * aterm_offsets  [n_slots + 1] int32, host, 0 = off[0] < off[1] < ... = n_t
+ * subgrid_size   L, even, L >= kernel_size + 1
+ * grid_size      N, even, N >= L
+ * cell_size_rad  pixel size of the image, > 0 (S = N * cell)
+ * w_step_lambda  >= 0, W-layer spacing in wavelengths (0: no W-layers)
+ * opts           NULL for defaults
+ * out            receives the plan (NULL on failure)
+ * Errors: IDG_ERR_INVALID_ARG (message says which argument), IDG_ERR_NO_MEMORY,
+ *         IDG_ERR_CUDA.
+ */
+idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const int32_t *baselines,
+                           const int32_t *aterm_offsets, int n_bl, int n_t, int n_chan,
+                           int n_stations, int n_slots, int subgrid_size, int grid_size,
+                           double cell_size_rad, double w_step_lambda,
+                           const idg_plan_options *opts, idg_plan **out);
+
+/* Summary numbers of a plan (host only). */
+idg_status idg_plan_info(const idg_plan *plan, idg_plan_stats *out);
+
+/* Copy the descriptors, IDG_DESC_FIELDS int32 per subgrid in plan order, into
+   desc[cap_subgrids][IDG_DESC_FIELDS] (host).  Fails with IDG_ERR_INVALID_ARG
+   if cap_subgrids < n_subgrids. */
+idg_status idg_plan_export(const idg_plan *plan, int32_t *desc, int64_t cap_subgrids);
+
+/* Release the plan and its device metadata.  The caller must ensure that no
+   work using the plan is still in flight.  NULL is ignored. */
+void idg_plan_destroy(idg_plan *plan);
+
+/*
+ * Gridding, Algorithm 1 (subgrid images, taper and A-terms, subgrid FFT, adder).
+ * d_vis     device complex64 [n_bl][n_t][n_chan][4]
+ * d_flags   device uint8 [n_bl][n_t][n_chan], nonzero = flagged (weight 0), or NULL
+ * d_aterms  device complex64 [n_slots][n_stations][L][L][4], or NULL = identity
+ * d_taper   device float32 [L][L] (required)
+ * d_grid    device complex64 [n_w][N][N][4]; the result is ADDED (Alg. 1 starts
+ *           from V = 0: zero it first), so several plans may sum into one grid.
+ * Summation order on the grid is not fixed (atomic adds): results agree with
+ * the FP64 definition to FP32 rounding, not bit for bit across runs.
+ * Device scratch of at most 512 MiB is taken from the stream-ordered allocator.
+ */
+idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
+                    const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);
+
+/*
+ * Degridding, Algorithm 2 (splitter, subgrid IFFT, taper and A-terms, degridder).
+ * d_grid     device complex64 [n_w][N][N][4]
+ * d_vis_out  device complex64 [n_bl][n_t][n_chan][4], OVERWRITTEN: flagged and
+ *            dropped visibilities are set to 0.
+ * Other arguments as for idg_grid.
+ */
+idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d_flags,
+                      const void *d_aterms, const float *d_taper, void *d_vis_out,
+                      idg_stream stream);
+
+/*
+ * The same two operations on HOST buffers (layouts as above): inputs are copied
+ * to device memory taken from the library's stream-ordered pool, the operation
+ * runs on `stream`, the result is copied back and the call returns when it is
+ * in h_grid / h_vis_out.  Page-locked host memory gives the full copy
+ * bandwidth.  h_grid is OVERWRITTEN with the grid of these visibilities (the
+ * device grid starts from zero); h_vis_out is overwritten as in idg_degrid.
+ */
+idg_status idg_grid_host(const idg_plan *plan, const void *h_vis, const uint8_t *h_flags,
+                         const void *h_aterms, const float *h_taper, void *h_grid, idg_stream stream);
+idg_status idg_degrid_host(const idg_plan *plan, const void *h_grid, const uint8_t *h_flags,
+                           const void *h_aterms, const float *h_taper, void *h_vis_out,
+                           idg_stream stream);
+
+/*
+ * Stage entry points over the plan's subgrids [first, first + count) in plan
+ * order.  d_subgrids is a device complex64 [count][L][L][4] buffer owned by
+ * the caller.  They expose the intermediate states of Algorithms 1 and 2.
+ *
+ * idg_grid_subgrids    direct sum + taper + A_p^H . A_q  (image domain)
+ * idg_fft_subgrids     in-place centred transform, direction -1 (image -> uv,
+ *                      Alg. 1) or +1 (uv -> image, Alg. 2), both scaled by L^-2
+ * idg_add_subgrids     grid[layer][r0 + i][q0 + j] += subgrid[i][j]
+ * idg_split_subgrids   subgrid[i][j] = grid[layer][r0 + i][q0 + j]
+ * idg_degrid_subgrids  taper + A_p . A_q^H, then the degridding sum, from image
+ *                      domain subgrids; writes only the visibilities of these
+ *                      subgrids (flagged ones as 0).
+ */
+idg_status idg_grid_subgrids(const idg_plan *plan, int64_t first, int64_t count, const void *d_vis,
+                             const uint8_t *d_flags, const void *d_aterms, const float *d_taper,
+                             void *d_subgrids, idg_stream stream);
+idg_status idg_fft_subgrids(const idg_plan *plan, int64_t count, int direction, void *d_subgrids,
+                            idg_stream stream);
+idg_status idg_add_subgrids(const idg_plan *plan, int64_t first, int64_t count, const void *d_subgrids,
+                            void *d_grid, idg_stream stream);
+idg_status idg_split_subgrids(const idg_plan *plan, int64_t first, int64_t count, const void *d_grid,
+                              void *d_subgrids, idg_stream stream);
+idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t count, const void *d_subgrids,
+                               const uint8_t *d_flags, const void *d_aterms, const float *d_taper,
+                               void *d_vis_out, idg_stream stream);
+
+/*
+ * Kernel timing.  While enabled, every kernel launch of the library is
+ * bracketed by two CUDA events recorded on the launch stream.  idg_profile_read
+ * waits for the recorded events, adds their elapsed times into per-kernel
+ * totals and returns the totals since the last reset:
+ *   launches[k]  number of launches of kernel k
+ *   ms[k]        summed device time (event to event) in milliseconds
+ *   work[k]      algorithmic work of those launches: visibility-pixel products
+ *                (sum of K_p * L^2) for the gridder and degridder, bytes moved
+ *                for the adder (read subgrid + read and write grid, 96 B per
+ *                pixel) and the splitter (64 B per pixel), subgrids for the FFT.
+ * Arrays have IDG_KERNEL_COUNT entries; any of them may be NULL.  Do not enable
+ * timing while a stream is being captured into a CUDA graph.
+ */
+enum { IDG_KERNEL_GRIDDER = 0, IDG_KERNEL_FFT, IDG_KERNEL_ADDER, IDG_KERNEL_SPLITTER, IDG_KERNEL_DEGRIDDER,
+       IDG_KERNEL_COUNT };
+void idg_profile_enable(int on);
+idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset);
+
+/* Text of a status code, and the last error message of the calling thread. */
+const char *idg_status_string(idg_status status);
+const char *idg_last_error(void);
+
+/* Subgrid sizes L compiled into this library: writes up to cap values, returns
+   how many there are. */
+int idg_supported_subgrid_sizes(int32_t *sizes, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDG_GB300_IDG_H */

@@ -1,0 +1,625 @@
+// C ABI: plan object, argument validation, device metadata and the composite
+// gridding / degridding calls built from the stage kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+
+#include "idg_internal.h"
+
+namespace idg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+idg_status fail(idg_status st, const std::string &msg) {
+    set_error(msg);
+    return st;
+}
+
+idg_status cuda_fail(int err, const char *what) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%d)", what, cudaGetErrorString((cudaError_t)err), err);
+    set_error(buf);
+    return err == cudaErrorMemoryAllocation ? IDG_ERR_NO_MEMORY : IDG_ERR_CUDA;
+}
+
+// One stream-ordered memory pool per device for the subgrid scratch, kept
+// alive (release threshold = max) so repeated calls do not return memory to
+// the driver between steps.
+static cudaMemPool_t scratch_pool(int device) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= 64) return nullptr;
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        pools[device] = pool;
+    }
+    return pools[device];
+}
+
+static idg_status scratch_alloc(int device, size_t bytes, cudaStream_t s, void **p) {
+    cudaMemPool_t pool = scratch_pool(device);
+    if (!pool) return fail(IDG_ERR_CUDA, "cannot create the scratch memory pool");
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
+    return IDG_OK;
+}
+
+static constexpr size_t kScratchBudget = size_t(512) << 20;
+
+static int64_t chunk_subgrids(const idg_plan *p) {
+    const size_t per = (size_t)p->L * p->L * 4 * 8;
+    int64_t c = (int64_t)(kScratchBudget / per);
+    return std::max<int64_t>(1, std::min<int64_t>(c, p->stats.n_subgrids));
+}
+
+static idg_status check_device(const idg_plan *p) {
+    if (p->device < 0) return fail(IDG_ERR_INVALID_ARG, "the plan was created without a CUDA device");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device)
+        return fail(IDG_ERR_INVALID_ARG, "plan was created on device " + std::to_string(p->device) +
+                                             " but the current device is " + std::to_string(dev));
+    return IDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing
+
+namespace {
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+    double work;
+};
+std::vector<ProfRec> g_prof_pending;
+int64_t g_prof_launches[IDG_KERNEL_COUNT] = {};
+double g_prof_ms[IDG_KERNEL_COUNT] = {};
+double g_prof_work[IDG_KERNEL_COUNT] = {};
+}  // namespace
+
+ProfileScope::ProfileScope(int k, void *s, double w) : kernel(k), stream(s), ev{nullptr, nullptr}, work(w), on(false) {
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        on = g_prof_on;
+    }
+    if (!on) return;
+    if (cudaEventCreate((cudaEvent_t *)&ev[0]) != cudaSuccess || cudaEventCreate((cudaEvent_t *)&ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        on = false;
+        return;
+    }
+    cudaEventRecord((cudaEvent_t)ev[0], (cudaStream_t)stream);
+}
+
+ProfileScope::~ProfileScope() {
+    if (!on) return;
+    cudaEventRecord((cudaEvent_t)ev[1], (cudaStream_t)stream);
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_pending.push_back({kernel, (cudaEvent_t)ev[0], (cudaEvent_t)ev[1], work});
+}
+
+}  // namespace idg
+
+using namespace idg;
+
+idg::Geometry idg_plan::geometry() const {
+    Geometry g;
+    g.L = L;
+    g.N = N;
+    g.n_t = n_t;
+    g.n_chan = n_chan;
+    g.n_stations = n_stations;
+    g.S = S;
+    g.k_uv = 6.283185307179586476925286766559 * S / (double)L;
+    g.sub = d_sub;
+    g.order = d_order;
+    g.uvw = d_uvw;
+    g.scale = d_scale;
+    g.nprime = d_nprime;
+    return g;
+}
+
+extern "C" {
+
+void idg_plan_options_default(idg_plan_options *o) {
+    if (!o) return;
+    o->kernel_size = 7.0;
+    o->max_timesteps_per_subgrid = 128;
+    o->precision_mode = IDG_PHASOR_SINCOS;
+    o->fft_mode = IDG_FFT_FP32;
+    o->adder_mode = IDG_ADDER_ATOMIC;
+    o->n_host_threads = 0;
+}
+
+const char *idg_status_string(idg_status s) {
+    switch (s) {
+    case IDG_OK: return "ok";
+    case IDG_ERR_INVALID_ARG: return "invalid argument";
+    case IDG_ERR_NO_MEMORY: return "out of memory";
+    case IDG_ERR_CUDA: return "CUDA error";
+    case IDG_ERR_TIMEOUT: return "device wait timed out";
+    case IDG_ERR_DEVICE_CHECK: return "device consistency check failed";
+    case IDG_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *idg_last_error(void) { return g_last_error.c_str(); }
+
+void idg_profile_enable(int on) {
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    g_prof_on = on != 0;
+}
+
+idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset) {
+    std::vector<ProfRec> pend;
+    {
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        pend.swap(g_prof_pending);
+    }
+    idg_status st = IDG_OK;
+    for (auto &r : pend) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && st == IDG_OK) st = cuda_fail(e, "reading kernel timing events");
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        std::lock_guard<std::mutex> lock(g_prof_mu);
+        g_prof_launches[r.kernel] += 1;
+        g_prof_ms[r.kernel] += t;
+        g_prof_work[r.kernel] += r.work;
+    }
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    for (int k = 0; k < IDG_KERNEL_COUNT; ++k) {
+        if (launches) launches[k] = g_prof_launches[k];
+        if (ms) ms[k] = g_prof_ms[k];
+        if (work) work[k] = g_prof_work[k];
+        if (reset) {
+            g_prof_launches[k] = 0;
+            g_prof_ms[k] = 0.0;
+            g_prof_work[k] = 0.0;
+        }
+    }
+    return st;
+}
+
+int idg_supported_subgrid_sizes(int32_t *sizes, int cap) {
+    static const int32_t all[] = {8, 16, 24, 32, 48, 64};
+    int n = 0;
+    for (int32_t L : all)
+        if (gridder_supported(L)) {
+            if (sizes && n < cap) sizes[n] = L;
+            ++n;
+        }
+    return n;
+}
+
+void idg_plan_destroy(idg_plan *p) {
+    if (!p) return;
+    if (p->device < 0) {
+        delete p;
+        return;
+    }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (p->device >= 0) cudaSetDevice(p->device);
+    cudaFree(p->d_sub);
+    cudaFree(p->d_order);
+    cudaFree(p->d_uvw);
+    cudaFree(p->d_scale);
+    cudaFree(p->d_nprime);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete p;
+}
+
+idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const int32_t *baselines,
+                           const int32_t *aterm_offsets, int n_bl, int n_t, int n_chan, int n_stations,
+                           int n_slots, int L, int N, double cell, double w_step,
+                           const idg_plan_options *opts, idg_plan **out) {
+    if (!out) return fail(IDG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    idg_plan_options o;
+    idg_plan_options_default(&o);
+    if (opts) o = *opts;
+    if (!uvw_m || !freqs_hz || !baselines || !aterm_offsets)
+        return fail(IDG_ERR_INVALID_ARG, "uvw, freqs, baselines and aterm_offsets are required");
+    if (n_bl < 1 || n_t < 1 || n_chan < 1 || n_stations < 1 || n_slots < 1)
+        return fail(IDG_ERR_INVALID_ARG, "n_bl, n_t, n_chan, n_stations and n_slots must be >= 1");
+    if (!(o.kernel_size >= 1.0) || !std::isfinite(o.kernel_size))
+        return fail(IDG_ERR_INVALID_ARG, "kernel_size must be a finite number >= 1");
+    if (L < 2 || L % 2 != 0) return fail(IDG_ERR_INVALID_ARG, "subgrid_size must be even and >= 2");
+    if ((double)L < o.kernel_size + 1.0)
+        return fail(IDG_ERR_INVALID_ARG, "subgrid_size must be >= kernel_size + 1");
+    if (N < L || N % 2 != 0) return fail(IDG_ERR_INVALID_ARG, "grid_size must be even and >= subgrid_size");
+    if (!(cell > 0.0) || !std::isfinite(cell)) return fail(IDG_ERR_INVALID_ARG, "cell_size must be > 0");
+    if (!((double)N * cell < 2.0))
+        return fail(IDG_ERR_INVALID_ARG, "image size N * cell must be < 2 (direction cosines)");
+    if (!(w_step >= 0.0) || !std::isfinite(w_step)) return fail(IDG_ERR_INVALID_ARG, "w_step must be >= 0");
+    if (o.max_timesteps_per_subgrid < 1) return fail(IDG_ERR_INVALID_ARG, "max_timesteps_per_subgrid must be >= 1");
+    if (o.precision_mode != IDG_PHASOR_SINCOS && o.precision_mode != IDG_PHASOR_RECURRENCE)
+        return fail(IDG_ERR_INVALID_ARG, "unknown precision_mode");
+    if (o.fft_mode != IDG_FFT_FP32) return fail(IDG_ERR_INVALID_ARG, "unknown fft_mode");
+    if (o.adder_mode != IDG_ADDER_ATOMIC) return fail(IDG_ERR_INVALID_ARG, "unknown adder_mode");
+    if (aterm_offsets[0] != 0 || aterm_offsets[n_slots] != n_t)
+        return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must start at 0 and end at n_t");
+    for (int a = 0; a < n_slots; ++a)
+        if (aterm_offsets[a + 1] <= aterm_offsets[a])
+            return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must be strictly increasing");
+    for (int b = 0; b < n_bl; ++b)
+        for (int k = 0; k < 2; ++k)
+            if (baselines[2 * b + k] < 0 || baselines[2 * b + k] >= n_stations)
+                return fail(IDG_ERR_INVALID_ARG, "baseline " + std::to_string(b) + " names a station out of range");
+    for (int c = 0; c < n_chan; ++c)
+        if (!(freqs_hz[c] > 0.0) || !std::isfinite(freqs_hz[c]))
+            return fail(IDG_ERR_INVALID_ARG, "frequencies must be finite and > 0");
+    const size_t n_uvw = (size_t)n_bl * n_t * 3;
+    for (size_t i = 0; i < n_uvw; ++i)
+        if (!std::isfinite(uvw_m[i])) return fail(IDG_ERR_INVALID_ARG, "uvw must be finite");
+
+    idg_plan *p = new (std::nothrow) idg_plan();
+    if (!p) return fail(IDG_ERR_NO_MEMORY, "host allocation of the plan failed");
+    p->opts = o;
+    p->n_bl = n_bl; p->n_t = n_t; p->n_chan = n_chan; p->n_stations = n_stations; p->n_slots = n_slots;
+    p->L = L; p->N = N; p->cell = cell; p->w_step = w_step;
+    p->S = (double)N * cell;
+    p->baselines.assign(baselines, baselines + 2 * (size_t)n_bl);
+
+    PlanParams pp{uvw_m, freqs_hz, aterm_offsets, n_bl, n_t, n_chan, n_slots, L, N, cell, w_step,
+                  o.kernel_size, o.max_timesteps_per_subgrid, o.n_host_threads};
+    PlanResult pr;
+    try {
+        pr = make_plan(pp);
+    } catch (const std::bad_alloc &) {
+        delete p;
+        return fail(IDG_ERR_NO_MEMORY, "host allocation in the planner failed");
+    }
+    const int64_t n_sub = (int64_t)(pr.desc.size() / kDescFields);
+    p->desc = std::move(pr.desc);
+    memset(&p->stats, 0, sizeof p->stats);
+    p->stats.n_subgrids = n_sub;
+    p->stats.n_vis_dropped = pr.n_dropped;
+    p->stats.n_w_layers = pr.n_w;
+    p->stats.w_layer_min = pr.k_min;
+    p->stats.subgrid_size = L;
+    p->stats.grid_size = N;
+    p->stats.n_bl = n_bl; p->stats.n_t = n_t; p->stats.n_chan = n_chan;
+    p->stats.n_stations = n_stations; p->stats.n_slots = n_slots;
+    int64_t planned = 0, max_kp = 0;
+    for (int64_t s = 0; s < n_sub; ++s) {
+        const int64_t kp = p->desc[s * kDescFields + IDG_DESC_KP];
+        planned += kp;
+        max_kp = std::max(max_kp, kp);
+    }
+    p->stats.n_vis_planned = planned;
+    p->kp_prefix_plan.assign((size_t)n_sub + 1, 0);
+    for (int64_t s = 0; s < n_sub; ++s)
+        p->kp_prefix_plan[s + 1] = p->kp_prefix_plan[s] + p->desc[s * kDescFields + IDG_DESC_KP];
+    p->stats.max_kp = max_kp;
+    p->any_dropped = pr.n_dropped > 0;
+
+    // device metadata; without any CUDA device the plan stays host-only
+    // (info and export work, device calls are rejected)
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || n_dev == 0) {
+        cudaGetLastError();
+        p->device = -1;
+        p->stats.device = -1;
+        *out = p;
+        return IDG_OK;
+    }
+    e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    p->stats.device = p->device;
+
+    std::vector<DevSubgrid> hsub((size_t)std::max<int64_t>(n_sub, 1));
+    for (int64_t s = 0; s < n_sub; ++s) {
+        const int32_t *d = &p->desc[s * kDescFields];
+        DevSubgrid &g = hsub[s];
+        g.bl = d[IDG_DESC_BASELINE]; g.slot = d[IDG_DESC_SLOT]; g.t0 = d[IDG_DESC_T0]; g.nt = d[IDG_DESC_NT];
+        g.c0 = d[IDG_DESC_C0]; g.nc = d[IDG_DESC_NC]; g.q0 = d[IDG_DESC_Q0]; g.r0 = d[IDG_DESC_R0];
+        g.layer = d[IDG_DESC_LAYER]; g.kp = d[IDG_DESC_KP];
+        g.st_p = baselines[2 * g.bl]; g.st_q = baselines[2 * g.bl + 1];
+        g.u0 = ((double)g.q0 + 0.5 * L - 0.5 * N) / p->S;
+        g.v0 = ((double)g.r0 + 0.5 * L - 0.5 * N) / p->S;
+        g.w0 = w_step > 0.0 ? (double)(g.layer + pr.k_min) * w_step : 0.0;
+        g.pad = 0.0;
+    }
+    // device work order: most visibilities first (longest-processing-time first
+    // for the block scheduler), ties in plan order
+    std::vector<int32_t> order((size_t)std::max<int64_t>(n_sub, 1));
+    std::iota(order.begin(), order.begin() + n_sub, 0);
+    std::stable_sort(order.begin(), order.begin() + n_sub,
+                     [&](int32_t a, int32_t b) { return hsub[a].kp > hsub[b].kp; });
+    p->kp_prefix_order.assign((size_t)n_sub + 1, 0);
+    for (int64_t s = 0; s < n_sub; ++s) p->kp_prefix_order[s + 1] = p->kp_prefix_order[s] + hsub[order[s]].kp;
+    std::vector<double> scale(n_chan);
+    for (int c = 0; c < n_chan; ++c) scale[c] = freqs_hz[c] / kSpeedOfLight;
+    std::vector<float> nprime((size_t)L * L);
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            const double l = ((double)x - 0.5 * L) * p->S / L;
+            const double m = ((double)y - 0.5 * L) * p->S / L;
+            nprime[(size_t)y * L + x] = (float)(std::sqrt(1.0 - l * l - m * m) - 1.0);
+        }
+
+    struct Up { void **dst; const void *src; size_t bytes; const char *what; };
+    Up ups[] = {
+        {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
+        {(void **)&p->d_order, order.data(), sizeof(int32_t) * order.size(), "work order"},
+        {(void **)&p->d_uvw, uvw_m, sizeof(double) * n_uvw, "uvw"},
+        {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
+        {(void **)&p->d_nprime, nprime.data(), sizeof(float) * nprime.size(), "n' table"},
+    };
+    for (auto &u : ups) {
+        e = cudaMalloc(u.dst, u.bytes);
+        if (e != cudaSuccess) {
+            idg_status st = cuda_fail(e, (std::string("cudaMalloc(") + u.what + ")").c_str());
+            idg_plan_destroy(p);
+            return st;
+        }
+        e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            idg_status st = cuda_fail(e, (std::string("cudaMemcpy(") + u.what + ")").c_str());
+            idg_plan_destroy(p);
+            return st;
+        }
+    }
+    *out = p;
+    return IDG_OK;
+}
+
+idg_status idg_plan_info(const idg_plan *p, idg_plan_stats *out) {
+    if (!p || !out) return fail(IDG_ERR_INVALID_ARG, "plan and out are required");
+    *out = p->stats;
+    return IDG_OK;
+}
+
+idg_status idg_plan_export(const idg_plan *p, int32_t *desc, int64_t cap) {
+    if (!p || !desc) return fail(IDG_ERR_INVALID_ARG, "plan and desc are required");
+    if (cap < p->stats.n_subgrids) return fail(IDG_ERR_INVALID_ARG, "desc capacity is smaller than n_subgrids");
+    std::copy(p->desc.begin(), p->desc.end(), desc);
+    return IDG_OK;
+}
+
+static idg_status check_call(const idg_plan *p, const void *a, const char *an, const void *b, const char *bn) {
+    if (!p) return fail(IDG_ERR_INVALID_ARG, "plan is NULL");
+    if (!a) return fail(IDG_ERR_INVALID_ARG, std::string(an) + " is NULL");
+    if (!b) return fail(IDG_ERR_INVALID_ARG, std::string(bn) + " is NULL");
+    if (!gridder_supported(p->L))
+        return fail(IDG_ERR_UNSUPPORTED, "subgrid size " + std::to_string(p->L) + " is not compiled in");
+    return check_device(p);
+}
+
+// algorithmic work of a launch over subgrids [first, first + count)
+static double vispix(const idg_plan *p, int64_t first, int64_t count, bool use_order) {
+    const auto &pre = use_order ? p->kp_prefix_order : p->kp_prefix_plan;
+    return (double)(pre[first + count] - pre[first]) * p->L * p->L;
+}
+static double pixels(const idg_plan *p, int64_t count) { return (double)count * p->L * p->L; }
+
+static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
+    if (first < 0 || count < 0 || first + count > p->stats.n_subgrids)
+        return fail(IDG_ERR_INVALID_ARG, "subgrid range out of the plan");
+    return IDG_OK;
+}
+
+idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
+                    const float *taper, void *grid, idg_stream stream) {
+    idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
+    if (st != IDG_OK) return st;
+    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    const int64_t n = p->stats.n_subgrids;
+    if (n == 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t chunk = chunk_subgrids(p);
+    void *scratch = nullptr;
+    st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    if (st != IDG_OK) return st;
+    const Geometry g = p->geometry();
+    for (int64_t first = 0; first < n && st == IDG_OK; first += chunk) {
+        const int64_t cnt = std::min(chunk, n - first);
+        {
+            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, cnt, true));
+            st = launch_gridder(g, first, cnt, true, vis, flags, aterms, taper, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
+            st = launch_fft(p->L, cnt, -1, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
+            st = launch_adder(g, first, cnt, true, scratch, grid, s);
+        }
+    }
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
+    return st;
+}
+
+idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags, const void *aterms,
+                      const float *taper, void *vis_out, idg_stream stream) {
+    idg_status st = check_call(p, grid, "d_grid", vis_out, "d_vis_out");
+    if (st != IDG_OK) return st;
+    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = p->stats.n_subgrids;
+    if (p->any_dropped || n == 0) {
+        cudaError_t e = cudaMemsetAsync(vis_out, 0, (size_t)p->n_bl * p->n_t * p->n_chan * 32, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(vis_out)");
+    }
+    if (n == 0) return IDG_OK;
+    const int64_t chunk = chunk_subgrids(p);
+    void *scratch = nullptr;
+    st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    if (st != IDG_OK) return st;
+    const Geometry g = p->geometry();
+    for (int64_t first = 0; first < n && st == IDG_OK; first += chunk) {
+        const int64_t cnt = std::min(chunk, n - first);
+        {
+            ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
+            st = launch_splitter(g, first, cnt, true, grid, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
+            st = launch_fft(p->L, cnt, +1, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, cnt, true));
+            st = launch_degridder(g, first, cnt, true, scratch, flags, aterms, taper, vis_out, s);
+        }
+    }
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// host-buffer variants
+
+namespace {
+struct DevBufs {
+    void *ptr[5] = {};
+    cudaStream_t s;
+    explicit DevBufs(cudaStream_t st) : s(st) {}
+    ~DevBufs() {
+        for (void *p : ptr)
+            if (p) cudaFreeAsync(p, s);
+    }
+};
+
+idg_status upload(int dev, DevBufs &b, int slot, const void *h, size_t bytes, const char *what) {
+    if (!h) return IDG_OK;
+    idg_status st = scratch_alloc(dev, bytes, b.s, &b.ptr[slot]);
+    if (st != IDG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(b.ptr[slot], h, bytes, cudaMemcpyHostToDevice, b.s);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return IDG_OK;
+}
+}  // namespace
+
+idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_flags, const void *h_aterms,
+                         const float *h_taper, void *h_grid, idg_stream stream) {
+    idg_status st = check_call(p, h_vis, "h_vis", h_grid, "h_grid");
+    if (st != IDG_OK) return st;
+    if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nvis = (size_t)p->n_bl * p->n_t * p->n_chan;
+    const size_t grid_bytes = (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    DevBufs b(s);
+    if ((st = upload(p->device, b, 0, h_vis, nvis * 32, "copy of visibilities")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 1, h_flags, nvis, "copy of flags")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 2, h_aterms, (size_t)p->n_slots * p->n_stations * p->L * p->L * 32,
+                     "copy of A-terms")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 3, h_taper, (size_t)p->L * p->L * 4, "copy of taper")) != IDG_OK) return st;
+    if ((st = scratch_alloc(p->device, grid_bytes, s, &b.ptr[4])) != IDG_OK) return st;
+    cudaError_t e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(grid)");
+    st = idg_grid(p, b.ptr[0], (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], stream);
+    if (st != IDG_OK) return st;
+    e = cudaMemcpyAsync(h_grid, b.ptr[4], grid_bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the grid to the host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return IDG_OK;
+}
+
+idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t *h_flags, const void *h_aterms,
+                           const float *h_taper, void *h_vis_out, idg_stream stream) {
+    idg_status st = check_call(p, h_grid, "h_grid", h_vis_out, "h_vis_out");
+    if (st != IDG_OK) return st;
+    if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nvis = (size_t)p->n_bl * p->n_t * p->n_chan;
+    const size_t grid_bytes = (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    DevBufs b(s);
+    if ((st = upload(p->device, b, 0, h_grid, grid_bytes, "copy of the grid")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 1, h_flags, nvis, "copy of flags")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 2, h_aterms, (size_t)p->n_slots * p->n_stations * p->L * p->L * 32,
+                     "copy of A-terms")) != IDG_OK) return st;
+    if ((st = upload(p->device, b, 3, h_taper, (size_t)p->L * p->L * 4, "copy of taper")) != IDG_OK) return st;
+    if ((st = scratch_alloc(p->device, nvis * 32, s, &b.ptr[4])) != IDG_OK) return st;
+    st = idg_degrid(p, b.ptr[0], (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], stream);
+    if (st != IDG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h_vis_out, b.ptr[4], nvis * 32, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the visibilities to the host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return IDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stage entry points
+
+idg_status idg_grid_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *vis,
+                             const uint8_t *flags, const void *aterms, const float *taper, void *sub,
+                             idg_stream stream) {
+    idg_status st = check_call(p, vis, "d_vis", sub, "d_subgrids");
+    if (st != IDG_OK) return st;
+    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
+    ProfileScope ps(IDG_KERNEL_GRIDDER, stream, vispix(p, first, count, false));
+    return launch_gridder(p->geometry(), first, count, false, vis, flags, aterms, taper, sub, (cudaStream_t)stream);
+}
+
+idg_status idg_fft_subgrids(const idg_plan *p, int64_t count, int direction, void *sub, idg_stream stream) {
+    idg_status st = check_call(p, sub, "d_subgrids", sub, "d_subgrids");
+    if (st != IDG_OK) return st;
+    if (direction != -1 && direction != 1) return fail(IDG_ERR_INVALID_ARG, "direction must be -1 or +1");
+    if (count < 0) return fail(IDG_ERR_INVALID_ARG, "count < 0");
+    if (count == 0) return IDG_OK;
+    ProfileScope ps(IDG_KERNEL_FFT, stream, (double)count);
+    return launch_fft(p->L, count, direction, sub, (cudaStream_t)stream);
+}
+
+idg_status idg_add_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *sub, void *grid,
+                            idg_stream stream) {
+    idg_status st = check_call(p, sub, "d_subgrids", grid, "d_grid");
+    if (st != IDG_OK) return st;
+    if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
+    ProfileScope ps(IDG_KERNEL_ADDER, stream, 96.0 * pixels(p, count));
+    return launch_adder(p->geometry(), first, count, false, sub, grid, (cudaStream_t)stream);
+}
+
+idg_status idg_split_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *grid, void *sub,
+                              idg_stream stream) {
+    idg_status st = check_call(p, grid, "d_grid", sub, "d_subgrids");
+    if (st != IDG_OK) return st;
+    if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
+    ProfileScope ps(IDG_KERNEL_SPLITTER, stream, 64.0 * pixels(p, count));
+    return launch_splitter(p->geometry(), first, count, false, grid, sub, (cudaStream_t)stream);
+}
+
+idg_status idg_degrid_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *sub,
+                               const uint8_t *flags, const void *aterms, const float *taper, void *vis_out,
+                               idg_stream stream) {
+    idg_status st = check_call(p, sub, "d_subgrids", vis_out, "d_vis_out");
+    if (st != IDG_OK) return st;
+    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
+    ProfileScope ps(IDG_KERNEL_DEGRIDDER, stream, vispix(p, first, count, false));
+    return launch_degridder(p->geometry(), first, count, false, sub, flags, aterms, taper, vis_out,
+                            (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Private declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/idg.h"
+
+namespace idg {
+
+constexpr double kSpeedOfLight = 299792458.0;   // m/s
+constexpr int kDescFields = IDG_DESC_FIELDS;
+
+// Work description of one subgrid on the device (80 B, 16-B aligned).
+struct alignas(16) DevSubgrid {
+    int32_t bl, slot, t0, nt, c0, nc, q0, r0, layer, kp, st_p, st_q;
+    double u0, v0, w0;     // centre of the subgrid in wavelengths (Sect. 3.3)
+    double pad;
+};
+static_assert(sizeof(DevSubgrid) == 80, "DevSubgrid layout");
+
+// Geometry and pointers the kernels read; passed by value to every launch.
+struct Geometry {
+    int L, N, n_t, n_chan, n_stations;
+    double S;             // N * cell: image size in direction cosines
+    double k_uv;          // 2 pi S / L: phase per pixel index per wavelength
+    const DevSubgrid *sub;     // [n_sub], plan order
+    const int32_t *order;      // [n_sub], device work order (plan indices)
+    const double *uvw;         // [n_bl][n_t][3] metres
+    const double *scale;       // [n_chan] f / c
+    const float *nprime;       // [L][L] n' = sqrt(1 - l^2 - m^2) - 1
+};
+
+// Host planner output.
+struct PlanResult {
+    std::vector<int32_t> desc;   // kDescFields per subgrid, plan order
+    int64_t n_dropped = 0;
+    int32_t n_w = 1;
+    int32_t k_min = 0;
+};
+
+struct PlanParams {
+    const double *uvw;
+    const double *freqs;
+    const int32_t *aterm_offsets;
+    int n_bl, n_t, n_chan, n_slots;
+    int L, N;
+    double cell, w_step, beta;
+    int t_max;
+    int n_threads;
+};
+
+// Sect. 3.2 partition; deterministic and independent of n_threads.
+PlanResult make_plan(const PlanParams &p);
+
+}  // namespace idg
+
+struct idg_plan {
+    idg_plan_options opts;
+    idg_plan_stats stats;
+    int n_bl, n_t, n_chan, n_stations, n_slots, L, N;
+    double cell, w_step, S;
+    std::vector<int32_t> desc;          // host copy, plan order
+    std::vector<int32_t> baselines;     // [n_bl][2]
+    int device = -1;
+    // device metadata (owned)
+    idg::DevSubgrid *d_sub = nullptr;
+    int32_t *d_order = nullptr;
+    double *d_uvw = nullptr;
+    double *d_scale = nullptr;
+    float *d_nprime = nullptr;
+    bool any_dropped = false;
+    std::vector<int64_t> kp_prefix_plan;    // [n_sub + 1], sum of K_p in plan order
+    std::vector<int64_t> kp_prefix_order;   // [n_sub + 1], sum of K_p in device work order
+
+    idg::Geometry geometry() const;
+};
+
+namespace idg {
+
+// thread-local error text
+void set_error(const std::string &msg);
+idg_status fail(idg_status st, const std::string &msg);
+idg_status cuda_fail(int err, const char *what);
+
+// event-based kernel timing (idg_profile_*); no-ops while disabled
+struct ProfileScope {
+    ProfileScope(int kernel, void *stream, double work);
+    ~ProfileScope();
+    int kernel;
+    void *stream;
+    void *ev[2];
+    double work;
+    bool on;
+};
+
+// kernel launchers (each returns IDG_OK or an error with the message set)
+bool gridder_supported(int L);
+idg_status launch_gridder(const Geometry &g, int64_t first, int64_t count, bool use_order,
+                          const void *vis, const uint8_t *flags, const void *aterms, const float *taper,
+                          void *subgrids, void *stream);
+idg_status launch_fft(int L, int64_t count, int direction, void *subgrids, void *stream);
+idg_status launch_adder(const Geometry &g, int64_t first, int64_t count, bool use_order,
+                        const void *subgrids, void *grid, void *stream);
+idg_status launch_splitter(const Geometry &g, int64_t first, int64_t count, bool use_order,
+                           const void *grid, void *subgrids, void *stream);
+idg_status launch_degridder(const Geometry &g, int64_t first, int64_t count, bool use_order,
+                            const void *subgrids, const uint8_t *flags, const void *aterms,
+                            const float *taper, void *vis_out, void *stream);
+
+}  // namespace idg

@@ -1,0 +1,338 @@
+"""Thin Python binding of the C ABI in ``include/idg.h`` (ctypes).
+
+Argument marshalling only: every step of gridding and degridding runs in the
+library's CUDA kernels.  Device buffers are torch CUDA tensors (torch supplies
+device memory and streams); host buffers are numpy arrays.  The functions
+carry the C names without the ``idg_`` prefix.  Importing works without a GPU;
+calling anything that needs the library raises if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libidg_gb300.so")
+
+IDG_OK = 0
+STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_NO_MEMORY", 3: "IDG_ERR_CUDA",
+                4: "IDG_ERR_TIMEOUT", 5: "IDG_ERR_DEVICE_CHECK", 6: "IDG_ERR_UNSUPPORTED"}
+DESC_FIELDS = 10
+PHASOR_SINCOS, PHASOR_RECURRENCE = 0, 1
+FFT_FP32 = 0
+ADDER_ATOMIC = 0
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTED = [
+    "idg_plan_options_default", "idg_plan_create", "idg_plan_info", "idg_plan_export", "idg_plan_destroy",
+    "idg_grid", "idg_degrid", "idg_grid_host", "idg_degrid_host",
+    "idg_grid_subgrids", "idg_fft_subgrids", "idg_add_subgrids", "idg_split_subgrids", "idg_degrid_subgrids",
+    "idg_status_string", "idg_last_error", "idg_supported_subgrid_sizes",
+    "idg_profile_enable", "idg_profile_read",
+]
+KERNELS = ["gridder", "fft", "adder", "splitter", "degridder"]
+
+
+class IDGError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("kernel_size", ctypes.c_double), ("max_timesteps_per_subgrid", ctypes.c_int),
+                ("precision_mode", ctypes.c_int), ("fft_mode", ctypes.c_int), ("adder_mode", ctypes.c_int),
+                ("n_host_threads", ctypes.c_int)]
+
+
+class PlanStats(ctypes.Structure):
+    _fields_ = [("n_subgrids", ctypes.c_int64), ("n_vis_planned", ctypes.c_int64),
+                ("n_vis_dropped", ctypes.c_int64), ("max_kp", ctypes.c_int64),
+                ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32),
+                ("subgrid_size", ctypes.c_int32), ("grid_size", ctypes.c_int32),
+                ("n_bl", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_chan", ctypes.c_int32),
+                ("n_stations", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"the CUDA library {path} is not built: run paper_1909_07226_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "idg_plan_options_default": (None, [P]),
+        "idg_plan_create": (I32, [P, P, P, P, I32, I32, I32, I32, I32, I32, I32, D, D, P, P]),
+        "idg_plan_info": (I32, [P, P]),
+        "idg_plan_export": (I32, [P, P, I64]),
+        "idg_plan_destroy": (None, [P]),
+        "idg_grid": (I32, [P, P, P, P, P, P, P]),
+        "idg_degrid": (I32, [P, P, P, P, P, P, P]),
+        "idg_grid_host": (I32, [P, P, P, P, P, P, P]),
+        "idg_degrid_host": (I32, [P, P, P, P, P, P, P]),
+        "idg_grid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
+        "idg_fft_subgrids": (I32, [P, I64, I32, P, P]),
+        "idg_add_subgrids": (I32, [P, I64, I64, P, P, P]),
+        "idg_split_subgrids": (I32, [P, I64, I64, P, P, P]),
+        "idg_degrid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
+        "idg_status_string": (ctypes.c_char_p, [I32]),
+        "idg_last_error": (ctypes.c_char_p, []),
+        "idg_supported_subgrid_sizes": (I32, [P, I32]),
+        "idg_profile_enable": (None, [I32]),
+        "idg_profile_read": (I32, [P, P, P, I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != IDG_OK:
+        msg = load().idg_last_error()
+        raise IDGError(status, where, msg.decode() if msg else "")
+
+
+def plan_options_default() -> PlanOptions:
+    o = PlanOptions()
+    load().idg_plan_options_default(ctypes.byref(o))
+    return o
+
+
+def supported_subgrid_sizes():
+    lib = load()
+    buf = (ctypes.c_int32 * 16)()
+    n = lib.idg_supported_subgrid_sizes(buf, 16)
+    return [int(buf[i]) for i in range(min(n, 16))]
+
+
+def profile_enable(on: bool = True):
+    load().idg_profile_enable(1 if on else 0)
+
+
+def profile_read(reset: bool = True) -> dict:
+    """Per-kernel {launches, ms, work} since the last reset (see idg_profile_read)."""
+    n = len(KERNELS)
+    la = (ctypes.c_int64 * n)()
+    ms = (ctypes.c_double * n)()
+    wk = (ctypes.c_double * n)()
+    _check(load().idg_profile_read(la, ms, wk, 1 if reset else 0), "idg_profile_read")
+    return {k: dict(launches=int(la[i]), ms=float(ms[i]), work=float(wk[i])) for i, k in enumerate(KERNELS)}
+
+
+@dataclasses.dataclass
+class Plan:
+    handle: ctypes.c_void_p
+    stats: PlanStats
+
+    @property
+    def n_subgrids(self):
+        return int(self.stats.n_subgrids)
+
+    @property
+    def n_w_layers(self):
+        return int(self.stats.n_w_layers)
+
+    def export(self) -> np.ndarray:
+        desc = np.zeros((self.n_subgrids, DESC_FIELDS), dtype=np.int32)
+        _check(load().idg_plan_export(self.handle, desc.ctypes.data_as(ctypes.c_void_p), self.n_subgrids),
+               "idg_plan_export")
+        return desc
+
+    def destroy(self):
+        if self.handle:
+            load().idg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def plan_create(uvw_m, freqs_hz, baselines, aterm_offsets, n_stations: int, subgrid_size: int, grid_size: int,
+                cell_size: float, w_step: float = 0.0, options: Optional[PlanOptions] = None, **opt) -> Plan:
+    """idg_plan_create from host numpy arrays; keyword options override fields of `options`."""
+    lib = load()
+    uvw = _np(uvw_m, np.float64)
+    fr = _np(freqs_hz, np.float64)
+    bl = _np(baselines, np.int32)
+    offs = _np(aterm_offsets, np.int32)
+    o = options if options is not None else plan_options_default()
+    for k, v in opt.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib.idg_plan_create(vp(uvw), vp(fr), vp(bl), vp(offs), uvw.shape[0], uvw.shape[1], fr.shape[0],
+                               int(n_stations), offs.shape[0] - 1, int(subgrid_size), int(grid_size),
+                               float(cell_size), float(w_step), ctypes.byref(o), ctypes.byref(h)),
+           "idg_plan_create")
+    st = PlanStats()
+    _check(lib.idg_plan_info(h, ctypes.byref(st)), "idg_plan_info")
+    return Plan(h, st)
+
+
+def plan_from_workload(wl, **opt) -> Plan:
+    return plan_create(wl.uvw_m, wl.freqs_hz, wl.baselines, wl.aterm_offsets, wl.n_stations, wl.subgrid_size,
+                       wl.grid_size, wl.cell_size, wl.w_step, kernel_size=float(wl.kernel_size),
+                       max_timesteps_per_subgrid=int(wl.max_timesteps), **opt)
+
+
+# ---------------------------------------------------------------------------
+# device-buffer calls (torch CUDA tensors)
+
+def _dptr(t, name, dtype=None, shape=None, optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _shapes(plan: Plan):
+    s = plan.stats
+    L, N = s.subgrid_size, s.grid_size
+    return dict(vis=(s.n_bl, s.n_t, s.n_chan, 4), flags=(s.n_bl, s.n_t, s.n_chan),
+                aterms=(s.n_slots, s.n_stations, L, L, 4), taper=(L, L), grid=(s.n_w_layers, N, N, 4))
+
+
+def grid(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_grid(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                           _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                           _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                           _dptr(taper, "taper", torch.float32, sh["taper"]),
+                           _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)), "idg_grid")
+
+
+def degrid(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None):
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_degrid(plan.handle, _dptr(grid_in, "grid", torch.complex64, sh["grid"]),
+                             _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                             _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                             _dptr(taper, "taper", torch.float32, sh["taper"]),
+                             _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)), "idg_degrid")
+
+
+def grid_subgrids(plan: Plan, first: int, count: int, vis, flags, aterms, taper, subgrids, stream=None):
+    import torch
+    sh = _shapes(plan)
+    L = plan.stats.subgrid_size
+    _check(load().idg_grid_subgrids(plan.handle, first, count, _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                                    _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                    _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                    _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                    _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
+                                    _stream(stream)), "idg_grid_subgrids")
+
+
+def fft_subgrids(plan: Plan, count: int, direction: int, subgrids, stream=None):
+    import torch
+    L = plan.stats.subgrid_size
+    _check(load().idg_fft_subgrids(plan.handle, count, direction,
+                                   _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
+                                   _stream(stream)), "idg_fft_subgrids")
+
+
+def add_subgrids(plan: Plan, first: int, count: int, subgrids, grid_out, stream=None):
+    import torch
+    L = plan.stats.subgrid_size
+    _check(load().idg_add_subgrids(plan.handle, first, count,
+                                   _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
+                                   _dptr(grid_out, "grid", torch.complex64, _shapes(plan)["grid"]),
+                                   _stream(stream)), "idg_add_subgrids")
+
+
+def split_subgrids(plan: Plan, first: int, count: int, grid_in, subgrids, stream=None):
+    import torch
+    L = plan.stats.subgrid_size
+    _check(load().idg_split_subgrids(plan.handle, first, count,
+                                     _dptr(grid_in, "grid", torch.complex64, _shapes(plan)["grid"]),
+                                     _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
+                                     _stream(stream)), "idg_split_subgrids")
+
+
+def degrid_subgrids(plan: Plan, first: int, count: int, subgrids, flags, aterms, taper, vis_out, stream=None):
+    import torch
+    sh = _shapes(plan)
+    L = plan.stats.subgrid_size
+    _check(load().idg_degrid_subgrids(plan.handle, first, count,
+                                      _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
+                                      _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                      _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                      _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                      _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)),
+           "idg_degrid_subgrids")
+
+
+# ---------------------------------------------------------------------------
+# host-buffer calls (numpy arrays; page-locked memory gives full copy speed)
+
+def _hptr(a, name, dtype, shape, optional=False):
+    if a is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"{name} must be a C-contiguous {dtype} array of shape {shape}")
+        return a.ctypes.data_as(ctypes.c_void_p)
+    import torch
+    if isinstance(a, torch.Tensor) and not a.is_cuda and a.is_contiguous() and tuple(a.shape) == tuple(shape):
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"{name} must be a host array")
+
+
+def grid_host(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
+    sh = _shapes(plan)
+    _check(load().idg_grid_host(plan.handle, _hptr(vis, "vis", np.complex64, sh["vis"]),
+                                _hptr(flags, "flags", np.uint8, sh["flags"], True),
+                                _hptr(aterms, "aterms", np.complex64, sh["aterms"], True),
+                                _hptr(taper, "taper", np.float32, sh["taper"]),
+                                _hptr(grid_out, "grid", np.complex64, sh["grid"]), _stream(stream)),
+           "idg_grid_host")
+
+
+def degrid_host(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None):
+    sh = _shapes(plan)
+    _check(load().idg_degrid_host(plan.handle, _hptr(grid_in, "grid", np.complex64, sh["grid"]),
+                                  _hptr(flags, "flags", np.uint8, sh["flags"], True),
+                                  _hptr(aterms, "aterms", np.complex64, sh["aterms"], True),
+                                  _hptr(taper, "taper", np.float32, sh["taper"]),
+                                  _hptr(vis_out, "vis_out", np.complex64, sh["vis"]), _stream(stream)),
+           "idg_degrid_host")

@@ -27,8 +27,10 @@ Conventions shared with the rest of the library (they define the *inputs*):
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 from typing import Optional
 
 import numpy as np
@@ -232,53 +234,70 @@ def point_source_visibilities(uvw_m: np.ndarray, freqs_hz: np.ndarray, baselines
     """V_pq = sum_s I_s J_p(l_s) J_q(l_s)^H exp(-2 pi i (u l_s + v m_s + w n'_s)).
 
     Unpolarised sources (brightness I_s times the 2x2 identity).  Returns
-    complex64 [n_bl][n_t][n_chan][4].  The phase per channel is advanced by a
-    complex recurrence over channels from an FP64 anchor, which is plenty for
-    synthetic input data.
+    complex64 [n_bl][n_t][n_chan][4].  For uniformly spaced channels the phase
+    is advanced over channels by a complex recurrence from an FP64 anchor,
+    which is plenty for synthetic input data.
     """
     n_bl, n_t, _ = uvw_m.shape
     n_chan = freqs_hz.shape[0]
     n_src = src_l.shape[0]
     src_n1 = np.sqrt(1.0 - src_l ** 2 - src_m ** 2) - 1.0
-    out = np.zeros((n_bl, n_t, n_chan, 4), dtype=np.complex64)
+    out = np.empty((n_bl, n_t, n_chan, 4), dtype=np.complex64)
+    if aterm_offsets is None:
+        aterm_offsets = np.array([0, n_t])
+    n_slots = len(aterm_offsets) - 1
     if screens is not None:
         jones = screens.evaluate(src_l, src_m)                 # [slots][st][src][4]
-        slot_of_t = np.searchsorted(aterm_offsets, np.arange(n_t), side="right") - 1
     uniform = n_chan > 1 and np.allclose(np.diff(freqs_hz), freqs_hz[1] - freqs_hz[0], rtol=0, atol=1e-6)
-    for b in range(n_bl):
+    coh0 = np.zeros((n_src, 4), dtype=np.complex128)
+    coh0[:, 0] = src_flux
+    coh0[:, 3] = src_flux
+
+    def one_baseline(b, phs):
         p, q = baselines[b]
         # geometric path difference in metres per (t, src)
-        geo = (uvw_m[b, :, 0:1] * src_l[None, :] + uvw_m[b, :, 1:2] * src_m[None, :]
-               + uvw_m[b, :, 2:3] * src_n1[None, :])             # [t][src]
+        geo = uvw_m[b, :, 0:1] * src_l[None, :] + uvw_m[b, :, 1:2] * src_m[None, :] + uvw_m[b, :, 2:3] * src_n1[None, :]
         if uniform:
             ph = np.exp(-2j * np.pi * geo * (freqs_hz[0] / C_LIGHT))
             step = np.exp(-2j * np.pi * geo * ((freqs_hz[1] - freqs_hz[0]) / C_LIGHT))
-            phs = np.empty((n_chan, n_t, n_src), dtype=np.complex128)
             for c in range(n_chan):
-                phs[c] = ph
+                phs[:, c, :] = ph
                 ph = ph * step
-            phs = np.transpose(phs, (1, 0, 2))                  # [t][c][src]
         else:
-            phs = np.exp(-2j * np.pi * geo[:, None, :] * (freqs_hz[None, :, None] / C_LIGHT))
-        if screens is None:
-            coh = np.zeros((n_t, n_src, 4), dtype=np.complex128)
-            coh[:, :, 0] = src_flux[None, :]
-            coh[:, :, 3] = src_flux[None, :]
-        else:
-            jp = jones[slot_of_t, p]                            # [t][src][4]
-            jq = jones[slot_of_t, q]
-            # M = I * Jp Jq^H
-            m00 = jp[..., 0] * np.conj(jq[..., 0]) + jp[..., 1] * np.conj(jq[..., 1])
-            m01 = jp[..., 0] * np.conj(jq[..., 2]) + jp[..., 1] * np.conj(jq[..., 3])
-            m10 = jp[..., 2] * np.conj(jq[..., 0]) + jp[..., 3] * np.conj(jq[..., 1])
-            m11 = jp[..., 2] * np.conj(jq[..., 2]) + jp[..., 3] * np.conj(jq[..., 3])
-            coh = np.stack([m00, m01, m10, m11], axis=-1) * src_flux[None, :, None]
-        out[b] = np.einsum("tcs,tsp->tcp", phs, coh).astype(np.complex64)
+            phs[:] = np.exp(-2j * np.pi * geo[:, None, :] * (freqs_hz[None, :, None] / C_LIGHT))
+        for a in range(n_slots):
+            t0, t1 = int(aterm_offsets[a]), int(aterm_offsets[a + 1])
+            if screens is None:
+                coh = coh0
+            else:
+                jp, jq = jones[a, p], jones[a, q]                 # [src][4]
+                coh = np.stack([jp[:, 0] * np.conj(jq[:, 0]) + jp[:, 1] * np.conj(jq[:, 1]),
+                                jp[:, 0] * np.conj(jq[:, 2]) + jp[:, 1] * np.conj(jq[:, 3]),
+                                jp[:, 2] * np.conj(jq[:, 0]) + jp[:, 3] * np.conj(jq[:, 1]),
+                                jp[:, 2] * np.conj(jq[:, 2]) + jp[:, 3] * np.conj(jq[:, 3])], axis=-1)
+                coh = coh * src_flux[:, None]
+            blk = phs[t0:t1].reshape(-1, n_src) @ coh
+            out[b, t0:t1] = blk.reshape(t1 - t0, n_chan, 4)
+
+    def worker(bs):
+        phs = np.empty((n_t, n_chan, n_src), dtype=np.complex128)
+        for b in bs:
+            one_baseline(b, phs)
+
+    n_workers = max(1, min(os.cpu_count() or 1, 16, n_bl // 8 + 1))
+    if n_workers == 1:
+        worker(range(n_bl))
+    else:
+        with concurrent.futures.ThreadPoolExecutor(n_workers) as ex:
+            list(ex.map(worker, [range(i, n_bl, n_workers) for i in range(n_workers)]))
     return out
 
 
 def gaussian_noise(rng: np.random.Generator, shape, sigma: float) -> np.ndarray:
-    return (rng.normal(0.0, sigma, size=shape) + 1j * rng.normal(0.0, sigma, size=shape)).astype(np.complex64)
+    """Complex Gaussian noise, sigma per real and imaginary part, complex64."""
+    re = rng.standard_normal(size=tuple(shape) + (2,), dtype=np.float32)
+    re *= np.float32(sigma)
+    return re.view(np.complex64)[..., 0]
 
 
 def random_flags(rng: np.random.Generator, shape, p: float) -> np.ndarray:
