@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="lofar", choices=["lofar", "tiny"])
+    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -96,15 +96,19 @@ def make_workload(name):
     from paper_1909_07226_gb300 import synthetic as syn
     if name == "tiny":
         return syn.make_tiny()
+    if name == "lofar-slice":
+        # the LOFAR-like workload cut to its first 256 timesteps (two A-term
+        # slots): still larger than L2, small enough for a detailed profile
+        return syn.make_lofar(with_vis=True, n_t=256)
     return syn.make_lofar(with_vis=True)
 
 
 def workload_config(wl, name):
     return {
-        "workload": ("LOFAR-like plain: 48 stations (1128 baselines), 4096 x 1 s, 16 ch 130-146 MHz, "
-                     "subgrid 32, grid 4096^2 x 4 c64, A-terms every 128 t"
-                     if name == "lofar" else
-                     "Tiny plain: 8 stations, 64 x 10 s, 8 ch 140-148 MHz, subgrid 24, grid 512^2 x 4 c64"),
+        "workload": {"lofar": "LOFAR-like plain: 48 stations (1128 baselines), 4096 x 1 s, 16 ch 130-146 MHz, "
+                              "subgrid 32, grid 4096^2 x 4 c64, A-terms every 128 t",
+                     "lofar-slice": "LOFAR-like plain, first 256 of 4096 timesteps (profiling slice)",
+                     "tiny": "Tiny plain: 8 stations, 64 x 10 s, 8 ch 140-148 MHz, subgrid 24, grid 512^2 x 4 c64"}[name],
         "n_vis": int(wl.n_vis), "n_baselines": int(wl.n_bl), "n_timesteps": int(wl.n_t),
         "n_channels": int(wl.n_chan), "subgrid_size": int(wl.subgrid_size), "grid_size": int(wl.grid_size),
         "kernel_size": float(wl.kernel_size), "max_timesteps_per_subgrid": int(wl.max_timesteps),
@@ -208,9 +212,10 @@ def oracle_sample(wl, op, target_s: float, seed: int = 0):
         t2 = time.perf_counter()
         return t2 - t0
 
-    # calibrate on a few subgrids, then size the sample
+    # calibrate on two subgrids per host core (the oracle runs one subgrid per
+    # OpenMP thread), then size the sample
     rng = np.random.default_rng(seed)
-    cal = np.sort(rng.choice(n, size=min(n, 4), replace=False)).astype(np.int32)
+    cal = np.sort(rng.choice(n, size=min(n, 2 * (os.cpu_count() or 1)), replace=False)).astype(np.int32)
     tc = run(cal)
     per_vis = tc / max(1, int(kp[cal].sum()))
     want_vis = target_s / max(per_vis, 1e-12)

@@ -41,7 +41,7 @@ def torch_zeros(shape, dtype=None):
 
 @pytest.mark.parametrize("L", SIZES)
 def test_gridder_stage(L):
-    wl = small(L)
+    wl = small(L, n_slots=1)
     p = idg.plan_from_workload(wl)
     op = O.plan(wl)
     d = workload_to_device(wl)
@@ -85,7 +85,7 @@ def test_adder_and_splitter_stages(L):
 
 @pytest.mark.parametrize("L", SIZES)
 def test_degridder_stage(L):
-    wl = small(L, n_chan=16, max_t=96, n_t=96)
+    wl = small(L, n_chan=16, n_t=100, max_t=96, n_slots=1)
     p = idg.plan_from_workload(wl)
     op = O.plan(wl)
     assert int(op.desc[:, O.D_KP].max()) > 1024         # several passes of the visibility lanes
