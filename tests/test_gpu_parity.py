@@ -155,8 +155,14 @@ def test_flat_grid_identity_on_gpu():
     v = torch_zeros(wl.vis.shape)
     idg.degrid(p, dev(g), None, None, dev(wl.taper), v)
     y = v.cpu().numpy()
-    assert np.max(np.abs(y[..., 0] - 1)) < 2e-6 and np.max(np.abs(y[..., 3] - 1)) < 2e-6
-    assert np.max(np.abs(y[..., 1:3])) < 2e-6
+    mask = np.zeros(y.shape[:3], dtype=bool)
+    for d in p.export():
+        mask[d[0], d[2]:d[2] + d[3], d[4]:d[4] + d[5]] = True
+    assert mask.sum() > 0 and p.stats.n_vis_dropped == int((~mask).sum())
+    ym = y[mask]
+    assert np.max(np.abs(ym[:, 0] - 1)) < 2e-6 and np.max(np.abs(ym[:, 3] - 1)) < 2e-6
+    assert np.max(np.abs(ym[:, 1:3])) < 2e-6
+    assert np.all(y[~mask] == 0)            # dropped visibilities are set to 0
 
 
 def test_empty_plan_and_all_flagged():
