@@ -198,6 +198,33 @@ idg_status idg_degrid_host(const idg_plan *plan, const void *h_grid, const uint8
                            idg_stream stream);
 
 /*
+ * Gridding that allocates no device memory (the paper has no counterpart: this
+ * is a deployment variant of idg_grid).  Some callers cannot allocate device
+ * memory when they grid -- a real-time pipeline that reserves its whole memory
+ * budget up front, or a host framework whose own allocator already holds all
+ * free device memory -- because a new allocation could fail mid-run or
+ * implicitly synchronise the device.  This call runs the same kernels as
+ * idg_grid but keeps the subgrid scratch in a fixed 64 MiB array compiled into
+ * the library (held by every GPU that loads the library, until the process
+ * exits).  It calls no allocator.
+ *   - The plan must need at most 64 MiB of scratch: n_subgrids * L * L * 32
+ *     bytes (2048 subgrids of L = 32, 3640 of L = 24, 8192 of L = 16).  A
+ *     larger plan is rejected with IDG_ERR_INVALID_ARG and a message giving
+ *     the need and the limit, before any work is enqueued.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture on the device.
+ *   - All calls on one device share the array.  Calls whose work overlaps on
+ *     the GPU (different streams without ordering between them) race on it:
+ *     order them on one stream or with events.  The array keeps the last
+ *     call's contents; every call overwrites the part it uses before reading
+ *     it, so nothing needs clearing.
+ * Arguments, layouts and the accumulation into d_grid are as for idg_grid.
+ */
+idg_status idg_grid_no_alloc(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
+                             const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);
+
+/*
  * Stage entry points over the plan's subgrids [first, first + count) in plan
  * order.  d_subgrids is a device complex64 [count][L][L][4] buffer owned by
  * the caller.  They expose the intermediate states of Algorithms 1 and 2.

@@ -32,7 +32,7 @@ EXPORTED = [
     "idg_grid", "idg_degrid", "idg_grid_host", "idg_degrid_host",
     "idg_grid_subgrids", "idg_fft_subgrids", "idg_add_subgrids", "idg_split_subgrids", "idg_degrid_subgrids",
     "idg_status_string", "idg_last_error", "idg_supported_subgrid_sizes",
-    "idg_profile_enable", "idg_profile_read",
+    "idg_profile_enable", "idg_profile_read", "idg_grid_no_alloc",
 ]
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder"]
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "idg_supported_subgrid_sizes": (I32, [P, I32]),
         "idg_profile_enable": (None, [I32]),
         "idg_profile_read": (I32, [P, P, P, I32]),
+        "idg_grid_no_alloc": (I32, [P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +248,19 @@ def degrid(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None):
                              _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
                              _dptr(taper, "taper", torch.float32, sh["taper"]),
                              _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)), "idg_degrid")
+
+
+def grid_no_alloc(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
+    """idg_grid without device allocation: the subgrid scratch is the library's
+    built-in 64 MiB array (for callers that cannot allocate device memory)."""
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_grid_no_alloc(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                                    _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                    _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                    _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                    _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)),
+           "idg_grid_no_alloc")
 
 
 def grid_subgrids(plan: Plan, first: int, count: int, vis, flags, aterms, taper, subgrids, stream=None):
