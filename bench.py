@@ -30,10 +30,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic issue slots per visibility-pixel of the gridder and degridder:
-# 16 FFMA (4 complex multiply-adds), 2 FFMA for the phase a*X + (b*Y + c*n'),
-# and 2 SFU ops (sin, cos).  Every SM dispatches 4 x 32 of these per cycle.
-ISSUE_PER_VISPIX = 20
+# Roofline of the gridder and degridder: FP32 FMA lanes.  Per visibility-pixel
+# the algorithm needs 16 FMAs (4 complex multiply-adds) and 2 FMAs for the phase
+# a*X + (b*Y + c*n'); sin and cos run on the SFU and, with packed f32x2 FMAs,
+# issue slots are not the binding limit.  Every SM retires 128 FP32 FMAs per
+# cycle, so the peak is SMs x 128 x f_max / 18 visibility-pixels per second.
+FMA_PER_VISPIX = 18
 LANES_PER_SM = 128
 
 
@@ -339,7 +341,7 @@ def run_gb300(args, world, rank, local):
     f_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    alu_peak = n_sm * LANES_PER_SM * f_max_mhz * 1e6 / ISSUE_PER_VISPIX / 1e9     # G vis-pix / s
+    alu_peak = n_sm * LANES_PER_SM * f_max_mhz * 1e6 / FMA_PER_VISPIX / 1e9       # G vis-pix / s
     kernels = {}
     for k, d in prof.items():
         if d["launches"] == 0:
@@ -356,7 +358,7 @@ def run_gb300(args, world, rank, local):
     dom = max(("gridder", "degridder"), key=lambda k: prof[k]["ms"])
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["achieved"], "peak": alu_peak,
             "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": None,
-            "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} lanes x {f_max_mhz:.0f} MHz / {ISSUE_PER_VISPIX} issue slots "
+            "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} FP32 FMA lanes x {f_max_mhz:.0f} MHz / {FMA_PER_VISPIX} FMA "
                           f"per visibility-pixel", "hbm_peak_basis": hbm_src}
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 

@@ -270,6 +270,37 @@ enum { IDG_KERNEL_GRIDDER = 0, IDG_KERNEL_FFT, IDG_KERNEL_ADDER, IDG_KERNEL_SPLI
 void idg_profile_enable(int on);
 idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset);
 
+/*
+ * Kernel variants and the autotuner.  The gridder and the degridder come in
+ * several compiled tile shapes per subgrid size L (pixels per thread,
+ * visibilities per shared-memory batch, block size, pixel-group split); the
+ * other kernels have one.  The process-wide choice per (kernel, L) starts at
+ * variant 0 and applies to every later call with that L.
+ *   idg_kernel_variant_count   number of variants (0: no such kernel or L)
+ *   idg_kernel_variant_name    a static string naming the variant, or NULL
+ *   idg_set/get_kernel_variant set or read the choice (IDG_ERR_INVALID_ARG if
+ *                              out of range)
+ *   idg_autotune               times every variant of the gridder and (when
+ *                              d_vis_scratch is given) the degridder on a
+ *                              strided sample of at most max_subgrids (<= 0:
+ *                              4096) of the plan's subgrids, on `stream`, and
+ *                              selects the fastest for the plan's L.  Mean
+ *                              milliseconds per launch of variant v go to
+ *                              gridder_ms[v] / degridder_ms[v] for v < cap
+ *                              (arrays may be NULL).  d_vis_scratch is a
+ *                              visibility-sized device buffer that the trial
+ *                              degrids overwrite.  Takes sample scratch from
+ *                              the stream-ordered pool; returns after the
+ *                              stream has finished the trials.
+ */
+int idg_kernel_variant_count(int kernel, int subgrid_size);
+const char *idg_kernel_variant_name(int kernel, int subgrid_size, int variant);
+idg_status idg_set_kernel_variant(int kernel, int subgrid_size, int variant);
+int idg_get_kernel_variant(int kernel, int subgrid_size);
+idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags, const void *d_aterms,
+                        const float *d_taper, void *d_vis_scratch, int64_t max_subgrids, double *gridder_ms,
+                        double *degridder_ms, int cap, idg_stream stream);
+
 /* Text of a status code, and the last error message of the calling thread. */
 const char *idg_status_string(idg_status status);
 const char *idg_last_error(void);

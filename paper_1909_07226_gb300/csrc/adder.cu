@@ -14,9 +14,9 @@ namespace {
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
-adder_kernel(Geometry g, int64_t first, int use_order, const float4 *__restrict__ sub, float4 *__restrict__ grid) {
-    const int64_t slot = first + blockIdx.x;
-    const int sid = use_order ? g.order[slot] : (int)slot;
+adder_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ sub,
+             float4 *__restrict__ grid) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     const DevSubgrid d = g.sub[sid];
     const int L = g.L;
     const float4 *src = sub + (size_t)blockIdx.x * L * L * 2;
@@ -30,9 +30,9 @@ adder_kernel(Geometry g, int64_t first, int use_order, const float4 *__restrict_
 }
 
 __global__ void __launch_bounds__(kThreads)
-splitter_kernel(Geometry g, int64_t first, int use_order, const float4 *__restrict__ grid, float4 *__restrict__ sub) {
-    const int64_t slot = first + blockIdx.x;
-    const int sid = use_order ? g.order[slot] : (int)slot;
+splitter_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
+                float4 *__restrict__ sub) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     const DevSubgrid d = g.sub[sid];
     const int L = g.L;
     float4 *out = sub + (size_t)blockIdx.x * L * L * 2;
@@ -47,19 +47,19 @@ splitter_kernel(Geometry g, int64_t first, int use_order, const float4 *__restri
 
 }  // namespace
 
-idg_status launch_adder(const Geometry &g, int64_t first, int64_t count, bool use_order, const void *sub,
-                        void *grid, void *stream) {
-    adder_kernel<<<(unsigned)count, kThreads, 0, (cudaStream_t)stream>>>(g, first, use_order ? 1 : 0,
-                                                                          (const float4 *)sub, (float4 *)grid);
+idg_status launch_adder(const Geometry &g, const SubgridSet &set, const void *sub, void *grid, void *stream) {
+    if (set.count <= 0) return IDG_OK;
+    adder_kernel<<<(unsigned)set.count, kThreads, 0, (cudaStream_t)stream>>>(g, set.idx, set.first,
+                                                                              (const float4 *)sub, (float4 *)grid);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adder launch");
     return IDG_OK;
 }
 
-idg_status launch_splitter(const Geometry &g, int64_t first, int64_t count, bool use_order, const void *grid,
-                           void *sub, void *stream) {
-    splitter_kernel<<<(unsigned)count, kThreads, 0, (cudaStream_t)stream>>>(g, first, use_order ? 1 : 0,
-                                                                             (const float4 *)grid, (float4 *)sub);
+idg_status launch_splitter(const Geometry &g, const SubgridSet &set, const void *grid, void *sub, void *stream) {
+    if (set.count <= 0) return IDG_OK;
+    splitter_kernel<<<(unsigned)set.count, kThreads, 0, (cudaStream_t)stream>>>(g, set.idx, set.first,
+                                                                                 (const float4 *)grid, (float4 *)sub);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "splitter launch");
     return IDG_OK;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -135,6 +136,9 @@ idg::Geometry idg_plan::geometry() const {
     g.uvw = d_uvw;
     g.scale = d_scale;
     g.nprime = d_nprime;
+    g.ds = ds;
+    g.recurrence = opts.precision_mode == IDG_PHASOR_RECURRENCE ? 1 : 0;
+    g.anchor = 8;
     return g;
 }
 
@@ -272,6 +276,20 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     for (int c = 0; c < n_chan; ++c)
         if (!(freqs_hz[c] > 0.0) || !std::isfinite(freqs_hz[c]))
             return fail(IDG_ERR_INVALID_ARG, "frequencies must be finite and > 0");
+    // the channel recurrence needs uniformly spaced channels
+    double ds = 0.0;
+    if (n_chan > 1) {
+        ds = (freqs_hz[n_chan - 1] - freqs_hz[0]) / (double)(n_chan - 1) / kSpeedOfLight;
+        for (int c = 0; c < n_chan; ++c) {
+            const double want = freqs_hz[0] / kSpeedOfLight + (double)c * ds;
+            if (std::fabs(freqs_hz[c] / kSpeedOfLight - want) > 1e-9 * freqs_hz[0] / kSpeedOfLight) {
+                ds = 0.0;
+                break;
+            }
+        }
+    }
+    if (o.precision_mode == IDG_PHASOR_RECURRENCE && n_chan > 1 && ds == 0.0)
+        return fail(IDG_ERR_INVALID_ARG, "precision_mode IDG_PHASOR_RECURRENCE needs uniformly spaced channels");
     const size_t n_uvw = (size_t)n_bl * n_t * 3;
     for (size_t i = 0; i < n_uvw; ++i)
         if (!std::isfinite(uvw_m[i])) return fail(IDG_ERR_INVALID_ARG, "uvw must be finite");
@@ -282,6 +300,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     p->n_bl = n_bl; p->n_t = n_t; p->n_chan = n_chan; p->n_stations = n_stations; p->n_slots = n_slots;
     p->L = L; p->N = N; p->cell = cell; p->w_step = w_step;
     p->S = (double)N * cell;
+    p->ds = ds;
     p->baselines.assign(baselines, baselines + 2 * (size_t)n_bl);
 
     PlanParams pp{uvw_m, freqs_hz, aterm_offsets, n_bl, n_t, n_chan, n_slots, L, N, cell, w_step,
@@ -312,8 +331,11 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     }
     p->stats.n_vis_planned = planned;
     p->kp_prefix_plan.assign((size_t)n_sub + 1, 0);
-    for (int64_t s = 0; s < n_sub; ++s)
-        p->kp_prefix_plan[s + 1] = p->kp_prefix_plan[s] + p->desc[s * kDescFields + IDG_DESC_KP];
+    p->kp_plan.assign((size_t)n_sub, 0);
+    for (int64_t s = 0; s < n_sub; ++s) {
+        p->kp_plan[s] = p->desc[s * kDescFields + IDG_DESC_KP];
+        p->kp_prefix_plan[s + 1] = p->kp_prefix_plan[s] + p->kp_plan[s];
+    }
     p->stats.max_kp = max_kp;
     p->any_dropped = pr.n_dropped > 0;
 
@@ -351,8 +373,13 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     std::iota(order.begin(), order.begin() + n_sub, 0);
     std::stable_sort(order.begin(), order.begin() + n_sub,
                      [&](int32_t a, int32_t b) { return hsub[a].kp > hsub[b].kp; });
+    p->order.assign(order.begin(), order.begin() + n_sub);
     p->kp_prefix_order.assign((size_t)n_sub + 1, 0);
-    for (int64_t s = 0; s < n_sub; ++s) p->kp_prefix_order[s + 1] = p->kp_prefix_order[s] + hsub[order[s]].kp;
+    p->kp_order.assign((size_t)n_sub, 0);
+    for (int64_t s = 0; s < n_sub; ++s) {
+        p->kp_order[s] = hsub[order[s]].kp;
+        p->kp_prefix_order[s + 1] = p->kp_prefix_order[s] + p->kp_order[s];
+    }
     std::vector<double> scale(n_chan);
     for (int c = 0; c < n_chan; ++c) scale[c] = freqs_hz[c] / kSpeedOfLight;
     std::vector<float> nprime((size_t)L * L);
@@ -411,6 +438,14 @@ static idg_status check_call(const idg_plan *p, const void *a, const char *an, c
     return check_device(p);
 }
 
+// subgrid sets: [first, first + count) of the device work order or of plan order
+static SubgridSet order_set(const idg_plan *p, int64_t first, int64_t count) {
+    return SubgridSet{p->d_order + first, 0, count, p->kp_order.data() + first};
+}
+static SubgridSet plan_set(const idg_plan *p, int64_t first, int64_t count) {
+    return SubgridSet{nullptr, first, count, p->kp_plan.data() + first};
+}
+
 // algorithmic work of a launch over subgrids [first, first + count)
 static double vispix(const idg_plan *p, int64_t first, int64_t count, bool use_order) {
     const auto &pre = use_order ? p->kp_prefix_order : p->kp_prefix_plan;
@@ -441,7 +476,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
         const int64_t cnt = std::min(chunk, n - first);
         {
             ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, cnt, true));
-            st = launch_gridder(g, first, cnt, true, vis, flags, aterms, taper, scratch, s);
+            st = launch_gridder(g, order_set(p, first, cnt), -1, vis, flags, aterms, taper, scratch, s);
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
@@ -449,7 +484,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
-            st = launch_adder(g, first, cnt, true, scratch, grid, s);
+            st = launch_adder(g, order_set(p, first, cnt), scratch, grid, s);
         }
     }
     cudaError_t e = cudaFreeAsync(scratch, s);
@@ -478,7 +513,7 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
         const int64_t cnt = std::min(chunk, n - first);
         {
             ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
-            st = launch_splitter(g, first, cnt, true, grid, scratch, s);
+            st = launch_splitter(g, order_set(p, first, cnt), grid, scratch, s);
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
@@ -486,7 +521,7 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, cnt, true));
-            st = launch_degridder(g, first, cnt, true, scratch, flags, aterms, taper, vis_out, s);
+            st = launch_degridder(g, order_set(p, first, cnt), -1, scratch, flags, aterms, taper, vis_out, s);
         }
     }
     cudaError_t e = cudaFreeAsync(scratch, s);
@@ -579,7 +614,7 @@ idg_status idg_grid_subgrids(const idg_plan *p, int64_t first, int64_t count, co
     if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_GRIDDER, stream, vispix(p, first, count, false));
-    return launch_gridder(p->geometry(), first, count, false, vis, flags, aterms, taper, sub, (cudaStream_t)stream);
+    return launch_gridder(p->geometry(), plan_set(p, first, count), -1, vis, flags, aterms, taper, sub, stream);
 }
 
 idg_status idg_fft_subgrids(const idg_plan *p, int64_t count, int direction, void *sub, idg_stream stream) {
@@ -598,7 +633,7 @@ idg_status idg_add_subgrids(const idg_plan *p, int64_t first, int64_t count, con
     if (st != IDG_OK) return st;
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_ADDER, stream, 96.0 * pixels(p, count));
-    return launch_adder(p->geometry(), first, count, false, sub, grid, (cudaStream_t)stream);
+    return launch_adder(p->geometry(), plan_set(p, first, count), sub, grid, stream);
 }
 
 idg_status idg_split_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *grid, void *sub,
@@ -607,7 +642,7 @@ idg_status idg_split_subgrids(const idg_plan *p, int64_t first, int64_t count, c
     if (st != IDG_OK) return st;
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_SPLITTER, stream, 64.0 * pixels(p, count));
-    return launch_splitter(p->geometry(), first, count, false, grid, sub, (cudaStream_t)stream);
+    return launch_splitter(p->geometry(), plan_set(p, first, count), grid, sub, stream);
 }
 
 idg_status idg_degrid_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *sub,
@@ -618,8 +653,122 @@ idg_status idg_degrid_subgrids(const idg_plan *p, int64_t first, int64_t count, 
     if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_DEGRIDDER, stream, vispix(p, first, count, false));
-    return launch_degridder(p->geometry(), first, count, false, sub, flags, aterms, taper, vis_out,
-                            (cudaStream_t)stream);
+    return launch_degridder(p->geometry(), plan_set(p, first, count), -1, sub, flags, aterms, taper, vis_out,
+                            stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// kernel variants and the autotuner
+
+namespace idg {
+namespace {
+std::atomic<int> g_variant[IDG_KERNEL_COUNT][65];
+}
+
+int get_variant(int kernel, int L) {
+    if (kernel < 0 || kernel >= IDG_KERNEL_COUNT || L < 0 || L > 64) return 0;
+    return g_variant[kernel][L].load(std::memory_order_relaxed);
+}
+
+void set_variant(int kernel, int L, int v) {
+    if (kernel < 0 || kernel >= IDG_KERNEL_COUNT || L < 0 || L > 64) return;
+    g_variant[kernel][L].store(v, std::memory_order_relaxed);
+}
+}  // namespace idg
+
+extern "C" {
+
+int idg_kernel_variant_count(int kernel, int L) {
+    if (kernel == IDG_KERNEL_GRIDDER) return gridder_variant_count(L);
+    if (kernel == IDG_KERNEL_DEGRIDDER) return degridder_variant_count(L);
+    if (kernel >= 0 && kernel < IDG_KERNEL_COUNT) return gridder_supported(L) ? 1 : 0;
+    return 0;
+}
+
+const char *idg_kernel_variant_name(int kernel, int L, int v) {
+    if (kernel == IDG_KERNEL_GRIDDER) return gridder_variant_name(L, v);
+    if (kernel == IDG_KERNEL_DEGRIDDER) return degridder_variant_name(L, v);
+    if (kernel >= 0 && kernel < IDG_KERNEL_COUNT && v == 0 && gridder_supported(L)) return "default";
+    return nullptr;
+}
+
+idg_status idg_set_kernel_variant(int kernel, int L, int v) {
+    const int n = idg_kernel_variant_count(kernel, L);
+    if (n == 0) return fail(IDG_ERR_INVALID_ARG, "no such kernel or subgrid size");
+    if (v < 0 || v >= n) return fail(IDG_ERR_INVALID_ARG, "variant out of range");
+    set_variant(kernel, L, v);
+    return IDG_OK;
+}
+
+int idg_get_kernel_variant(int kernel, int L) { return get_variant(kernel, L); }
+
+idg_status idg_autotune(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
+                        const float *taper, void *vis_scratch, int64_t max_subgrids, double *gridder_ms,
+                        double *degridder_ms, int cap, idg_stream stream) {
+    idg_status st = check_call(p, vis, "d_vis", taper, "d_taper");
+    if (st != IDG_OK) return st;
+    const int64_t n = p->stats.n_subgrids;
+    if (n == 0) return IDG_OK;
+    const int64_t m = std::min<int64_t>(n, max_subgrids > 0 ? max_subgrids : 4096);
+    cudaStream_t s = (cudaStream_t)stream;
+    // strided sample of the work order: it stays sorted by K_p
+    std::vector<int32_t> hidx((size_t)m), hkp((size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+        const int64_t pos = i * n / m;
+        hidx[i] = p->order[pos];
+        hkp[i] = p->kp_order[pos];
+    }
+    void *d_idx = nullptr, *scratch = nullptr;
+    if ((st = scratch_alloc(p->device, sizeof(int32_t) * (size_t)m, s, &d_idx)) != IDG_OK) return st;
+    if ((st = scratch_alloc(p->device, (size_t)m * p->L * p->L * 32, s, &scratch)) != IDG_OK) {
+        cudaFreeAsync(d_idx, s);
+        return st;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t ce = cudaMemcpyAsync(d_idx, hidx.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "autotune index upload");
+    const Geometry g = p->geometry();
+    const SubgridSet set{(const int32_t *)d_idx, 0, m, hkp.data()};
+    constexpr int kReps = 3;
+    auto time_variants = [&](int kernel, int nvar, double *out_ms, auto &&launch) -> int {
+        int best = 0;
+        double best_ms = 1e300;
+        for (int v = 0; v < nvar && st == IDG_OK; ++v) {
+            st = launch(v);   // warm-up
+            if (st != IDG_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < kReps && st == IDG_OK; ++r) st = launch(v);
+            cudaEventRecord(e1, s);
+            ce = cudaEventSynchronize(e1);
+            if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune timing"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double t = ms / kReps;
+            if (out_ms && v < cap) out_ms[v] = t;
+            if (t < best_ms) { best_ms = t; best = v; }
+        }
+        if (st == IDG_OK) set_variant(kernel, p->L, best);
+        return best;
+    };
+    if (st == IDG_OK)
+        time_variants(IDG_KERNEL_GRIDDER, gridder_variant_count(p->L), gridder_ms, [&](int v) {
+            return launch_gridder(g, set, v, vis, flags, aterms, taper, scratch, s);
+        });
+    if (st == IDG_OK && vis_scratch)
+        time_variants(IDG_KERNEL_DEGRIDDER, degridder_variant_count(p->L), degridder_ms, [&](int v) {
+            return launch_degridder(g, set, v, scratch, flags, aterms, taper, vis_scratch, s);
+        });
+    cudaFreeAsync(scratch, s);
+    cudaFreeAsync(d_idx, s);
+    ce = cudaStreamSynchronize(s);
+    if (st == IDG_OK && ce != cudaSuccess) st = cuda_fail(ce, "autotune synchronize");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 }  // extern "C"

@@ -1,0 +1,33 @@
+// Degridder variants for L = 32 (the LOFAR-like workload), kept in their own
+// translation unit so they compile in parallel with the rest.
+#include "degridder_impl.cuh"
+
+namespace idg {
+namespace {
+
+using namespace dev;
+
+#define DV_RT(L, NV, NT) {"nv" #NV "_nt" #NT "_pg_runtime", degrid_launch_kernel<L, NV, 0, NT, 1>}
+#define DV_ST(L, NV, NT, MINB) {"nv" #NV "_nt" #NT "_minb" #MINB "_pg_static", degrid_launch_static<L, NV, NT, MINB>}
+
+#define DV_RTM(L, NV, NT, MINB) {"nv" #NV "_nt" #NT "_minb" #MINB "_pg_runtime", degrid_launch_kernel<L, NV, 0, NT, MINB>}
+#define DV_F2(L, NV, NT, MINB) {"f32x2_nv" #NV "_nt" #NT "_minb" #MINB "_pg_static", degrid_f2_launch_static<L, NV, NT, MINB>}
+const DegridVariant kD32[] = {DV_F2(32, 4, 128, 3),      DV_RT(32, 4, 256),    DV_ST(32, 4, 256, 3),
+                              DV_ST(32, 4, 128, 5),      DV_ST(32, 4, 128, 6), DV_ST(32, 2, 256, 4),
+                              DV_RTM(32, 4, 256, 3),     DV_F2(32, 4, 128, 4), DV_F2(32, 2, 128, 4),
+                              DV_F2(32, 4, 256, 2)};
+#undef DV_F2
+#undef DV_RTM
+
+#undef DV_RT
+#undef DV_ST
+
+}  // namespace
+
+bool degridder_table_l32(const DegridVariant **v, int *n) {
+    *v = kD32;
+    *n = (int)(sizeof(kD32) / sizeof(DegridVariant));
+    return true;
+}
+
+}  // namespace idg

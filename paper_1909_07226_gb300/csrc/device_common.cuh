@@ -100,6 +100,27 @@ __device__ __forceinline__ M22 mul_mul_herm(const M22 &A, const M22 &P, const M2
 }
 
 // ---------------------------------------------------------------------------
+// packed FP32 pairs (sm_100 family): one instruction performs two IEEE fmas on
+// the halves of 64-bit registers; the pair (lo, hi) is (re, im) of a complex
+// value or a broadcast (x, x)
+
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
 // compile-time twiddles exp(-2 pi i e / n) for the subgrid transform sizes.
 //
 // sin and cos are summed from their Taylor series in FP64 at compile time on

@@ -4,10 +4,14 @@
 //
 // One CTA per subgrid.  Each thread owns NPX consecutive pixels of one row and
 // keeps their 4-pol complex accumulators in registers; visibilities are staged
-// in shared memory in batches of VB (phase coefficients and the 2x2 visibility)
-// and read back as block-wide broadcasts.  Per visibility and pixel the inner
-// loop issues 2 FFMA for the phase, sin and cos on the SFU, and 16 FFMA for the
-// four complex multiply-adds.
+// in shared memory in batches of VB (FP32 phase coefficients and the 2x2
+// visibility) and read back as block-wide broadcasts.  Per visibility and pixel
+// the inner loop issues 2 FFMA for the phase, sin and cos on the SFU, and 16
+// FFMA for the four complex multiply-adds.
+//
+// With PREFETCH the next batch is fetched from global memory into registers
+// while the current one is summed, then converted and stored into the other
+// half of a double buffer: one barrier per batch, global latency hidden.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -17,21 +21,177 @@ namespace {
 
 using namespace dev;
 
-template <int L, int NPX, int VB>
-__global__ void __launch_bounds__(L * L / NPX)
-gridder_kernel(Geometry g, int64_t first, int use_order, const float4 *__restrict__ vis,
+struct RawVis {
+    float4 v01, v23;
+    double u, v, w, sc;
+    int ok;
+};
+
+__device__ __forceinline__ void fetch_raw(const Geometry &g, const DevSubgrid &d, int k, const float4 *vis,
+                                          const uint8_t *flags, RawVis &r) {
+    int t, c;
+    const size_t vi = vis_index(g, d, k, t, c);
+    const double *x = g.uvw + ((size_t)d.bl * g.n_t + t) * 3;
+    r.u = x[0];
+    r.v = x[1];
+    r.w = x[2];
+    r.sc = g.scale[c];
+    r.v01 = vis[2 * vi];
+    r.v23 = vis[2 * vi + 1];
+    r.ok = !(flags && flags[vi]);
+}
+
+__device__ __forceinline__ void store_raw(const Geometry &g, const DevSubgrid &d, const RawVis &r, float4 *s_coef,
+                                          float4 *s_v01, float4 *s_v23, int i) {
+    const double du = r.u * r.sc - d.u0;
+    const double dv = r.v * r.sc - d.v0;
+    const double dw = r.w * r.sc - d.w0;
+    s_coef[i] = make_float4((float)(du * g.k_uv), (float)(dv * g.k_uv),
+                            (float)(dw * 6.283185307179586476925286766559), 0.0f);
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    s_v01[i] = r.ok ? r.v01 : z;     // flagged: weight 0
+    s_v23[i] = r.ok ? r.v23 : z;
+}
+
+template <int NPX>
+__device__ __forceinline__ void sum_batch(const float4 *s_coef, const float4 *s_v01, const float4 *s_v23, int nb,
+                                          float Y, const float (&X)[NPX], const float (&NP)[NPX],
+                                          float (&acc)[NPX][8]) {
+#pragma unroll 2
+    for (int i = 0; i < nb; ++i) {
+        const float4 cf = s_coef[i];
+        const float4 v01 = s_v01[i];
+        const float4 v23 = s_v23[i];
+        const float bY = cf.y * Y;
+#pragma unroll
+        for (int j = 0; j < NPX; ++j) {
+            const float phase = fmaf(cf.x, X[j], fmaf(cf.z, NP[j], bY));
+            float sn, cs;
+            __sincosf(phase, &sn, &cs);
+            // acc += V * (cs + i sn)
+            acc[j][0] = fmaf(v01.x, cs, acc[j][0]); acc[j][0] = fmaf(-v01.y, sn, acc[j][0]);
+            acc[j][1] = fmaf(v01.x, sn, acc[j][1]); acc[j][1] = fmaf(v01.y, cs, acc[j][1]);
+            acc[j][2] = fmaf(v01.z, cs, acc[j][2]); acc[j][2] = fmaf(-v01.w, sn, acc[j][2]);
+            acc[j][3] = fmaf(v01.z, sn, acc[j][3]); acc[j][3] = fmaf(v01.w, cs, acc[j][3]);
+            acc[j][4] = fmaf(v23.x, cs, acc[j][4]); acc[j][4] = fmaf(-v23.y, sn, acc[j][4]);
+            acc[j][5] = fmaf(v23.x, sn, acc[j][5]); acc[j][5] = fmaf(v23.y, cs, acc[j][5]);
+            acc[j][6] = fmaf(v23.z, cs, acc[j][6]); acc[j][6] = fmaf(-v23.w, sn, acc[j][6]);
+            acc[j][7] = fmaf(v23.z, sn, acc[j][7]); acc[j][7] = fmaf(v23.w, cs, acc[j][7]);
+        }
+    }
+}
+
+// Packed form: acc (re, im) += c (vr, vi) + s (-vi, vr) as two f32x2 fmas per
+// polarisation; (vr, vi) and i V = (-vi, vr) are staged in shared memory.
+template <int NPX>
+__device__ __forceinline__ void sum_batch_f2(const float4 *s_coef, const float4 *s_v01, const float4 *s_v23,
+                                             const float4 *s_iv01, const float4 *s_iv23, int nb, float Y,
+                                             const float (&X)[NPX], const float (&NP)[NPX], f2_t (&acc)[NPX][4]) {
+#pragma unroll 2
+    for (int i = 0; i < nb; ++i) {
+        const float4 cf = s_coef[i];
+        const ulonglong2 v01 = *reinterpret_cast<const ulonglong2 *>(s_v01 + i);
+        const ulonglong2 v23 = *reinterpret_cast<const ulonglong2 *>(s_v23 + i);
+        const ulonglong2 w01 = *reinterpret_cast<const ulonglong2 *>(s_iv01 + i);
+        const ulonglong2 w23 = *reinterpret_cast<const ulonglong2 *>(s_iv23 + i);
+        const float bY = cf.y * Y;
+#pragma unroll
+        for (int j = 0; j < NPX; ++j) {
+            const float phase = fmaf(cf.x, X[j], fmaf(cf.z, NP[j], bY));
+            float sn, cs;
+            __sincosf(phase, &sn, &cs);
+            const f2_t cc = f2_pack(cs, cs), ss = f2_pack(sn, sn);
+            acc[j][0] = f2_fma(ss, w01.x, f2_fma(cc, v01.x, acc[j][0]));
+            acc[j][1] = f2_fma(ss, w01.y, f2_fma(cc, v01.y, acc[j][1]));
+            acc[j][2] = f2_fma(ss, w23.x, f2_fma(cc, v23.x, acc[j][2]));
+            acc[j][3] = f2_fma(ss, w23.y, f2_fma(cc, v23.y, acc[j][3]));
+        }
+    }
+}
+
+template <int L, int NPX, int VB, int MINB>
+__global__ void __launch_bounds__(L * L / NPX, MINB)
+gridder_f2_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
+                  const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                  const float *__restrict__ taper, float4 *__restrict__ out) {
+    constexpr int NT = L * L / NPX;
+    constexpr int TPR = L / NPX;
+    __shared__ float4 s_coef[VB];
+    __shared__ float4 s_v01[VB];
+    __shared__ float4 s_v23[VB];
+    __shared__ float4 s_iv01[VB];
+    __shared__ float4 s_iv23[VB];
+
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    const DevSubgrid d = g.sub[sid];
+    const int tid = threadIdx.x;
+    const int y = tid / TPR;
+    const int x0 = (tid % TPR) * NPX;
+    const float Y = (float)(y - L / 2);
+    float X[NPX], NP[NPX];
+#pragma unroll
+    for (int j = 0; j < NPX; ++j) {
+        X[j] = (float)(x0 + j - L / 2);
+        NP[j] = g.nprime[y * L + x0 + j];
+    }
+    f2_t acc[NPX][4];
+#pragma unroll
+    for (int j = 0; j < NPX; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[j][q] = f2_pack(0.0f, 0.0f);
+
+    for (int k0 = 0; k0 < d.kp; k0 += VB) {
+        const int nb = min(VB, d.kp - k0);
+        for (int i = tid; i < nb; i += NT) {
+            RawVis r;
+            fetch_raw(g, d, k0 + i, vis, flags, r);
+            store_raw(g, d, r, s_coef, s_v01, s_v23, i);
+            const float4 a = s_v01[i], b = s_v23[i];
+            s_iv01[i] = make_float4(-a.y, a.x, -a.w, a.z);
+            s_iv23[i] = make_float4(-b.y, b.x, -b.w, b.z);
+        }
+        __syncthreads();
+        sum_batch_f2<NPX>(s_coef, s_v01, s_v23, s_iv01, s_iv23, nb, Y, X, NP, acc);
+        __syncthreads();
+    }
+
+    float4 *o = out + (size_t)blockIdx.x * L * L * 2;
+#pragma unroll
+    for (int j = 0; j < NPX; ++j) {
+        const int pix = y * L + x0 + j;
+        M22 P;
+        f2_unpack(acc[j][0], P.m[0].x, P.m[0].y);
+        f2_unpack(acc[j][1], P.m[1].x, P.m[1].y);
+        f2_unpack(acc[j][2], P.m[2].x, P.m[2].y);
+        f2_unpack(acc[j][3], P.m[3].x, P.m[3].y);
+        if (aterms) {
+            const size_t base = ((size_t)d.slot * g.n_stations) * L * L;
+            const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * L * L + pix));
+            const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * L * L + pix));
+            P = herm_mul_mul(Ap, P, Aq);
+        }
+        const float tw = taper[pix];
+        o[2 * pix] = make_float4(tw * P.m[0].x, tw * P.m[0].y, tw * P.m[1].x, tw * P.m[1].y);
+        o[2 * pix + 1] = make_float4(tw * P.m[2].x, tw * P.m[2].y, tw * P.m[3].x, tw * P.m[3].y);
+    }
+}
+
+template <int L, int NPX, int VB, int MINB, bool PREFETCH>
+__global__ void __launch_bounds__(L * L / NPX, MINB)
+gridder_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                const float *__restrict__ taper, float4 *__restrict__ out) {
     constexpr int NT = L * L / NPX;
     constexpr int TPR = L / NPX;
+    constexpr int NBUF = PREFETCH ? 2 : 1;
+    constexpr int NS = (VB + NT - 1) / NT;   // visibilities staged per thread per batch
     static_assert(L % NPX == 0, "pixels per thread must divide L");
 
-    __shared__ float4 s_coef[VB];
-    __shared__ float4 s_v01[VB];
-    __shared__ float4 s_v23[VB];
+    __shared__ float4 s_coef[NBUF][VB];
+    __shared__ float4 s_v01[NBUF][VB];
+    __shared__ float4 s_v23[NBUF][VB];
 
-    const int64_t slot = first + blockIdx.x;
-    const int sid = use_order ? g.order[slot] : (int)slot;
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     const DevSubgrid d = g.sub[sid];
     const int tid = threadIdx.x;
     const int y = tid / TPR;
@@ -50,45 +210,51 @@ gridder_kernel(Geometry g, int64_t first, int use_order, const float4 *__restric
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[j][q] = 0.0f;
 
-    for (int k0 = 0; k0 < d.kp; k0 += VB) {
-        const int nb = min(VB, d.kp - k0);
-        for (int i = tid; i < nb; i += NT) {
-            int t, c;
-            const size_t vi = vis_index(g, d, k0 + i, t, c);
-            const PhaseCoef pc = phase_coef(g, d, t, c);
-            float4 v01 = vis[2 * vi], v23 = vis[2 * vi + 1];
-            if (flags && flags[vi]) {   // zero weight (flags)
-                v01 = make_float4(0.f, 0.f, 0.f, 0.f);
-                v23 = v01;
-            }
-            s_coef[i] = make_float4(pc.a, pc.b, pc.c, 0.0f);
-            s_v01[i] = v01;
-            s_v23[i] = v23;
-        }
-        __syncthreads();
-#pragma unroll 2
-        for (int i = 0; i < nb; ++i) {
-            const float4 cf = s_coef[i];
-            const float4 v01 = s_v01[i];
-            const float4 v23 = s_v23[i];
-            const float bY = cf.y * Y;
+    if (PREFETCH) {
+        {   // stage batch 0
+            const int nb = min(VB, d.kp);
 #pragma unroll
-            for (int j = 0; j < NPX; ++j) {
-                const float phase = fmaf(cf.x, X[j], fmaf(cf.z, NP[j], bY));
-                float sn, cs;
-                __sincosf(phase, &sn, &cs);
-                // acc += V * (cs + i sn)
-                acc[j][0] = fmaf(v01.x, cs, acc[j][0]); acc[j][0] = fmaf(-v01.y, sn, acc[j][0]);
-                acc[j][1] = fmaf(v01.x, sn, acc[j][1]); acc[j][1] = fmaf(v01.y, cs, acc[j][1]);
-                acc[j][2] = fmaf(v01.z, cs, acc[j][2]); acc[j][2] = fmaf(-v01.w, sn, acc[j][2]);
-                acc[j][3] = fmaf(v01.z, sn, acc[j][3]); acc[j][3] = fmaf(v01.w, cs, acc[j][3]);
-                acc[j][4] = fmaf(v23.x, cs, acc[j][4]); acc[j][4] = fmaf(-v23.y, sn, acc[j][4]);
-                acc[j][5] = fmaf(v23.x, sn, acc[j][5]); acc[j][5] = fmaf(v23.y, cs, acc[j][5]);
-                acc[j][6] = fmaf(v23.z, cs, acc[j][6]); acc[j][6] = fmaf(-v23.w, sn, acc[j][6]);
-                acc[j][7] = fmaf(v23.z, sn, acc[j][7]); acc[j][7] = fmaf(v23.w, cs, acc[j][7]);
+            for (int s = 0; s < NS; ++s) {
+                const int i = tid + s * NT;
+                if (i < nb) {
+                    RawVis r;
+                    fetch_raw(g, d, i, vis, flags, r);
+                    store_raw(g, d, r, s_coef[0], s_v01[0], s_v23[0], i);
+                }
             }
         }
         __syncthreads();
+        for (int k0 = 0, b = 0; k0 < d.kp; k0 += VB, ++b) {
+            const int cur = b & 1;
+            const int nb = min(VB, d.kp - k0);
+            const int nbn = min(VB, d.kp - k0 - VB);   // next batch (<= 0: none)
+            RawVis raw[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int i = tid + s * NT;
+                if (i < nbn) fetch_raw(g, d, k0 + VB + i, vis, flags, raw[s]);
+            }
+            sum_batch<NPX>(s_coef[cur], s_v01[cur], s_v23[cur], nb, Y, X, NP, acc);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int i = tid + s * NT;
+                if (i < nbn) store_raw(g, d, raw[s], s_coef[cur ^ (NBUF - 1)], s_v01[cur ^ (NBUF - 1)],
+                                       s_v23[cur ^ (NBUF - 1)], i);
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int k0 = 0; k0 < d.kp; k0 += VB) {
+            const int nb = min(VB, d.kp - k0);
+            for (int i = tid; i < nb; i += NT) {
+                RawVis r;
+                fetch_raw(g, d, k0 + i, vis, flags, r);
+                store_raw(g, d, r, s_coef[0], s_v01[0], s_v23[0], i);
+            }
+            __syncthreads();
+            sum_batch<NPX>(s_coef[0], s_v01[0], s_v23[0], nb, Y, X, NP, acc);
+            __syncthreads();
+        }
     }
 
     // image-domain kernel: taper * A_p^H . I . A_q, then store [L][L][4]
@@ -113,40 +279,95 @@ gridder_kernel(Geometry g, int64_t first, int use_order, const float4 *__restric
     }
 }
 
-template <int L, int NPX, int VB>
-idg_status launch(const Geometry &g, int64_t first, int64_t count, bool use_order, const void *vis,
-                  const uint8_t *flags, const void *aterms, const float *taper, void *out, cudaStream_t s) {
+using LaunchFn = idg_status (*)(const Geometry &, const SubgridSet &, const void *, const uint8_t *, const void *,
+                                const float *, void *, cudaStream_t);
+
+template <int L, int NPX, int VB, int MINB, bool PF>
+idg_status launch_one(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                      const void *aterms, const float *taper, void *out, cudaStream_t s) {
     constexpr int NT = L * L / NPX;
-    int64_t done = 0;
-    while (done < count) {   // grid-size limit of one launch
-        const int64_t n = count - done < 2147483647 ? count - done : 2147483647;
-        gridder_kernel<L, NPX, VB><<<(unsigned)n, NT, 0, s>>>(
-            g, first + done, use_order ? 1 : 0, (const float4 *)vis, flags, (const float4 *)aterms, taper,
-            (float4 *)out + (size_t)done * L * L * 2);
-        done += n;
-    }
+    gridder_kernel<L, NPX, VB, MINB, PF><<<(unsigned)set.count, NT, 0, s>>>(
+        g, set.idx, set.first, (const float4 *)vis, flags, (const float4 *)aterms, taper, (float4 *)out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "gridder launch");
     return IDG_OK;
 }
 
+template <int L, int NPX, int VB, int MINB>
+idg_status launch_f2(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                     const void *aterms, const float *taper, void *out, cudaStream_t s) {
+    constexpr int NT = L * L / NPX;
+    gridder_f2_kernel<L, NPX, VB, MINB><<<(unsigned)set.count, NT, 0, s>>>(
+        g, set.idx, set.first, (const float4 *)vis, flags, (const float4 *)aterms, taper, (float4 *)out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gridder launch");
+    return IDG_OK;
+}
+
+struct Variant {
+    const char *name;
+    LaunchFn fn;
+};
+
+#define GV(L, NPX, VB, MINB, PF) {"npx" #NPX "_vb" #VB "_minb" #MINB "_prefetch_" #PF, launch_one<L, NPX, VB, MINB, PF>}
+
+#define GF(L, NPX, VB, MINB) {"f32x2_npx" #NPX "_vb" #VB "_minb" #MINB, launch_f2<L, NPX, VB, MINB>}
+const Variant kV8[] = {GF(8, 1, 128, 4), GV(8, 1, 128, 4, false), GV(8, 2, 256, 8, true)};
+const Variant kV16[] = {GF(16, 2, 128, 3), GV(16, 2, 128, 3, false), GV(16, 2, 256, 3, true),
+                        GV(16, 4, 256, 6, true), GF(16, 4, 128, 2)};
+const Variant kV24[] = {GF(24, 3, 128, 3), GV(24, 3, 128, 3, false), GV(24, 3, 256, 3, true),
+                        GV(24, 6, 256, 6, true), GF(24, 6, 128, 2)};
+const Variant kV32[] = {GF(32, 4, 128, 2),        GV(32, 4, 128, 3, false), GV(32, 4, 256, 3, true),
+                        GV(32, 4, 256, 4, true),  GV(32, 8, 256, 4, true),  GV(32, 2, 256, 2, true),
+                        GF(32, 4, 128, 3),        GF(32, 2, 128, 3),        GF(32, 8, 128, 4)};
+const Variant kV48[] = {GF(48, 4, 128, 1), GV(48, 6, 128, 2, false), GV(48, 6, 256, 2, true),
+                        GV(48, 4, 256, 1, true), GF(48, 6, 128, 1)};
+const Variant kV64[] = {GF(64, 4, 128, 1), GV(64, 8, 128, 1, false), GV(64, 8, 256, 1, true),
+                        GV(64, 4, 256, 1, true)};
+
+#undef GV
+#undef GF
+
+bool table(int L, const Variant **v, int *n) {
+    switch (L) {
+#define T(X) case X: *v = kV##X; *n = (int)(sizeof(kV##X) / sizeof(Variant)); return true;
+        T(8) T(16) T(24) T(32) T(48) T(64)
+#undef T
+    }
+    return false;
+}
+
 }  // namespace
 
-bool gridder_supported(int L) { return L == 8 || L == 16 || L == 24 || L == 32 || L == 48 || L == 64; }
+bool gridder_supported(int L) {
+    const Variant *v;
+    int n;
+    return table(L, &v, &n);
+}
 
-idg_status launch_gridder(const Geometry &g, int64_t first, int64_t count, bool use_order, const void *vis,
-                          const uint8_t *flags, const void *aterms, const float *taper, void *out,
-                          void *stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (g.L) {
-    case 8: return launch<8, 1, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    case 16: return launch<16, 2, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    case 24: return launch<24, 3, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    case 32: return launch<32, 4, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    case 48: return launch<48, 6, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    case 64: return launch<64, 8, 128>(g, first, count, use_order, vis, flags, aterms, taper, out, s);
-    }
-    return fail(IDG_ERR_UNSUPPORTED, "subgrid size not compiled in");
+int gridder_variant_count(int L) {
+    const Variant *v;
+    int n;
+    return table(L, &v, &n) ? n : 0;
+}
+
+const char *gridder_variant_name(int L, int i) {
+    const Variant *v;
+    int n;
+    if (!table(L, &v, &n) || i < 0 || i >= n) return nullptr;
+    return v[i].name;
+}
+
+idg_status launch_gridder(const Geometry &g, const SubgridSet &set, int variant, const void *vis,
+                          const uint8_t *flags, const void *aterms, const float *taper, void *out, void *stream) {
+    const Variant *v;
+    int n;
+    if (!table(g.L, &v, &n)) return fail(IDG_ERR_UNSUPPORTED, "subgrid size not compiled in");
+    if (set.count <= 0) return IDG_OK;
+    if (g.recurrence) return launch_gridder_rec(g, set, vis, flags, aterms, taper, out, stream);
+    if (variant < 0) variant = get_variant(IDG_KERNEL_GRIDDER, g.L);
+    if (variant >= n) variant = 0;
+    return v[variant].fn(g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
 }
 
 }  // namespace idg

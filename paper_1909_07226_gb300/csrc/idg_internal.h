@@ -30,6 +30,9 @@ struct Geometry {
     const double *uvw;         // [n_bl][n_t][3] metres
     const double *scale;       // [n_chan] f / c
     const float *nprime;       // [L][L] n' = sqrt(1 - l^2 - m^2) - 1
+    double ds;                 // channel scale step (f_{c+1} - f_c)/c for uniformly spaced channels
+    int recurrence;            // 1: phasors by channel recurrence (IDG_PHASOR_RECURRENCE)
+    int anchor;                // channels per recurrence run (re-anchor interval)
 };
 
 // Host planner output.
@@ -71,8 +74,12 @@ struct idg_plan {
     double *d_scale = nullptr;
     float *d_nprime = nullptr;
     bool any_dropped = false;
+    double ds = 0.0;                        // uniform channel scale step (0 if not uniform)
     std::vector<int64_t> kp_prefix_plan;    // [n_sub + 1], sum of K_p in plan order
     std::vector<int64_t> kp_prefix_order;   // [n_sub + 1], sum of K_p in device work order
+    std::vector<int32_t> kp_plan;           // [n_sub] K_p in plan order
+    std::vector<int32_t> kp_order;          // [n_sub] K_p in device work order (non-increasing)
+    std::vector<int32_t> order;             // [n_sub] plan index of each work-order slot (host copy)
 
     idg::Geometry geometry() const;
 };
@@ -95,18 +102,43 @@ struct ProfileScope {
     bool on;
 };
 
-// kernel launchers (each returns IDG_OK or an error with the message set)
+// A set of subgrids processed by one launch: block b works on plan index
+// idx[b] (idx: device array) or, without idx, on first + b.  kp_host (host,
+// count entries, may be null for the gridder) holds the members' K_p so a
+// launcher can split the set into runs of equal work shape.
+struct SubgridSet {
+    const int32_t *idx;
+    int64_t first;
+    int64_t count;
+    const int32_t *kp_host;
+};
+
+// kernel launchers (each returns IDG_OK or an error with the message set).
+// variant < 0 selects the process-wide choice for L (see set_variant).
 bool gridder_supported(int L);
-idg_status launch_gridder(const Geometry &g, int64_t first, int64_t count, bool use_order,
-                          const void *vis, const uint8_t *flags, const void *aterms, const float *taper,
-                          void *subgrids, void *stream);
+int gridder_variant_count(int L);
+const char *gridder_variant_name(int L, int v);
+idg_status launch_gridder(const Geometry &g, const SubgridSet &set, int variant, const void *vis,
+                          const uint8_t *flags, const void *aterms, const float *taper, void *subgrids,
+                          void *stream);
+int degridder_variant_count(int L);
+const char *degridder_variant_name(int L, int v);
+idg_status launch_degridder(const Geometry &g, const SubgridSet &set, int variant, const void *subgrids,
+                            const uint8_t *flags, const void *aterms, const float *taper, void *vis_out,
+                            void *stream);
 idg_status launch_fft(int L, int64_t count, int direction, void *subgrids, void *stream);
-idg_status launch_adder(const Geometry &g, int64_t first, int64_t count, bool use_order,
-                        const void *subgrids, void *grid, void *stream);
-idg_status launch_splitter(const Geometry &g, int64_t first, int64_t count, bool use_order,
-                           const void *grid, void *subgrids, void *stream);
-idg_status launch_degridder(const Geometry &g, int64_t first, int64_t count, bool use_order,
-                            const void *subgrids, const uint8_t *flags, const void *aterms,
-                            const float *taper, void *vis_out, void *stream);
+idg_status launch_adder(const Geometry &g, const SubgridSet &set, const void *subgrids, void *grid, void *stream);
+idg_status launch_splitter(const Geometry &g, const SubgridSet &set, const void *grid, void *subgrids, void *stream);
+
+// channel-recurrence forms (precision_mode = IDG_PHASOR_RECURRENCE)
+idg_status launch_gridder_rec(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                              const void *aterms, const float *taper, void *subgrids, void *stream);
+idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const void *subgrids,
+                                const uint8_t *flags, const void *aterms, const float *taper, void *vis_out,
+                                void *stream);
+
+// process-wide kernel variant choice per (kernel, L); default 0
+int get_variant(int kernel, int L);
+void set_variant(int kernel, int L, int v);
 
 }  // namespace idg

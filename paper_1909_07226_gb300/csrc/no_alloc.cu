@@ -82,8 +82,9 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
     // FFT and the adder read it, so nothing in the scratch has to start at zero.
     cudaStream_t s = (cudaStream_t)stream;
     const Geometry g = p->geometry();
-    st = launch_gridder(g, 0, n, true, vis, flags, aterms, taper, scratch, s);
+    const SubgridSet all{p->d_order, 0, n, p->kp_order.data()};
+    st = launch_gridder(g, all, -1, vis, flags, aterms, taper, scratch, s);
     if (st == IDG_OK) st = launch_fft(p->L, n, -1, scratch, s);
-    if (st == IDG_OK) st = launch_adder(g, 0, n, true, scratch, grid, s);
+    if (st == IDG_OK) st = launch_adder(g, all, scratch, grid, s);
     return st;
 }

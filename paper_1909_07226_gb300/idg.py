@@ -33,6 +33,8 @@ EXPORTED = [
     "idg_grid_subgrids", "idg_fft_subgrids", "idg_add_subgrids", "idg_split_subgrids", "idg_degrid_subgrids",
     "idg_status_string", "idg_last_error", "idg_supported_subgrid_sizes",
     "idg_profile_enable", "idg_profile_read", "idg_grid_no_alloc",
+    "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
+    "idg_autotune",
 ]
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder"]
 
@@ -91,6 +93,11 @@ def load(path: str = LIB_PATH):
         "idg_profile_enable": (None, [I32]),
         "idg_profile_read": (I32, [P, P, P, I32]),
         "idg_grid_no_alloc": (I32, [P, P, P, P, P, P, P]),
+        "idg_kernel_variant_count": (I32, [I32, I32]),
+        "idg_kernel_variant_name": (ctypes.c_char_p, [I32, I32, I32]),
+        "idg_set_kernel_variant": (I32, [I32, I32, I32]),
+        "idg_get_kernel_variant": (I32, [I32, I32]),
+        "idg_autotune": (I32, [P, P, P, P, P, P, I64, P, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,6 +138,86 @@ def profile_read(reset: bool = True) -> dict:
     wk = (ctypes.c_double * n)()
     _check(load().idg_profile_read(la, ms, wk, 1 if reset else 0), "idg_profile_read")
     return {k: dict(launches=int(la[i]), ms=float(ms[i]), work=float(wk[i])) for i, k in enumerate(KERNELS)}
+
+
+# ---------------------------------------------------------------------------
+# kernel variants and the autotuner
+
+KERNEL_ID = {k: i for i, k in enumerate(KERNELS)}
+
+
+def kernel_variants(kernel: str, L: int):
+    lib = load()
+    k = KERNEL_ID[kernel]
+    n = lib.idg_kernel_variant_count(k, L)
+    return [lib.idg_kernel_variant_name(k, L, v).decode() for v in range(n)]
+
+
+def set_kernel_variant(kernel: str, L: int, variant: int):
+    _check(load().idg_set_kernel_variant(KERNEL_ID[kernel], L, variant), "idg_set_kernel_variant")
+
+
+def get_kernel_variant(kernel: str, L: int) -> int:
+    return int(load().idg_get_kernel_variant(KERNEL_ID[kernel], L))
+
+
+def autotune(plan, vis, flags, aterms, taper, vis_scratch=None, max_subgrids: int = 4096, stream=None) -> dict:
+    """idg_autotune: time every gridder (and degridder) variant on a sample of the
+    plan's subgrids and select the fastest for its L.  Returns the timings."""
+    import torch
+    L = plan.stats.subgrid_size
+    sh = _shapes(plan)
+    cap = 32
+    gms = (ctypes.c_double * cap)(*([-1.0] * cap))
+    dms = (ctypes.c_double * cap)(*([-1.0] * cap))
+    _check(load().idg_autotune(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                               _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                               _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                               _dptr(taper, "taper", torch.float32, sh["taper"]),
+                               _dptr(vis_scratch, "vis_scratch", torch.complex64, sh["vis"], True),
+                               int(max_subgrids), gms, dms, cap, _stream(stream)), "idg_autotune")
+    g_names, d_names = kernel_variants("gridder", L), kernel_variants("degridder", L)
+    return {"L": L,
+            "gridder": {"ms": {n: gms[i] for i, n in enumerate(g_names)}, "chosen": get_kernel_variant("gridder", L)},
+            "degridder": {"ms": {n: dms[i] for i, n in enumerate(d_names) if dms[i] >= 0},
+                          "chosen": get_kernel_variant("degridder", L)}}
+
+
+def _device_key() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def save_tuning(path: str):
+    """Persist the current per-L variant choices for this GPU model (JSON)."""
+    import json
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    entry = {}
+    for L in supported_subgrid_sizes():
+        entry[str(L)] = {"gridder": get_kernel_variant("gridder", L), "degridder": get_kernel_variant("degridder", L)}
+    data[_device_key()] = entry
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1)
+
+
+def load_tuning(path: str) -> bool:
+    """Restore choices saved by save_tuning for this GPU model; False if none."""
+    import json
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        data = json.load(f)
+    entry = data.get(_device_key())
+    if not entry:
+        return False
+    for L, ch in entry.items():
+        for k, v in ch.items():
+            if v < len(kernel_variants(k, int(L))):
+                set_kernel_variant(k, int(L), int(v))
+    return True
 
 
 @dataclasses.dataclass

@@ -130,3 +130,14 @@ def test_host_only_plan_rejects_device_calls(lib):
     st = lib.idg_grid(p.handle, ctypes.c_void_p(16), None, None, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
     assert st == 1
     assert b"without a CUDA device" in lib.idg_last_error()
+
+
+def test_recurrence_needs_uniform_channels(lib):
+    wl = syn.make_small(seed=1, n_st=4, n_t=8, n_chan=4, L=16, N=64, with_vis=False, aterms="identity")
+    f = wl.freqs_hz.copy()
+    f[2] += 3e5
+    with pytest.raises(idg.IDGError) as ei:
+        _create(freqs_hz=f, precision_mode=idg.PHASOR_RECURRENCE)
+    assert "uniformly spaced" in str(ei.value)
+    _create(freqs_hz=f)                                   # the direct form accepts any channels
+    _create(precision_mode=idg.PHASOR_RECURRENCE)         # uniform channels are accepted

@@ -47,10 +47,13 @@ def test_gridder_stage(L):
     d = workload_to_device(wl)
     n = p.n_subgrids
     assert int(op.desc[:, O.D_KP].max()) > 128          # several shared-memory batches
-    sub = torch_zeros((n, L, L, 4))
-    idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
     ref = O.subgrid_images(wl, op)
-    parity(sub.cpu().numpy(), ref, f"gridder L={L}")
+    for v, name in enumerate(idg.kernel_variants("gridder", L)):      # every compiled tile shape
+        idg.set_kernel_variant("gridder", L, v)
+        sub = torch_zeros((n, L, L, 4))
+        idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
+        parity(sub.cpu().numpy(), ref, f"gridder L={L} {name}")
+    idg.set_kernel_variant("gridder", L, 0)
 
 
 @pytest.mark.parametrize("L", SIZES)
@@ -94,10 +97,13 @@ def test_degridder_stage(L):
     n = p.n_subgrids
     rng = np.random.default_rng(11)
     img = (rng.normal(size=(n, L, L, 4)) + 1j * rng.normal(size=(n, L, L, 4))).astype(np.complex64)
-    out = torch_zeros(wl.vis.shape)
-    idg.degrid_subgrids(p, 0, n, dev(img), d["flags"], d["aterms"], d["taper"], out)
     ref = O.degrid_images(wl, op, img.astype(np.complex128))
-    parity(out.cpu().numpy(), ref, f"degridder L={L}")
+    for v, name in enumerate(idg.kernel_variants("degridder", L)):    # every compiled tile shape
+        idg.set_kernel_variant("degridder", L, v)
+        out = torch_zeros(wl.vis.shape)
+        idg.degrid_subgrids(p, 0, n, dev(img), d["flags"], d["aterms"], d["taper"], out)
+        parity(out.cpu().numpy(), ref, f"degridder L={L} {name}")
+    idg.set_kernel_variant("degridder", L, 0)
 
 
 CASES = {
@@ -215,3 +221,50 @@ def test_device_call_errors():
         idg.grid(p, torch_zeros((1, 2, 3, 4)), None, None, dev(wl.taper), torch_zeros((1, 4, 4, 4)))
     with pytest.raises(idg.IDGError):
         idg.fft_subgrids(p, 4, 0, torch_zeros((4, 16, 16, 4)))
+
+
+def test_autotune_selects_a_variant_and_results_hold():
+    import torch
+    wl = small(32, n_chan=16, n_t=100, max_t=96, n_slots=1)
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    scratch = torch_zeros(wl.vis.shape)
+    res = idg.autotune(p, d["vis"], d["flags"], d["aterms"], d["taper"], scratch, max_subgrids=64)
+    assert all(ms > 0 for ms in res["gridder"]["ms"].values())
+    assert len(res["degridder"]["ms"]) == len(idg.kernel_variants("degridder", 32))
+    g = torch_zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4))
+    idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+    parity(g.cpu().numpy(), O.grid(wl, op), "grid after autotune")
+    for k in ("gridder", "degridder"):
+        idg.set_kernel_variant(k, 32, 0)
+
+
+REC_CASES = {
+    "tiny": lambda: syn.make_tiny(),
+    "L8": lambda: small(8, n_chan=9, n_t=24, dt=5.0),
+    "L16_flags_aterms_13ch": lambda: small(16, n_chan=13, n_t=24, max_t=24, n_slots=1),
+    "L24_wlayers": lambda: small(24, w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12, n_chan=11),
+    "L32_wide": lambda: small(32, n_chan=16, diameter_m=30000.0, df=2e6, n_t=40),
+    "L48_1ch": lambda: small(48, n_chan=1, n_t=30),
+    "L64": lambda: small(64, n_chan=6, n_t=16),
+}
+
+
+@pytest.mark.parametrize("case", sorted(REC_CASES))
+def test_recurrence_form_grid_and_degrid(case):
+    # precision form: phasors advanced along channels, re-anchored every 8
+    # channels; compared with the same FP64 oracle at the same tolerance
+    import torch
+    wl = REC_CASES[case]()
+    p = idg.plan_from_workload(wl, precision_mode=idg.PHASOR_RECURRENCE)
+    op = O.plan(wl)
+    assert np.array_equal(p.export(), op.desc)
+    d = workload_to_device(wl)
+    g = torch_zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4))
+    idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+    parity(g.cpu().numpy(), O.grid(wl, op), f"recurrence grid {case}")
+    g_in = syn.random_grid(np.random.default_rng(8), p.n_w_layers, wl.grid_size)
+    v = torch.full(wl.vis.shape, 3.0 + 3.0j, dtype=torch.complex64, device="cuda")
+    idg.degrid(p, dev(g_in), d["flags"], d["aterms"], d["taper"], v)
+    parity(v.cpu().numpy(), O.degrid(wl, op, g_in), f"recurrence degrid {case}")
