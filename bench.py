@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny"])
+    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny", "batched"])
+    ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched configuration")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -418,12 +419,96 @@ def run_gb300(args, world, rank, local):
         print(json.dumps(rec))
 
 
+def run_batched(args, world, rank, local):
+    """The uneven batch (SURVEY config B): the same jobs gridded and degridded
+    (a) one after another with idg_grid / idg_degrid (plain per-job form) and
+    (b) as one batch: one persistent launch per subgrid size, subgrids kept in
+    shared memory, the launch sequence replayed from a CUDA graph."""
+    import torch
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    jobs = syn.make_batched_jobs(args.jobs)
+    t0 = time.perf_counter()
+    plans = [idg.plan_from_workload(w) for w in jobs]
+    plan_s = time.perf_counter() - t0
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1912)
+    bufs = []
+    for w, p in zip(jobs, plans):
+        vis = torch.randn(w.vis_shape if hasattr(w, "vis_shape") else (w.n_bl, w.n_t, w.n_chan, 4),
+                          dtype=torch.complex64, device=dev, generator=gen)
+        flags = (torch.rand((w.n_bl, w.n_t, w.n_chan), device=dev, generator=gen) < w.flag_p).to(torch.uint8)
+        grid = torch.zeros((p.n_w_layers, w.grid_size, w.grid_size, 4), dtype=torch.complex64, device=dev)
+        bufs.append(dict(vis=vis, vis_out=vis, flags=flags, aterms=None, taper=torch.from_numpy(w.taper).to(dev),
+                         grid=grid))
+    n_vis = float(sum(w.n_vis for w in jobs))
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_step():
+        for p, b in zip(plans, bufs):
+            b["grid"].zero_()
+            idg.grid(p, b["vis"], b["flags"], None, b["taper"], b["grid"], stream)
+            idg.degrid(p, b["grid"], b["flags"], None, b["taper"], b["vis_out"], stream)
+
+    batch = idg.Batch(plans, bufs, graph=True)
+
+    def batch_step():
+        for b in bufs:
+            b["grid"].zero_()
+        batch.grid(stream)
+        batch.degrid(stream)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_plain = timed(plain_step, max(1, args.steps // 2))
+    ms_batch = timed(batch_step, args.steps)
+    clocks = sampler.stop()
+    info = batch.info()
+    rec = {
+        "metric": "grid+degrid MVis/s (batched form vs plain per-job form)", "value": n_vis / ms_batch / 1e3,
+        "unit": "MVis/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"Batched uneven: {args.jobs} snapshot jobs, U{{12..64}} stations, U{{64..1024}} t, "
+                               f"U{{4..32}} ch of 0.2 MHz in 100-200 MHz, 0-20% flags, L in {{16,24,32}}, "
+                               f"N in {{1024,2048,4096}}", "jobs": args.jobs, "n_vis": int(n_vis),
+                   "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
+                   "graph": True, "l2": "inputs larger than L2, no flush"},
+        "plain_per_job": {"value": n_vis / ms_plain / 1e3, "unit": "MVis/s", "ms_per_step": ms_plain,
+                          "launches_per_step": None},
+        "batched_over_plain": ms_plain / ms_batch,
+        "clocks": clocks, "plan_seconds": plan_s,
+    }
+    print(json.dumps(rec))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.config == "batched":
+            run_batched(args, world, rank, local)
         else:
             run_gb300(args, world, rank, local)
     finally:

@@ -252,6 +252,47 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
                                void *d_vis_out, idg_stream stream);
 
 /*
+ * Batched form: many independent jobs processed together.  A batch binds each
+ * job's plan to its device buffers at creation.  All subgrids of all jobs with
+ * the same subgrid size L form one work list ordered by cost (K_p, largest
+ * first) and run in ONE persistent launch per L (a few CTAs per SM pulling
+ * work items from a device counter).  Each work item is the whole per-subgrid
+ * pipeline in one CTA, the subgrid staying in shared memory:
+ *   idg_batch_grid    direct sum, taper and A_p^H . A_q, FFT, add into grid
+ *                     (accumulated, as idg_grid)
+ *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
+ *                     into vis_out (overwritten; flagged and dropped -> 0)
+ * No device scratch is used.  With IDG_BATCH_GRAPH the first call of each
+ * direction captures its launch sequence into a CUDA graph, and later calls
+ * replay it (the buffers are fixed by the batch, so the graph stays valid).
+ * Supported: subgrid sizes 8, 16, 24, 32 and the direct phasor form.  The
+ * plans and buffers must outlive the batch; calls on one batch must not
+ * overlap (they share the work counters).
+ * idg_job_buffers per job (device pointers, layouts as above):
+ *   vis      gridding input (may be NULL for a degrid-only batch)
+ *   vis_out  degridding output (may be NULL for a grid-only batch)
+ *   flags    or NULL;  aterms  or NULL (identity);  taper (required)
+ *   grid     gridding output (accumulated) / degridding input
+ * idg_batch_info returns the planned visibilities, work items and launches.
+ */
+typedef struct idg_batch idg_batch;
+typedef struct {
+    const void *vis;
+    void *vis_out;
+    const uint8_t *flags;
+    const void *aterms;
+    const float *taper;
+    void *grid;
+} idg_job_buffers;
+enum { IDG_BATCH_GRAPH = 1 };
+idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers *buffers, int n_jobs, int flags,
+                            idg_batch **out);
+idg_status idg_batch_grid(idg_batch *batch, idg_stream stream);
+idg_status idg_batch_degrid(idg_batch *batch, idg_stream stream);
+idg_status idg_batch_info(const idg_batch *batch, int64_t *n_vis, int64_t *n_items, int *n_launches);
+void idg_batch_destroy(idg_batch *batch);
+
+/*
  * Kernel timing.  While enabled, every kernel launch of the library is
  * bracketed by two CUDA events recorded on the launch stream.  idg_profile_read
  * waits for the recorded events, adds their elapsed times into per-kernel
@@ -259,22 +300,24 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   launches[k]  number of launches of kernel k
  *   ms[k]        summed device time (event to event) in milliseconds
  *   work[k]      algorithmic work of those launches: visibility-pixel products
- *                (sum of K_p * L^2) for the gridder and degridder, bytes moved
+ *                (sum of K_p * L^2) for the gridder, the degridder and the two
+ *                fused batch kernels (IDG_KERNEL_BATCH_*), bytes moved
  *                for the adder (read subgrid + read and write grid, 96 B per
  *                pixel) and the splitter (64 B per pixel), subgrids for the FFT.
  * Arrays have IDG_KERNEL_COUNT entries; any of them may be NULL.  Do not enable
  * timing while a stream is being captured into a CUDA graph.
  */
 enum { IDG_KERNEL_GRIDDER = 0, IDG_KERNEL_FFT, IDG_KERNEL_ADDER, IDG_KERNEL_SPLITTER, IDG_KERNEL_DEGRIDDER,
-       IDG_KERNEL_COUNT };
+       IDG_KERNEL_BATCH_GRID, IDG_KERNEL_BATCH_DEGRID, IDG_KERNEL_COUNT };
 void idg_profile_enable(int on);
 idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset);
 
 /*
  * Kernel variants and the autotuner.  The gridder and the degridder come in
  * several compiled tile shapes per subgrid size L (pixels per thread,
- * visibilities per shared-memory batch, block size, pixel-group split); the
- * other kernels have one.  The process-wide choice per (kernel, L) starts at
+ * visibilities per shared-memory batch, block size, pixel-group split), and so
+ * do the fused batch kernels (IDG_KERNEL_BATCH_GRID / _DEGRID, chosen when a
+ * batch is created); the other kernels have one.  The process-wide choice per (kernel, L) starts at
  * variant 0 and applies to every later call with that L.
  *   idg_kernel_variant_count   number of variants (0: no such kernel or L)
  *   idg_kernel_variant_name    a static string naming the variant, or NULL

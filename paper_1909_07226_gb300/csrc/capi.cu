@@ -103,6 +103,12 @@ ProfileScope::ProfileScope(int k, void *s, double w) : kernel(k), stream(s), ev{
         on = g_prof_on;
     }
     if (!on) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        on = false;       // no timing events inside a graph capture
+        return;
+    }
     if (cudaEventCreate((cudaEvent_t *)&ev[0]) != cudaSuccess || cudaEventCreate((cudaEvent_t *)&ev[1]) != cudaSuccess) {
         cudaGetLastError();
         on = false;
@@ -683,6 +689,7 @@ extern "C" {
 int idg_kernel_variant_count(int kernel, int L) {
     if (kernel == IDG_KERNEL_GRIDDER) return gridder_variant_count(L);
     if (kernel == IDG_KERNEL_DEGRIDDER) return degridder_variant_count(L);
+    if (kernel == IDG_KERNEL_BATCH_GRID || kernel == IDG_KERNEL_BATCH_DEGRID) return batch_variant_count(kernel, L);
     if (kernel >= 0 && kernel < IDG_KERNEL_COUNT) return gridder_supported(L) ? 1 : 0;
     return 0;
 }
@@ -690,6 +697,7 @@ int idg_kernel_variant_count(int kernel, int L) {
 const char *idg_kernel_variant_name(int kernel, int L, int v) {
     if (kernel == IDG_KERNEL_GRIDDER) return gridder_variant_name(L, v);
     if (kernel == IDG_KERNEL_DEGRIDDER) return degridder_variant_name(L, v);
+    if (kernel == IDG_KERNEL_BATCH_GRID || kernel == IDG_KERNEL_BATCH_DEGRID) return batch_variant_name(kernel, L, v);
     if (kernel >= 0 && kernel < IDG_KERNEL_COUNT && v == 0 && gridder_supported(L)) return "default";
     return nullptr;
 }

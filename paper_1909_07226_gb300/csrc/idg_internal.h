@@ -137,6 +137,10 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
                                 const uint8_t *flags, const void *aterms, const float *taper, void *vis_out,
                                 void *stream);
 
+// fused batch kernel shapes (batch.cu)
+int batch_variant_count(int kernel, int L);
+const char *batch_variant_name(int kernel, int L, int v);
+
 // process-wide kernel variant choice per (kernel, L); default 0
 int get_variant(int kernel, int L);
 void set_variant(int kernel, int L, int v);

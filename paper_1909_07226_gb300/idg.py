@@ -34,9 +34,11 @@ EXPORTED = [
     "idg_status_string", "idg_last_error", "idg_supported_subgrid_sizes",
     "idg_profile_enable", "idg_profile_read", "idg_grid_no_alloc",
     "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
-    "idg_autotune",
+    "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
+    "idg_batch_destroy",
 ]
-KERNELS = ["gridder", "fft", "adder", "splitter", "degridder"]
+BATCH_GRAPH = 1
+KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
 
 
 class IDGError(RuntimeError):
@@ -98,6 +100,11 @@ def load(path: str = LIB_PATH):
         "idg_set_kernel_variant": (I32, [I32, I32, I32]),
         "idg_get_kernel_variant": (I32, [I32, I32]),
         "idg_autotune": (I32, [P, P, P, P, P, P, I64, P, P, I32, P]),
+        "idg_batch_create": (I32, [P, P, I32, I32, P]),
+        "idg_batch_grid": (I32, [P, P]),
+        "idg_batch_degrid": (I32, [P, P]),
+        "idg_batch_info": (I32, [P, P, P, P]),
+        "idg_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -437,3 +444,59 @@ def degrid_host(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None)
                                   _hptr(taper, "taper", np.float32, sh["taper"]),
                                   _hptr(vis_out, "vis_out", np.complex64, sh["vis"]), _stream(stream)),
            "idg_degrid_host")
+
+
+# ---------------------------------------------------------------------------
+# batched form
+
+class JobBuffers(ctypes.Structure):
+    _fields_ = [("vis", ctypes.c_void_p), ("vis_out", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("aterms", ctypes.c_void_p), ("taper", ctypes.c_void_p), ("grid", ctypes.c_void_p)]
+
+
+class Batch:
+    """idg_batch: jobs (plan + device tensors) gridded/degridded together in one
+    persistent launch per subgrid size.  Keeps references to the plans and
+    tensors so they outlive the batch."""
+
+    def __init__(self, plans, jobs, graph: bool = False):
+        import torch
+        self._keep = (list(plans), [dict(j) for j in jobs])
+        n = len(plans)
+        bufs = (JobBuffers * n)()
+        for i, (p, j) in enumerate(zip(plans, jobs)):
+            sh = _shapes(p)
+            bufs[i].vis = _dptr(j.get("vis"), "vis", torch.complex64, sh["vis"], True)
+            bufs[i].vis_out = _dptr(j.get("vis_out"), "vis_out", torch.complex64, sh["vis"], True)
+            bufs[i].flags = _dptr(j.get("flags"), "flags", torch.uint8, sh["flags"], True)
+            bufs[i].aterms = _dptr(j.get("aterms"), "aterms", torch.complex64, sh["aterms"], True)
+            bufs[i].taper = _dptr(j.get("taper"), "taper", torch.float32, sh["taper"])
+            bufs[i].grid = _dptr(j.get("grid"), "grid", torch.complex64, sh["grid"], True)
+        arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+        h = ctypes.c_void_p()
+        _check(load().idg_batch_create(arr, bufs, n, BATCH_GRAPH if graph else 0, ctypes.byref(h)),
+               "idg_batch_create")
+        self.handle = h
+
+    def grid(self, stream=None):
+        _check(load().idg_batch_grid(self.handle, _stream(stream)), "idg_batch_grid")
+
+    def degrid(self, stream=None):
+        _check(load().idg_batch_degrid(self.handle, _stream(stream)), "idg_batch_degrid")
+
+    def info(self):
+        nv, ni, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(load().idg_batch_info(self.handle, ctypes.byref(nv), ctypes.byref(ni), ctypes.byref(nl)),
+               "idg_batch_info")
+        return {"n_vis": nv.value, "n_items": ni.value, "n_launches": nl.value}
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            load().idg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -460,3 +460,38 @@ def random_grid(rng: np.random.Generator, n_w: int, N: int) -> np.ndarray:
     """A random complex64 uv grid [n_w][N][N][4] (input of degridding tests)."""
     g = rng.normal(size=(n_w, N, N, 4, 2)).astype(np.float32)
     return np.ascontiguousarray(g.view(np.complex64)[..., 0])
+
+
+def make_batched_jobs(n_jobs: int = 256, seed: Optional[int] = None, scale_t: float = 1.0):
+    """The uneven batch: n_jobs snapshot jobs, each with U{12..64} stations in a
+    Gaussian layout (sigma 3 km), U{64..1024} timesteps of 1 s from a random
+    start hour angle, U{4..32} channels of 0.2 MHz placed uniformly so the band
+    lies in 100-200 MHz, flag probability U[0, 0.2], subgrid size from
+    {16, 24, 32}, grid size from {1024, 2048, 4096}, image pixel
+    cell = 1/(2.2 max|uv|) (so the longest baseline lands N/2.2 pixels from the
+    centre), 128 timesteps per subgrid, beta = 7, identity A-terms.  Visibility
+    values are not made here.  scale_t shrinks the timestep counts for tests."""
+    rng = np.random.default_rng(SEED_BASE + CONFIG_INDEX["batched"] if seed is None else seed)
+    jobs = []
+    for j in range(n_jobs):
+        n_st = int(rng.integers(12, 65))
+        n_t = max(2, int(int(rng.integers(64, 1025)) * scale_t))
+        n_ch = int(rng.integers(4, 33))
+        p_flag = float(rng.uniform(0.0, 0.2))
+        L = int(rng.choice([16, 24, 32]))
+        N = int(rng.choice([1024, 2048, 4096]))
+        enu = np.concatenate([rng.normal(0.0, 3000.0, size=(n_st, 2)), np.zeros((n_st, 1))], axis=1)
+        bl = all_baselines(n_st)
+        ha0 = float(rng.uniform(-3.0, 3.0)) * np.pi / 12.0
+        uvw = earth_rotation_uvw(enu, bl, hour_angles(n_t, 1.0, start_rad=ha0), math.radians(SOURCE_DEC_DEG),
+                                 math.radians(LOFAR_LATITUDE_DEG))
+        df = 0.2e6
+        f_lo = float(rng.uniform(100e6, 200e6 - n_ch * df))
+        freqs = channel_centres(f_lo, df, n_ch)
+        uv_max = float(np.max(np.hypot(uvw[:, :, 0], uvw[:, :, 1]))) * freqs[-1] / C_LIGHT
+        cell = 1.0 / (2.2 * uv_max)
+        wl = Workload(f"batch{j}", uvw, freqs, bl, np.array([0, n_t], dtype=np.int32), n_st, L, N, cell, 0.0, 7.0,
+                      128, separable_taper(pswf_1d(L, 7.0)))
+        wl.flag_p = p_flag
+        jobs.append(wl)
+    return jobs
