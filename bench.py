@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny", "batched"])
+    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny", "batched", "serving"])
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (jobs/s)")
     ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched configuration")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
@@ -501,6 +502,51 @@ def run_batched(args, world, rank, local):
     print(json.dumps(rec))
 
 
+def run_serving(args, world, rank, local):
+    """Serving (SURVEY config S): a Poisson stream of requests drawn from the
+    batched distribution ("cycle": 5 major cycles of degrid -> residual -> grid,
+    "grid", "degrid"), served by the continuous-batching engine, and the same
+    trace served one job at a time by the plain per-job form."""
+    import torch
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg, serving
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    wls = syn.make_batched_jobs(args.jobs, seed=1913)
+    kinds = ("cycle", "grid", "degrid")
+    sampler = ClockSampler(local)
+    # warm up kernels, pools and graphs on a few jobs
+    serving.Engine(budget_bytes=150 << 30).run(serving.make_trace(
+        syn.make_batched_jobs(4, seed=7, scale_t=0.25), 1000.0, kinds, seed=7))
+    torch.cuda.synchronize()
+    sampler.start()
+    points = []
+    for rate in (args.rate, 4.0 * args.rate):
+        eng = serving.Engine(budget_bytes=150 << 30, max_slots=32, graph=False)
+        srv = eng.run(serving.make_trace(wls, rate, kinds))
+        fifo = serving.run_plain_fifo(serving.make_trace(wls, rate, kinds))
+        points.append({"rate_jobs_per_s": rate, "serving": srv, "plain_fifo": fifo,
+                       "engine": {"iterations": eng.iterations, "max_active_jobs": eng.max_active,
+                                  "host_batch_build_s": eng.host_batch_s}})
+    clocks = sampler.stop()
+    srv = points[0]["serving"]
+    rec = {
+        "metric": "grid+degrid MVis/s and latency (serving form vs plain per-job FIFO)",
+        "value": srv["grid_degrid_mvis_per_s"],
+        "unit": "MVis/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * srv["makespan_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Serving: Poisson arrivals, {args.jobs} requests from the batched "
+                               f"distribution, kinds {list(kinds)} (uniform), 5 major cycles per cycle job, "
+                               f"150 GB admission budget, 32 slots; rates {args.rate} and {4 * args.rate} jobs/s",
+                   "jobs": args.jobs},
+        "points": points, "clocks": clocks,
+    }
+    print(json.dumps(rec))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -509,6 +555,8 @@ def main():
             run_reference(args, world, rank)
         elif args.config == "batched":
             run_batched(args, world, rank, local)
+        elif args.config == "serving":
+            run_serving(args, world, rank, local)
         else:
             run_gb300(args, world, rank, local)
     finally:

@@ -86,7 +86,10 @@ typedef struct {
 enum { IDG_PHASOR_SINCOS = 0,      /* FP32 sin/cos of every phase                  */
        IDG_PHASOR_RECURRENCE = 1 };/* channel recurrence, re-anchored periodically  */
 enum { IDG_FFT_FP32 = 0 };
-enum { IDG_ADDER_ATOMIC = 0 };
+enum { IDG_ADDER_ATOMIC = 0,       /* 16-byte vector atomic adds                    */
+       IDG_ADDER_COMPENSATED = 1 };/* atomics + exact TwoSum error into a compensation
+                                      grid folded in at the end (O(eps) instead of
+                                      O(n eps) summation error; grid-sized scratch) */
 
 typedef struct {
     int64_t n_subgrids;       /* P, number of blocks                              */
@@ -167,7 +170,8 @@ void idg_plan_destroy(idg_plan *plan);
  *           from V = 0: zero it first), so several plans may sum into one grid.
  * Summation order on the grid is not fixed (atomic adds): results agree with
  * the FP64 definition to FP32 rounding, not bit for bit across runs.
- * Device scratch of at most 512 MiB is taken from the stream-ordered allocator.
+ * Device scratch of at most 512 MiB is taken from the stream-ordered allocator
+ * (plus one grid-sized compensation buffer with IDG_ADDER_COMPENSATED).
  */
 idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
                     const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);

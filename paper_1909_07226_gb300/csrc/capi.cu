@@ -269,7 +269,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     if (o.precision_mode != IDG_PHASOR_SINCOS && o.precision_mode != IDG_PHASOR_RECURRENCE)
         return fail(IDG_ERR_INVALID_ARG, "unknown precision_mode");
     if (o.fft_mode != IDG_FFT_FP32) return fail(IDG_ERR_INVALID_ARG, "unknown fft_mode");
-    if (o.adder_mode != IDG_ADDER_ATOMIC) return fail(IDG_ERR_INVALID_ARG, "unknown adder_mode");
+    if (o.adder_mode != IDG_ADDER_ATOMIC && o.adder_mode != IDG_ADDER_COMPENSATED)
+        return fail(IDG_ERR_INVALID_ARG, "unknown adder_mode");
     if (aterm_offsets[0] != 0 || aterm_offsets[n_slots] != n_t)
         return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must start at 0 and end at n_t");
     for (int a = 0; a < n_slots; ++a)
@@ -478,6 +479,16 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
     st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
     const Geometry g = p->geometry();
+    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
+    const size_t grid_f4 = (size_t)p->stats.n_w_layers * p->N * p->N * 2;
+    void *cbuf = nullptr;
+    if (comp) {
+        st = scratch_alloc(p->device, grid_f4 * 16, s, &cbuf);
+        if (st == IDG_OK) {
+            cudaError_t e0 = cudaMemsetAsync(cbuf, 0, grid_f4 * 16, s);
+            if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(compensation)");
+        }
+    }
     for (int64_t first = 0; first < n && st == IDG_OK; first += chunk) {
         const int64_t cnt = std::min(chunk, n - first);
         {
@@ -490,8 +501,13 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
-            st = launch_adder(g, order_set(p, first, cnt), scratch, grid, s);
+            st = comp ? launch_adder_compensated(g, order_set(p, first, cnt), scratch, grid, cbuf, s)
+                      : launch_adder(g, order_set(p, first, cnt), scratch, grid, s);
         }
+    }
+    if (comp && cbuf) {
+        if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
+        cudaFreeAsync(cbuf, s);
     }
     cudaError_t e = cudaFreeAsync(scratch, s);
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");

@@ -129,6 +129,9 @@ idg_status launch_degridder(const Geometry &g, const SubgridSet &set, int varian
 idg_status launch_fft(int L, int64_t count, int direction, void *subgrids, void *stream);
 idg_status launch_adder(const Geometry &g, const SubgridSet &set, const void *subgrids, void *grid, void *stream);
 idg_status launch_splitter(const Geometry &g, const SubgridSet &set, const void *grid, void *subgrids, void *stream);
+idg_status launch_adder_compensated(const Geometry &g, const SubgridSet &set, const void *subgrids, void *grid,
+                                    void *comp, void *stream);
+idg_status launch_fold_compensation(void *grid, const void *comp, size_t n_float4, void *stream);
 
 // channel-recurrence forms (precision_mode = IDG_PHASOR_RECURRENCE)
 idg_status launch_gridder_rec(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
