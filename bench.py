@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default="lofar", choices=["lofar", "lofar-slice", "tiny", "batched", "serving"])
+    ap.add_argument("--config", default="lofar",
+                    choices=["lofar", "lofar-slice", "tiny", "batched", "serving", "precision"])
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (jobs/s)")
     ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched configuration")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -547,6 +548,102 @@ def run_serving(args, world, rank, local):
     print(json.dumps(rec))
 
 
+def run_precision(args, world, rank, local):
+    """Precision forms (SURVEY config P): the LOFAR-like workload with A-terms
+    refreshed every 16 timesteps.  For every form: grid+degrid MVis/s on the
+    full workload, and the error against the FP64 oracle of the full grid and of
+    all visibilities on the first 256 timesteps (which the oracle redoes)."""
+    import torch
+    from oracle import oracle as O
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    O.build()
+    forms = {"direct_sincos": dict(precision_mode=idg.PHASOR_SINCOS),
+             "channel_recurrence": dict(precision_mode=idg.PHASOR_RECURRENCE),
+             "direct_sincos+compensated_adder": dict(precision_mode=idg.PHASOR_SINCOS,
+                                                     adder_mode=idg.ADDER_COMPENSATED),
+             "channel_recurrence+compensated_adder": dict(precision_mode=idg.PHASOR_RECURRENCE,
+                                                          adder_mode=idg.ADDER_COMPENSATED)}
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    # accuracy on the slice, against the oracle
+    sl = syn.make_lofar(with_vis=True, n_t=256, slot_len=16, name="precision")
+    op = O.plan(sl)
+    ref_grid = O.grid(sl, op)
+    model_h = syn.random_grid(np.random.default_rng(7), op.n_w, sl.grid_size)
+    ref_vis = O.degrid(sl, op, model_h)
+    d_vis = torch.from_numpy(sl.vis).to(dev)
+    d_at = torch.from_numpy(sl.aterms).to(dev)
+    d_tp = torch.from_numpy(sl.taper).to(dev)
+    d_model = torch.from_numpy(model_h).to(dev)
+    for name, kw in forms.items():
+        p = idg.plan_from_workload(sl, **kw)
+        g = torch.zeros(ref_grid.shape, dtype=torch.complex64, device=dev)
+        idg.grid(p, d_vis, None, d_at, d_tp, g, stream)
+        v = torch.zeros(sl.vis.shape, dtype=torch.complex64, device=dev)
+        idg.degrid(p, d_model, None, d_at, d_tp, v, stream)
+        gg = g.cpu().numpy().astype(np.complex128)
+        vv = v.cpu().numpy().astype(np.complex128)
+        out[name] = {"grid_rel_rms": float(np.linalg.norm(gg - ref_grid) / np.linalg.norm(ref_grid)),
+                     "grid_max_err_rel": float(np.max(np.abs(gg - ref_grid)) / np.max(np.abs(ref_grid))),
+                     "vis_rel_rms": float(np.linalg.norm(vv - ref_vis) / np.linalg.norm(ref_vis)),
+                     "vis_max_err_rel": float(np.max(np.abs(vv - ref_vis)) / np.max(np.abs(ref_vis)))}
+        p.destroy()
+    del d_vis, d_at, d_model
+    # throughput on the full workload
+    wl = syn.make_lofar(with_vis=True, slot_len=16, name="precision")
+    vis = torch.from_numpy(wl.vis).to(dev)
+    aterms = torch.from_numpy(wl.aterms).to(dev)
+    taper = torch.from_numpy(wl.taper).to(dev)
+    n_w = 1
+    model = torch.from_numpy(syn.random_grid(np.random.default_rng(7), n_w, wl.grid_size)).to(dev)
+    grid = torch.empty((n_w, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
+    vis_out = torch.empty_like(vis)
+    sampler = ClockSampler(local)
+    sampler.start()
+    n_sub = None
+    for name, kw in forms.items():
+        p = idg.plan_from_workload(wl, **kw)
+        n_sub = p.n_subgrids
+
+        def step():
+            grid.zero_()
+            idg.grid(p, vis, None, aterms, taper, grid, stream)
+            idg.degrid(p, model, None, aterms, taper, vis_out, stream)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name]["mvis_per_s"] = wl.n_vis / ms / 1e3
+        out[name]["ms_per_step"] = ms
+        p.destroy()
+    clocks = sampler.stop()
+    best = max(out.values(), key=lambda r: r["mvis_per_s"])
+    rec = {"metric": "grid+degrid MVis/s per precision form, with error vs the FP64 oracle",
+           "value": out["direct_sincos"]["mvis_per_s"], "unit": "MVis/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": out["direct_sincos"]["ms_per_step"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Precision: LOFAR-like with A-terms every 16 timesteps (256 slots); accuracy on "
+                                  "the first 256 timesteps against the FP64 oracle", "n_vis": int(wl.n_vis),
+                      "n_subgrids": n_sub},
+           "forms": out, "best_form_mvis_per_s": best["mvis_per_s"], "clocks": clocks}
+    print(json.dumps(rec))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -557,6 +654,8 @@ def main():
             run_batched(args, world, rank, local)
         elif args.config == "serving":
             run_serving(args, world, rank, local)
+        elif args.config == "precision":
+            run_precision(args, world, rank, local)
         else:
             run_gb300(args, world, rank, local)
     finally:
