@@ -348,6 +348,17 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
                         const float *d_taper, void *d_vis_scratch, int64_t max_subgrids, double *gridder_ms,
                         double *degridder_ms, int cap, idg_stream stream);
 
+/*
+ * Device error word.  The tensor-core gridder variant (L = 32, named
+ * "tcgen05_...") waits on shared-memory barriers for its matrix operations;
+ * every wait has an iteration limit, after which the kernel records an error
+ * in a device word, releases its tensor memory and leaves its subgrids
+ * unwritten.  idg_device_errors synchronises `stream`, reads and clears that
+ * word, and returns IDG_ERR_TIMEOUT if any wait gave up since the last call
+ * (IDG_OK otherwise).  The word is per device and per process.
+ */
+idg_status idg_device_errors(idg_stream stream);
+
 /* Text of a status code, and the last error message of the calling thread. */
 const char *idg_status_string(idg_status status);
 const char *idg_last_error(void);

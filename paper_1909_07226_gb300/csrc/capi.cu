@@ -175,6 +175,14 @@ const char *idg_status_string(idg_status s) {
 
 const char *idg_last_error(void) { return g_last_error.c_str(); }
 
+idg_status idg_device_errors(idg_stream stream) {
+    int code = 0;
+    idg_status st = read_device_errors(&code, stream);
+    if (st != IDG_OK) return st;
+    if (code) return fail(IDG_ERR_TIMEOUT, "a bounded wait of the tensor-core gridder gave up; its subgrids are invalid");
+    return IDG_OK;
+}
+
 void idg_profile_enable(int on) {
     std::lock_guard<std::mutex> lock(g_prof_mu);
     g_prof_on = on != 0;

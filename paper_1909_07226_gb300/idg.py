@@ -35,7 +35,7 @@ EXPORTED = [
     "idg_profile_enable", "idg_profile_read", "idg_grid_no_alloc",
     "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
     "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
-    "idg_batch_destroy",
+    "idg_batch_destroy", "idg_device_errors",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
         "idg_batch_degrid": (I32, [P, P]),
         "idg_batch_info": (I32, [P, P, P, P]),
         "idg_batch_destroy": (None, [P]),
+        "idg_device_errors": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +167,12 @@ def set_kernel_variant(kernel: str, L: int, variant: int):
 
 def get_kernel_variant(kernel: str, L: int) -> int:
     return int(load().idg_get_kernel_variant(KERNEL_ID[kernel], L))
+
+
+def device_errors(stream=None):
+    """idg_device_errors: synchronise the stream and raise IDGError if a bounded
+    device wait (tensor-core gridder) gave up since the last call."""
+    _check(load().idg_device_errors(_stream(stream)), "idg_device_errors")
 
 
 def autotune(plan, vis, flags, aterms, taper, vis_scratch=None, max_subgrids: int = 4096, stream=None) -> dict:

@@ -52,6 +52,7 @@ def test_gridder_stage(L):
         idg.set_kernel_variant("gridder", L, v)
         sub = torch_zeros((n, L, L, 4))
         idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
+        idg.device_errors()
         parity(sub.cpu().numpy(), ref, f"gridder L={L} {name}")
     idg.set_kernel_variant("gridder", L, 0)
 
