@@ -97,6 +97,12 @@ def sum_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
+def whole_job_rate(world, seconds_local: float, units_local: float) -> float:
+    """Units per second of the whole job: the units all ranks processed over the
+    slowest rank's time (each rank times the same bracketed region)."""
+    return sum_over_ranks(world, units_local) / max_over_ranks(world, seconds_local)
+
+
 def make_workload(name):
     from paper_1909_07226_gb300 import synthetic as syn
     if name == "tiny":
@@ -327,11 +333,10 @@ def run_gb300(args, world, rank, local):
     clocks = sampler.stop()
     idg.profile_enable(False)
     prof = idg.profile_read(reset=True)
-    ms_total = ev0.elapsed_time(ev1)
-    ms_total = max_over_ranks(world, ms_total)
+    ms_local = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(world, ms_local)
     ms_step = ms_total / args.steps
-    total_vis = sum_over_ranks(world, float(wl.n_vis) * args.steps)
-    value = total_vis / (ms_total * 1e-3) / 1e6
+    value = whole_job_rate(world, ms_local * 1e-3, float(wl.n_vis) * args.steps) / 1e6
 
     # kernels: achieved against their rooflines
     props = torch.cuda.get_device_properties(local)
@@ -387,8 +392,7 @@ def run_gb300(args, world, rank, local):
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e_value = sum_over_ranks(world, float(wl.n_vis) * args.e2e_steps) / e2e_s / 1e6
+    e2e_value = whole_job_rate(world, time.perf_counter() - t0, float(wl.n_vis) * args.e2e_steps) / 1e6
     nvis = wl.n_vis
     fl = 0 if wl.flags is None else wl.flags.nbytes
     # grid_host: visibilities, flags, A-terms, taper in, grid out;
