@@ -572,7 +572,9 @@ def run_precision(args, world, rank, local):
              "direct_sincos+compensated_adder": dict(precision_mode=idg.PHASOR_SINCOS,
                                                      adder_mode=idg.ADDER_COMPENSATED),
              "channel_recurrence+compensated_adder": dict(precision_mode=idg.PHASOR_RECURRENCE,
-                                                          adder_mode=idg.ADDER_COMPENSATED)}
+                                                          adder_mode=idg.ADDER_COMPENSATED),
+             "direct_sincos+tc_split_transform": dict(precision_mode=idg.PHASOR_SINCOS,
+                                                      fft_mode=idg.FFT_TC_SPLIT)}
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     out = {}

@@ -85,7 +85,11 @@ typedef struct {
 
 enum { IDG_PHASOR_SINCOS = 0,      /* FP32 sin/cos of every phase                  */
        IDG_PHASOR_RECURRENCE = 1 };/* channel recurrence, re-anchored periodically  */
-enum { IDG_FFT_FP32 = 0 };
+enum { IDG_FFT_FP32 = 0,           /* FP32 FFT in shared memory                     */
+       IDG_FFT_TC_SPLIT = 1 };     /* centred DFT as two matrix products on the tensor
+                                      cores, FP16 hi/lo split operands (three products
+                                      per stage), FP32 accumulation; subgrid size 32
+                                      only (IDG_ERR_UNSUPPORTED otherwise)          */
 enum { IDG_ADDER_ATOMIC = 0,       /* 16-byte vector atomic adds                    */
        IDG_ADDER_COMPENSATED = 1 };/* atomics + exact TwoSum error into a compensation
                                       grid folded in at the end (O(eps) instead of

@@ -467,6 +467,8 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         if (p->device != dev) return fail(IDG_ERR_INVALID_ARG, "plan " + std::to_string(j) + " is not on the current device");
         if (p->opts.precision_mode != IDG_PHASOR_SINCOS)
             return fail(IDG_ERR_UNSUPPORTED, "batches run the direct (sin/cos) phasor form only");
+        if (p->opts.fft_mode != IDG_FFT_FP32)
+            return fail(IDG_ERR_UNSUPPORTED, "batches run the FP32 subgrid transform only");
         KernelShape a, c;
         if (!shapes_for(p->L, &a, &c))
             return fail(IDG_ERR_UNSUPPORTED, "batches support subgrid sizes 8, 16, 24 and 32 (job " + std::to_string(j) + ")");

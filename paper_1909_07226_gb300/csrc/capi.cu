@@ -31,6 +31,11 @@ idg_status cuda_fail(int err, const char *what) {
     return err == cudaErrorMemoryAllocation ? IDG_ERR_NO_MEMORY : IDG_ERR_CUDA;
 }
 
+idg_status launch_subgrid_fft(const idg_plan *p, int64_t count, int direction, void *subgrids, void *stream) {
+    if (p->opts.fft_mode == IDG_FFT_TC_SPLIT) return launch_dft_tc(p->L, count, direction, subgrids, stream);
+    return launch_fft(p->L, count, direction, subgrids, stream);
+}
+
 // One stream-ordered memory pool per device for the subgrid scratch, kept
 // alive (release threshold = max) so repeated calls do not return memory to
 // the driver between steps.
@@ -276,7 +281,10 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     if (o.max_timesteps_per_subgrid < 1) return fail(IDG_ERR_INVALID_ARG, "max_timesteps_per_subgrid must be >= 1");
     if (o.precision_mode != IDG_PHASOR_SINCOS && o.precision_mode != IDG_PHASOR_RECURRENCE)
         return fail(IDG_ERR_INVALID_ARG, "unknown precision_mode");
-    if (o.fft_mode != IDG_FFT_FP32) return fail(IDG_ERR_INVALID_ARG, "unknown fft_mode");
+    if (o.fft_mode != IDG_FFT_FP32 && o.fft_mode != IDG_FFT_TC_SPLIT)
+        return fail(IDG_ERR_INVALID_ARG, "unknown fft_mode");
+    if (o.fft_mode == IDG_FFT_TC_SPLIT && !dft_tc_supported(L))
+        return fail(IDG_ERR_UNSUPPORTED, "the tensor-core subgrid transform is built for subgrid size 32");
     if (o.adder_mode != IDG_ADDER_ATOMIC && o.adder_mode != IDG_ADDER_COMPENSATED)
         return fail(IDG_ERR_INVALID_ARG, "unknown adder_mode");
     if (aterm_offsets[0] != 0 || aterm_offsets[n_slots] != n_t)
@@ -505,7 +513,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
-            st = launch_fft(p->L, cnt, -1, scratch, s);
+            st = launch_subgrid_fft(p, cnt, -1, scratch, s);
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
@@ -547,7 +555,7 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
-            st = launch_fft(p->L, cnt, +1, scratch, s);
+            st = launch_subgrid_fft(p, cnt, +1, scratch, s);
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, cnt, true));
@@ -654,7 +662,7 @@ idg_status idg_fft_subgrids(const idg_plan *p, int64_t count, int direction, voi
     if (count < 0) return fail(IDG_ERR_INVALID_ARG, "count < 0");
     if (count == 0) return IDG_OK;
     ProfileScope ps(IDG_KERNEL_FFT, stream, (double)count);
-    return launch_fft(p->L, count, direction, sub, (cudaStream_t)stream);
+    return launch_subgrid_fft(p, count, direction, sub, stream);
 }
 
 idg_status idg_add_subgrids(const idg_plan *p, int64_t first, int64_t count, const void *sub, void *grid,

@@ -374,10 +374,13 @@ idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const voi
 idg_status read_device_errors(int *code, void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    int zero = 0;
-    e = cudaMemcpyFromSymbol(code, g_tc_error, sizeof(int));
+    int zero = 0, mine = 0, dft = 0;
+    e = cudaMemcpyFromSymbol(&mine, g_tc_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    const idg_status st = read_dft_error(&dft);
+    if (st != IDG_OK) return st;
+    *code = mine | dft;
     return IDG_OK;
 }
 

@@ -146,6 +146,13 @@ idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const voi
                              const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);
 
+// tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
+bool dft_tc_supported(int L);
+idg_status launch_dft_tc(int L, int64_t count, int direction, void *subgrids, void *stream);
+idg_status read_dft_error(int *code);
+// the plan's transform (FP32 shared-memory FFT or the tensor-core form)
+idg_status launch_subgrid_fft(const idg_plan *p, int64_t count, int direction, void *subgrids, void *stream);
+
 // fused batch kernel shapes (batch.cu)
 int batch_variant_count(int kernel, int L);
 const char *batch_variant_name(int kernel, int L, int v);

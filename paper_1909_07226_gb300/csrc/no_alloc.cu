@@ -84,7 +84,7 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
     const Geometry g = p->geometry();
     const SubgridSet all{p->d_order, 0, n, p->kp_order.data()};
     st = launch_gridder(g, all, -1, vis, flags, aterms, taper, scratch, s);
-    if (st == IDG_OK) st = launch_fft(p->L, n, -1, scratch, s);
+    if (st == IDG_OK) st = launch_subgrid_fft(p, n, -1, scratch, s);
     if (st == IDG_OK) st = launch_adder(g, all, scratch, grid, s);
     return st;
 }

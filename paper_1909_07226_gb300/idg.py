@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_NO_MEMORY", 3
                 4: "IDG_ERR_TIMEOUT", 5: "IDG_ERR_DEVICE_CHECK", 6: "IDG_ERR_UNSUPPORTED"}
 DESC_FIELDS = 10
 PHASOR_SINCOS, PHASOR_RECURRENCE = 0, 1
-FFT_FP32 = 0
+FFT_FP32, FFT_TC_SPLIT = 0, 1
 ADDER_ATOMIC, ADDER_COMPENSATED = 0, 1
 
 # Every symbol the header declares (checked by the CPU test-suite).

@@ -141,3 +141,15 @@ def test_recurrence_needs_uniform_channels(lib):
     assert "uniformly spaced" in str(ei.value)
     _create(freqs_hz=f)                                   # the direct form accepts any channels
     _create(precision_mode=idg.PHASOR_RECURRENCE)         # uniform channels are accepted
+
+
+def test_tensor_core_transform_only_for_subgrid_size_32(lib):
+    with pytest.raises(idg.IDGError) as ei:
+        _create(fft_mode=idg.FFT_TC_SPLIT)                 # L = 16
+    assert ei.value.status == 6 and "subgrid size 32" in str(ei.value)
+    with pytest.raises(idg.IDGError) as ei:
+        _create(fft_mode=5)
+    assert ei.value.status == 1 and "fft_mode" in str(ei.value)
+    wl = syn.make_small(seed=1, n_st=4, n_t=8, n_chan=2, L=32, N=128, with_vis=False, aterms="identity")
+    p = idg.plan_from_workload(wl, fft_mode=idg.FFT_TC_SPLIT)
+    assert p.stats.subgrid_size == 32

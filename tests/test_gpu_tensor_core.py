@@ -136,3 +136,82 @@ def test_tc_gridder_lofar_slice_sampled(tc_selected):
     ids = np.linspace(0, n - 1, 96).round().astype(np.int32)
     parity(sub[torch.from_numpy(ids).long().cuda()].cpu().numpy(), O.subgrid_images(wl, op, ids=ids),
            "tc gridder LOFAR slice, sampled")
+
+
+# ---------------------------------------------------------------------------
+# subgrid transform on the tensor cores (fft_mode = FFT_TC_SPLIT)
+
+def _tc_plan(wl):
+    return idg.plan_from_workload(wl, fft_mode=idg.FFT_TC_SPLIT)
+
+
+@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("case", ["gaussian", "huge", "tiny", "mixed_rows", "zero_and_delta"])
+def test_tc_transform_stage(direction, case):
+    wl = small32(n_t=8, max_t=8)
+    p = _tc_plan(wl)
+    rng = np.random.default_rng(500 + direction)
+    n = 41
+    x = (rng.normal(size=(n, 32, 32, 4)) + 1j * rng.normal(size=(n, 32, 32, 4)))
+    if case == "huge":
+        x *= 1e12
+    elif case == "tiny":
+        x *= 1e-12
+    elif case == "mixed_rows":
+        x *= 10.0 ** rng.uniform(-6, 6, size=(n, 32, 1, 1))     # dynamic range inside a subgrid
+    elif case == "zero_and_delta":
+        x[0] = 0.0
+        x[1] = 0.0
+        x[1, 3, 29, 2] = 5.0 - 2.0j
+    x = x.astype(np.complex64)
+    t = dev(x)
+    idg.fft_subgrids(p, n, direction, t)
+    idg.device_errors()
+    out = t.cpu().numpy()
+    ref = O.dft2(x, direction)
+    if case == "zero_and_delta":
+        assert not np.any(out[0])
+    parity(out, ref, f"tc transform {case} dir={direction}")
+
+
+def test_tc_transform_inverse_pair():
+    # forward then backward returns the input scaled by L^-2 (both carry 1/L^2)
+    wl = small32(n_t=8, max_t=8)
+    p = _tc_plan(wl)
+    rng = np.random.default_rng(9)
+    x = (rng.normal(size=(16, 32, 32, 4)) + 1j * rng.normal(size=(16, 32, 32, 4))).astype(np.complex64)
+    t = dev(x)
+    idg.fft_subgrids(p, 16, -1, t)
+    idg.fft_subgrids(p, 16, 1, t)
+    idg.device_errors()
+    parity(t.cpu().numpy() * 1024.0, x, "tc transform round trip")
+
+
+@pytest.mark.parametrize("case", ["points_flags_aterms", "w_layers", "long_kp"])
+def test_tc_transform_in_grid_and_degrid(case):
+    import torch
+    wl = CASES[case]()
+    p = _tc_plan(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+    idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+    idg.device_errors()
+    parity(g.cpu().numpy(), O.grid(wl, op), f"grid with tc transform, {case}")
+    rng = np.random.default_rng(3)
+    g_in = syn.random_grid(rng, p.n_w_layers, wl.grid_size)
+    v = torch.zeros(wl.vis.shape, dtype=torch.complex64, device="cuda")
+    idg.degrid(p, dev(g_in), d["flags"], d["aterms"], d["taper"], v)
+    idg.device_errors()
+    parity(v.cpu().numpy(), O.degrid(wl, op, g_in), f"degrid with tc transform, {case}")
+
+
+def test_tc_transform_rejected_by_batches():
+    wl = small32(n_t=8, max_t=8)
+    p = _tc_plan(wl)
+    d = workload_to_device(wl)
+    import torch
+    g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+    with pytest.raises(idg.IDGError):
+        idg.Batch([p], [dict(vis=d["vis"], vis_out=None, flags=d["flags"], aterms=d["aterms"], taper=d["taper"],
+                             grid=g)])
