@@ -335,12 +335,12 @@ idg_status launch_dft_tc(int L, int64_t count, int direction, void *data, void *
     auto kern = direction < 0 ? dft_tc_kernel<-1> : dft_tc_kernel<1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform smem attribute");
-    int dev = 0, n_sm = 0, per_sm = 0;
+    int dev = 0, n_sm = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DNT, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform occupancy");
-    const int64_t grid = std::min<int64_t>(count, (int64_t)std::max(1, per_sm) * n_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform device query");
+    // two CTAs per SM (81 KB of shared memory and 64 tensor-memory columns each)
+    const int64_t grid = std::min<int64_t>(count, 2 * (int64_t)std::max(1, n_sm));
     kern<<<(unsigned)grid, DNT, smem, s>>>((float4 *)data, count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core transform launch");
