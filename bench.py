@@ -37,6 +37,12 @@ sys.path.insert(0, ROOT)
 # cycle, so the peak is SMs x 128 x f_max / 18 visibility-pixels per second.
 FMA_PER_VISPIX = 18
 LANES_PER_SM = 128
+# DRAM bytes (read + write) of one gridder launch per visibility-pixel, from the
+# ncu capture of the default L=32 gridder on the LOFAR-like slice
+# (profiles/gridder_degridder_f32x2_lofar_slice.md: 159.1 + 54.4 MB for 4.73e9
+# visibility-pixels).  The traffic is the visibilities and the subgrid writes,
+# proportional to the work, so it scales to a full launch by the units it processes.
+GRIDDER_TRAFFIC = {"variant": "f32x2_npx4_vb128_minb2", "bytes_per_vispix": (159.1e6 + 54.4e6) / 4.73e9}
 
 
 def parse():
@@ -364,8 +370,15 @@ def run_gb300(args, world, rank, local):
             ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
         kernels[k] = ent
     dom = max(("gridder", "degridder"), key=lambda k: prof[k]["ms"])
+    traffic = None
+    L = wl.subgrid_size
+    if dom == "gridder" and idg.kernel_variants("gridder", L)[idg.get_kernel_variant("gridder", L)] == \
+            GRIDDER_TRAFFIC["variant"]:
+        traffic = GRIDDER_TRAFFIC["bytes_per_vispix"] * prof["gridder"]["work"] / prof["gridder"]["launches"]
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["achieved"], "peak": alu_peak,
-            "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": None,
+            "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": traffic,
+            "traffic_basis": "ncu dram bytes per visibility-pixel of the slice capture x visibility-pixels per launch"
+            if traffic is not None else None,
             "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} FP32 FMA lanes x {f_max_mhz:.0f} MHz / {FMA_PER_VISPIX} FMA "
                           f"per visibility-pixel", "hbm_peak_basis": hbm_src}
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
