@@ -144,6 +144,8 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
 // tensor memory) and the device error word of its bounded waits
 idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                              const void *aterms, const float *taper, void *subgrids, void *stream);
+idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                              const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)

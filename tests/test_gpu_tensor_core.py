@@ -19,7 +19,7 @@ from tests.gpu_util import dev, parity, workload_to_device
 
 pytestmark = pytest.mark.gpu
 
-TC = "tcgen05_fp16x3_nt256"
+TC_VARIANTS = ["tcgen05_fp16x3_nt256", "tcgen05_tmemA_ws_nt288"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,12 +29,12 @@ def built():
     idg.load()
 
 
-@pytest.fixture
-def tc_selected():
+@pytest.fixture(params=TC_VARIANTS)
+def tc_selected(request):
     names = idg.kernel_variants("gridder", 32)
-    assert TC in names
-    idg.set_kernel_variant("gridder", 32, names.index(TC))
-    yield
+    assert request.param in names
+    idg.set_kernel_variant("gridder", 32, names.index(request.param))
+    yield request.param
     idg.set_kernel_variant("gridder", 32, 0)
 
 
@@ -85,7 +85,7 @@ def test_tc_gridder_stage(case, tc_selected):
     sub = torch.zeros((n, 32, 32, 4), dtype=torch.complex64, device="cuda")
     idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
     idg.device_errors()
-    parity(sub.cpu().numpy(), O.subgrid_images(wl, op), f"tc gridder {case}")
+    parity(sub.cpu().numpy(), O.subgrid_images(wl, op), f"{tc_selected} {case}")
 
 
 def test_tc_gridder_kp_spans_batches(tc_selected):
@@ -118,7 +118,7 @@ def test_tc_full_grid(tc_selected):
     g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
     idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
     idg.device_errors()
-    parity(g.cpu().numpy(), O.grid(wl, op), "tc grid")
+    parity(g.cpu().numpy(), O.grid(wl, op), f"{tc_selected} grid")
 
 
 def test_tc_gridder_lofar_slice_sampled(tc_selected):
@@ -135,7 +135,7 @@ def test_tc_gridder_lofar_slice_sampled(tc_selected):
     idg.device_errors()
     ids = np.linspace(0, n - 1, 96).round().astype(np.int32)
     parity(sub[torch.from_numpy(ids).long().cuda()].cpu().numpy(), O.subgrid_images(wl, op, ids=ids),
-           "tc gridder LOFAR slice, sampled")
+           f"{tc_selected} LOFAR slice, sampled")
 
 
 # ---------------------------------------------------------------------------
