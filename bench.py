@@ -37,12 +37,17 @@ sys.path.insert(0, ROOT)
 # cycle, so the peak is SMs x 128 x f_max / 18 visibility-pixels per second.
 FMA_PER_VISPIX = 18
 LANES_PER_SM = 128
-# DRAM bytes (read + write) of one gridder launch per visibility-pixel, from the
-# ncu capture of the default L=32 gridder on the LOFAR-like slice
+# DRAM bytes (read + write) per visibility-pixel of one launch, from the ncu
+# captures of the packed-FP32 L=32 kernels on the LOFAR-like slice
 # (profiles/gridder_degridder_f32x2_lofar_slice.md: 159.1 + 54.4 MB for 4.73e9
 # visibility-pixels).  The traffic is the visibilities and the subgrid writes,
 # proportional to the work, so it scales to a full launch by the units it processes.
-GRIDDER_TRAFFIC = {"variant": "f32x2_npx4_vb128_minb2", "bytes_per_vispix": (159.1e6 + 54.4e6) / 4.73e9}
+# The same for the default L=32 degridder: its pixel-group-1 launch on the slice moved
+# 115.7 + 99.7 MB for ~4.728e9 visibility-pixels (all but 18 small subgrids of the slice).
+KERNEL_TRAFFIC = {
+    "gridder": {"variant": "f32x2_npx4_vb128_minb2", "bytes_per_vispix": (159.1e6 + 54.4e6) / 4.73e9},
+    "degridder": {"variant": "f32x2_nv4_nt128_minb3_pg_static", "bytes_per_vispix": (115.7e6 + 99.7e6) / 4.728e9},
+}
 
 
 def parse():
@@ -364,7 +369,8 @@ def run_gb300(args, world, rank, local):
                "share": d["ms"] / ms_total if ms_total > 0 else None}
         if k in ("gridder", "degridder"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
-            ent.update(bound="alu", achieved=ach, peak=alu_peak, unit="Gvispix/s", frac=ach / alu_peak)
+            ent.update(bound="alu", achieved=ach, peak=alu_peak, unit="Gvispix/s", frac=ach / alu_peak,
+                       variant=idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)])
         elif k in ("adder", "splitter"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
             ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
@@ -372,9 +378,9 @@ def run_gb300(args, world, rank, local):
     dom = max(("gridder", "degridder"), key=lambda k: prof[k]["ms"])
     traffic = None
     L = wl.subgrid_size
-    if dom == "gridder" and idg.kernel_variants("gridder", L)[idg.get_kernel_variant("gridder", L)] == \
-            GRIDDER_TRAFFIC["variant"]:
-        traffic = GRIDDER_TRAFFIC["bytes_per_vispix"] * prof["gridder"]["work"] / prof["gridder"]["launches"]
+    tr = KERNEL_TRAFFIC.get(dom)
+    if tr and L == 32 and idg.kernel_variants(dom, L)[idg.get_kernel_variant(dom, L)] == tr["variant"]:
+        traffic = tr["bytes_per_vispix"] * prof[dom]["work"] / prof[dom]["launches"]
     roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["achieved"], "peak": alu_peak,
             "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": traffic,
             "traffic_basis": "ncu dram bytes per visibility-pixel of the slice capture x visibility-pixels per launch"

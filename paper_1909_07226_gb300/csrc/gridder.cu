@@ -239,10 +239,11 @@ const Variant kV16[] = {GF(16, 2, 128, 3), GV(16, 2, 128, 3, false), GV(16, 2, 2
                         GV(16, 4, 256, 6, true), GF(16, 4, 128, 2)};
 const Variant kV24[] = {GF(24, 3, 128, 3), GV(24, 3, 128, 3, false), GV(24, 3, 256, 3, true),
                         GV(24, 6, 256, 6, true), GF(24, 6, 128, 2)};
-const Variant kV32[] = {GF(32, 4, 128, 2),        GV(32, 4, 128, 3, false), GV(32, 4, 256, 3, true),
+const Variant kV32[] = {{"tcgen05_tmemA_ws_nt288", launch_tcw}, GF(32, 4, 128, 2), GV(32, 4, 128, 3, false),
+                        GV(32, 4, 256, 3, true),
                         GV(32, 4, 256, 4, true),  GV(32, 8, 256, 4, true),  GV(32, 2, 256, 2, true),
                         GF(32, 4, 128, 3),        GF(32, 2, 128, 3),        GF(32, 8, 128, 4),
-                        {"tcgen05_fp16x3_nt256", launch_tc}, {"tcgen05_tmemA_ws_nt288", launch_tcw}};
+                        {"tcgen05_fp16x3_nt256", launch_tc}};
 const Variant kV48[] = {GF(48, 4, 128, 1), GV(48, 6, 128, 2, false), GV(48, 6, 256, 2, true),
                         GV(48, 4, 256, 1, true), GF(48, 6, 128, 1)};
 const Variant kV64[] = {GF(64, 4, 128, 1), GV(64, 8, 128, 1, false), GV(64, 8, 256, 1, true),

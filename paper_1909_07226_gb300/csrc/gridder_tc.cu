@@ -111,6 +111,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ uint32_t pack_h2(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
 
+// FP16 hi/lo parts of (cs, sn): hi = fp16(E) rounded, lo = fp16(E - hi) with E - hi
+// formed exactly by one mixed-precision fma per component (FP16 hi times -1 plus
+// FP32 E), with no conversion of hi back to FP32.  Low halves hold cs.
+__device__ __forceinline__ void split_e(float cs, float sn, uint32_t &hi, uint32_t &lo) {
+    asm("{\n"
+        " .reg .b16 hc, hs, m1;\n"
+        " .reg .f32 lc, ls;\n"
+        " mov.b16 m1, 0xBC00;\n"
+        " cvt.rn.f16x2.f32 %0, %3, %2;\n"
+        " mov.b32 {hc, hs}, %0;\n"
+        " fma.rn.f32.f16 lc, hc, m1, %2;\n"
+        " fma.rn.f32.f16 ls, hs, m1, %3;\n"
+        " cvt.rn.f16x2.f32 %1, ls, lc;\n"
+        "}" : "=r"(hi), "=r"(lo) : "f"(cs), "f"(sn));
+}
+
 __global__ void __launch_bounds__(TC_NT, 2)
 gridder_tc_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                   const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
@@ -371,7 +387,7 @@ gridder_tc_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, co
 
 constexpr int WS_NP = 256;                       // producer threads
 constexpr int WS_NT = WS_NP + 32;                // + the MMA warp
-constexpr int WS_VB = 64;                        // visibilities per staged batch
+constexpr int WS_VB = 128;                       // visibilities per staged batch
 constexpr int WS_GROUPS = WS_VB / 8;
 constexpr int WS_FOLD = 16;                      // groups between folds (two accumulations per group)
 constexpr int WS_COLS = 256;
@@ -500,14 +516,14 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
         const float scale = ldexpf(1.0f, 10 - e2);
         const float inv_scale = ldexpf(1.0f, e2 - 10);
         // pixel s = 2 h + i of this thread: tile 4 h + ltw + 2 i, row 32 q4 + lane
-        float X[4], Yv[4], NP[4];
+        float Yv[4], NP[4];
         int PIX[4];
+        const float Xc = (float)(lane - TC_L / 2);   // pixel 128 mt + 32 q4 + lane lies in column lane
 #pragma unroll
         for (int s4 = 0; s4 < 4; ++s4) {
             const int mt = 4 * (s4 >> 1) + ltw + 2 * (s4 & 1);
             const int pix = 128 * mt + 32 * q4 + lane;
             PIX[s4] = pix;
-            X[s4] = (float)((pix & (TC_L - 1)) - TC_L / 2);
             Yv[s4] = (float)((pix >> 5) - TC_L / 2);
             NP[s4] = g.nprime[pix];
         }
@@ -557,11 +573,12 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
             const int ng = min(WS_GROUPS, total_groups - bt * WS_GROUPS);
             for (int gi = 0; gi < ng; ++gi) {
                 const int gc = bt * WS_GROUPS + gi;
-                float ca[8], cb[8], cc[8];
+                // the thread's four pixels share the column x = lane, so a X is formed once per visibility
+                float aX[8], cb[8], cc[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float4 cf = coef[gi * 8 + j];
-                    ca[j] = cf.x;
+                    aX[j] = cf.x * Xc;
                     cb[j] = cf.y;
                     cc[j] = cf.z;
                 }
@@ -574,13 +591,10 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
                         uint32_t e[16];      // 8 hi (k = 2j, 2j + 1 = cos, sin of visibility j), then 8 lo
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            const float phase = fmaf(ca[j], X[s4], fmaf(cc[j], NP[s4], cb[j] * Yv[s4]));
+                            const float phase = fmaf(cb[j], Yv[s4], fmaf(cc[j], NP[s4], aX[j]));
                             float sn, cs;
                             __sincosf(phase, &sn, &cs);
-                            const __half2 eh = __floats2half2_rn(cs, sn);
-                            const float2 ef = __half22float2(eh);
-                            e[j] = pack_h2(eh);
-                            e[8 + j] = pack_h2(__floats2half2_rn(cs - ef.x, sn - ef.y));
+                            split_e(cs, sn, e[j], e[8 + j]);
                         }
                         tmem_st16(lane_base + (uint32_t)(128 + 64 * h + 16 * (ltw + 2 * i)), e);
                     }
