@@ -37,6 +37,12 @@ sys.path.insert(0, ROOT)
 # cycle, so the peak is SMs x 128 x f_max / 18 visibility-pixels per second.
 FMA_PER_VISPIX = 18
 LANES_PER_SM = 128
+# Tensor-core forms: the complex multiply-adds run on the tensor cores and the
+# CUDA cores generate the phasors.  Per visibility-pixel that takes at least 9
+# issue slots: 2 FFMA for the phase, 1 FMUL for the sin/cos argument, 2 SFU
+# (sin, cos) and 4 for the FP16 hi/lo split (2 packs, 2 mixed-precision fma).
+# An SM issues 4 x 32 thread-instructions per clock.
+ISSUE_PER_VISPIX_TC = 9
 # DRAM bytes (read + write) per visibility-pixel of one launch, from the ncu
 # captures of the packed-FP32 L=32 kernels on the LOFAR-like slice
 # (profiles/gridder_degridder_f32x2_lofar_slice.md: 159.1 + 54.4 MB for 4.73e9
@@ -44,9 +50,13 @@ LANES_PER_SM = 128
 # proportional to the work, so it scales to a full launch by the units it processes.
 # The same for the default L=32 degridder: its pixel-group-1 launch on the slice moved
 # 115.7 + 99.7 MB for ~4.728e9 visibility-pixels (all but 18 small subgrids of the slice).
+# The tensor-core kernels on the same slice (one launch of all 3206 subgrids, 4.73e9 visibility-pixels):
+# gridder 159.2 + 56.0 MB, degridder 118.0 + 110.1 MB (profiles/*_tcw_lofar_slice.md).
 KERNEL_TRAFFIC = {
-    "gridder": {"variant": "f32x2_npx4_vb128_minb2", "bytes_per_vispix": (159.1e6 + 54.4e6) / 4.73e9},
-    "degridder": {"variant": "f32x2_nv4_nt128_minb3_pg_static", "bytes_per_vispix": (115.7e6 + 99.7e6) / 4.728e9},
+    "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
+                "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9},
+    "degridder": {"f32x2_nv4_nt128_minb3_pg_static": (115.7e6 + 99.7e6) / 4.728e9,
+                  "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9},
 }
 
 
@@ -361,6 +371,11 @@ def run_gb300(args, world, rank, local):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     alu_peak = n_sm * LANES_PER_SM * f_max_mhz * 1e6 / FMA_PER_VISPIX / 1e9       # G vis-pix / s
+    tc_peak = n_sm * LANES_PER_SM * f_max_mhz * 1e6 / ISSUE_PER_VISPIX_TC / 1e9
+    fma_basis = (f"{n_sm} SMs x {LANES_PER_SM} FP32 FMA lanes x {f_max_mhz:.0f} MHz / {FMA_PER_VISPIX} FMA "
+                 f"per visibility-pixel")
+    tc_basis = (f"{n_sm} SMs x {LANES_PER_SM} issue slots x {f_max_mhz:.0f} MHz / {ISSUE_PER_VISPIX_TC} "
+                f"phasor-generation instructions per visibility-pixel (multiply-adds on the tensor cores)")
     kernels = {}
     for k, d in prof.items():
         if d["launches"] == 0:
@@ -369,8 +384,11 @@ def run_gb300(args, world, rank, local):
                "share": d["ms"] / ms_total if ms_total > 0 else None}
         if k in ("gridder", "degridder"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
-            ent.update(bound="alu", achieved=ach, peak=alu_peak, unit="Gvispix/s", frac=ach / alu_peak,
-                       variant=idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)])
+            var = idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)]
+            tc = var.startswith("tcgen05")
+            pk = tc_peak if tc else alu_peak
+            ent.update(bound="alu", achieved=ach, peak=pk, unit="Gvispix/s", frac=ach / pk, variant=var,
+                       peak_basis=tc_basis if tc else fma_basis, frac_of_fp32_fma_peak=ach / alu_peak)
         elif k in ("adder", "splitter"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
             ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
@@ -378,15 +396,16 @@ def run_gb300(args, world, rank, local):
     dom = max(("gridder", "degridder"), key=lambda k: prof[k]["ms"])
     traffic = None
     L = wl.subgrid_size
-    tr = KERNEL_TRAFFIC.get(dom)
-    if tr and L == 32 and idg.kernel_variants(dom, L)[idg.get_kernel_variant(dom, L)] == tr["variant"]:
-        traffic = tr["bytes_per_vispix"] * prof[dom]["work"] / prof[dom]["launches"]
-    roof = {"kernel": dom, "bound": "alu", "achieved": kernels[dom]["achieved"], "peak": alu_peak,
+    per_vispix = KERNEL_TRAFFIC.get(dom, {}).get(kernels[dom]["variant"]) if L == 32 else None
+    if per_vispix is not None:
+        traffic = per_vispix * prof[dom]["work"] / prof[dom]["launches"]
+    roof = {"kernel": dom, "variant": kernels[dom]["variant"], "bound": "alu",
+            "achieved": kernels[dom]["achieved"], "peak": kernels[dom]["peak"],
             "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": traffic,
             "traffic_basis": "ncu dram bytes per visibility-pixel of the slice capture x visibility-pixels per launch"
             if traffic is not None else None,
-            "peak_basis": f"{n_sm} SMs x {LANES_PER_SM} FP32 FMA lanes x {f_max_mhz:.0f} MHz / {FMA_PER_VISPIX} FMA "
-                          f"per visibility-pixel", "hbm_peak_basis": hbm_src}
+            "peak_basis": kernels[dom]["peak_basis"], "frac_of_fp32_fma_peak": kernels[dom]["frac_of_fp32_fma_peak"],
+            "hbm_peak_basis": hbm_src}
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 
     # end to end through the host-buffer C-ABI calls

@@ -12,7 +12,14 @@ using namespace dev;
 
 #define DV_RTM(L, NV, NT, MINB) {"nv" #NV "_nt" #NT "_minb" #MINB "_pg_runtime", degrid_launch_kernel<L, NV, 0, NT, MINB>}
 #define DV_F2(L, NV, NT, MINB) {"f32x2_nv" #NV "_nt" #NT "_minb" #MINB "_pg_static", degrid_f2_launch_static<L, NV, NT, MINB>}
-const DegridVariant kD32[] = {DV_F2(32, 4, 128, 3),      DV_RT(32, 4, 256),    DV_ST(32, 4, 256, 3),
+
+idg_status launch_tcw(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
+                      const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
+    return launch_degridder_tcw(g, set, sub, flags, aterms, taper, vis_out, (void *)s);
+}
+
+const DegridVariant kD32[] = {{"tcgen05_tmemA_ws_nt288", launch_tcw}, DV_F2(32, 4, 128, 3), DV_RT(32, 4, 256),
+                              DV_ST(32, 4, 256, 3),
                               DV_ST(32, 4, 128, 5),      DV_ST(32, 4, 128, 6), DV_ST(32, 2, 256, 4),
                               DV_RTM(32, 4, 256, 3),     DV_F2(32, 4, 128, 4), DV_F2(32, 2, 128, 4),
                               DV_F2(32, 4, 256, 2)};

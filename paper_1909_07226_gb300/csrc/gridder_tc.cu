@@ -706,9 +706,11 @@ idg_status read_device_errors(int *code, void *stream) {
     e = cudaMemcpyFromSymbol(&mine, g_tc_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    const idg_status st = read_dft_error(&dft);
+    int deg = 0;
+    idg_status st = read_dft_error(&dft);
+    if (st == IDG_OK) st = read_tcd_error(&deg);
     if (st != IDG_OK) return st;
-    *code = mine | dft;
+    *code = mine | dft | deg;
     return IDG_OK;
 }
 

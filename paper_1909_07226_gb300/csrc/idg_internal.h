@@ -147,6 +147,10 @@ idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const voi
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);
+// tensor-core degridder (L = 32) and its device error word
+idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *subgrids, const uint8_t *flags,
+                                const void *aterms, const float *taper, void *vis_out, void *stream);
+idg_status read_tcd_error(int *code);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);

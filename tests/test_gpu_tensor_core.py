@@ -215,3 +215,75 @@ def test_tc_transform_rejected_by_batches():
     with pytest.raises(idg.IDGError):
         idg.Batch([p], [dict(vis=d["vis"], vis_out=None, flags=d["flags"], aterms=d["aterms"], taper=d["taper"],
                              grid=g)])
+
+
+# ---------------------------------------------------------------------------
+# tensor-core degridder
+
+TCD = "tcgen05_tmemA_ws_nt288"
+
+
+@pytest.fixture
+def tcd_selected():
+    names = idg.kernel_variants("degridder", 32)
+    assert TCD in names
+    prev = idg.get_kernel_variant("degridder", 32)
+    idg.set_kernel_variant("degridder", 32, names.index(TCD))
+    yield TCD
+    idg.set_kernel_variant("degridder", 32, prev)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("image", ["gaussian", "huge", "tiny"])
+def test_tc_degridder_stage(case, image, tcd_selected):
+    import torch
+    wl = CASES[case]()
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    n = p.n_subgrids
+    rng = np.random.default_rng(31)
+    img = rng.normal(size=(n, 32, 32, 4)) + 1j * rng.normal(size=(n, 32, 32, 4))
+    img *= {"gaussian": 1.0, "huge": 1e12, "tiny": 1e-12}[image]
+    img = img.astype(np.complex64)
+    out = torch.zeros(wl.vis.shape, dtype=torch.complex64, device="cuda")   # dropped samples stay 0
+    idg.degrid_subgrids(p, 0, n, dev(img), d["flags"], d["aterms"], d["taper"], out)
+    idg.device_errors()
+    parity(out.cpu().numpy(), O.degrid_images(wl, op, img.astype(np.complex128)), f"tc degridder {case} {image}")
+
+
+def test_tc_degrid_full(tcd_selected):
+    import torch
+    wl = small32(w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12)
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    rng = np.random.default_rng(3)
+    g_in = syn.random_grid(rng, p.n_w_layers, wl.grid_size)
+    v = torch.zeros(wl.vis.shape, dtype=torch.complex64, device="cuda")
+    idg.degrid(p, dev(g_in), d["flags"], d["aterms"], d["taper"], v)
+    idg.device_errors()
+    parity(v.cpu().numpy(), O.degrid(wl, op, g_in), "tc degrid")
+
+
+def test_tc_degridder_lofar_slice_sampled(tcd_selected):
+    import torch
+    wl = syn.make_lofar(n_t=64, slot_len=64, name="lofar-tc")
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    n = p.n_subgrids
+    rng = np.random.default_rng(41)
+    ids = np.linspace(0, n - 1, 64).round().astype(np.int32)
+    img = (rng.normal(size=(n, 32, 32, 4)) + 1j * rng.normal(size=(n, 32, 32, 4))).astype(np.complex64)
+    out = torch.zeros(wl.vis.shape, dtype=torch.complex64, device="cuda")
+    idg.degrid_subgrids(p, 0, n, dev(img), d["flags"], d["aterms"], d["taper"], out)
+    idg.device_errors()
+    # the visibilities of the sampled subgrids, against the oracle on those subgrids alone
+    ref = O.degrid_images(wl, op, img[ids].astype(np.complex128), ids=ids)
+    desc = op.desc[ids]
+    sel = np.zeros(wl.vis.shape[:3], dtype=bool)
+    for row in desc:
+        bl, t0, nt, c0, nc = row[O.D_BL], row[O.D_T0], row[O.D_NT], row[O.D_C0], row[O.D_NC]
+        sel[bl, t0:t0 + nt, c0:c0 + nc] = True
+    parity(out.cpu().numpy()[sel], ref[sel], "tc degridder LOFAR slice, sampled")
