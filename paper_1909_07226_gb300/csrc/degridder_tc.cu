@@ -155,11 +155,13 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
     if (mma_warp) {
         if (lane == 0) {
             bool failed = false;
+            int st = 0;
+            uint32_t full_par = 0;                 // parity of the current use of stage st
             for (int S = 0; S < total_steps; ++S) {
-                const int s = S % DSTEPS, st = S % DSTAGES, P = S / DFOLD, r = P & 1;
+                const int s = S % DSTEPS, P = S / DFOLD, r = P & 1;
                 if (S % DFOLD == 0 && P >= 2)      // the producers have folded period P - 2 out of region r
                     wait_or_fail(smem_u32(&s_folded[r]), (uint32_t)(((P - 2) >> 1) & 1), failed);
-                wait_or_fail(smem_u32(&s_full[st]), (uint32_t)((S / DSTAGES) & 1), failed);
+                wait_or_fail(smem_u32(&s_full[st]), full_par, failed);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                 for (int t = 0; t < 2; ++t)
@@ -174,6 +176,10 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
                     }
                 commit(smem_u32(&s_empty[st]));
                 if (S % DFOLD == DFOLD - 1) commit(smem_u32(&s_foldbar[r]));
+                if (++st == DSTAGES) {
+                    st = 0;
+                    full_par ^= 1u;
+                }
             }
             commit(smem_u32(&s_drain));
             bool drained = false;
@@ -218,6 +224,8 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
         };
 
         int S = 0;
+        int st = 0;                  // A stage of step S (S mod 3)
+        uint32_t empty_par = 0;      // parity of the MMAs that last read stage st (from step S - 3)
         bool prev_valid = false;
         size_t prev_vi = 0;
         for (int blk = 0; blk < nblk; ++blk) {
@@ -233,8 +241,7 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
                 nc = -pc.c;
             }
             for (int s = 0; s < DSTEPS; ++s, ++S) {
-                const int st = S % DSTAGES;
-                if (S >= DSTAGES) wait_or_fail(smem_u32(&s_empty[st]), (uint32_t)((S / DSTAGES - 1) & 1), failed);
+                if (S >= DSTAGES) wait_or_fail(smem_u32(&s_empty[st]), empty_par, failed);
                 const int y = s >> 1, x0 = 16 * (s & 1);
                 const float base = fmaf(na, (float)(x0 - DL / 2), nb * (float)(y - DL / 2));
                 const float4 *np4 = (const float4 *)(s_np + 16 * s);
@@ -261,6 +268,10 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
                 if (s % DFOLD == 1 && S > DFOLD) {
                     fold(S / DFOLD - 1);
                     if (s == 1) flush(prev_valid, prev_vi);
+                }
+                if (++st == DSTAGES) {
+                    st = 0;
+                    if (S >= DSTAGES) empty_par ^= 1u;   // the wait at step S + 1 is for step S - 2
                 }
             }
             prev_valid = k < d.kp;
