@@ -56,7 +56,9 @@ KERNEL_TRAFFIC = {
     "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
                 "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9},
     "degridder": {"f32x2_nv4_nt128_minb3_pg_static": (115.7e6 + 99.7e6) / 4.728e9,
-                  "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9},
+                  "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9,
+                  # the per-call choice runs the LOFAR-like workload on the same kernel
+                  "tcgen05_tmemA_ws_nt288_auto512": (118.0e6 + 110.1e6) / 4.73e9},
 }
 
 

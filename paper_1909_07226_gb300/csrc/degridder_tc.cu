@@ -159,6 +159,7 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
             uint32_t full_par = 0;                 // parity of the current use of stage st
             for (int S = 0; S < total_steps; ++S) {
                 const int s = S % DSTEPS, P = S / DFOLD, r = P & 1;
+                const int nt = (S / DSTEPS) * DBLK + 128 < d.kp ? 2 : 1;   // the block's second tile may be empty
                 if (S % DFOLD == 0 && P >= 2)      // the producers have folded period P - 2 out of region r
                     wait_or_fail(smem_u32(&s_folded[r]), (uint32_t)(((P - 2) >> 1) & 1), failed);
                 wait_or_fail(smem_u32(&s_full[st]), full_par, failed);
@@ -167,6 +168,7 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
                 for (int t = 0; t < 2; ++t)
 #pragma unroll
                     for (int kc = 0; kc < 2; ++kc) {
+                        if (t >= nt) continue;
                         const uint32_t dt = tmem + (uint32_t)(32 * r + 16 * t);
                         const uint32_t at = tmem + (uint32_t)(64 + 64 * st + 32 * t + 16 * kc);
                         const uint64_t db = smem_desc(smem_u32(sB + (2 * s + kc) * kTile16));
@@ -230,6 +232,7 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
         size_t prev_vi = 0;
         for (int blk = 0; blk < nblk; ++blk) {
             const int k = blk * DBLK + t * 128 + 32 * q4 + lane;      // this thread's visibility
+            const bool live = blk * DBLK + t * 128 < d.kp;            // the tile holds a visibility
             float na = 0.0f, nb = 0.0f, nc = 0.0f;                    // -a, -b, -c: sin/cos give exp(-i phi)
             size_t vi = 0;
             if (k < d.kp) {
@@ -243,21 +246,23 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
             for (int s = 0; s < DSTEPS; ++s, ++S) {
                 if (S >= DSTAGES) wait_or_fail(smem_u32(&s_empty[st]), empty_par, failed);
                 const int y = s >> 1, x0 = 16 * (s & 1);
-                const float base = fmaf(na, (float)(x0 - DL / 2), nb * (float)(y - DL / 2));
-                const float4 *np4 = (const float4 *)(s_np + 16 * s);
+                if (live) {
+                    const float base = fmaf(na, (float)(x0 - DL / 2), nb * (float)(y - DL / 2));
+                    const float4 *np4 = (const float4 *)(s_np + 16 * s);
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    const float4 n0 = np4[2 * kc], n1 = np4[2 * kc + 1];
-                    const float np[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-                    uint32_t e[16];
+                    for (int kc = 0; kc < 2; ++kc) {
+                        const float4 n0 = np4[2 * kc], n1 = np4[2 * kc + 1];
+                        const float np[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+                        uint32_t e[16];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float phase = fmaf(na, (float)(8 * kc + j), fmaf(nc, np[j], base));
-                        float sn, cs;
-                        __sincosf(phase, &sn, &cs);
-                        split_e(cs, sn, e[j], e[8 + j]);
+                        for (int j = 0; j < 8; ++j) {
+                            const float phase = fmaf(na, (float)(8 * kc + j), fmaf(nc, np[j], base));
+                            float sn, cs;
+                            __sincosf(phase, &sn, &cs);
+                            split_e(cs, sn, e[j], e[8 + j]);
+                        }
+                        tmem_st16(lane_base + (uint32_t)(64 + 64 * st + 32 * t + 16 * kc), e);
                     }
-                    tmem_st16(lane_base + (uint32_t)(64 + 64 * st + 32 * t + 16 * kc), e);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
