@@ -195,9 +195,15 @@ idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d
  * The same two operations on HOST buffers (layouts as above): inputs are copied
  * to device memory taken from the library's stream-ordered pool, the operation
  * runs on `stream`, the result is copied back and the call returns when it is
- * in h_grid / h_vis_out.  Page-locked host memory gives the full copy
- * bandwidth.  h_grid is OVERWRITTEN with the grid of these visibilities (the
- * device grid starts from zero); h_vis_out is overwritten as in idg_degrid.
+ * in h_grid / h_vis_out.  The work is cut into spans of whole baselines (about
+ * 256 MB of visibilities each, at least 4 when there are that many baselines);
+ * a library-owned copy stream per device moves the visibilities of one span
+ * while `stream` computes another (gridding: copy in ahead; degridding: copy
+ * out behind), ordered by events.  Page-locked host memory gives the full copy
+ * bandwidth and the overlap; pageable memory works with staged copies.
+ * h_grid is OVERWRITTEN with the grid of these visibilities (the device grid
+ * starts from zero); h_vis_out is overwritten as in idg_degrid.  Host buffers
+ * must not be touched by the caller until the call returns.
  */
 idg_status idg_grid_host(const idg_plan *plan, const void *h_vis, const uint8_t *h_flags,
                          const void *h_aterms, const float *h_taper, void *h_grid, idg_stream stream);

@@ -482,6 +482,56 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
     return IDG_OK;
 }
 
+// Grid the subgrids [first, first + count): positions in the work order
+// (use_order) or plan indices, in pieces of at most `chunk` subgrids that pass
+// through the subgrid scratch (gridder -> transform -> adder).
+static idg_status grid_span(const idg_plan *p, const Geometry &g, bool use_order, int64_t first, int64_t count,
+                            void *scratch, int64_t chunk, const void *vis, const uint8_t *flags, const void *aterms,
+                            const float *taper, void *grid, void *cbuf, cudaStream_t s) {
+    idg_status st = IDG_OK;
+    for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
+        const int64_t cnt = std::min(chunk, first + count - f);
+        const SubgridSet set = use_order ? order_set(p, f, cnt) : plan_set(p, f, cnt);
+        {
+            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, f, cnt, use_order));
+            st = launch_gridder(g, set, -1, vis, flags, aterms, taper, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
+            st = launch_subgrid_fft(p, cnt, -1, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
+            st = cbuf ? launch_adder_compensated(g, set, scratch, grid, cbuf, s) : launch_adder(g, set, scratch, grid, s);
+        }
+    }
+    return st;
+}
+
+// Degrid the subgrids [first, first + count) (splitter -> transform -> degridder).
+static idg_status degrid_span(const idg_plan *p, const Geometry &g, bool use_order, int64_t first, int64_t count,
+                              void *scratch, int64_t chunk, const void *grid, const uint8_t *flags, const void *aterms,
+                              const float *taper, void *vis_out, cudaStream_t s) {
+    idg_status st = IDG_OK;
+    for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
+        const int64_t cnt = std::min(chunk, first + count - f);
+        const SubgridSet set = use_order ? order_set(p, f, cnt) : plan_set(p, f, cnt);
+        {
+            ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
+            st = launch_splitter(g, set, grid, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
+            st = launch_subgrid_fft(p, cnt, +1, scratch, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, f, cnt, use_order));
+            st = launch_degridder(g, set, -1, scratch, flags, aterms, taper, vis_out, s);
+        }
+    }
+    return st;
+}
+
 idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
                     const float *taper, void *grid, idg_stream stream) {
     idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
@@ -505,22 +555,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
             if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(compensation)");
         }
     }
-    for (int64_t first = 0; first < n && st == IDG_OK; first += chunk) {
-        const int64_t cnt = std::min(chunk, n - first);
-        {
-            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, cnt, true));
-            st = launch_gridder(g, order_set(p, first, cnt), -1, vis, flags, aterms, taper, scratch, s);
-        }
-        if (st == IDG_OK) {
-            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
-            st = launch_subgrid_fft(p, cnt, -1, scratch, s);
-        }
-        if (st == IDG_OK) {
-            ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
-            st = comp ? launch_adder_compensated(g, order_set(p, first, cnt), scratch, grid, cbuf, s)
-                      : launch_adder(g, order_set(p, first, cnt), scratch, grid, s);
-        }
-    }
+    if (st == IDG_OK) st = grid_span(p, g, true, 0, n, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
     if (comp && cbuf) {
         if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
         cudaFreeAsync(cbuf, s);
@@ -546,22 +581,7 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
     void *scratch = nullptr;
     st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
-    const Geometry g = p->geometry();
-    for (int64_t first = 0; first < n && st == IDG_OK; first += chunk) {
-        const int64_t cnt = std::min(chunk, n - first);
-        {
-            ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
-            st = launch_splitter(g, order_set(p, first, cnt), grid, scratch, s);
-        }
-        if (st == IDG_OK) {
-            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
-            st = launch_subgrid_fft(p, cnt, +1, scratch, s);
-        }
-        if (st == IDG_OK) {
-            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, cnt, true));
-            st = launch_degridder(g, order_set(p, first, cnt), -1, scratch, flags, aterms, taper, vis_out, s);
-        }
-    }
+    st = degrid_span(p, p->geometry(), true, 0, n, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
     cudaError_t e = cudaFreeAsync(scratch, s);
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
     return st;
@@ -569,10 +589,17 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
 
 // ---------------------------------------------------------------------------
 // host-buffer variants
+//
+// Visibilities are stored baseline-major and the plan orders subgrids by
+// baseline, so the call is cut into spans of whole baselines whose
+// visibilities are one contiguous range.  A private copy stream moves span k
+// while the caller's stream computes span k - 1 (gridding) or k + 1
+// (degridding); events order the two streams.  The grid itself moves before
+// (degridding) or after (gridding) the spans.
 
 namespace {
 struct DevBufs {
-    void *ptr[5] = {};
+    void *ptr[7] = {};
     cudaStream_t s;
     explicit DevBufs(cudaStream_t st) : s(st) {}
     ~DevBufs() {
@@ -581,13 +608,64 @@ struct DevBufs {
     }
 };
 
-idg_status upload(int dev, DevBufs &b, int slot, const void *h, size_t bytes, const char *what) {
-    if (!h) return IDG_OK;
-    idg_status st = scratch_alloc(dev, bytes, b.s, &b.ptr[slot]);
-    if (st != IDG_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(b.ptr[slot], h, bytes, cudaMemcpyHostToDevice, b.s);
-    if (e != cudaSuccess) return cuda_fail(e, what);
+struct Events {
+    std::vector<cudaEvent_t> ev;
+    ~Events() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    cudaError_t add(cudaEvent_t *out) {
+        cudaError_t e = cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+        if (e == cudaSuccess) ev.push_back(*out);
+        return e;
+    }
+};
+
+std::mutex g_copy_mu;
+cudaStream_t g_copy_stream[64] = {};
+
+idg_status copy_stream(int dev, cudaStream_t *out) {
+    if (dev < 0 || dev >= 64) return fail(IDG_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_copy_mu);
+    if (!g_copy_stream[dev]) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "creating the copy stream");
+    }
+    *out = g_copy_stream[dev];
     return IDG_OK;
+}
+
+// spans of whole baselines: plan index bounds first[k] .. first[k + 1], baselines bl[k] .. bl[k + 1]
+struct Spans {
+    std::vector<int64_t> first;
+    std::vector<int32_t> bl;
+};
+
+Spans baseline_spans(const idg_plan *p) {
+    const int64_t vis_bytes = (int64_t)p->n_bl * p->n_t * p->n_chan * 32;
+    int nk = (int)std::min<int64_t>(16, std::max<int64_t>(4, vis_bytes / (256ll << 20)));   // ~256 MB spans
+    nk = std::min(nk, p->n_bl);
+    const int64_t n = p->stats.n_subgrids;
+    auto bl_of = [&](int64_t i) { return p->desc[(size_t)i * kDescFields + IDG_DESC_BASELINE]; };
+    for (int64_t i = 1; i < n; ++i)      // the planner emits baseline-major order; otherwise one span
+        if (bl_of(i) < bl_of(i - 1)) {
+            nk = 1;
+            break;
+        }
+    Spans sp;
+    int64_t i = 0;
+    for (int k = 0; k <= nk; ++k) {
+        const int32_t b = (int32_t)((int64_t)p->n_bl * k / nk);
+        while (i < n && bl_of(i) < b) ++i;
+        sp.first.push_back(k == nk ? n : i);
+        sp.bl.push_back(b);
+    }
+    return sp;
+}
+
+idg_status h2d(void *d, const void *h, size_t bytes, cudaStream_t cs, const char *what) {
+    if (!h || !bytes) return IDG_OK;
+    cudaError_t e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, cs);
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, what);
 }
 }  // namespace
 
@@ -596,19 +674,53 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     idg_status st = check_call(p, h_vis, "h_vis", h_grid, "h_grid");
     if (st != IDG_OK) return st;
     if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t nvis = (size_t)p->n_bl * p->n_t * p->n_chan;
+    cudaStream_t s = (cudaStream_t)stream, cs = nullptr;
+    if ((st = copy_stream(p->device, &cs)) != IDG_OK) return st;
+    const size_t per_bl = (size_t)p->n_t * p->n_chan;      // visibilities per baseline
+    const size_t nvis = (size_t)p->n_bl * per_bl;
     const size_t grid_bytes = (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
+    const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
-    if ((st = upload(p->device, b, 0, h_vis, nvis * 32, "copy of visibilities")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 1, h_flags, nvis, "copy of flags")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 2, h_aterms, (size_t)p->n_slots * p->n_stations * p->L * p->L * 32,
-                     "copy of A-terms")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 3, h_taper, (size_t)p->L * p->L * 4, "copy of taper")) != IDG_OK) return st;
-    if ((st = scratch_alloc(p->device, grid_bytes, s, &b.ptr[4])) != IDG_OK) return st;
-    cudaError_t e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(grid)");
-    st = idg_grid(p, b.ptr[0], (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], stream);
+    const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, (size_t)p->L * p->L * 4, grid_bytes,
+                             (size_t)chunk * p->L * p->L * 32};
+    for (int k = 0; k < 6 && st == IDG_OK; ++k)
+        if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
+    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
+    const size_t grid_f4 = grid_bytes / 16;
+    if (st == IDG_OK && comp) st = scratch_alloc(p->device, grid_f4 * 16, s, &b.ptr[6]);
+    if (st != IDG_OK) return st;
+    Events ev;
+    cudaEvent_t e_alloc, e_end;
+    cudaError_t e = ev.add(&e_alloc);
+    if (e == cudaSuccess) e = ev.add(&e_end);
+    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e_alloc, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
+    if (e == cudaSuccess && comp) e = cudaMemsetAsync(b.ptr[6], 0, grid_f4 * 16, s);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_host setup");
+    if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
+    const Spans sp = baseline_spans(p);
+    const Geometry g = p->geometry();
+    for (size_t k = 0; k + 1 < sp.first.size() && st == IDG_OK; ++k) {
+        const size_t v0 = (size_t)sp.bl[k] * per_bl, nv = (size_t)(sp.bl[k + 1] - sp.bl[k]) * per_bl;
+        st = h2d((char *)b.ptr[0] + v0 * 32, (const char *)h_vis + v0 * 32, nv * 32, cs, "copy of visibilities");
+        if (st == IDG_OK && h_flags)
+            st = h2d((char *)b.ptr[1] + v0, h_flags + v0, nv, cs, "copy of flags");
+        cudaEvent_t e_up;
+        if (st == IDG_OK && (e = ev.add(&e_up)) == cudaSuccess && (e = cudaEventRecord(e_up, cs)) == cudaSuccess)
+            e = cudaStreamWaitEvent(s, e_up, 0);
+        if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+        if (st == IDG_OK && sp.first[k + 1] > sp.first[k])
+            st = grid_span(p, g, false, sp.first[k], sp.first[k + 1] - sp.first[k], b.ptr[5], chunk, b.ptr[0],
+                           (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], b.ptr[6], s);
+    }
+    if (st == IDG_OK && comp) st = launch_fold_compensation(b.ptr[4], b.ptr[6], grid_f4, s);
+    // the copy stream's work ends before the buffers are released on s
+    e = cudaEventRecord(e_end, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
     if (st != IDG_OK) return st;
     e = cudaMemcpyAsync(h_grid, b.ptr[4], grid_bytes, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy of the grid to the host");
@@ -622,20 +734,56 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     idg_status st = check_call(p, h_grid, "h_grid", h_vis_out, "h_vis_out");
     if (st != IDG_OK) return st;
     if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t nvis = (size_t)p->n_bl * p->n_t * p->n_chan;
+    cudaStream_t s = (cudaStream_t)stream, cs = nullptr;
+    if ((st = copy_stream(p->device, &cs)) != IDG_OK) return st;
+    const size_t per_bl = (size_t)p->n_t * p->n_chan;
+    const size_t nvis = (size_t)p->n_bl * per_bl;
     const size_t grid_bytes = (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
+    const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
-    if ((st = upload(p->device, b, 0, h_grid, grid_bytes, "copy of the grid")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 1, h_flags, nvis, "copy of flags")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 2, h_aterms, (size_t)p->n_slots * p->n_stations * p->L * p->L * 32,
-                     "copy of A-terms")) != IDG_OK) return st;
-    if ((st = upload(p->device, b, 3, h_taper, (size_t)p->L * p->L * 4, "copy of taper")) != IDG_OK) return st;
-    if ((st = scratch_alloc(p->device, nvis * 32, s, &b.ptr[4])) != IDG_OK) return st;
-    st = idg_degrid(p, b.ptr[0], (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], stream);
+    const size_t sizes[6] = {grid_bytes, h_flags ? nvis : 0, at_bytes, (size_t)p->L * p->L * 4, nvis * 32,
+                             (size_t)chunk * p->L * p->L * 32};
+    for (int k = 0; k < 6 && st == IDG_OK; ++k)
+        if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
     if (st != IDG_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(h_vis_out, b.ptr[4], nvis * 32, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copy of the visibilities to the host");
+    Events ev;
+    cudaEvent_t e_alloc, e_in, e_end;
+    cudaError_t e = ev.add(&e_alloc);
+    if (e == cudaSuccess) e = ev.add(&e_in);
+    if (e == cudaSuccess) e = ev.add(&e_end);
+    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e_alloc, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "degrid_host setup");
+    if ((st = h2d(b.ptr[0], h_grid, grid_bytes, cs, "copy of the grid")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[1], h_flags, sizes[1], cs, "copy of flags")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
+    e = cudaEventRecord(e_in, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_in, 0);
+    if (e == cudaSuccess && p->any_dropped) e = cudaMemsetAsync(b.ptr[4], 0, nvis * 32, s);
+    if (e != cudaSuccess) return cuda_fail(e, "degrid_host inputs");
+    const Spans sp = baseline_spans(p);
+    const Geometry g = p->geometry();
+    for (size_t k = 0; k + 1 < sp.first.size() && st == IDG_OK; ++k) {
+        if (sp.first[k + 1] > sp.first[k])
+            st = degrid_span(p, g, false, sp.first[k], sp.first[k + 1] - sp.first[k], b.ptr[5], chunk, b.ptr[0],
+                             (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], s);
+        cudaEvent_t e_done;
+        if (st == IDG_OK && (e = ev.add(&e_done)) == cudaSuccess && (e = cudaEventRecord(e_done, s)) == cudaSuccess)
+            e = cudaStreamWaitEvent(cs, e_done, 0);
+        if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+        if (st == IDG_OK) {
+            const size_t v0 = (size_t)sp.bl[k] * per_bl, nv = (size_t)(sp.bl[k + 1] - sp.bl[k]) * per_bl;
+            e = cudaMemcpyAsync((char *)h_vis_out + v0 * 32, (const char *)b.ptr[4] + v0 * 32, nv * 32,
+                                cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) st = cuda_fail(e, "copy of the visibilities to the host");
+        }
+    }
+    e = cudaEventRecord(e_end, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+    if (st != IDG_OK) return st;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return IDG_OK;

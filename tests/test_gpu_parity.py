@@ -294,3 +294,49 @@ def test_compensated_adder_reduces_summation_error():
         parity(got, ref, f"grid adder_mode={mode}")
     print(f"centre error: atomic {errs[0]:.3e} compensated {errs[1]:.3e}")
     assert errs[1] < errs[0]
+
+
+# ---------------------------------------------------------------------------
+# host-buffer calls: copies pipelined over spans of whole baselines
+
+HOST_CASES = {
+    "tiny": lambda: syn.make_tiny(),
+    "L16_flags_aterms": lambda: small(16),
+    "L24_wlayers": lambda: small(24, w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12),
+    "L32_identity_wide": lambda: small(32, aterms="identity", n_chan=16, diameter_m=30000.0, df=4e6),
+    "L64_dropped": lambda: small(64, cell=1.2e-3, diameter_m=6000.0, n_t=24),
+    "L32_many_baselines": lambda: small(32, n_st=12, n_t=16, max_t=16),
+}
+
+
+@pytest.mark.parametrize("case", sorted(HOST_CASES))
+def test_grid_and_degrid_host_buffers(case):
+    import torch
+    wl = HOST_CASES[case]()
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    taper = wl.taper.astype(np.float32)
+    # pinned host buffers, as a streaming caller would hold them
+    vis = torch.from_numpy(wl.vis).pin_memory()
+    flags = None if wl.flags is None else torch.from_numpy(wl.flags).pin_memory()
+    aterms = None if wl.aterms is None else torch.from_numpy(wl.aterms).pin_memory()
+    g = torch.full((p.n_w_layers, wl.grid_size, wl.grid_size, 4), 9.0 + 9.0j, dtype=torch.complex64).pin_memory()
+    idg.grid_host(p, vis.numpy(), None if flags is None else flags.numpy(), None if aterms is None else aterms.numpy(),
+                  taper, g.numpy())
+    idg.device_errors()
+    parity(g.numpy(), O.grid(wl, op), f"grid_host {case}")          # overwritten, not accumulated
+    rng = np.random.default_rng(3)
+    g_in = syn.random_grid(rng, p.n_w_layers, wl.grid_size)
+    v = np.full(wl.vis.shape, 7.0 + 7.0j, dtype=np.complex64)         # pageable memory works too
+    idg.degrid_host(p, g_in, wl.flags, wl.aterms, taper, v)
+    idg.device_errors()
+    parity(v, O.degrid(wl, op, g_in), f"degrid_host {case}")
+
+
+def test_host_buffers_compensated_adder():
+    wl = small(32, w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12)
+    p = idg.plan_from_workload(wl, adder_mode=idg.ADDER_COMPENSATED)
+    op = O.plan(wl)
+    g = np.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=np.complex64)
+    idg.grid_host(p, wl.vis, wl.flags, wl.aterms, wl.taper.astype(np.float32), g)
+    parity(g, O.grid(wl, op), "grid_host compensated")
