@@ -359,13 +359,15 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
                         double *degridder_ms, int cap, idg_stream stream);
 
 /*
- * Device error word.  The tensor-core gridder variant (L = 32, named
- * "tcgen05_...") waits on shared-memory barriers for its matrix operations;
+ * Device error words.  The tensor-core kernels (the L = 32 gridder and
+ * degridder, variants named "tcgen05_...", and the IDG_FFT_TC_SPLIT transform)
+ * wait on shared-memory barriers for their matrix operations and bulk copies;
  * every wait has an iteration limit, after which the kernel records an error
- * in a device word, releases its tensor memory and leaves its subgrids
- * unwritten.  idg_device_errors synchronises `stream`, reads and clears that
- * word, and returns IDG_ERR_TIMEOUT if any wait gave up since the last call
- * (IDG_OK otherwise).  The word is per device and per process.
+ * in a device word, waits (bounded) for its own operations in flight, releases
+ * its tensor memory and leaves its outputs unwritten.  idg_device_errors
+ * synchronises `stream`, reads and clears the words, and returns
+ * IDG_ERR_TIMEOUT if any wait gave up since the last call (IDG_OK otherwise).
+ * The words are per device and per process.
  */
 idg_status idg_device_errors(idg_stream stream);
 

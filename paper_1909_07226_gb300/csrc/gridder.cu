@@ -216,11 +216,6 @@ idg_status launch_f2(const Geometry &g, const SubgridSet &set, const void *vis, 
     return IDG_OK;
 }
 
-idg_status launch_tc(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
-                     const void *aterms, const float *taper, void *out, cudaStream_t s) {
-    return launch_gridder_tc(g, set, vis, flags, aterms, taper, out, (void *)s);
-}
-
 idg_status launch_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                       const void *aterms, const float *taper, void *out, cudaStream_t s) {
     return launch_gridder_tcw(g, set, vis, flags, aterms, taper, out, (void *)s);
@@ -242,8 +237,7 @@ const Variant kV24[] = {GF(24, 3, 128, 3), GV(24, 3, 128, 3, false), GV(24, 3, 2
 const Variant kV32[] = {{"tcgen05_tmemA_ws_nt288", launch_tcw}, GF(32, 4, 128, 2), GV(32, 4, 128, 3, false),
                         GV(32, 4, 256, 3, true),
                         GV(32, 4, 256, 4, true),  GV(32, 8, 256, 4, true),  GV(32, 2, 256, 2, true),
-                        GF(32, 4, 128, 3),        GF(32, 2, 128, 3),        GF(32, 8, 128, 4),
-                        {"tcgen05_fp16x3_nt256", launch_tc}};
+                        GF(32, 4, 128, 3),        GF(32, 2, 128, 3),        GF(32, 8, 128, 4)};
 const Variant kV48[] = {GF(48, 4, 128, 1), GV(48, 6, 128, 2, false), GV(48, 6, 256, 2, true),
                         GV(48, 4, 256, 1, true), GF(48, 6, 128, 1)};
 const Variant kV64[] = {GF(64, 4, 128, 1), GV(64, 8, 128, 1, false), GV(64, 8, 256, 1, true),

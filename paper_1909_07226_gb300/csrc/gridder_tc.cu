@@ -8,416 +8,57 @@
 //
 // Precision.  E is formed on the CUDA cores (phase, sin/cos) and split into
 // FP16 parts E = E_hi + E_lo (E_hi = fp16(E), E_lo = fp16(E - E_hi), the
-// difference exact in FP32); V, scaled by a power of two per subgrid so that
-// its largest component lies in [2^9, 2^10), is split the same way.  One B
-// tile [V_hi | V_lo] (N = 16) serves two MMAs per accumulator tile:
-//   columns  0..15 of the tile:  E_hi [V_hi | V_lo]     (hh | hl)
-//   columns 16..31 of the tile:  E_lo [V_hi | V_lo]     (lh | ll)
-// The tensor cores accumulate in FP32 but do not round to nearest: each
-// accumulation step can lose up to an ulp, biased towards zero, so the error
-// of a long sum grows linearly with the number of steps.  Only hh is large;
-// every FOLD_GROUPS groups (256 visibilities) the CTA waits for its MMAs,
-// adds hh + hl into an FP32 sum in shared memory (IEEE round to nearest) and
-// restarts hh | hl from zero.  lh | ll (2^-11 of the magnitude) run unfolded.
-// The result is (fold + hh + hl + lh + ll) / scale.
+// difference exact); V, scaled by a power of two per subgrid so that its
+// largest component lies in [2^9, 2^10), is split the same way.  One B tile
+// [V_hi | V_lo] (N = 16) serves two MMAs per 128-pixel tile and group of 8
+// visibilities (K = 16): E_hi [V_hi | V_lo] and E_lo [V_hi | V_lo] into the
+// same accumulator, whose columns 0..7 + 8..15 are the result.  The tensor
+// cores accumulate in FP32 without rounding to nearest (each step can lose up
+// to an ulp, biased towards zero), so every WS_FOLD groups the accumulators are
+// added into an FP32 sum in shared memory and restarted.
 //
-// Schedule.  One CTA (256 threads, 8 warps) per subgrid, two CTAs per SM.  A
-// step takes 8 visibilities (K = 16) and 4 of the 8 M-tiles of 128 pixels:
-// each thread writes the A rows (hi and lo) of 2 pixels into one half of a
-// double-buffered shared ring in the canonical no-swizzle K-major layout
-// (8-row x 16-byte core matrices); thread 0 issues 8 MMAs (M = 128, N = 16,
-// K = 16, FP16 inputs, FP32 accumulation in tensor memory, 256 columns) and
-// commits them to the half's mbarrier, which the CTA waits on before it
-// refills that half.  Every wait is bounded: on timeout the kernel records an
-// error word, waits (bounded) for its own MMAs, frees its tensor memory and
-// leaves its subgrid unwritten.
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
+// Schedule.  One CTA per subgrid: eight producer warps form the phasors and
+// write their FP16 hi/lo rows straight into tensor memory (tcgen05.st; warp w
+// owns lanes 32 (w % 4) ..); a ninth warp issues the MMAs with A read from
+// tensor memory.  Hand-off is by mbarriers, not CTA barriers:
+// full[h] (8 producer arrivals) -> MMAs -> commit -> empty[h].
+// Tensor memory per CTA (256 columns, two CTAs per SM):
+//   columns   0..127  accumulators, tile mt at 16 mt
+//   columns 128..255  two A stages of 4 tiles, tile lt of stage h at 128 + 64 h + 16 lt
+//                     (8 columns hi, 8 lo; column c holds k = 2c and 2c + 1)
+// At a fold the producers wait for the MMAs, add the accumulators into the
+// shared-memory sum and release the MMA warp (folded), which restarts them
+// from zero.  Every wait is bounded; after a failed wait a thread skips every
+// later wait, so control flow stays uniform and the kernel ends; the error word
+// is set and no output is written.
 #include "device_common.cuh"
+#include "tc_common.cuh"
 
 namespace idg {
 
-// device error word of the tensor-core kernels (0 = ok); read and cleared by
+// device error word of the tensor-core gridder (0 = ok); read and cleared by
 // idg_device_errors
 __device__ int g_tc_error = 0;
 
 namespace {
 
 using namespace dev;
+using namespace tc;
 
 constexpr int TC_L = 32;
-constexpr int TC_NT = 256;
-constexpr int TC_PIX = TC_L * TC_L;             // 1024
-constexpr int TC_MT = TC_PIX / 128;             // 8 accumulator tiles of 32 columns
-constexpr int TC_COLS = 32 * TC_MT;             // tensor-memory columns per CTA
-constexpr int TC_VB = 64;                       // visibilities per staged batch
-constexpr int TC_GROUPS = TC_VB / 8;            // groups of 8 visibilities (K = 16) per batch
-constexpr int FOLD_GROUPS = 32;                 // groups between folds of hh | hl
-constexpr uint32_t TC_LBO = 128, TC_SBO = 256;  // core-matrix strides (K, M/N directions)
-constexpr int A_TILE = 128 * 32;                // bytes of one 128 x 16 FP16 tile
-constexpr int A_HALF = 4 * 2 * A_TILE;          // 4 M-tiles x (hi, lo) = 32 KB
-constexpr int B_TILE = 16 * 32;                 // 512 B: 16 rows x 16 FP16
-constexpr int B_BATCH = TC_GROUPS * B_TILE;     // 4 KB
-constexpr int FOLD_BYTES = 8 * TC_PIX * 4;      // [8][1024] FP32
-constexpr long kSpin = 1L << 20;                // bounded spin on an mbarrier (milliseconds at most)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of (row, k) in a K-major tile of 16 columns: core matrix
-// (row / 8, k / 8) at (row / 8) SBO + (k / 8) LBO, inside it 16 B per row, 2 B per k
-__device__ __forceinline__ uint32_t kmaj_off(int row, int k) {
-    return (uint32_t)(row >> 3) * TC_SBO + (uint32_t)(k >> 3) * TC_LBO + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 7) * 2;
-}
-
-// shared-memory matrix descriptor: start, leading and stride byte offsets (>> 4),
-// descriptor version 1 (bit 46), no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-// kind::f16 instruction descriptor: D F32, A and B F16, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < kSpin; ++it) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
-                 :: "r"(dtmem), "l"(da), "l"(db), "r"(kIdesc), "r"(acc) : "memory");
-}
-
-__device__ __forceinline__ void commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t pack_h2(__half2 h) { return *reinterpret_cast<uint32_t *>(&h); }
-
-// FP16 hi/lo parts of (cs, sn): hi = fp16(E) rounded, lo = fp16(E - hi) with E - hi
-// formed exactly by one mixed-precision fma per component (FP16 hi times -1 plus
-// FP32 E), with no conversion of hi back to FP32.  Low halves hold cs.
-__device__ __forceinline__ void split_e(float cs, float sn, uint32_t &hi, uint32_t &lo) {
-    asm("{\n"
-        " .reg .b16 hc, hs, m1;\n"
-        " .reg .f32 lc, ls;\n"
-        " mov.b16 m1, 0xBC00;\n"
-        " cvt.rn.f16x2.f32 %0, %3, %2;\n"
-        " mov.b32 {hc, hs}, %0;\n"
-        " fma.rn.f32.f16 lc, hc, m1, %2;\n"
-        " fma.rn.f32.f16 ls, hs, m1, %3;\n"
-        " cvt.rn.f16x2.f32 %1, ls, lc;\n"
-        "}" : "=r"(hi), "=r"(lo) : "f"(cs), "f"(sn));
-}
-
-__global__ void __launch_bounds__(TC_NT, 2)
-gridder_tc_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
-                  const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
-                  const float *__restrict__ taper, float4 *__restrict__ out) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *sA = smem;                               // 2 halves x 32 KB
-    uint8_t *sB = smem + 2 * A_HALF;                  // 2 batches x 4 KB
-    float *s_fold = (float *)(sB + 2 * B_BATCH);      // [8][1024]
-    float4 *s_coef = (float4 *)(sB + 2 * B_BATCH + FOLD_BYTES);   // 2 batches x 64
-    __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_bar[3];        // two ring halves; folds and the final drain
-    __shared__ float s_red[TC_NT / 32];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    const DevSubgrid d = g.sub[sid];
-
-    // this thread's four pixels: t, t + 256, t + 512, t + 768
-    float X[4], Yv[4], NP[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int pix = tid + 256 * i;
-        X[i] = (float)((pix & (TC_L - 1)) - TC_L / 2);
-        Yv[i] = (float)((pix >> 5) - TC_L / 2);
-        NP[i] = g.nprime[pix];
-    }
-
-    // per-subgrid scale: a power of two that brings max |V| into [2^9, 2^10)
-    float vmax = 0.0f;
-    for (int k = tid; k < d.kp; k += TC_NT) {
-        int t, c;
-        const size_t vi = vis_index(g, d, k, t, c);
-        if (!(flags && flags[vi])) {
-            const float4 a = vis[2 * vi], b = vis[2 * vi + 1];
-            vmax = fmaxf(vmax, fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
-                                     fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w)))));
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if (lane == 0) s_red[warp] = vmax;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&s_tmem)), "n"(TC_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&s_bar[i])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = s_tmem;
-    float m = 0.0f;
-#pragma unroll
-    for (int w = 0; w < TC_NT / 32; ++w) m = fmaxf(m, s_red[w]);
-    int e2 = 0;
-    if (m > 0.0f) frexpf(m, &e2);                  // m in [2^(e2-1), 2^e2)
-    const float scale = ldexpf(1.0f, 10 - e2);
-    const float inv_scale = ldexpf(1.0f, e2 - 10);
-
-    // warp w owns TMEM lanes 32 (w % 4) .. + 31 of tiles w / 4, w / 4 + 2, w / 4 + 4, w / 4 + 6
-    const int q4 = warp & 3;
-    const int total_groups = (d.kp + 7) / 8;
-    const int n_batches = (d.kp + TC_VB - 1) / TC_VB;
-    long step = 0;                                  // 2 per group
-    int gc = 0;                                     // groups issued
-    int n_folds = 0;
-    uint32_t drain_phase = 0;                       // completed waits on s_bar[2]
-    bool ok = true;
-    for (int bt = 0; bt < n_batches && ok; ++bt) {
-        const int bb = bt & 1;
-        uint8_t *sBb = sB + bb * B_BATCH;
-        float4 *coef = s_coef + bb * TC_VB;
-        // stage the batch: thread t < 64 takes visibility t (coefficients and its B column pairs)
-        if (tid < TC_VB) {
-            const int k = bt * TC_VB + tid;
-            float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-            float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (k < d.kp) {
-                int t, c;
-                const size_t vi = vis_index(g, d, k, t, c);
-                const PhaseCoef pc = phase_coef(g, d, t, c);
-                cf = make_float4(pc.a, pc.b, pc.c, 0.f);
-                if (!(flags && flags[vi])) {
-                    const float4 a = vis[2 * vi], b = vis[2 * vi + 1];
-                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-                }
-            }
-            coef[tid] = cf;
-            const int grp = tid >> 3, j = tid & 7;
-            uint8_t *Bt = sBb + grp * B_TILE;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float re = v[2 * q] * scale, im = v[2 * q + 1] * scale;
-                const __half re_h = __float2half_rn(re), im_h = __float2half_rn(im);
-                const __half re_l = __float2half_rn(re - __half2float(re_h));
-                const __half im_l = __float2half_rn(im - __half2float(im_h));
-                // output column 2q (Re of pol q): K rows 2j -> Re V, 2j+1 -> -Im V;
-                // column 2q+1 (Im): Im V, Re V; columns 8.. the same for V_lo
-                *(__half *)(Bt + kmaj_off(2 * q, 2 * j)) = re_h;
-                *(__half *)(Bt + kmaj_off(2 * q, 2 * j + 1)) = __hneg(im_h);
-                *(__half *)(Bt + kmaj_off(2 * q + 1, 2 * j)) = im_h;
-                *(__half *)(Bt + kmaj_off(2 * q + 1, 2 * j + 1)) = re_h;
-                *(__half *)(Bt + kmaj_off(8 + 2 * q, 2 * j)) = re_l;
-                *(__half *)(Bt + kmaj_off(8 + 2 * q, 2 * j + 1)) = __hneg(im_l);
-                *(__half *)(Bt + kmaj_off(8 + 2 * q + 1, 2 * j)) = im_l;
-                *(__half *)(Bt + kmaj_off(8 + 2 * q + 1, 2 * j + 1)) = re_l;
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        const int ng = min(TC_GROUPS, total_groups - bt * TC_GROUPS);
-        for (int gi = 0; gi < ng && ok; ++gi, ++gc) {
-            float ca[8], cb[8], cc[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 cf = coef[gi * 8 + j];
-                ca[j] = cf.x;
-                cb[j] = cf.y;
-                cc[j] = cf.z;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h, ++step) {
-                const int half = h;                    // = step & 1: every group has two steps
-                const int waited_out =
-                    step >= 2 && !mbar_wait(smem_u32(&s_bar[half]), (uint32_t)(((step >> 1) - 1) & 1));
-                uint8_t *Ah = sA + half * A_HALF;
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int pi = 2 * h + i;                 // which of the thread's 4 pixels
-                    const int row = tid + 256 * i;            // row in this half's 512 rows
-                    const int lt = row >> 7, r = row & 127;   // local tile, row in tile
-                    uint32_t hi[8], lo[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float phase = fmaf(ca[j], X[pi], fmaf(cc[j], NP[pi], cb[j] * Yv[pi]));
-                        float sn, cs;
-                        __sincosf(phase, &sn, &cs);
-                        const __half2 eh = __floats2half2_rn(cs, sn);
-                        const float2 ef = __half22float2(eh);
-                        hi[j] = pack_h2(eh);
-                        lo[j] = pack_h2(__floats2half2_rn(cs - ef.x, sn - ef.y));
-                    }
-                    uint8_t *th = Ah + lt * 2 * A_TILE, *tl = th + A_TILE;
-                    *(uint4 *)(th + kmaj_off(r, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    *(uint4 *)(th + kmaj_off(r, 8)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-                    *(uint4 *)(tl + kmaj_off(r, 0)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                    *(uint4 *)(tl + kmaj_off(r, 8)) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (__syncthreads_or(waited_out)) {   // the same answer in every thread
-                    ok = false;
-                    break;
-                }
-                if (tid == 0) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint64_t db = smem_desc(smem_u32(sBb + gi * B_TILE));
-                    const uint32_t acc_hi = (gc % FOLD_GROUPS == 0) ? 0u : 1u;   // hh | hl restart after a fold
-                    const uint32_t acc_lo = (gc == 0) ? 0u : 1u;
-#pragma unroll
-                    for (int lt = 0; lt < 4; ++lt) {
-                        const uint32_t dt = tmem + (uint32_t)(32 * (4 * h + lt));
-                        const uint8_t *th = Ah + lt * 2 * A_TILE;
-                        mma_f16(dt, smem_desc(smem_u32(th)), db, acc_hi);
-                        mma_f16(dt + 16, smem_desc(smem_u32(th + A_TILE)), db, acc_lo);
-                    }
-                    commit(smem_u32(&s_bar[half]));
-                }
-            }
-            if (ok && (gc + 1) % FOLD_GROUPS == 0 && gc + 1 < total_groups) {
-                // fold hh + hl into the FP32 sum in shared memory
-                if (tid == 0) commit(smem_u32(&s_bar[2]));
-                const int fold_out = !mbar_wait(smem_u32(&s_bar[2]), drain_phase);
-                drain_phase ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int mt = warp >> 2; mt < TC_MT; mt += 2) {
-                    uint32_t r[16];
-                    tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * mt), r);
-                    const int pix = mt * 128 + 32 * q4 + lane;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float v = __uint_as_float(r[c]) + __uint_as_float(r[8 + c]);
-                        s_fold[c * TC_PIX + pix] = n_folds ? s_fold[c * TC_PIX + pix] + v : v;
-                    }
-                }
-                ++n_folds;
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                if (__syncthreads_or(fold_out)) ok = false;
-            }
-        }
-    }
-    // drain: wait for every MMA issued (bounded), then read the accumulators
-    if (tid == 0) commit(smem_u32(&s_bar[2]));
-    const int drain_out = !mbar_wait(smem_u32(&s_bar[2]), drain_phase);
-    const bool failed = __syncthreads_or(drain_out) || !ok;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float4 *o = out + (size_t)blockIdx.x * TC_PIX * 2;
-    if (failed) {
-        if (tid == 0) atomicExch(&g_tc_error, 1);
-    } else if (total_groups == 0) {
-        // no visibilities: the accumulators were never written
-        for (int pix = tid; pix < TC_PIX; pix += TC_NT) {
-            o[2 * pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-            o[2 * pix + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    } else {
-        for (int mt = warp >> 2; mt < TC_MT; mt += 2) {
-            const uint32_t taddr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(32 * mt);
-            uint32_t a[16], b[16];
-            tmem_ld16(taddr, a);          // hh | hl
-            tmem_ld16(taddr + 16, b);     // lh | ll
-            const int pix = mt * 128 + 32 * q4 + lane;
-            float s[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float v = (__uint_as_float(a[c]) + __uint_as_float(a[8 + c])) +
-                          (__uint_as_float(b[c]) + __uint_as_float(b[8 + c]));
-                if (n_folds) v += s_fold[c * TC_PIX + pix];
-                s[c] = v * inv_scale;
-            }
-            M22 P;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) P.m[c] = make_float2(s[2 * c], s[2 * c + 1]);
-            if (aterms) {
-                const size_t base = ((size_t)d.slot * g.n_stations) * TC_PIX;
-                const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * TC_PIX + pix));
-                const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * TC_PIX + pix));
-                P = herm_mul_mul(Ap, P, Aq);
-            }
-            const float tw = taper[pix];
-            o[2 * pix] = make_float4(tw * P.m[0].x, tw * P.m[0].y, tw * P.m[1].x, tw * P.m[1].y);
-            o[2 * pix + 1] = make_float4(tw * P.m[2].x, tw * P.m[2].y, tw * P.m[3].x, tw * P.m[3].y);
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(TC_COLS));
-}
-
-// ---------------------------------------------------------------------------
-// Warp-specialised form with the phasor operand in tensor memory.
-//
-// Eight producer warps form the phasors and write their FP16 hi/lo rows straight
-// into tensor memory (tcgen05.st; warp w owns lanes 32 (w % 4) ..); a ninth warp
-// issues the MMAs with A read from tensor memory.  Hand-off is by mbarriers, not
-// CTA barriers: full[h] (8 producer arrivals) -> MMAs -> commit -> empty[h].
-// Tensor memory per CTA (256 columns, two CTAs per SM):
-//   columns   0..127  accumulators, tile mt at 16 mt: E_hi [V_hi | V_lo] + E_lo [V_hi | V_lo]
-//   columns 128..255  two A stages of 4 tiles, tile lt of stage h at 128 + 64 h + 16 lt
-//                     (8 columns hi, 8 lo; column c holds k = 2c and 2c + 1)
-// The result is columns 0..7 + 8..15 of a tile.  Every WS_FOLD groups the
-// producers wait for the MMAs, add the accumulators into an FP32 sum in shared
-// memory and release the MMA warp (folded), which restarts them from zero.
-// After a failed (bounded) wait a thread skips every later wait, so control flow
-// stays uniform and the kernel ends; the error word is set and no output is written.
-
+constexpr int TC_PIX = TC_L * TC_L;              // 1024
+constexpr int B_TILE = kTile16;                  // 512 B: 16 rows x 16 FP16
+constexpr int FOLD_BYTES = 8 * TC_PIX * 4;       // [8][1024] FP32
 constexpr int WS_NP = 256;                       // producer threads
 constexpr int WS_NT = WS_NP + 32;                // + the MMA warp
 constexpr int WS_VB = 128;                       // visibilities per staged batch
 constexpr int WS_GROUPS = WS_VB / 8;
 constexpr int WS_FOLD = 16;                      // groups between folds (two accumulations per group)
 constexpr int WS_COLS = 256;
-constexpr int WS_B_BATCH = WS_GROUPS * B_TILE;   // 4 KB
+constexpr int WS_B_BATCH = WS_GROUPS * B_TILE;   // 8 KB
 constexpr int WS_SMEM = 2 * WS_B_BATCH + 2 * WS_VB * 16 + FOLD_BYTES;
 
-__device__ __forceinline__ void mma_f16_ta(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
-                 :: "r"(dtmem), "r"(atmem), "l"(db), "r"(kIdesc), "r"(acc) : "memory");
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
-                    "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-                    "r"(v[15])
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
-}
-
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WS_NP) : "memory"); }
-
-// a bounded wait that is skipped once this thread has seen a failure
-__device__ __forceinline__ void wait_or_fail(uint32_t bar, uint32_t parity, bool &failed) {
-    if (!failed && !mbar_wait(bar, parity)) failed = true;
-}
 
 __global__ void __launch_bounds__(WS_NT, 2)
 gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
@@ -493,8 +134,8 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
                     for (int lt = 0; lt < 4; ++lt) {
                         const uint32_t dt = tmem + (uint32_t)(16 * (4 * h + lt));
                         const uint32_t at = tmem + (uint32_t)(128 + 64 * h + 16 * lt);
-                        mma_f16_ta(dt, at, db, acc_hi);
-                        mma_f16_ta(dt, at + 8, db, 1u);
+                        mma_ta(dt, at, db, acc_hi);
+                        mma_ta(dt, at + 8, db, 1u);
                     }
                     commit(smem_u32(&s_empty[h]));
                 }
@@ -667,23 +308,6 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
 }
 
 }  // namespace
-
-size_t gridder_tc_smem() { return (size_t)2 * A_HALF + 2 * B_BATCH + FOLD_BYTES + 2 * TC_VB * sizeof(float4); }
-
-idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
-                             const void *aterms, const float *taper, void *out, void *stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (g.L != TC_L) return fail(IDG_ERR_UNSUPPORTED, "the tensor-core gridder is built for L = 32");
-    if (set.count <= 0) return IDG_OK;
-    const size_t smem = gridder_tc_smem();
-    cudaError_t e = cudaFuncSetAttribute(gridder_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core gridder smem attribute");
-    gridder_tc_kernel<<<(unsigned)set.count, TC_NT, smem, s>>>(g, set.idx, set.first, (const float4 *)vis, flags,
-                                                               (const float4 *)aterms, taper, (float4 *)out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core gridder launch");
-    return IDG_OK;
-}
 
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {

@@ -141,9 +141,7 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
                                 void *stream);
 
 // tensor-core gridder (L = 32; FP16 hi/lo split products, FP32 accumulation in
-// tensor memory) and the device error word of its bounded waits
-idg_status launch_gridder_tc(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
-                             const void *aterms, const float *taper, void *subgrids, void *stream);
+// tensor memory) and the device error word of the bounded waits
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);

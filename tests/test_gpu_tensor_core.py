@@ -19,7 +19,7 @@ from tests.gpu_util import dev, parity, workload_to_device
 
 pytestmark = pytest.mark.gpu
 
-TC_VARIANTS = ["tcgen05_fp16x3_nt256", "tcgen05_tmemA_ws_nt288"]
+TC_VARIANTS = ["tcgen05_tmemA_ws_nt288"]
 
 
 @pytest.fixture(scope="module", autouse=True)
