@@ -276,9 +276,15 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *                     (accumulated, as idg_grid)
  *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
  *                     into vis_out (overwritten; flagged and dropped -> 0)
- * No device scratch is used.  With IDG_BATCH_GRAPH the first call of each
- * direction captures its launch sequence into a CUDA graph, and later calls
- * replay it (the buffers are fixed by the batch, so the graph stays valid).
+ * For L = 32 the default batch variant ("tcgen05_unfused", IDG_KERNEL_BATCH_*)
+ * instead runs the tensor-core gridder (degridder) with one CTA per work item,
+ * the transform and an adder (splitter) as launches over chunks of at most
+ * 16384 items through a device scratch of the batch (512 MiB at most); a
+ * class whose visibilities lie mostly in subgrids of fewer than 512 takes the
+ * fused persistent kernel.  Otherwise no device scratch is used.  With
+ * IDG_BATCH_GRAPH the first call of each direction captures its launch
+ * sequence into a CUDA graph, and later calls replay it (the buffers are fixed
+ * by the batch, so the graph stays valid).
  * Supported: subgrid sizes 8, 16, 24, 32 and the direct phasor form.  The
  * plans and buffers must outlive the batch; calls on one batch must not
  * overlap (they share the work counters).
@@ -287,7 +293,8 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   vis_out  degridding output (may be NULL for a grid-only batch)
  *   flags    or NULL;  aterms  or NULL (identity);  taper (required)
  *   grid     gridding output (accumulated) / degridding input
- * idg_batch_info returns the planned visibilities, work items and launches.
+ * idg_batch_info returns the planned visibilities, work items and launches per
+ * direction (1 per fused class, 3 per chunk of a tensor-core class).
  */
 typedef struct idg_batch idg_batch;
 typedef struct {

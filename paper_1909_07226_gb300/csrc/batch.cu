@@ -17,20 +17,11 @@
 #include <vector>
 
 #include "degridder_impl.cuh"
+#include "batch_jobs.cuh"
 #include "fft_impl.cuh"
 #include "gridder_impl.cuh"
 
 namespace idg {
-
-struct JobDev {
-    Geometry g;
-    const float4 *vis;
-    float4 *vis_out;
-    const uint8_t *flags;
-    const float4 *aterms;
-    const float *taper;
-    float4 *grid;
-};
 
 namespace {
 
@@ -285,10 +276,51 @@ size_t degrid_smem() {
 
 struct KernelShape {
     const char *name;
-    const void *fn;
+    const void *fn;      // persistent fused kernel, or null for the tensor-core path
     int threads;
     size_t smem;
+    bool tc = false;     // unfused tensor-core path: sum, transform and adder/splitter as launches per chunk
 };
+
+// L = 32 on the tensor cores: per chunk of the class's work items, the
+// tensor-core gridder (degridder) with one CTA per item, the shared-memory
+// transform, and the adder (splitter) below
+const KernelShape kTcShape = {"tcgen05_unfused", nullptr, 288, 0, true};
+
+// the adder and splitter of Algorithms 1 and 2 over work items; subgrid b of the launch at sub + b L^2
+__global__ void __launch_bounds__(256)
+batch_adder_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
+                   const float4 *__restrict__ sub) {
+    const int2 it = items[first + blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    const DevSubgrid d = J.g.sub[it.y];
+    const int L = J.g.L, N = J.g.N;
+    const float4 *src = sub + (size_t)blockIdx.x * L * L * 2;
+    float4 *dst = J.grid + (size_t)d.layer * N * N * 2;
+    for (int pix = threadIdx.x; pix < L * L; pix += 256) {
+        const int i = pix / L, j = pix - (pix / L) * L;
+        const size_t gp = (size_t)(d.r0 + i) * N + (d.q0 + j);
+        atomicAdd(dst + 2 * gp, src[2 * pix]);
+        atomicAdd(dst + 2 * gp + 1, src[2 * pix + 1]);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+batch_splitter_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
+                      float4 *__restrict__ sub) {
+    const int2 it = items[first + blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    const DevSubgrid d = J.g.sub[it.y];
+    const int L = J.g.L, N = J.g.N;
+    float4 *out = sub + (size_t)blockIdx.x * L * L * 2;
+    const float4 *src = J.grid + (size_t)d.layer * N * N * 2;
+    for (int pix = threadIdx.x; pix < L * L; pix += 256) {
+        const int i = pix / L, j = pix - (pix / L) * L;
+        const size_t gp = (size_t)(d.r0 + i) * N + (d.q0 + j);
+        out[2 * pix] = src[2 * gp];
+        out[2 * pix + 1] = src[2 * gp + 1];
+    }
+}
 
 template <int L, int NPX, int MINB>
 KernelShape gshape(const char *name) {
@@ -306,8 +338,8 @@ std::vector<KernelShape> grid_shapes(int L) {
     case 8: return {gshape<8, 1, 4>("npx1_minb4"), gshape<8, 2, 6>("npx2_minb6")};
     case 16: return {gshape<16, 2, 2>("npx2_minb2"), gshape<16, 2, 4>("npx2_minb4"), gshape<16, 4, 4>("npx4_minb4")};
     case 24: return {gshape<24, 3, 2>("npx3_minb2"), gshape<24, 3, 3>("npx3_minb3"), gshape<24, 6, 4>("npx6_minb4")};
-    case 32: return {gshape<32, 8, 4>("npx8_minb4"), gshape<32, 4, 3>("npx4_minb3"), gshape<32, 4, 2>("npx4_minb2"),
-                     gshape<32, 2, 2>("npx2_minb2")};
+    case 32: return {kTcShape, gshape<32, 8, 4>("npx8_minb4"), gshape<32, 4, 3>("npx4_minb3"),
+                     gshape<32, 4, 2>("npx4_minb2"), gshape<32, 2, 2>("npx2_minb2")};
     }
     return {};
 }
@@ -319,7 +351,7 @@ std::vector<KernelShape> degrid_shapes(int L) {
                      dshape<16, 2, 256, 3>("nv2_nt256_minb3")};
     case 24: return {dshape<24, 4, 128, 3>("nv4_nt128_minb3"), dshape<24, 4, 256, 2>("nv4_nt256_minb2"),
                      dshape<24, 2, 256, 3>("nv2_nt256_minb3")};
-    case 32: return {dshape<32, 4, 128, 2>("nv4_nt128_minb2"), dshape<32, 4, 128, 3>("nv4_nt128_minb3"),
+    case 32: return {kTcShape, dshape<32, 4, 128, 2>("nv4_nt128_minb2"), dshape<32, 4, 128, 3>("nv4_nt128_minb3"),
                      dshape<32, 4, 256, 2>("nv4_nt256_minb2"), dshape<32, 2, 256, 3>("nv2_nt256_minb3")};
     }
     return {};
@@ -358,6 +390,8 @@ struct idg_batch {
     std::vector<std::pair<void *, size_t>> zero_on_degrid;   // vis_out of jobs with dropped samples
     cudaGraphExec_t graph_grid = nullptr, graph_degrid = nullptr;
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are recorded on
+    void *tc_scratch = nullptr;              // subgrids of one chunk of the tensor-core path
+    int64_t tc_chunk = 0;                    // subgrids per chunk
 };
 
 static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
@@ -372,6 +406,32 @@ static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
         auto &cl = b->classes[c];
         if (cl.n_items == 0) continue;
         const KernelShape &ks = degrid ? cl.degrid : cl.grid;
+        if (ks.tc) {
+            ProfileScope ps(degrid ? IDG_KERNEL_BATCH_DEGRID : IDG_KERNEL_BATCH_GRID, s, cl.vispix);
+            for (int64_t f = 0; f < cl.n_items; f += b->tc_chunk) {
+                const int64_t cnt = std::min(b->tc_chunk, cl.n_items - f);
+                idg_status st;
+                if (!degrid) {
+                    st = launch_gridder_tcw_batch(b->d_jobs, cl.d_items, f, cnt, b->tc_scratch, s);
+                    if (st == IDG_OK) st = launch_fft(cl.L, cnt, -1, b->tc_scratch, s);
+                    if (st == IDG_OK) {
+                        batch_adder_kernel<<<(unsigned)cnt, 256, 0, s>>>(b->d_jobs, cl.d_items, f,
+                                                                       (const float4 *)b->tc_scratch);
+                        e = cudaGetLastError();
+                        if (e != cudaSuccess) st = cuda_fail(e, "batch adder launch");
+                    }
+                } else {
+                    batch_splitter_kernel<<<(unsigned)cnt, 256, 0, s>>>(b->d_jobs, cl.d_items, f,
+                                                                      (float4 *)b->tc_scratch);
+                    e = cudaGetLastError();
+                    st = e == cudaSuccess ? IDG_OK : cuda_fail(e, "batch splitter launch");
+                    if (st == IDG_OK) st = launch_fft(cl.L, cnt, +1, b->tc_scratch, s);
+                    if (st == IDG_OK) st = launch_degridder_tcw_batch(b->d_jobs, cl.d_items, f, cnt, b->tc_scratch, s);
+                }
+                if (st != IDG_OK) return st;
+            }
+            continue;
+        }
         const int blocks = degrid ? cl.degrid_blocks : cl.grid_blocks;
         const JobDev *jobs = b->d_jobs;
         const int2 *items = cl.d_items;
@@ -446,6 +506,7 @@ void idg_batch_destroy(idg_batch *b) {
     if (b->graph_degrid) cudaGraphExecDestroy(b->graph_degrid);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     for (auto &c : b->classes) cudaFree(c.d_items);
+    cudaFree(b->tc_scratch);
     cudaFree(b->d_jobs);
     cudaFree(b->d_counters);
     if (prev >= 0) cudaSetDevice(prev);
@@ -512,6 +573,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         }
     }
     idg_status st = IDG_OK;
+    int64_t need_tc = 0;                          // items of the largest tensor-core class
     for (size_t c = 0; c < b->classes.size() && st == IDG_OK; ++c) {
         auto &items = per_class[c];
         // cost order: most visibilities first, ties by job and subgrid
@@ -526,9 +588,30 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
             if (e == cudaSuccess) e = cudaMemcpy(cl.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = cuda_fail(e, "batch work list");
         }
+        // the tensor-core path pays a fixed cost per subgrid: classes whose
+        // visibilities sit mostly in subgrids of fewer than 512 take the fused kernels
+        int64_t small = 0, all = 0;
+        for (const int2 &it : items) {
+            const int64_t kp = plans[it.x]->kp_plan[it.y];
+            all += kp;
+            if (kp < 512) small += kp;
+        }
+        for (int k = 0; k < 2; ++k) {
+            KernelShape &ks = k ? cl.degrid : cl.grid;
+            if (ks.tc && 2 * small > all) {
+                auto alt = k ? degrid_shapes(cl.L) : grid_shapes(cl.L);
+                for (const KernelShape &x : alt)
+                    if (!x.tc) {
+                        ks = x;
+                        break;
+                    }
+            }
+            if (ks.tc) need_tc = std::max(need_tc, cl.n_items);
+        }
         // persistent grid: resident CTAs per SM x SMs, never more than the items
         for (int k = 0; k < 2 && st == IDG_OK; ++k) {
             KernelShape &ks = k ? cl.degrid : cl.grid;
+            if (ks.tc) continue;
             e = cudaFuncSetAttribute(ks.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks.smem);
             int per_sm = 0;
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.fn, ks.threads, ks.smem);
@@ -539,6 +622,12 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
             const int64_t blocks = std::min<int64_t>(std::max(1, per_sm) * (int64_t)n_sm, std::max<int64_t>(1, cl.n_items));
             (k ? cl.degrid_blocks : cl.grid_blocks) = (int)blocks;
         }
+    }
+    if (st == IDG_OK && need_tc > 0) {
+        b->tc_chunk = std::min<int64_t>(need_tc, 16384);      // 512 MiB of L = 32 subgrids
+        e = cudaMalloc(&b->tc_scratch, (size_t)b->tc_chunk * 32 * 32 * 32);
+        if (e == cudaSuccess) e = prepare_tcw_batch_kernels();
+        if (e != cudaSuccess) st = cuda_fail(e, "batch tensor-core scratch");
     }
     if (st == IDG_OK) {
         e = cudaMalloc(&b->d_jobs, sizeof(JobDev) * hj.size());
@@ -564,7 +653,9 @@ idg_status idg_batch_info(const idg_batch *b, int64_t *n_vis, int64_t *n_items, 
     int launches = 0;
     for (auto &c : b->classes) {
         items += c.n_items;
-        launches += c.n_items > 0 ? 1 : 0;
+        if (c.n_items == 0) continue;
+        // the tensor-core path (grid shape) launches sum, transform and adder per chunk
+        launches += c.grid.tc ? 3 * (int)((c.n_items + b->tc_chunk - 1) / b->tc_chunk) : 1;
     }
     if (n_vis) *n_vis = b->n_vis;
     if (n_items) *n_items = items;

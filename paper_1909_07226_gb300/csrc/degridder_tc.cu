@@ -29,6 +29,7 @@
 // block's visibilities are written then.  Waits are bounded;
 // after a failed wait a thread skips every later wait, the error word is set
 // and no output is written.
+#include "batch_jobs.cuh"
 #include "degridder_impl.cuh"
 #include "tc_common.cuh"
 
@@ -54,10 +55,11 @@ constexpr int DCOLS = 256;
 constexpr int D_B_BYTES = (2 * DPIX / 16) * kTile16;   // 128 K chunks of 8 pixels = 64 KB
 constexpr int D_SMEM = D_B_BYTES + DPIX * 4;            // + n'
 
-__global__ void __launch_bounds__(DNT, 2)
-degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ sub,
-                     const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
-                     const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+// Visibilities of subgrid d of geometry g from its image src[L][L][4].
+__device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevSubgrid d,
+                                                   const float4 *__restrict__ src, const uint8_t *__restrict__ flags,
+                                                   const float4 *__restrict__ aterms, const float *__restrict__ taper,
+                                                   float4 *__restrict__ vis_out) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;                               // P operand, chunk c (pixels 8c .. 8c + 7) at c * 512
     float *s_np = (float *)(smem + D_B_BYTES);        // n' per pixel
@@ -67,11 +69,8 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool mma_warp = warp == 8;
-    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    const DevSubgrid d = g.sub[sid];
     const int nblk = (d.kp + DBLK - 1) / DBLK;
     const int total_steps = nblk * DSTEPS;
-    const float4 *src = sub + (size_t)blockIdx.x * DPIX * 2;
 
     if (mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -293,7 +292,44 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
     if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(DCOLS));
 }
 
+// one CTA per subgrid of one plan (plan index idx[b] or first + b; image b of sub)
+__global__ void __launch_bounds__(DNT, 2)
+degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ sub,
+                     const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                     const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    degridder_tcw_body(g, g.sub[sid], sub + (size_t)blockIdx.x * DPIX * 2, flags, aterms, taper, vis_out);
+}
+
+// one CTA per work item (job, subgrid) of a batch; image b of sub
+__global__ void __launch_bounds__(DNT, 2)
+degridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
+                           const float4 *__restrict__ sub) {
+    const int2 it = items[first + blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    degridder_tcw_body(J.g, J.g.sub[it.y], sub + (size_t)blockIdx.x * DPIX * 2, J.flags, J.aterms, J.taper,
+                       J.vis_out);
+}
+
 }  // namespace
+
+cudaError_t prepare_tcw_batch_kernels() {
+    cudaError_t e = prepare_gridder_tcw_batch();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(degridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM);
+    return e;
+}
+
+// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
+idg_status launch_degridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t first, int64_t count,
+                                      const void *sub, void *stream) {
+    if (count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    degridder_tcw_batch_kernel<<<(unsigned)count, DNT, D_SMEM, s>>>(jobs, items, first, (const float4 *)sub);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch degridder launch");
+    return IDG_OK;
+}
 
 idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {

@@ -31,6 +31,7 @@
 // from zero.  Every wait is bounded; after a failed wait a thread skips every
 // later wait, so control flow stays uniform and the kernel ends; the error word
 // is set and no output is written.
+#include "batch_jobs.cuh"
 #include "device_common.cuh"
 #include "tc_common.cuh"
 
@@ -60,10 +61,11 @@ constexpr int WS_SMEM = 2 * WS_B_BATCH + 2 * WS_VB * 16 + FOLD_BYTES;
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WS_NP) : "memory"); }
 
-__global__ void __launch_bounds__(WS_NT, 2)
-gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
-                   const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
-                   const float *__restrict__ taper, float4 *__restrict__ out) {
+// One subgrid d of geometry g into o[L][L][4] (taper and A-terms applied).
+__device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSubgrid d,
+                                                 const float4 *__restrict__ vis, const uint8_t *__restrict__ flags,
+                                                 const float4 *__restrict__ aterms, const float *__restrict__ taper,
+                                                 float4 *__restrict__ o) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;                                         // 2 batches x 4 KB
     float4 *s_coef = (float4 *)(smem + 2 * WS_B_BATCH);         // 2 batches x 64
@@ -74,8 +76,6 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool mma_warp = warp == 8;
-    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    const DevSubgrid d = g.sub[sid];
     const int total_groups = (d.kp + 7) / 8;
     const int n_batches = (d.kp + WS_VB - 1) / WS_VB;
 
@@ -273,7 +273,6 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
         if (failed) {
             if (lane == 0) atomicExch(&g_tc_error, 1);
         } else {
-            float4 *o = out + (size_t)blockIdx.x * TC_PIX * 2;
 #pragma unroll
             for (int s4 = 0; s4 < 4; ++s4) {
                 const int pix = PIX[s4];
@@ -307,7 +306,40 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
     if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(WS_COLS));
 }
 
+// one CTA per subgrid of one plan (plan index idx[b] or first + b)
+__global__ void __launch_bounds__(WS_NT, 2)
+gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
+                   const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                   const float *__restrict__ taper, float4 *__restrict__ out) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    gridder_tcw_body(g, g.sub[sid], vis, flags, aterms, taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+}
+
+// one CTA per work item (job, subgrid) of a batch
+__global__ void __launch_bounds__(WS_NT, 2)
+gridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
+                         float4 *__restrict__ out) {
+    const int2 it = items[first + blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    gridder_tcw_body(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+}
+
 }  // namespace
+
+cudaError_t prepare_gridder_tcw_batch() {
+    return cudaFuncSetAttribute(gridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
+}
+
+// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
+idg_status launch_gridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t first, int64_t count, void *out,
+                                    void *stream) {
+    if (count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    gridder_tcw_batch_kernel<<<(unsigned)count, WS_NT, WS_SMEM, s>>>(jobs, items, first, (float4 *)out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch gridder launch");
+    return IDG_OK;
+}
 
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {

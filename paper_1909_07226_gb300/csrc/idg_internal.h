@@ -149,6 +149,13 @@ idg_status read_device_errors(int *code, void *stream);
 idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *subgrids, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream);
 idg_status read_tcd_error(int *code);
+// the same two kernels over the (job, subgrid) work items [first, first + count) of
+// a batch (jobs: device job table, see batch_jobs.cuh); subgrid b of the launch at b
+struct JobDev;
+idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t first, int64_t count,
+                                    void *subgrids, void *stream);
+idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t first, int64_t count,
+                                      const void *subgrids, void *stream);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);

@@ -48,6 +48,7 @@ def test_batch_grid_and_degrid_match_the_oracle(graph):
                          vis_out=torch.full(w.vis.shape, 5.0 + 5.0j, dtype=torch.complex64, device="cuda")))
     b = idg.Batch(plans, jobs, graph=graph)
     info = b.info()
+    # one fused launch per subgrid size (the L = 32 job has only small subgrids)
     assert info["n_launches"] == 4 and info["n_items"] == sum(p.n_subgrids for p in plans)
     for rep in range(2):                 # second pass replays the captured graph
         for j in jobs:
@@ -78,3 +79,43 @@ def test_batch_rejects_unsupported_jobs():
     d = workload_to_device(wl)
     with pytest.raises(idg.IDGError):
         idg.Batch([p], [dict(vis=d["vis"], taper=d["taper"])])
+
+
+def _big_l32_jobs():
+    # L = 32 jobs with K_p up to 1024, so the class runs on the tensor-core path
+    # (the W-layered job adds partial tiles: 28 % of the class's visibilities lie in subgrids below 512)
+    return [syn.make_small(seed=320 + i, n_st=5 + i, n_t=64, n_chan=16, L=32, N=256, max_t=64, flag_p=0.05 * i,
+                           diameter_m=3000.0 + 1000.0 * i, w_step=20.0 * (i == 2), n_slots=2) for i in range(3)]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_tensor_core_class_matches_the_oracle(graph):
+    import torch
+    wls = _big_l32_jobs()
+    plans = [idg.plan_from_workload(w) for w in wls]
+    ops = [O.plan(w) for w in wls]
+    rng = np.random.default_rng(21)
+    jobs, models = [], []
+    for w, p in zip(wls, plans):
+        d = workload_to_device(w)
+        models.append(syn.random_grid(rng, p.n_w_layers, w.grid_size))
+        jobs.append(dict(vis=d["vis"], flags=d["flags"], aterms=d["aterms"], taper=d["taper"],
+                         grid=torch.zeros((p.n_w_layers, w.grid_size, w.grid_size, 4), dtype=torch.complex64,
+                                          device="cuda"),
+                         vis_out=torch.full(w.vis.shape, 5.0 + 5.0j, dtype=torch.complex64, device="cuda")))
+    b = idg.Batch(plans, jobs, graph=graph)
+    assert b.info()["n_launches"] == 3       # sum, transform, adder: the tensor-core path
+    for rep in range(2):
+        for j in jobs:
+            j["grid"].zero_()
+        b.grid()
+        idg.device_errors()
+        for i, (w, op, j) in enumerate(zip(wls, ops, jobs)):
+            parity(j["grid"].cpu().numpy(), O.grid(w, op), f"tc batch grid job {i} pass {rep}")
+    djobs = [dict(j, grid=dev(m), vis=None) for j, m in zip(jobs, models)]
+    bd = idg.Batch(plans, djobs, graph=graph)
+    for rep in range(2):
+        bd.degrid()
+        idg.device_errors()
+        for i, (w, op, j, m) in enumerate(zip(wls, ops, djobs, models)):
+            parity(j["vis_out"].cpu().numpy(), O.degrid(w, op, m), f"tc batch degrid job {i} pass {rep}")
