@@ -248,6 +248,7 @@ void idg_plan_destroy(idg_plan *p) {
     if (p->device >= 0) cudaSetDevice(p->device);
     cudaFree(p->d_sub);
     cudaFree(p->d_order);
+    cudaFree(p->d_span_order);
     cudaFree(p->d_uvw);
     cudaFree(p->d_scale);
     cudaFree(p->d_nprime);
@@ -390,6 +391,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         g.w0 = w_step > 0.0 ? (double)(g.layer + pr.k_min) * w_step : 0.0;
         g.pad = 0.0;
     }
+    std::vector<int32_t> span_order;
     // device work order: most visibilities first (longest-processing-time first
     // for the block scheduler), ties in plan order
     std::vector<int32_t> order((size_t)std::max<int64_t>(n_sub, 1));
@@ -402,6 +404,43 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     for (int64_t s = 0; s < n_sub; ++s) {
         p->kp_order[s] = hsub[order[s]].kp;
         p->kp_prefix_order[s + 1] = p->kp_prefix_order[s] + p->kp_order[s];
+    }
+    // spans of whole baselines for the host-buffer calls (about 256 MB of
+    // visibilities each, at least 4; the first and last cut to a quarter so the
+    // copy pipeline fills and drains sooner), each span's subgrids by K_p descending
+    {
+        const int64_t vis_bytes = (int64_t)n_bl * n_t * n_chan * 32;
+        int nk = (int)std::min<int64_t>(16, std::max<int64_t>(4, vis_bytes / (256ll << 20)));
+        std::vector<double> frac;
+        for (int k = 0; k <= nk; ++k) frac.push_back((double)k / nk);
+        frac.insert(frac.begin() + 1, 0.25 / nk);
+        frac.insert(frac.end() - 1, 1.0 - 0.25 / nk);
+        bool sorted_bl = true;                   // the planner emits baseline-major order; otherwise one span
+        for (int64_t s = 1; s < n_sub; ++s)
+            if (hsub[s].bl < hsub[s - 1].bl) sorted_bl = false;
+        if (!sorted_bl) frac = {0.0, 1.0};
+        int64_t i = 0;
+        int32_t last_b = -1;
+        for (size_t k = 0; k < frac.size(); ++k) {
+            const int32_t b = (int32_t)std::llround(frac[k] * n_bl);
+            if (b == last_b) continue;           // spans of at least one baseline
+            while (i < n_sub && hsub[i].bl < b) ++i;
+            p->span_first.push_back(k + 1 == frac.size() ? n_sub : i);
+            p->span_bl.push_back(b);
+            last_b = b;
+        }
+        std::vector<int32_t> so((size_t)std::max<int64_t>(n_sub, 1));
+        std::iota(so.begin(), so.begin() + n_sub, 0);
+        for (size_t k = 0; k + 1 < p->span_first.size(); ++k)
+            std::stable_sort(so.begin() + p->span_first[k], so.begin() + p->span_first[k + 1],
+                             [&](int32_t a, int32_t b) { return hsub[a].kp > hsub[b].kp; });
+        p->kp_span_order.assign((size_t)n_sub, 0);
+        p->kp_prefix_span.assign((size_t)n_sub + 1, 0);
+        for (int64_t s = 0; s < n_sub; ++s) {
+            p->kp_span_order[s] = hsub[so[s]].kp;
+            p->kp_prefix_span[s + 1] = p->kp_prefix_span[s] + p->kp_span_order[s];
+        }
+        span_order.swap(so);
     }
     std::vector<double> scale(n_chan);
     for (int c = 0; c < n_chan; ++c) scale[c] = freqs_hz[c] / kSpeedOfLight;
@@ -417,6 +456,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     Up ups[] = {
         {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
         {(void **)&p->d_order, order.data(), sizeof(int32_t) * order.size(), "work order"},
+        {(void **)&p->d_span_order, span_order.data(), sizeof(int32_t) * span_order.size(), "span order"},
         {(void **)&p->d_uvw, uvw_m, sizeof(double) * n_uvw, "uvw"},
         {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
         {(void **)&p->d_nprime, nprime.data(), sizeof(float) * nprime.size(), "n' table"},
@@ -468,10 +508,21 @@ static SubgridSet order_set(const idg_plan *p, int64_t first, int64_t count) {
 static SubgridSet plan_set(const idg_plan *p, int64_t first, int64_t count) {
     return SubgridSet{nullptr, first, count, p->kp_plan.data() + first};
 }
+static SubgridSet span_set(const idg_plan *p, int64_t first, int64_t count) {
+    return SubgridSet{p->d_span_order + first, 0, count, p->kp_span_order.data() + first};
+}
 
-// algorithmic work of a launch over subgrids [first, first + count)
-static double vispix(const idg_plan *p, int64_t first, int64_t count, bool use_order) {
-    const auto &pre = use_order ? p->kp_prefix_order : p->kp_prefix_plan;
+// positions of a launch: in the work order, in plan order, or in the span order
+enum class Order { Work, Plan, Span };
+
+static SubgridSet order_of(const idg_plan *p, Order o, int64_t first, int64_t count) {
+    return o == Order::Work ? order_set(p, first, count)
+                            : o == Order::Plan ? plan_set(p, first, count) : span_set(p, first, count);
+}
+
+// algorithmic work of a launch over positions [first, first + count)
+static double vispix(const idg_plan *p, int64_t first, int64_t count, Order o) {
+    const auto &pre = o == Order::Work ? p->kp_prefix_order : o == Order::Plan ? p->kp_prefix_plan : p->kp_prefix_span;
     return (double)(pre[first + count] - pre[first]) * p->L * p->L;
 }
 static double pixels(const idg_plan *p, int64_t count) { return (double)count * p->L * p->L; }
@@ -482,18 +533,18 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
     return IDG_OK;
 }
 
-// Grid the subgrids [first, first + count): positions in the work order
-// (use_order) or plan indices, in pieces of at most `chunk` subgrids that pass
-// through the subgrid scratch (gridder -> transform -> adder).
-static idg_status grid_span(const idg_plan *p, const Geometry &g, bool use_order, int64_t first, int64_t count,
+// Grid the subgrids at positions [first, first + count) of the order o, in
+// pieces of at most `chunk` subgrids that pass through the subgrid scratch
+// (gridder -> transform -> adder).
+static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                             void *scratch, int64_t chunk, const void *vis, const uint8_t *flags, const void *aterms,
                             const float *taper, void *grid, void *cbuf, cudaStream_t s) {
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
         const int64_t cnt = std::min(chunk, first + count - f);
-        const SubgridSet set = use_order ? order_set(p, f, cnt) : plan_set(p, f, cnt);
+        const SubgridSet set = order_of(p, o, f, cnt);
         {
-            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, f, cnt, use_order));
+            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, f, cnt, o));
             st = launch_gridder(g, set, -1, vis, flags, aterms, taper, scratch, s);
         }
         if (st == IDG_OK) {
@@ -509,13 +560,13 @@ static idg_status grid_span(const idg_plan *p, const Geometry &g, bool use_order
 }
 
 // Degrid the subgrids [first, first + count) (splitter -> transform -> degridder).
-static idg_status degrid_span(const idg_plan *p, const Geometry &g, bool use_order, int64_t first, int64_t count,
+static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                               void *scratch, int64_t chunk, const void *grid, const uint8_t *flags, const void *aterms,
                               const float *taper, void *vis_out, cudaStream_t s) {
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
         const int64_t cnt = std::min(chunk, first + count - f);
-        const SubgridSet set = use_order ? order_set(p, f, cnt) : plan_set(p, f, cnt);
+        const SubgridSet set = order_of(p, o, f, cnt);
         {
             ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
             st = launch_splitter(g, set, grid, scratch, s);
@@ -525,7 +576,7 @@ static idg_status degrid_span(const idg_plan *p, const Geometry &g, bool use_ord
             st = launch_subgrid_fft(p, cnt, +1, scratch, s);
         }
         if (st == IDG_OK) {
-            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, f, cnt, use_order));
+            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, f, cnt, o));
             st = launch_degridder(g, set, -1, scratch, flags, aterms, taper, vis_out, s);
         }
     }
@@ -555,7 +606,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
             if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(compensation)");
         }
     }
-    if (st == IDG_OK) st = grid_span(p, g, true, 0, n, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
+    if (st == IDG_OK) st = grid_span(p, g, Order::Work, 0, n, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
     if (comp && cbuf) {
         if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
         cudaFreeAsync(cbuf, s);
@@ -581,7 +632,7 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
     void *scratch = nullptr;
     st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
-    st = degrid_span(p, p->geometry(), true, 0, n, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
+    st = degrid_span(p, p->geometry(), Order::Work, 0, n, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
     cudaError_t e = cudaFreeAsync(scratch, s);
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
     return st;
@@ -634,34 +685,6 @@ idg_status copy_stream(int dev, cudaStream_t *out) {
     return IDG_OK;
 }
 
-// spans of whole baselines: plan index bounds first[k] .. first[k + 1], baselines bl[k] .. bl[k + 1]
-struct Spans {
-    std::vector<int64_t> first;
-    std::vector<int32_t> bl;
-};
-
-Spans baseline_spans(const idg_plan *p) {
-    const int64_t vis_bytes = (int64_t)p->n_bl * p->n_t * p->n_chan * 32;
-    int nk = (int)std::min<int64_t>(16, std::max<int64_t>(4, vis_bytes / (256ll << 20)));   // ~256 MB spans
-    nk = std::min(nk, p->n_bl);
-    const int64_t n = p->stats.n_subgrids;
-    auto bl_of = [&](int64_t i) { return p->desc[(size_t)i * kDescFields + IDG_DESC_BASELINE]; };
-    for (int64_t i = 1; i < n; ++i)      // the planner emits baseline-major order; otherwise one span
-        if (bl_of(i) < bl_of(i - 1)) {
-            nk = 1;
-            break;
-        }
-    Spans sp;
-    int64_t i = 0;
-    for (int k = 0; k <= nk; ++k) {
-        const int32_t b = (int32_t)((int64_t)p->n_bl * k / nk);
-        while (i < n && bl_of(i) < b) ++i;
-        sp.first.push_back(k == nk ? n : i);
-        sp.bl.push_back(b);
-    }
-    return sp;
-}
-
 idg_status h2d(void *d, const void *h, size_t bytes, cudaStream_t cs, const char *what) {
     if (!h || !bytes) return IDG_OK;
     cudaError_t e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, cs);
@@ -701,10 +724,11 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     if (e != cudaSuccess) return cuda_fail(e, "grid_host setup");
     if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
     if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
-    const Spans sp = baseline_spans(p);
+    const auto &sf = p->span_first;
+    const auto &sb = p->span_bl;
     const Geometry g = p->geometry();
-    for (size_t k = 0; k + 1 < sp.first.size() && st == IDG_OK; ++k) {
-        const size_t v0 = (size_t)sp.bl[k] * per_bl, nv = (size_t)(sp.bl[k + 1] - sp.bl[k]) * per_bl;
+    for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
+        const size_t v0 = (size_t)sb[k] * per_bl, nv = (size_t)(sb[k + 1] - sb[k]) * per_bl;
         st = h2d((char *)b.ptr[0] + v0 * 32, (const char *)h_vis + v0 * 32, nv * 32, cs, "copy of visibilities");
         if (st == IDG_OK && h_flags)
             st = h2d((char *)b.ptr[1] + v0, h_flags + v0, nv, cs, "copy of flags");
@@ -712,8 +736,8 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
         if (st == IDG_OK && (e = ev.add(&e_up)) == cudaSuccess && (e = cudaEventRecord(e_up, cs)) == cudaSuccess)
             e = cudaStreamWaitEvent(s, e_up, 0);
         if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
-        if (st == IDG_OK && sp.first[k + 1] > sp.first[k])
-            st = grid_span(p, g, false, sp.first[k], sp.first[k + 1] - sp.first[k], b.ptr[5], chunk, b.ptr[0],
+        if (st == IDG_OK && sf[k + 1] > sf[k])
+            st = grid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
                            (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], b.ptr[6], s);
     }
     if (st == IDG_OK && comp) st = launch_fold_compensation(b.ptr[4], b.ptr[6], grid_f4, s);
@@ -763,18 +787,19 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_in, 0);
     if (e == cudaSuccess && p->any_dropped) e = cudaMemsetAsync(b.ptr[4], 0, nvis * 32, s);
     if (e != cudaSuccess) return cuda_fail(e, "degrid_host inputs");
-    const Spans sp = baseline_spans(p);
+    const auto &sf = p->span_first;
+    const auto &sb = p->span_bl;
     const Geometry g = p->geometry();
-    for (size_t k = 0; k + 1 < sp.first.size() && st == IDG_OK; ++k) {
-        if (sp.first[k + 1] > sp.first[k])
-            st = degrid_span(p, g, false, sp.first[k], sp.first[k + 1] - sp.first[k], b.ptr[5], chunk, b.ptr[0],
+    for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
+        if (sf[k + 1] > sf[k])
+            st = degrid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
                              (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], s);
         cudaEvent_t e_done;
         if (st == IDG_OK && (e = ev.add(&e_done)) == cudaSuccess && (e = cudaEventRecord(e_done, s)) == cudaSuccess)
             e = cudaStreamWaitEvent(cs, e_done, 0);
         if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
         if (st == IDG_OK) {
-            const size_t v0 = (size_t)sp.bl[k] * per_bl, nv = (size_t)(sp.bl[k + 1] - sp.bl[k]) * per_bl;
+            const size_t v0 = (size_t)sb[k] * per_bl, nv = (size_t)(sb[k + 1] - sb[k]) * per_bl;
             e = cudaMemcpyAsync((char *)h_vis_out + v0 * 32, (const char *)b.ptr[4] + v0 * 32, nv * 32,
                                 cudaMemcpyDeviceToHost, cs);
             if (e != cudaSuccess) st = cuda_fail(e, "copy of the visibilities to the host");
@@ -799,7 +824,7 @@ idg_status idg_grid_subgrids(const idg_plan *p, int64_t first, int64_t count, co
     if (st != IDG_OK) return st;
     if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
-    ProfileScope ps(IDG_KERNEL_GRIDDER, stream, vispix(p, first, count, false));
+    ProfileScope ps(IDG_KERNEL_GRIDDER, stream, vispix(p, first, count, Order::Plan));
     return launch_gridder(p->geometry(), plan_set(p, first, count), -1, vis, flags, aterms, taper, sub, stream);
 }
 
@@ -838,7 +863,7 @@ idg_status idg_degrid_subgrids(const idg_plan *p, int64_t first, int64_t count, 
     if (st != IDG_OK) return st;
     if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
-    ProfileScope ps(IDG_KERNEL_DEGRIDDER, stream, vispix(p, first, count, false));
+    ProfileScope ps(IDG_KERNEL_DEGRIDDER, stream, vispix(p, first, count, Order::Plan));
     return launch_degridder(p->geometry(), plan_set(p, first, count), -1, sub, flags, aterms, taper, vis_out,
                             stream);
 }

@@ -80,6 +80,14 @@ struct idg_plan {
     std::vector<int32_t> kp_plan;           // [n_sub] K_p in plan order
     std::vector<int32_t> kp_order;          // [n_sub] K_p in device work order (non-increasing)
     std::vector<int32_t> order;             // [n_sub] plan index of each work-order slot (host copy)
+    // spans of whole baselines for the host-buffer calls: span k holds plan indices
+    // [span_first[k], span_first[k + 1]) and baselines [span_bl[k], span_bl[k + 1]);
+    // span_order lists each span's subgrids by K_p descending (positions as in plan order)
+    std::vector<int64_t> span_first;
+    std::vector<int32_t> span_bl;
+    int32_t *d_span_order = nullptr;
+    std::vector<int32_t> kp_span_order;
+    std::vector<int64_t> kp_prefix_span;
 
     idg::Geometry geometry() const;
 };
