@@ -14,8 +14,9 @@
 // visibilities (K = 16): E_hi [V_hi | V_lo] and E_lo [V_hi | V_lo] into the
 // same accumulator, whose columns 0..7 + 8..15 are the result.  The tensor
 // cores accumulate in FP32 without rounding to nearest (each step can lose up
-// to an ulp, biased towards zero), so every WS_FOLD groups the accumulators are
-// added into an FP32 sum in shared memory and restarted.
+// to an ulp, biased towards zero), so every WS_FOLD groups (256 visibilities,
+// one staged batch, so that the fold and the batch barrier fall together) the
+// accumulators are added into an FP32 sum in shared memory and restarted.
 //
 // Schedule.  One CTA per subgrid: eight producer warps form the phasors and
 // write their FP16 hi/lo rows straight into tensor memory (tcgen05.st; warp w
@@ -52,11 +53,11 @@ constexpr int B_TILE = kTile16;                  // 512 B: 16 rows x 16 FP16
 constexpr int FOLD_BYTES = 8 * TC_PIX * 4;       // [8][1024] FP32
 constexpr int WS_NP = 256;                       // producer threads
 constexpr int WS_NT = WS_NP + 32;                // + the MMA warp
-constexpr int WS_VB = 128;                       // visibilities per staged batch
+constexpr int WS_VB = 256;                       // visibilities per staged batch (one per producer)
 constexpr int WS_GROUPS = WS_VB / 8;
-constexpr int WS_FOLD = 16;                      // groups between folds (two accumulations per group)
+constexpr int WS_FOLD = 32;                      // groups between folds = one batch (two accumulations per group)
 constexpr int WS_COLS = 256;
-constexpr int WS_B_BATCH = WS_GROUPS * B_TILE;   // 8 KB
+constexpr int WS_B_BATCH = WS_GROUPS * B_TILE;   // 16 KB
 constexpr int WS_SMEM = 2 * WS_B_BATCH + 2 * WS_VB * 16 + FOLD_BYTES;
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WS_NP) : "memory"); }
