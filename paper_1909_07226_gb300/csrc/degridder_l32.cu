@@ -18,34 +18,11 @@ idg_status launch_tcw(const Geometry &g, const SubgridSet &set, const void *sub,
     return launch_degridder_tcw(g, set, sub, flags, aterms, taper, vis_out, (void *)s);
 }
 
-// Subgrids with at least KPMIN visibilities on the tensor cores, the rest on the
-// packed-FP32 kernel: the tensor-core form pays a fixed cost per subgrid (the
-// split image operand) and pads K_p to blocks of 256, which small subgrids do
-// not repay.  Runs of consecutive subgrids on the same side share a launch.
-template <int KPMIN>
-idg_status launch_tcw_split(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
-                            const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
-    if (!set.kp_host) return fail(IDG_ERR_INVALID_ARG, "degridder: K_p of the subgrid set is required");
-    int64_t b = 0;
-    while (b < set.count) {
-        const bool big = set.kp_host[b] >= KPMIN;
-        int64_t e = b + 1;
-        while (e < set.count && (set.kp_host[e] >= KPMIN) == big) ++e;
-        const SubgridSet run{set.idx ? set.idx + b : nullptr, set.first + b, e - b, set.kp_host + b};
-        const void *rsub = (const float4 *)sub + (size_t)b * 32 * 32 * 2;
-        const idg_status st = big ? launch_tcw(g, run, rsub, flags, aterms, taper, vis_out, s)
-                                  : degrid_f2_launch_static<32, 4, 128, 3>(g, run, rsub, flags, aterms, taper, vis_out, s);
-        if (st != IDG_OK) return st;
-        b = e;
-    }
-    return IDG_OK;
-}
-
 // One kernel family per call: the tensor-core form unless most of the call's
 // visibilities sit in subgrids of fewer than KPMIN, where its fixed cost per
 // subgrid (the split image operand, filling and draining the pipeline, padding to
 // 128 visibilities) outweighs its faster sum; splitting one call across both
-// kernels costs more in launch tails than it saves.
+// kernels by K_p was measured slower (launch tails).
 template <int KPMIN>
 idg_status launch_tcw_auto(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                            const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
@@ -60,9 +37,7 @@ idg_status launch_tcw_auto(const Geometry &g, const SubgridSet &set, const void 
 }
 
 const DegridVariant kD32[] = {{"tcgen05_tmemA_ws_nt288_auto512", launch_tcw_auto<512>},
-                              {"tcgen05_tmemA_ws_nt288_kpmin512", launch_tcw_split<512>},
                               DV_F2(32, 4, 128, 3),      {"tcgen05_tmemA_ws_nt288", launch_tcw},
-                              {"tcgen05_tmemA_ws_nt288_kpmin256", launch_tcw_split<256>},
                               DV_RT(32, 4, 256),         DV_ST(32, 4, 256, 3),
                               DV_ST(32, 4, 128, 5),      DV_ST(32, 4, 128, 6), DV_ST(32, 2, 256, 4),
                               DV_RTM(32, 4, 256, 3),     DV_F2(32, 4, 128, 4), DV_F2(32, 2, 128, 4),

@@ -21,7 +21,7 @@
 //   columns  0..63   two accumulator regions r (32 r, tile t at + 16 t)
 //   columns 64..255  three A stages s (64 + 64 s, tile t at + 32 t, chunk at + 16 kc; 8 hi, 8 lo)
 // The tensor cores' FP32 accumulation truncates, so the sum over 1024 pixels
-// is cut into periods of 8 steps that alternate between the two regions: the
+// is cut into periods of 16 steps that alternate between the two regions: the
 // MMA warp commits a period to foldbar[r]; one step into the next period each
 // producer adds its own row of region r into FP32 registers and arrives on
 // folded[r], which the MMA warp waits for before it reuses the region.  The
@@ -49,7 +49,7 @@ constexpr int DNP = 256;                          // producer threads
 constexpr int DNT = DNP + 32;                     // + the MMA warp
 constexpr int DBLK = 256;                         // visibilities per block
 constexpr int DSTEPS = DPIX / 16;                 // 64 steps of 16 pixels per block
-constexpr int DFOLD = 8;                          // steps per accumulation period
+constexpr int DFOLD = 16;                         // steps per accumulation period
 constexpr int DSTAGES = 3;
 constexpr int DCOLS = 256;
 constexpr int D_B_BYTES = (2 * DPIX / 16) * kTile16;   // 128 K chunks of 8 pixels = 64 KB
@@ -242,6 +242,7 @@ __device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevS
                 nb = -pc.b;
                 nc = -pc.c;
             }
+#pragma unroll 2      // a row of 32 pixels per iteration: the column offset of each half is constant
             for (int s = 0; s < DSTEPS; ++s, ++S) {
                 if (S >= DSTAGES) wait_or_fail(smem_u32(&s_empty[st]), empty_par, failed);
                 const int y = s >> 1, x0 = 16 * (s & 1);
