@@ -52,6 +52,7 @@ ISSUE_PER_VISPIX_TC = 9
 # 115.7 + 99.7 MB for ~4.728e9 visibility-pixels (all but 18 small subgrids of the slice).
 # The tensor-core kernels on the same slice (one launch of all 3206 subgrids, 4.73e9 visibility-pixels):
 # gridder 159.2 + 56.0 MB, degridder 118.0 + 110.1 MB (profiles/*_tcw_lofar_slice.md).
+FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
 KERNEL_TRAFFIC = {
     "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
                 "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9},
@@ -387,6 +388,10 @@ def run_gb300(args, world, rank, local):
         if k in ("gridder", "degridder"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
             var = idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)]
+            # a step without adder (splitter) launches ran the fused tensor-core gridder
+            # (degridder): transform and adder (splitter) inside the same kernel
+            if prof["adder" if k == "gridder" else "splitter"]["launches"] == 0:
+                var = FUSED_VARIANT
             tc = var.startswith("tcgen05")
             pk = tc_peak if tc else alu_peak
             ent.update(bound="alu", achieved=ach, peak=pk, unit="Gvispix/s", frac=ach / pk, variant=var,

@@ -176,6 +176,10 @@ void idg_plan_destroy(idg_plan *plan);
  * the FP64 definition to FP32 rounding, not bit for bit across runs.
  * Device scratch of at most 512 MiB is taken from the stream-ordered allocator
  * (plus one grid-sized compensation buffer with IDG_ADDER_COMPENSATED).
+ * At L = 32 with the default kernel choice, IDG_FFT_FP32, IDG_PHASOR_SINCOS and
+ * IDG_ADDER_ATOMIC the whole call is one fused tensor-core launch (image-domain
+ * sum, taper and A-terms, transform and adder per subgrid in one CTA) and takes
+ * no subgrid scratch.
  */
 idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
                     const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);
@@ -186,6 +190,10 @@ idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_fl
  * d_vis_out  device complex64 [n_bl][n_t][n_chan][4], OVERWRITTEN: flagged and
  *            dropped visibilities are set to 0.
  * Other arguments as for idg_grid.
+ * At L = 32 with the default kernel choice, IDG_FFT_FP32 and IDG_PHASOR_SINCOS,
+ * when at least half the visibilities lie in subgrids of 512 or more, the call
+ * is one fused tensor-core launch (splitter, transform, A-terms and taper, and
+ * the visibility sums per subgrid in one CTA) without subgrid scratch.
  */
 idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d_flags,
                       const void *d_aterms, const float *d_taper, void *d_vis_out,

@@ -533,12 +533,37 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
     return IDG_OK;
 }
 
+// The fused tensor-core kernels (L = 32) take the whole sequence of Algorithm 1
+// (2) for a subgrid in one CTA, with the transform in shared memory; they serve
+// the default kernel choice with the FP32 transform, direct phasors and the
+// plain adder.  The degridder takes them when most visibilities of the launch
+// lie in subgrids of at least 512 (as the default per-call choice does).
+static bool fused_grid(const idg_plan *p) {
+    return p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+           p->opts.adder_mode == IDG_ADDER_ATOMIC && get_variant(IDG_KERNEL_GRIDDER, 32) == 0;
+}
+static bool fused_degrid(const idg_plan *p, const SubgridSet &set) {
+    if (!(p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+          get_variant(IDG_KERNEL_DEGRIDDER, 32) == 0))
+        return false;
+    int64_t small = 0, all = 0;
+    for (int64_t i = 0; i < set.count; ++i) {
+        all += set.kp_host[i];
+        if (set.kp_host[i] < 512) small += set.kp_host[i];
+    }
+    return 2 * small <= all;
+}
+
 // Grid the subgrids at positions [first, first + count) of the order o, in
 // pieces of at most `chunk` subgrids that pass through the subgrid scratch
-// (gridder -> transform -> adder).
+// (gridder -> transform -> adder), or in one fused launch (no scratch).
 static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                             void *scratch, int64_t chunk, const void *vis, const uint8_t *flags, const void *aterms,
                             const float *taper, void *grid, void *cbuf, cudaStream_t s) {
+    if (!cbuf && fused_grid(p)) {
+        ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, count, o));
+        return launch_gridder_tcw_fused(g, order_of(p, o, first, count), vis, flags, aterms, taper, grid, s);
+    }
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
         const int64_t cnt = std::min(chunk, first + count - f);
@@ -559,10 +584,16 @@ static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64
     return st;
 }
 
-// Degrid the subgrids [first, first + count) (splitter -> transform -> degridder).
+// Degrid the subgrids [first, first + count) (splitter -> transform -> degridder),
+// or in one fused launch.
 static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                               void *scratch, int64_t chunk, const void *grid, const uint8_t *flags, const void *aterms,
                               const float *taper, void *vis_out, cudaStream_t s) {
+    const SubgridSet all = order_of(p, o, first, count);
+    if (fused_degrid(p, all)) {
+        ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, count, o));
+        return launch_degridder_tcw_fused(g, all, grid, flags, aterms, taper, vis_out, s);
+    }
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {
         const int64_t cnt = std::min(chunk, first + count - f);
@@ -592,11 +623,11 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
     if (n == 0) return IDG_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t chunk = chunk_subgrids(p);
-    void *scratch = nullptr;
-    st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
+    void *scratch = nullptr;     // the subgrid scratch, unless one fused launch takes the call
+    if (comp || !fused_grid(p)) st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
     const Geometry g = p->geometry();
-    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     const size_t grid_f4 = (size_t)p->stats.n_w_layers * p->N * p->N * 2;
     void *cbuf = nullptr;
     if (comp) {
@@ -611,7 +642,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
         if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
         cudaFreeAsync(cbuf, s);
     }
-    cudaError_t e = cudaFreeAsync(scratch, s);
+    cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
     return st;
 }
@@ -630,10 +661,11 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
     if (n == 0) return IDG_OK;
     const int64_t chunk = chunk_subgrids(p);
     void *scratch = nullptr;
-    st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    if (!fused_degrid(p, order_of(p, Order::Work, 0, n)))
+        st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
     st = degrid_span(p, p->geometry(), Order::Work, 0, n, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
-    cudaError_t e = cudaFreeAsync(scratch, s);
+    cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
     return st;
 }
@@ -705,11 +737,11 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
     const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
+    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, (size_t)p->L * p->L * 4, grid_bytes,
-                             (size_t)chunk * p->L * p->L * 32};
+                             comp || !fused_grid(p) ? (size_t)chunk * p->L * p->L * 32 : 0};
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
-    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     const size_t grid_f4 = grid_bytes / 16;
     if (st == IDG_OK && comp) st = scratch_alloc(p->device, grid_f4 * 16, s, &b.ptr[6]);
     if (st != IDG_OK) return st;

@@ -31,6 +31,7 @@
 // and no output is written.
 #include "batch_jobs.cuh"
 #include "degridder_impl.cuh"
+#include "fft_impl.cuh"
 #include "tc_common.cuh"
 
 namespace idg {
@@ -54,8 +55,13 @@ constexpr int DSTAGES = 3;
 constexpr int DCOLS = 256;
 constexpr int D_B_BYTES = (2 * DPIX / 16) * kTile16;   // 128 K chunks of 8 pixels = 64 KB
 constexpr int D_SMEM = D_B_BYTES + DPIX * 4;            // + n'
+constexpr int FFT_P = DL + 1;                            // padded row pitch of the transform planes (float2)
+static_assert(4 * DL * FFT_P * 8 <= D_B_BYTES, "transform planes fit in the P operand buffer");
 
-// Visibilities of subgrid d of geometry g from its image src[L][L][4].
+// Visibilities of subgrid d of geometry g from its image src[L][L][4], or with
+// FUSED from the grid src[layer][N][N][4]: split and transformed in shared memory
+// first (Algorithm 2: split from the master grid, "IFFT", image-domain kernel, sum).
+template <bool FUSED>
 __device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevSubgrid d,
                                                    const float4 *__restrict__ src, const uint8_t *__restrict__ flags,
                                                    const float4 *__restrict__ aterms, const float *__restrict__ taper,
@@ -63,6 +69,7 @@ __device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevS
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;                               // P operand, chunk c (pixels 8c .. 8c + 7) at c * 512
     float *s_np = (float *)(smem + D_B_BYTES);        // n' per pixel
+    float2 *s_fft = (float2 *)smem;                   // FUSED prologue: [4][L][L + 1], before the P operand is built
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_full[DSTAGES], s_empty[DSTAGES], s_foldbar[2], s_folded[2], s_drain;
     __shared__ float s_red[8];
@@ -90,6 +97,22 @@ __device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevS
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
 
+    if (FUSED) {
+        // every thread: split from the grid with the (-1)^(i+j) factor, then the inverse transform
+        const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
+        for (int pix = tid; pix < DPIX; pix += DNT) {
+            const int i = pix / DL, j = pix % DL;
+            const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
+            const float sg = ((i + j) & 1) ? -1.0f : 1.0f;
+            const float4 a = gsrc[2 * gp], b = gsrc[2 * gp + 1];
+            s_fft[(0 * DL + i) * FFT_P + j] = make_float2(sg * a.x, sg * a.y);
+            s_fft[(1 * DL + i) * FFT_P + j] = make_float2(sg * a.z, sg * a.w);
+            s_fft[(2 * DL + i) * FFT_P + j] = make_float2(sg * b.x, sg * b.y);
+            s_fft[(3 * DL + i) * FFT_P + j] = make_float2(sg * b.z, sg * b.w);
+        }
+        __syncthreads();
+        fft2_planar<DL, +1>(s_fft, tid, DNT);
+    }
     // image-domain kernel: P = taper * A_p . I . A_q^H, four pixels per producer thread
     float pv[4][8];
     float m = 0.0f;
@@ -97,7 +120,18 @@ __device__ __forceinline__ void degridder_tcw_body(const Geometry &g, const DevS
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int pix = tid + DNP * i;
-            M22 P = load_m22(src + 2 * pix);
+            M22 P;
+            if (FUSED) {      // (-1)^(x+y) / L^2 of the transform
+                const int y = pix / DL, x = pix % DL;
+                const float sg = ((x + y) & 1) ? -1.0f / DPIX : 1.0f / DPIX;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 v = s_fft[(q * DL + y) * FFT_P + x];
+                    P.m[q] = make_float2(sg * v.x, sg * v.y);
+                }
+            } else {
+                P = load_m22(src + 2 * pix);
+            }
             if (aterms) {
                 const size_t base = ((size_t)d.slot * g.n_stations) * DPIX;
                 const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * DPIX + pix));
@@ -299,7 +333,16 @@ degridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first,
                      const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                      const float *__restrict__ taper, float4 *__restrict__ vis_out) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    degridder_tcw_body(g, g.sub[sid], sub + (size_t)blockIdx.x * DPIX * 2, flags, aterms, taper, vis_out);
+    degridder_tcw_body<false>(g, g.sub[sid], sub + (size_t)blockIdx.x * DPIX * 2, flags, aterms, taper, vis_out);
+}
+
+// fused: one CTA per subgrid, read from the grid
+__global__ void __launch_bounds__(DNT, 2)
+degridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
+                           const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                           const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    degridder_tcw_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
 }
 
 // one CTA per work item (job, subgrid) of a batch; image b of sub
@@ -308,11 +351,26 @@ degridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restri
                            const float4 *__restrict__ sub) {
     const int2 it = items[first + blockIdx.x];
     const JobDev &J = jobs[it.x];
-    degridder_tcw_body(J.g, J.g.sub[it.y], sub + (size_t)blockIdx.x * DPIX * 2, J.flags, J.aterms, J.taper,
-                       J.vis_out);
+    degridder_tcw_body<false>(J.g, J.g.sub[it.y], sub + (size_t)blockIdx.x * DPIX * 2, J.flags, J.aterms, J.taper,
+                              J.vis_out);
 }
 
 }  // namespace
+
+idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                      const void *aterms, const float *taper, void *vis_out, void *stream) {
+    if (g.L != DL) return fail(IDG_ERR_UNSUPPORTED, "the tensor-core degridder is built for L = 32");
+    if (set.count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(degridder_tcw_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core degridder smem attribute");
+    degridder_tcw_fused_kernel<<<(unsigned)set.count, DNT, D_SMEM, s>>>(g, set.idx, set.first, (const float4 *)grid,
+                                                                         flags, (const float4 *)aterms, taper,
+                                                                         (float4 *)vis_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core fused degridder launch");
+    return IDG_OK;
+}
 
 cudaError_t prepare_tcw_batch_kernels() {
     cudaError_t e = prepare_gridder_tcw_batch();

@@ -34,6 +34,7 @@
 // is set and no output is written.
 #include "batch_jobs.cuh"
 #include "device_common.cuh"
+#include "fft_impl.cuh"
 #include "tc_common.cuh"
 
 namespace idg {
@@ -59,10 +60,15 @@ constexpr int WS_FOLD = 32;                      // groups between folds = one b
 constexpr int WS_COLS = 256;
 constexpr int WS_B_BATCH = WS_GROUPS * B_TILE;   // 16 KB
 constexpr int WS_SMEM = 2 * WS_B_BATCH + 2 * WS_VB * 16 + FOLD_BYTES;
+constexpr int FFT_P = TC_L + 1;                  // padded row pitch of the transform planes (float2)
+static_assert(4 * TC_L * FFT_P * 8 <= 2 * WS_B_BATCH + 2 * WS_VB * 16, "transform planes fit over the B buffers");
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(WS_NP) : "memory"); }
 
-// One subgrid d of geometry g into o[L][L][4] (taper and A-terms applied).
+// One subgrid d of geometry g (taper and A-terms applied): into o[L][L][4], or with
+// FUSED transformed in shared memory and added into the grid o[layer][N][N][4]
+// (Algorithm 1: direct sum, image-domain kernel, "FFT", add to the master grid).
+template <bool FUSED>
 __device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSubgrid d,
                                                  const float4 *__restrict__ vis, const uint8_t *__restrict__ flags,
                                                  const float4 *__restrict__ aterms, const float *__restrict__ taper,
@@ -71,6 +77,8 @@ __device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSub
     uint8_t *sB = smem;                                         // 2 batches x 4 KB
     float4 *s_coef = (float4 *)(smem + 2 * WS_B_BATCH);         // 2 batches x 64
     float *s_fold = (float *)(smem + 2 * WS_B_BATCH + 2 * WS_VB * 16);   // [8][1024]
+    float2 *s_fft = (float2 *)smem;                 // FUSED epilogue: [4][L][L + 1], over the B and coefficient buffers
+    bool failed_out = false;                        // a producer's bounded wait gave up
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_foldbar, s_folded, s_drain;
     __shared__ float s_red[8];
@@ -147,6 +155,7 @@ __device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSub
             bool drained = false;
             wait_or_fail(smem_u32(&s_drain), 0u, drained);     // bounded: let own MMAs finish before the free
             if (failed) atomicExch(&g_tc_error, 1);
+            failed_out = failed;
         }
     } else {
         const int q4 = warp & 3, ltw = warp >> 2;
@@ -296,13 +305,40 @@ __device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSub
                     const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * TC_PIX + pix));
                     P = herm_mul_mul(Ap, P, Aq);
                 }
-                const float tw = taper[pix];
-                o[2 * pix] = make_float4(tw * P.m[0].x, tw * P.m[0].y, tw * P.m[1].x, tw * P.m[1].y);
-                o[2 * pix + 1] = make_float4(tw * P.m[2].x, tw * P.m[2].y, tw * P.m[3].x, tw * P.m[3].y);
+                if (FUSED) {
+                    // the (-1)^(x+y) centring factor, into the transform planes
+                    const int x = pix & (TC_L - 1), y = pix >> 5;
+                    const float tw = ((x + y) & 1) ? -taper[pix] : taper[pix];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        s_fft[(q * TC_L + y) * FFT_P + x] = make_float2(tw * P.m[q].x, tw * P.m[q].y);
+                } else {
+                    const float tw = taper[pix];
+                    o[2 * pix] = make_float4(tw * P.m[0].x, tw * P.m[0].y, tw * P.m[1].x, tw * P.m[1].y);
+                    o[2 * pix + 1] = make_float4(tw * P.m[2].x, tw * P.m[2].y, tw * P.m[3].x, tw * P.m[3].y);
+                }
+            }
+        }
+        failed_out = failed;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (FUSED) {
+        // every thread: transform the planes, then add with the (-1)^(i+j) factor and 1/L^2
+        if (!__syncthreads_or(failed_out)) {
+            fft2_planar<TC_L, -1>(s_fft, tid, WS_NT);
+            const float inv = 1.0f / (float)TC_PIX;
+            float4 *dst = o + (size_t)d.layer * g.N * g.N * 2;
+            for (int pix = tid; pix < TC_PIX; pix += WS_NT) {
+                const int i = pix >> 5, j = pix & (TC_L - 1);
+                const float sg = ((i + j) & 1) ? -inv : inv;
+                const float2 p0 = s_fft[(0 * TC_L + i) * FFT_P + j], p1 = s_fft[(1 * TC_L + i) * FFT_P + j];
+                const float2 p2 = s_fft[(2 * TC_L + i) * FFT_P + j], p3 = s_fft[(3 * TC_L + i) * FFT_P + j];
+                const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
+                atomicAdd(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
+                atomicAdd(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(WS_COLS));
 }
@@ -313,7 +349,16 @@ gridder_tcw_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, c
                    const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                    const float *__restrict__ taper, float4 *__restrict__ out) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    gridder_tcw_body(g, g.sub[sid], vis, flags, aterms, taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+    gridder_tcw_body<false>(g, g.sub[sid], vis, flags, aterms, taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+}
+
+// fused: one CTA per subgrid, transformed and added into grid (accumulated)
+__global__ void __launch_bounds__(WS_NT, 2)
+gridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
+                         const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                         const float *__restrict__ taper, float4 *__restrict__ grid) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    gridder_tcw_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
 }
 
 // one CTA per work item (job, subgrid) of a batch
@@ -322,10 +367,25 @@ gridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict
                          float4 *__restrict__ out) {
     const int2 it = items[first + blockIdx.x];
     const JobDev &J = jobs[it.x];
-    gridder_tcw_body(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+    gridder_tcw_body<false>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, out + (size_t)blockIdx.x * TC_PIX * 2);
 }
 
 }  // namespace
+
+idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *grid, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g.L != TC_L) return fail(IDG_ERR_UNSUPPORTED, "the tensor-core gridder is built for L = 32");
+    if (set.count <= 0) return IDG_OK;
+    cudaError_t e = cudaFuncSetAttribute(gridder_tcw_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core gridder smem attribute");
+    gridder_tcw_fused_kernel<<<(unsigned)set.count, WS_NT, WS_SMEM, s>>>(g, set.idx, set.first, (const float4 *)vis,
+                                                                          flags, (const float4 *)aterms, taper,
+                                                                          (float4 *)grid);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core fused gridder launch");
+    return IDG_OK;
+}
 
 cudaError_t prepare_gridder_tcw_batch() {
     return cudaFuncSetAttribute(gridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);

@@ -157,6 +157,12 @@ idg_status read_device_errors(int *code, void *stream);
 idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *subgrids, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream);
 idg_status read_tcd_error(int *code);
+// fused forms (L = 32): the gridder transforms each subgrid in shared memory and adds it
+// into `grid` (accumulated); the degridder splits and transforms from `grid`
+idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *grid, void *stream);
+idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                      const void *aterms, const float *taper, void *vis_out, void *stream);
 // the same two kernels over the (job, subgrid) work items [first, first + count) of
 // a batch (jobs: device job table, see batch_jobs.cuh); subgrid b of the launch at b
 struct JobDev;

@@ -306,6 +306,8 @@ HOST_CASES = {
     "L32_identity_wide": lambda: small(32, aterms="identity", n_chan=16, diameter_m=30000.0, df=4e6),
     "L64_dropped": lambda: small(64, cell=1.2e-3, diameter_m=6000.0, n_t=24),
     "L32_many_baselines": lambda: small(32, n_st=12, n_t=16, max_t=16),
+    # K_p = 2048: the spans take the fused tensor-core degridder as well
+    "L32_long_kp": lambda: small(32, n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6),
 }
 
 

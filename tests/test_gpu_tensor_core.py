@@ -287,3 +287,93 @@ def test_tc_degridder_lofar_slice_sampled(tcd_selected):
         bl, t0, nt, c0, nc = row[O.D_BL], row[O.D_T0], row[O.D_NT], row[O.D_C0], row[O.D_NC]
         sel[bl, t0:t0 + nt, c0:c0 + nc] = True
     parity(out.cpu().numpy()[sel], ref[sel], "tc degridder LOFAR slice, sampled")
+
+
+# ---------------------------------------------------------------------------
+# fused tensor-core kernels: with the default choices at L = 32 (FP32
+# transform, direct phasors, plain adder) a composite call grids each subgrid
+# in one CTA (gridder, transform and adder) and degrids it in one CTA
+# (splitter, transform and degridder) when most of its visibilities lie in
+# subgrids of K_p >= 512.  The launch counters show which path ran.
+
+FUSED_CASES = {
+    "long_kp": CASES["long_kp"],
+    # four w layers, K_p 96 .. 2048: fused degridder
+    "long_kp_w_layers": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6, w_step=50.0),
+    # two A-term slots and two w layers, K_p 8 .. 768: fused degridder, ragged groups
+    "long_kp_slots_layers": lambda: small32(n_t=192, n_chan=8, max_t=96, n_st=4, df=0.25e6, n_slots=2,
+                                            w_step=100.0, diameter_m=2000.0),
+    # many small subgrids (K_p <= 160): fused gridder, separate degridding stages
+    "short_kp_w_layers": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6, w_step=20.0,
+                                         diameter_m=20000.0),
+    "points_flags_aterms": CASES["points_flags_aterms"],
+    "huge_magnitudes": CASES["huge_magnitudes"],
+}
+
+
+def _launches(prof):
+    return {k: v["launches"] for k, v in prof.items() if v["launches"]}
+
+
+def _kp_mostly_long(p):
+    kp = p.export()[:, O.D_KP]
+    return 2 * kp[kp < 512].sum() <= kp.sum()
+
+
+@pytest.mark.parametrize("case", sorted(FUSED_CASES))
+def test_fused_grid_and_degrid(case):
+    import torch
+    wl = FUSED_CASES[case]()
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+    idg.profile_enable(True)
+    try:
+        idg.profile_read(reset=True)
+        idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+        grid_launches = _launches(idg.profile_read(reset=True))
+        rng = np.random.default_rng(5)
+        g_in = syn.random_grid(rng, p.n_w_layers, wl.grid_size)
+        v = torch.zeros(wl.vis.shape, dtype=torch.complex64, device="cuda")
+        idg.degrid(p, dev(g_in), d["flags"], d["aterms"], d["taper"], v)
+        degrid_launches = _launches(idg.profile_read(reset=True))
+    finally:
+        idg.profile_enable(False)
+    idg.device_errors()
+    assert grid_launches == {"gridder": 1}
+    if _kp_mostly_long(p):
+        assert degrid_launches == {"degridder": 1}
+    else:
+        assert "splitter" in degrid_launches and "fft" in degrid_launches
+    parity(g.cpu().numpy(), O.grid(wl, op), f"fused grid {case}")
+    parity(v.cpu().numpy(), O.degrid(wl, op, g_in), f"fused degrid {case}")
+
+
+def test_fused_grid_accumulates_into_the_grid():
+    # the fused adder adds into what the grid holds, as the separate adder does
+    import torch
+    wl = CASES["long_kp"]()
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    rng = np.random.default_rng(9)
+    g0 = syn.random_grid(rng, p.n_w_layers, wl.grid_size)
+    g = dev(g0)
+    idg.grid(p, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+    idg.device_errors()
+    parity(g.cpu().numpy(), O.grid(wl, op) + g0, "fused grid accumulated")
+
+
+def test_stage_calls_stay_unfused():
+    # grid_subgrids writes subgrid images: the fused kernels never serve it
+    import torch
+    wl = CASES["long_kp"]()
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    d = workload_to_device(wl)
+    n = p.n_subgrids
+    sub = torch.zeros((n, 32, 32, 4), dtype=torch.complex64, device="cuda")
+    idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
+    idg.device_errors()
+    parity(sub.cpu().numpy(), O.subgrid_images(wl, op), "stage gridder, long K_p")
