@@ -52,14 +52,21 @@ ISSUE_PER_VISPIX_TC = 9
 # 115.7 + 99.7 MB for ~4.728e9 visibility-pixels (all but 18 small subgrids of the slice).
 # The tensor-core kernels on the same slice (one launch of all 3206 subgrids, 4.73e9 visibility-pixels):
 # gridder 159.2 + 56.0 MB, degridder 118.0 + 110.1 MB (profiles/*_tcw_lofar_slice.md).
+# The fused tensor-core kernels of the composite calls, same slice and launch
+# (profiles/gridder_degridder_tcw_fused_lofar_slice.md): gridder 176.3 + 5.5 MB
+# (visibilities in, grid lines read; the atomically updated grid lines are still
+# dirty in L2 when the launch ends), degridder 28.6 + 91.9 MB (grid lines in,
+# model visibilities out).
 FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
 KERNEL_TRAFFIC = {
     "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
-                "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9},
+                "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9,
+                FUSED_VARIANT: (176.3e6 + 5.5e6) / 4.731e9},
     "degridder": {"f32x2_nv4_nt128_minb3_pg_static": (115.7e6 + 99.7e6) / 4.728e9,
                   "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9,
                   # the per-call choice runs the LOFAR-like workload on the same kernel
-                  "tcgen05_tmemA_ws_nt288_auto512": (118.0e6 + 110.1e6) / 4.73e9},
+                  "tcgen05_tmemA_ws_nt288_auto512": (118.0e6 + 110.1e6) / 4.73e9,
+                  FUSED_VARIANT: (28.6e6 + 91.9e6) / 4.731e9},
 }
 
 

@@ -284,12 +284,11 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *                     (accumulated, as idg_grid)
  *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
  *                     into vis_out (overwritten; flagged and dropped -> 0)
- * For L = 32 the default batch variant ("tcgen05_unfused", IDG_KERNEL_BATCH_*)
- * instead runs the tensor-core gridder (degridder) with one CTA per work item,
- * the transform and an adder (splitter) as launches over chunks of at most
- * 16384 items through a device scratch of the batch (512 MiB at most); a
- * class whose visibilities lie mostly in subgrids of fewer than 512 takes the
- * fused persistent kernel.  Otherwise no device scratch is used.  With
+ * For L = 32 the default batch variant ("tcgen05_fused", IDG_KERNEL_BATCH_*)
+ * instead runs the fused tensor-core gridder (degridder) with one CTA per work
+ * item, the sums on the tensor cores and the transform and adder (splitter) in
+ * the same CTA; a class whose visibilities lie mostly in subgrids of fewer
+ * than 512 takes the persistent kernel.  No device scratch is used.  With
  * IDG_BATCH_GRAPH the first call of each direction captures its launch
  * sequence into a CUDA graph, and later calls replay it (the buffers are fixed
  * by the batch, so the graph stays valid).
@@ -302,7 +301,7 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   flags    or NULL;  aterms  or NULL (identity);  taper (required)
  *   grid     gridding output (accumulated) / degridding input
  * idg_batch_info returns the planned visibilities, work items and launches per
- * direction (1 per fused class, 3 per chunk of a tensor-core class).
+ * direction (1 per class).
  */
 typedef struct idg_batch idg_batch;
 typedef struct {

@@ -279,48 +279,13 @@ struct KernelShape {
     const void *fn;      // persistent fused kernel, or null for the tensor-core path
     int threads;
     size_t smem;
-    bool tc = false;     // unfused tensor-core path: sum, transform and adder/splitter as launches per chunk
+    bool tc = false;     // tensor-core path: one CTA per work item instead of a persistent grid
 };
 
-// L = 32 on the tensor cores: per chunk of the class's work items, the
-// tensor-core gridder (degridder) with one CTA per item, the shared-memory
-// transform, and the adder (splitter) below
-const KernelShape kTcShape = {"tcgen05_unfused", nullptr, 288, 0, true};
-
-// the adder and splitter of Algorithms 1 and 2 over work items; subgrid b of the launch at sub + b L^2
-__global__ void __launch_bounds__(256)
-batch_adder_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
-                   const float4 *__restrict__ sub) {
-    const int2 it = items[first + blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    const DevSubgrid d = J.g.sub[it.y];
-    const int L = J.g.L, N = J.g.N;
-    const float4 *src = sub + (size_t)blockIdx.x * L * L * 2;
-    float4 *dst = J.grid + (size_t)d.layer * N * N * 2;
-    for (int pix = threadIdx.x; pix < L * L; pix += 256) {
-        const int i = pix / L, j = pix - (pix / L) * L;
-        const size_t gp = (size_t)(d.r0 + i) * N + (d.q0 + j);
-        atomicAdd(dst + 2 * gp, src[2 * pix]);
-        atomicAdd(dst + 2 * gp + 1, src[2 * pix + 1]);
-    }
-}
-
-__global__ void __launch_bounds__(256)
-batch_splitter_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
-                      float4 *__restrict__ sub) {
-    const int2 it = items[first + blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    const DevSubgrid d = J.g.sub[it.y];
-    const int L = J.g.L, N = J.g.N;
-    float4 *out = sub + (size_t)blockIdx.x * L * L * 2;
-    const float4 *src = J.grid + (size_t)d.layer * N * N * 2;
-    for (int pix = threadIdx.x; pix < L * L; pix += 256) {
-        const int i = pix / L, j = pix - (pix / L) * L;
-        const size_t gp = (size_t)(d.r0 + i) * N + (d.q0 + j);
-        out[2 * pix] = src[2 * gp];
-        out[2 * pix + 1] = src[2 * gp + 1];
-    }
-}
+// L = 32 on the tensor cores: the fused tensor-core gridder (degridder), one
+// CTA per work item, with the transform in shared memory and the adder
+// (splitter) in the same CTA
+const KernelShape kTcShape = {"tcgen05_fused", nullptr, 288, 0, true};
 
 template <int L, int NPX, int MINB>
 KernelShape gshape(const char *name) {
@@ -390,8 +355,6 @@ struct idg_batch {
     std::vector<std::pair<void *, size_t>> zero_on_degrid;   // vis_out of jobs with dropped samples
     cudaGraphExec_t graph_grid = nullptr, graph_degrid = nullptr;
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are recorded on
-    void *tc_scratch = nullptr;              // subgrids of one chunk of the tensor-core path
-    int64_t tc_chunk = 0;                    // subgrids per chunk
 };
 
 static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
@@ -408,28 +371,9 @@ static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
         const KernelShape &ks = degrid ? cl.degrid : cl.grid;
         if (ks.tc) {
             ProfileScope ps(degrid ? IDG_KERNEL_BATCH_DEGRID : IDG_KERNEL_BATCH_GRID, s, cl.vispix);
-            for (int64_t f = 0; f < cl.n_items; f += b->tc_chunk) {
-                const int64_t cnt = std::min(b->tc_chunk, cl.n_items - f);
-                idg_status st;
-                if (!degrid) {
-                    st = launch_gridder_tcw_batch(b->d_jobs, cl.d_items, f, cnt, b->tc_scratch, s);
-                    if (st == IDG_OK) st = launch_fft(cl.L, cnt, -1, b->tc_scratch, s);
-                    if (st == IDG_OK) {
-                        batch_adder_kernel<<<(unsigned)cnt, 256, 0, s>>>(b->d_jobs, cl.d_items, f,
-                                                                       (const float4 *)b->tc_scratch);
-                        e = cudaGetLastError();
-                        if (e != cudaSuccess) st = cuda_fail(e, "batch adder launch");
-                    }
-                } else {
-                    batch_splitter_kernel<<<(unsigned)cnt, 256, 0, s>>>(b->d_jobs, cl.d_items, f,
-                                                                      (float4 *)b->tc_scratch);
-                    e = cudaGetLastError();
-                    st = e == cudaSuccess ? IDG_OK : cuda_fail(e, "batch splitter launch");
-                    if (st == IDG_OK) st = launch_fft(cl.L, cnt, +1, b->tc_scratch, s);
-                    if (st == IDG_OK) st = launch_degridder_tcw_batch(b->d_jobs, cl.d_items, f, cnt, b->tc_scratch, s);
-                }
-                if (st != IDG_OK) return st;
-            }
+            const idg_status st = degrid ? launch_degridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s)
+                                         : launch_gridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s);
+            if (st != IDG_OK) return st;
             continue;
         }
         const int blocks = degrid ? cl.degrid_blocks : cl.grid_blocks;
@@ -506,7 +450,6 @@ void idg_batch_destroy(idg_batch *b) {
     if (b->graph_degrid) cudaGraphExecDestroy(b->graph_degrid);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     for (auto &c : b->classes) cudaFree(c.d_items);
-    cudaFree(b->tc_scratch);
     cudaFree(b->d_jobs);
     cudaFree(b->d_counters);
     if (prev >= 0) cudaSetDevice(prev);
@@ -573,7 +516,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         }
     }
     idg_status st = IDG_OK;
-    int64_t need_tc = 0;                          // items of the largest tensor-core class
+    bool need_tc = false;                         // some class runs the tensor-core kernels
     for (size_t c = 0; c < b->classes.size() && st == IDG_OK; ++c) {
         auto &items = per_class[c];
         // cost order: most visibilities first, ties by job and subgrid
@@ -606,7 +549,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
                         break;
                     }
             }
-            if (ks.tc) need_tc = std::max(need_tc, cl.n_items);
+            if (ks.tc) need_tc = true;
         }
         // persistent grid: resident CTAs per SM x SMs, never more than the items
         for (int k = 0; k < 2 && st == IDG_OK; ++k) {
@@ -623,11 +566,9 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
             (k ? cl.degrid_blocks : cl.grid_blocks) = (int)blocks;
         }
     }
-    if (st == IDG_OK && need_tc > 0) {
-        b->tc_chunk = std::min<int64_t>(need_tc, 16384);      // 512 MiB of L = 32 subgrids
-        e = cudaMalloc(&b->tc_scratch, (size_t)b->tc_chunk * 32 * 32 * 32);
-        if (e == cudaSuccess) e = prepare_tcw_batch_kernels();
-        if (e != cudaSuccess) st = cuda_fail(e, "batch tensor-core scratch");
+    if (st == IDG_OK && need_tc) {
+        e = prepare_tcw_batch_kernels();      // outside any graph capture
+        if (e != cudaSuccess) st = cuda_fail(e, "batch tensor-core kernel attributes");
     }
     if (st == IDG_OK) {
         e = cudaMalloc(&b->d_jobs, sizeof(JobDev) * hj.size());
@@ -654,8 +595,7 @@ idg_status idg_batch_info(const idg_batch *b, int64_t *n_vis, int64_t *n_items, 
     for (auto &c : b->classes) {
         items += c.n_items;
         if (c.n_items == 0) continue;
-        // the tensor-core path (grid shape) launches sum, transform and adder per chunk
-        launches += c.grid.tc ? 3 * (int)((c.n_items + b->tc_chunk - 1) / b->tc_chunk) : 1;
+        launches += 1;      // one launch per class and direction
     }
     if (n_vis) *n_vis = b->n_vis;
     if (n_items) *n_items = items;

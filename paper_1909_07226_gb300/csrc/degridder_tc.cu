@@ -345,14 +345,12 @@ degridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t 
     degridder_tcw_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
 }
 
-// one CTA per work item (job, subgrid) of a batch; image b of sub
+// fused, one CTA per work item (job, subgrid) of a batch: split from the job's grid
 __global__ void __launch_bounds__(DNT, 2)
-degridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
-                           const float4 *__restrict__ sub) {
-    const int2 it = items[first + blockIdx.x];
+degridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
     const JobDev &J = jobs[it.x];
-    degridder_tcw_body<false>(J.g, J.g.sub[it.y], sub + (size_t)blockIdx.x * DPIX * 2, J.flags, J.aterms, J.taper,
-                              J.vis_out);
+    degridder_tcw_body<true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
 }
 
 }  // namespace
@@ -380,11 +378,10 @@ cudaError_t prepare_tcw_batch_kernels() {
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_degridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t first, int64_t count,
-                                      const void *sub, void *stream) {
+idg_status launch_degridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    degridder_tcw_batch_kernel<<<(unsigned)count, DNT, D_SMEM, s>>>(jobs, items, first, (const float4 *)sub);
+    degridder_tcw_batch_kernel<<<(unsigned)count, DNT, D_SMEM, s>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch degridder launch");
     return IDG_OK;

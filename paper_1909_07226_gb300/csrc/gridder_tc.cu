@@ -361,13 +361,12 @@ gridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t fi
     gridder_tcw_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
 }
 
-// one CTA per work item (job, subgrid) of a batch
+// fused, one CTA per work item (job, subgrid) of a batch: added into the job's grid
 __global__ void __launch_bounds__(WS_NT, 2)
-gridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items, int64_t first,
-                         float4 *__restrict__ out) {
-    const int2 it = items[first + blockIdx.x];
+gridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
     const JobDev &J = jobs[it.x];
-    gridder_tcw_body<false>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, out + (size_t)blockIdx.x * TC_PIX * 2);
+    gridder_tcw_body<true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
 }
 
 }  // namespace
@@ -392,11 +391,10 @@ cudaError_t prepare_gridder_tcw_batch() {
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_gridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t first, int64_t count, void *out,
-                                    void *stream) {
+idg_status launch_gridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    gridder_tcw_batch_kernel<<<(unsigned)count, WS_NT, WS_SMEM, s>>>(jobs, items, first, (float4 *)out);
+    gridder_tcw_batch_kernel<<<(unsigned)count, WS_NT, WS_SMEM, s>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch gridder launch");
     return IDG_OK;

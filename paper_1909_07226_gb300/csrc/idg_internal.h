@@ -163,13 +163,12 @@ idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, co
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
                                       const void *aterms, const float *taper, void *vis_out, void *stream);
-// the same two kernels over the (job, subgrid) work items [first, first + count) of
-// a batch (jobs: device job table, see batch_jobs.cuh); subgrid b of the launch at b
+// the fused kernels over the (job, subgrid) work items items[0 .. count) of a
+// batch (jobs: device job table, see batch_jobs.cuh): each item added into
+// (split from) its job's grid
 struct JobDev;
-idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t first, int64_t count,
-                                    void *subgrids, void *stream);
-idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t first, int64_t count,
-                                      const void *subgrids, void *stream);
+idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);
