@@ -106,6 +106,11 @@ typedef struct {
     int32_t grid_size;        /* N                                                */
     int32_t n_bl, n_t, n_chan, n_stations, n_slots;
     int32_t device;           /* CUDA device holding the plan's metadata          */
+    int32_t separable;        /* 1: the separable tensor-core kernels apply (L = 32
+                                 and sep_phase <= 1.38e-3), see idg_grid         */
+    double sep_phase;         /* max |2 pi (w - w0)| * max |r(x, y)| in radians, r the
+                                 part of n' = sqrt(1 - l^2 - m^2) - 1 that is not
+                                 n'(l, 0) + n'(0, m)                              */
 } idg_plan_stats;
 
 /* Number of int32 fields per exported subgrid descriptor, and their order. */

@@ -133,6 +133,13 @@ ProfileScope::~ProfileScope() {
 
 using namespace idg;
 
+// The separable kernels (L = 32) write the phasor of visibility k at pixel (x, y) as
+// exp(i (a X + c s(x))) exp(i (b Y + c t(y))) exp(i c r(x, y)) and keep the last
+// factor to first order, 1 + i c r; the dropped terms are at most theta^2 / 2 in
+// relative terms, theta = max |c| max |r|.  Below this bound that is <= 2^-20
+// (9.5e-7), the order of the rounding of the FP16 split sums themselves.
+constexpr double kSepThetaMax = 1.38e-3;
+
 idg::Geometry idg_plan::geometry() const {
     Geometry g;
     g.L = L;
@@ -147,6 +154,9 @@ idg::Geometry idg_plan::geometry() const {
     g.uvw = d_uvw;
     g.scale = d_scale;
     g.nprime = d_nprime;
+    g.sep = d_nprime + (size_t)L * L;
+    g.separable = stats.separable;
+    g.c_scale = c_scale;
     g.ds = ds;
     g.recurrence = opts.precision_mode == IDG_PHASOR_RECURRENCE ? 1 : 0;
     g.anchor = 8;
@@ -363,6 +373,36 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     p->stats.max_kp = max_kp;
     p->any_dropped = pr.n_dropped > 0;
 
+    // bound on the phase of the separable remainder: max |c_k| max |r(x, y)| with
+    // c_k = 2 pi (w_k - w0) and r = n'(x, y) - n'(x, L/2) - n'(L/2, y); per
+    // subgrid the ends of its channel range bound the linear dependence on f
+    {
+        auto n1 = [&](int x, int y) {
+            const double l = ((double)x - 0.5 * L) * p->S / L;
+            const double m = ((double)y - 0.5 * L) * p->S / L;
+            return std::sqrt(1.0 - l * l - m * m) - 1.0;
+        };
+        double r_max = 0.0, dw_max = 0.0;
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) r_max = std::max(r_max, std::fabs(n1(x, y) - n1(x, L / 2) - n1(L / 2, y)));
+        for (int64_t s = 0; s < n_sub; ++s) {
+            const int32_t *d = &p->desc[s * kDescFields];
+            const double w0 = w_step > 0.0 ? (double)(d[IDG_DESC_LAYER] + pr.k_min) * w_step : 0.0;
+            const int c0 = d[IDG_DESC_C0], c1 = d[IDG_DESC_C0] + d[IDG_DESC_NC] - 1;
+            for (int t = d[IDG_DESC_T0]; t < d[IDG_DESC_T0] + d[IDG_DESC_NT]; ++t) {
+                const double w = uvw_m[((size_t)d[IDG_DESC_BASELINE] * n_t + t) * 3 + 2];
+                dw_max = std::max(dw_max, std::max(std::fabs(w * freqs_hz[c0] / kSpeedOfLight - w0),
+                                                   std::fabs(w * freqs_hz[c1] / kSpeedOfLight - w0)));
+            }
+        }
+        const double c_max = 6.283185307179586476925286766559 * dw_max;
+        p->sep_theta = c_max * r_max;
+        p->c_scale = 1.0f;
+        if (c_max > 1.0) p->c_scale = (float)std::ldexp(1.0, -(int)std::ceil(std::log2(c_max)));
+        p->stats.separable = (L == 32 && p->sep_theta <= kSepThetaMax) ? 1 : 0;
+        p->stats.sep_phase = p->sep_theta;
+    }
+
     // device metadata; without any CUDA device the plan stays host-only
     // (info and export work, device calls are rejected)
     int n_dev = 0;
@@ -444,13 +484,23 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     }
     std::vector<double> scale(n_chan);
     for (int c = 0; c < n_chan; ++c) scale[c] = freqs_hz[c] / kSpeedOfLight;
-    std::vector<float> nprime((size_t)L * L);
+    // n' table, then the separable split n' = s(x) + t(y) + r(x, y) with s and t
+    // the row and column through the centre pixel (l = 0 at X = 0, m = 0 at Y = 0)
+    std::vector<float> nprime((size_t)2 * L * L + 2 * L);
+    auto n1 = [&](int x, int y) {
+        const double l = ((double)x - 0.5 * L) * p->S / L;
+        const double m = ((double)y - 0.5 * L) * p->S / L;
+        return std::sqrt(1.0 - l * l - m * m) - 1.0;
+    };
     for (int y = 0; y < L; ++y)
         for (int x = 0; x < L; ++x) {
-            const double l = ((double)x - 0.5 * L) * p->S / L;
-            const double m = ((double)y - 0.5 * L) * p->S / L;
-            nprime[(size_t)y * L + x] = (float)(std::sqrt(1.0 - l * l - m * m) - 1.0);
+            nprime[(size_t)y * L + x] = (float)n1(x, y);
+            nprime[(size_t)L * L + 2 * L + (size_t)y * L + x] = (float)(n1(x, y) - n1(x, L / 2) - n1(L / 2, y));
         }
+    for (int i = 0; i < L; ++i) {
+        nprime[(size_t)L * L + i] = (float)n1(i, L / 2);
+        nprime[(size_t)L * L + L + i] = (float)n1(L / 2, i);
+    }
 
     struct Up { void **dst; const void *src; size_t bytes; const char *what; };
     Up ups[] = {
@@ -562,7 +612,9 @@ static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64
                             const float *taper, void *grid, void *cbuf, cudaStream_t s) {
     if (!cbuf && fused_grid(p)) {
         ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, count, o));
-        return launch_gridder_tcw_fused(g, order_of(p, o, first, count), vis, flags, aterms, taper, grid, s);
+        const SubgridSet set = order_of(p, o, first, count);
+        return g.separable ? launch_gridder_sep_fused(g, set, vis, flags, aterms, taper, grid, s)
+                           : launch_gridder_tcw_fused(g, set, vis, flags, aterms, taper, grid, s);
     }
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {

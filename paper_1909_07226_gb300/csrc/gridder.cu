@@ -221,6 +221,13 @@ idg_status launch_tcw(const Geometry &g, const SubgridSet &set, const void *vis,
     return launch_gridder_tcw(g, set, vis, flags, aterms, taper, out, (void *)s);
 }
 
+// separable tensor-core form where the plan allows it, else the direct one
+idg_status launch_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                      const void *aterms, const float *taper, void *out, cudaStream_t s) {
+    if (!g.separable) return launch_gridder_tcw(g, set, vis, flags, aterms, taper, out, (void *)s);
+    return launch_gridder_sep(g, set, vis, flags, aterms, taper, out, (void *)s);
+}
+
 struct Variant {
     const char *name;
     LaunchFn fn;
@@ -234,7 +241,7 @@ const Variant kV16[] = {GF(16, 2, 128, 3), GV(16, 2, 128, 3, false), GV(16, 2, 2
                         GV(16, 4, 256, 6, true), GF(16, 4, 128, 2)};
 const Variant kV24[] = {GF(24, 3, 128, 3), GV(24, 3, 128, 3, false), GV(24, 3, 256, 3, true),
                         GV(24, 6, 256, 6, true), GF(24, 6, 128, 2)};
-const Variant kV32[] = {{"tcgen05_tmemA_ws_nt288", launch_tcw}, GF(32, 4, 128, 2), GV(32, 4, 128, 3, false),
+const Variant kV32[] = {{"tcgen05_separable", launch_sep}, {"tcgen05_tmemA_ws_nt288", launch_tcw}, GF(32, 4, 128, 2), GV(32, 4, 128, 3, false),
                         GV(32, 4, 256, 3, true),
                         GV(32, 4, 256, 4, true),  GV(32, 8, 256, 4, true),  GV(32, 2, 256, 2, true),
                         GF(32, 4, 128, 3),        GF(32, 2, 128, 3),        GF(32, 8, 128, 4)};

@@ -33,6 +33,12 @@ struct Geometry {
     double ds;                 // channel scale step (f_{c+1} - f_c)/c for uniformly spaced channels
     int recurrence;            // 1: phasors by channel recurrence (IDG_PHASOR_RECURRENCE)
     int anchor;                // channels per recurrence run (re-anchor interval)
+    // separable split n'(x, y) = s(x) + t(y) + r(x, y): s(x) = n'(x, Y = 0),
+    // t(y) = n'(X = 0, y), r the remainder; sep = [s[L] | t[L] | r[L][L]] (FP64
+    // differences rounded to FP32)
+    const float *sep;
+    int separable;             // 1: max |c_k| max |r| is small enough for the first-order w remainder
+    float c_scale;             // power of two with max |c_k| c_scale <= 1 (c_k = 2 pi (w - w0))
 };
 
 // Host planner output.
@@ -72,7 +78,9 @@ struct idg_plan {
     int32_t *d_order = nullptr;
     double *d_uvw = nullptr;
     double *d_scale = nullptr;
-    float *d_nprime = nullptr;
+    float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
+    double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
+    float c_scale = 1.0f;
     bool any_dropped = false;
     double ds = 0.0;                        // uniform channel scale step (0 if not uniform)
     std::vector<int64_t> kp_prefix_plan;    // [n_sub + 1], sum of K_p in plan order
@@ -150,6 +158,13 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
 
 // tensor-core gridder (L = 32; FP16 hi/lo split products, FP32 accumulation in
 // tensor memory) and the device error word of the bounded waits
+// separable tensor-core gridder (L = 32, g.separable): subgrid images, or fused
+// with the transform and the adder into grid
+idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                              const void *aterms, const float *taper, void *out, void *stream);
+idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *grid, void *stream);
+idg_status read_sep_error(int *code);
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);

@@ -34,6 +34,26 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 // kind::f16 instruction descriptor: D F32, A and B F16, both K-major, N = 16, M = 128
 constexpr uint32_t kIdescM128N16 = (1u << 4) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
+// kind::f16 instruction descriptor for M = 128 and a given N (multiple of 16, <= 256)
+__host__ __device__ constexpr uint32_t idesc_m128(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// D (tensor memory) += A (tensor memory, 128 x 16) x B (shared memory, N x 16 K-major)^T with
+// instruction descriptor idesc; acc = 0 overwrites
+__device__ __forceinline__ void mma_ta_i(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
+                 :: "r"(dtmem), "r"(atmem), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+
+// D (tensor memory) += A (shared memory, 128 x 16 K-major) x B (shared memory, N x 16 K-major)^T
+__device__ __forceinline__ void mma_ss_i(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(dtmem), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+
 // D (tensor memory) += A (tensor memory, 128 x 16) x B (shared memory, 16 x 16)^T; acc = 0 overwrites
 __device__ __forceinline__ void mma_ta(uint32_t dtmem, uint32_t atmem, uint64_t db, uint32_t acc) {
     asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -79,12 +99,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t v0, uint32_t v1) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" :: "r"(taddr), "r"(v0), "r"(v1) : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
                  :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
                     "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
                     "r"(v[15])
                  : "memory");
+}
+
+// FP16 pair (x in the low half, y in the high half), round to nearest
+__device__ __forceinline__ uint32_t pack_f16x2(float x, float y) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(x), "f"(y));
+    return r;
 }
 
 // FP16 hi/lo parts of (x, y): hi = fp16 rounded, lo = fp16(v - hi) with v - hi formed

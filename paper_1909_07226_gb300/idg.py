@@ -59,7 +59,8 @@ class PlanStats(ctypes.Structure):
                 ("n_w_layers", ctypes.c_int32), ("w_layer_min", ctypes.c_int32),
                 ("subgrid_size", ctypes.c_int32), ("grid_size", ctypes.c_int32),
                 ("n_bl", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_chan", ctypes.c_int32),
-                ("n_stations", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("n_stations", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("separable", ctypes.c_int32), ("sep_phase", ctypes.c_double)]
 
 
 _lib = None

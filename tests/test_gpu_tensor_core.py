@@ -19,7 +19,7 @@ from tests.gpu_util import dev, parity, workload_to_device
 
 pytestmark = pytest.mark.gpu
 
-TC_VARIANTS = ["tcgen05_tmemA_ws_nt288"]
+TC_VARIANTS = ["tcgen05_separable", "tcgen05_tmemA_ws_nt288"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -71,6 +71,10 @@ CASES = {
     # K_p = 2048 as in the LOFAR configuration: 8 folds of the hh | hl accumulators
     "long_kp": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6),
     "wide_channels": lambda: small32(aterms="identity", n_chan=16, diameter_m=30000.0, df=4e6),
+    # wide field with the separable remainder phase just under its bound (1.35e-3 rad)
+    "wide_field_near_bound": lambda: small32(N=256, cell=1e-3, diameter_m=300.0),
+    # wide field far over the bound (6.2e-2 rad): the separable choice falls back to the direct kernel
+    "wide_field_direct": lambda: small32(N=512, cell=1e-3, diameter_m=800.0),
 }
 
 
@@ -377,3 +381,10 @@ def test_stage_calls_stay_unfused():
     idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
     idg.device_errors()
     parity(sub.cpu().numpy(), O.subgrid_images(wl, op), "stage gridder, long K_p")
+
+
+def test_separable_flag_follows_the_bound():
+    near = idg.plan_from_workload(CASES["wide_field_near_bound"]())
+    far = idg.plan_from_workload(CASES["wide_field_direct"]())
+    assert near.stats.separable == 1 and 1.2e-3 < near.stats.sep_phase <= 1.38e-3
+    assert far.stats.separable == 0 and far.stats.sep_phase > 1e-2

@@ -1,0 +1,89 @@
+"""Host-side pins of the separable form (no GPU).
+
+The separable kernels write the phasor of Eq. (ShiftedDirectImaging) as
+exp(i (a X + c s(x))) exp(i (b Y + c t(y))) (1 + i c r(x, y)) with
+n'(x, y) = s(x) + t(y) + r(x, y).  These tests check, in FP64 numpy and
+independently of the library's code, (1) that the factorisation is exact up to
+the dropped remainder and that the dropped part obeys the theta^2 / 2 bound the
+plan relies on, and (2) that the plan's reported theta equals its definition:
+max over planned visibilities of |2 pi (w - w0)| times max |r|.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1909_07226_gb300 import synthetic as syn
+
+
+def _nprime(L, S):
+    X = np.arange(L) - L / 2
+    l = X * S / L
+    m = X * S / L
+    ll, mm = np.meshgrid(l, m)            # [y][x]
+    return np.sqrt(1.0 - ll * ll - mm * mm) - 1.0
+
+
+def _split(L, S):
+    n1 = _nprime(L, S)
+    s = n1[L // 2, :]                      # row through the centre: n'(x, Y = 0)
+    t = n1[:, L // 2]                      # column: n'(X = 0, y)
+    r = n1 - s[None, :] - t[:, None]
+    return n1, s, t, r
+
+
+@pytest.mark.parametrize("S,c_max", [(0.04096, 2080.0), (0.128, 700.0), (0.5, 20.0)])
+def test_first_order_separable_phasor_error_bound(S, c_max):
+    L = 32
+    n1, s, t, r = _split(L, S)
+    rng = np.random.default_rng(5)
+    X = np.arange(L) - L / 2
+    for _ in range(20):
+        a, b = rng.uniform(-np.pi, np.pi, 2)
+        c = rng.uniform(-c_max, c_max)
+        exact = np.exp(1j * (a * X[None, :] + b * X[:, None] + c * n1))
+        ex = np.exp(1j * (a * X + c * s))
+        ey = np.exp(1j * (b * X + c * t))
+        sep0 = ey[:, None] * ex[None, :]
+        # the zeroth-order factorisation leaves exactly exp(i c r)
+        np.testing.assert_allclose(exact, sep0 * np.exp(1j * c * r), rtol=0, atol=1e-12)
+        first = sep0 * (1.0 + 1j * c * r)
+        theta = abs(c) * np.abs(r).max()
+        err = np.abs(first - exact).max()
+        assert err <= 0.5 * theta ** 2 * (1 + 1e-9) + 1e-14
+
+
+def test_remainder_is_fourth_order_in_the_direction_cosines():
+    # r = -l^2 m^2 / 4 + O(6th order): halving the field shrinks it 16x
+    L = 32
+    r1 = np.abs(_split(L, 0.04)[3]).max()
+    r2 = np.abs(_split(L, 0.02)[3]).max()
+    assert 15.5 < r1 / r2 < 16.5
+
+
+def _theta_definition(wl):
+    op = O.plan(wl)
+    L, S = wl.subgrid_size, wl.grid_size * wl.cell_size
+    r_max = np.abs(_split(L, S)[3]).max()
+    c = 299792458.0
+    dw = 0.0
+    for row in op.desc:
+        bl, t0, nt, c0, nc = row[O.D_BL], row[O.D_T0], row[O.D_NT], row[O.D_C0], row[O.D_NC]
+        w0 = (row[O.D_LAYER] + op.k_min) * wl.w_step if wl.w_step > 0 else 0.0
+        w = wl.uvw_m[bl, t0:t0 + nt, 2][:, None] * wl.freqs_hz[None, c0:c0 + nc] / c
+        dw = max(dw, np.abs(w - w0).max())
+    return 2 * np.pi * dw * r_max
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12),
+                                dict(N=256, cell=5e-4, diameter_m=800.0), dict(N=256, cell=1e-3, diameter_m=300.0),
+                                dict(N=512, cell=1e-3, diameter_m=800.0)])
+def test_plan_reports_the_remainder_phase(kw):
+    from paper_1909_07226_gb300 import idg
+    args = dict(seed=1032, n_st=5, n_t=48, n_chan=5, L=32, N=128, max_t=48, n_slots=1, flag_p=0.1,
+                diameter_m=3000.0)
+    args.update(kw)
+    wl = syn.make_small(**args)
+    p = idg.plan_from_workload(wl)
+    want = _theta_definition(wl)
+    assert p.stats.sep_phase == pytest.approx(want, rel=1e-9, abs=1e-15)
+    assert p.stats.separable == (1 if want <= 1.38e-3 else 0)
