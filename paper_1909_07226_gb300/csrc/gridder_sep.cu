@@ -30,8 +30,11 @@
 // A_hi [B_hi (128 rows) | B_lo (m = 0, 64 rows)], a second of N = 64 adds
 // A_lo B_hi (m = 0) to the correction columns.  The tensor cores accumulate
 // without rounding to nearest, so every FOLD groups of 8 visibilities the
-// accumulators are added into FP32 sums in shared memory (RN) and restarted;
-// two accumulator sets alternate so the MMAs never wait for a fold.
+// accumulator is added into FP32 sums in shared memory (RN) and restarted.
+// The producers read it as soon as the period's MMAs are done and release it
+// before adding, so the MMAs wait only for the tensor-memory loads; the
+// tensor memory goes to four A stages instead (three stages of lookahead
+// cover the round trip MMA -> producers -> MMA).
 //
 // Schedule.  One CTA per subgrid, one CTA per SM: sixteen producer warps and
 // one MMA warp.  A stage is four groups of 8 visibilities: per stage each
@@ -42,8 +45,8 @@
 // Visibilities are staged 512 at a time; the next batch is loaded into
 // registers while the current one is processed.
 // Tensor memory (512 columns):
-//   accumulator set p at 192 p: main (m, x, re/im) 0..127, correction (m = 0) 128..191
-//   A stage s at 384 + 64 s, group i at + 16 i: 8 columns hi, 8 lo
+//   accumulator: main (m, re/im, x) 0..127, correction (m = 0) 128..191
+//   A stage s at 192 + 64 s, group i at + 16 i: 8 columns hi, 8 lo
 // Every wait is bounded; after a failed wait a thread skips every later wait,
 // the error word is set and no output is written.
 #include "batch_jobs.cuh"
@@ -71,7 +74,7 @@ constexpr int VB = NP;                         // visibilities per staged batch 
 constexpr int GB = VB / 8;                     // groups per batch
 constexpr int FOLD = 64;                       // groups per accumulation period
 constexpr int SG = 4;                          // groups of 8 visibilities per stage
-constexpr int STAGES = 2;
+constexpr int STAGES = 4;
 constexpr int B_GROUP = 192 * 32;              // B of one group: 192 rows x 16 K FP16 (hi 128 rows, then lo 64)
 constexpr int B_STAGE = SG * B_GROUP;
 constexpr int COEF_OFF = STAGES * B_STAGE;     // [2][VB] float4 (a, b, c, 0)
@@ -79,10 +82,12 @@ constexpr int VIS_OFF = COEF_OFF + 2 * VB * 16;   // [2][VB][4] float2 (scaled V
 constexpr int FOLD_OFF = VIS_OFF + 2 * VB * 32;   // [32][NP] float: folded sums of each producer
 constexpr int SEP_SMEM = FOLD_OFF + 32 * NP * 4;
 constexpr int FFT_P = SL + 1;
-constexpr uint32_t ACC_STRIDE = 192, A_COL = 384;
+constexpr uint32_t A_COL = 192;                 // accumulator 0..191, then the A stages
 constexpr uint32_t IDESC_N192 = idesc_m128(192), IDESC_N64 = idesc_m128(64);
 static_assert(4 * SL * FFT_P * 8 <= FOLD_OFF, "transform planes fit over the stage buffers");
 static_assert(A_COL + 16 * SG * STAGES <= 512, "tensor memory");
+static_assert(FOLD / SG >= STAGES, "a period spans at least STAGES stages");
+static_assert((STAGES & (STAGES - 1)) == 0, "STAGES is a power of two");
 static_assert(FOLD % SG == 0 && GB % SG == 0, "periods and batches are whole stages");
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
@@ -102,14 +107,13 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     float2 *s_fft = (float2 *)smem;                 // [4][L][L + 1] after the main loop
     float *s_fold = (float *)(smem + FOLD_OFF);     // [32][NP]: m = 0 sums (16), then m = 1 (16)
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_foldbar[2], s_folded[2], s_drain;
-    __shared__ float s_red[NPW];
+    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_foldbar, s_folded, s_drain;
+    __shared__ float s_red[2][NPW];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool mma_warp = warp == NPW;
     const int total_groups = (d.kp + 7) / 8;
-    const int n_batches = (d.kp + VB - 1) / VB;
-    const int n_per = (total_groups + FOLD - 1) / FOLD;
+    const int n_batches = (d.kp + VB - 1) / VB;     // = accumulation periods (FOLD = GB)
 
     if (mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -121,59 +125,46 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             mbar_init(smem_u32(&s_full[s]), NPW);
             mbar_init(smem_u32(&s_empty[s]), 1);
         }
-        for (int p = 0; p < 2; ++p) {
-            mbar_init(smem_u32(&s_foldbar[p]), 1);
-            mbar_init(smem_u32(&s_folded[p]), NPW);
-        }
+        mbar_init(smem_u32(&s_foldbar), 1);
+        mbar_init(smem_u32(&s_folded), NPW);
         mbar_init(smem_u32(&s_drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // per-subgrid scale of V (producers)
-    float vmax = 0.0f;
-    if (!mma_warp)
-        for (int k = tid; k < d.kp; k += NP) {
-            int t, c;
-            const size_t vi = vis_index(g, d, k, t, c);
-            if (!(flags && flags[vi])) {
-                const float4 a = vis[2 * vi], b = vis[2 * vi + 1];
-                vmax = fmaxf(vmax, fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
-                                         fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w)))));
-            }
-        }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, off));
-    if (lane == 0 && !mma_warp) s_red[warp] = vmax;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
     bool failed = false;
-    float inv_scale = 1.0f;
-    const int q = warp & 3, sl = warp >> 2;         // lane quarter (polarisation) and column slice of the fold
+    const int yq = warp & 3, sl = warp >> 2;        // lane quarter (rows 32 yq ..) and fold column slice
 
     if (mma_warp) {
         if (lane == 0) {
+            // descriptors and tensor-memory addresses advance by constants: stage s, group i at
+            // B + s B_STAGE + i B_GROUP (the descriptor's address field counts 16-byte units)
+            const uint64_t db0 = smem_desc(smem_u32(sB));
             const int n_stages = (total_groups + SG - 1) / SG;
+            constexpr int SPP = FOLD / SG;                  // stages per accumulation period
             for (int st = 0; st < n_stages; ++st) {
-                const int s = st % STAGES;
+                const int s = st & (STAGES - 1);
+                const bool first = st % SPP == 0, last = st % SPP == SPP - 1 || st == n_stages - 1;
+                if (first && st > 0) {         // the producers have read the previous period
+                    wait_or_fail(smem_u32(&s_folded), (uint32_t)(((st / SPP) - 1) & 1), failed);
+                }
                 wait_or_fail(smem_u32(&s_full[s]), (uint32_t)((st / STAGES) & 1), failed);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int ng = min(SG, total_groups - st * SG);
-                for (int i = 0; i < ng; ++i) {
-                    const int gc = st * SG + i, P = gc / FOLD, p = P & 1;
-                    const bool first = gc % FOLD == 0;
-                    if (first && P >= 2) {
-                        wait_or_fail(smem_u32(&s_folded[p]), (uint32_t)(((P - 2) >> 1) & 1), failed);
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t dbs = db0 + (uint64_t)((s * B_STAGE) >> 4);
+                const uint32_t ats = tmem + A_COL + 64u * (uint32_t)s;
+#pragma unroll
+                for (int i = 0; i < SG; ++i) {
+                    if (i < ng) {
+                        mma_ta_i(tmem, ats + 16u * i, dbs + (uint64_t)((i * B_GROUP) >> 4), IDESC_N192,
+                                 (first && i == 0) ? 0u : 1u);
+                        mma_ta_i(tmem + 128u, ats + 16u * i + 8u, dbs + (uint64_t)((i * B_GROUP) >> 4), IDESC_N64, 1u);
                     }
-                    const uint64_t db = smem_desc(smem_u32(sB + s * B_STAGE + i * B_GROUP));
-                    const uint32_t at = tmem + A_COL + 64u * (uint32_t)s + 16u * (uint32_t)i;
-                    const uint32_t dt = tmem + ACC_STRIDE * (uint32_t)p;
-                    mma_ta_i(dt, at, db, IDESC_N192, first ? 0u : 1u);
-                    mma_ta_i(dt + 128u, at + 8u, db, IDESC_N64, 1u);
-                    if (gc % FOLD == FOLD - 1 || gc == total_groups - 1) commit(smem_u32(&s_foldbar[p]));
                 }
+                if (last) commit(smem_u32(&s_foldbar));
                 commit(smem_u32(&s_empty[s]));
             }
             commit(smem_u32(&s_drain));
@@ -182,26 +173,19 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         }
         failed = __shfl_sync(0xffffffffu, failed, 0);
     } else {
-        float m = 0.0f;
-#pragma unroll
-        for (int w = 0; w < NPW; ++w) m = fmaxf(m, s_red[w]);
-        int e2 = 0;
-        if (m > 0.0f) frexpf(m, &e2);
-        const float scale = ldexpf(1.0f, 10 - e2);
-        inv_scale = ldexpf(1.0f, e2 - 10);
-        // A rows (q, y = lane) of group warp / 4 of each stage
-        const int ga = warp >> 2;
-        const float Yv = (float)(lane - SL / 2);
-        const float ty = g.sep[SL + lane];
-        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-        // B entries: x = 4 (warp & 7) + (lane & 3), re/im = (lane >> 2) & 1, j = 4 (warp >> 3) + (lane >> 3)
-        const int xb = 4 * (warp & 7) + (lane & 3), cb = (lane >> 2) & 1, jb = 4 * (warp >> 3) + (lane >> 3);
+        // A rows: r = 32 yq + lane holds polarisation qa = lane / 8 of pixel row y = 8 yq + lane % 8
+        const int qa = lane >> 3, ylo = lane & 7;
+        const int ga = warp >> 2;                   // group of the stage whose A entries this warp writes
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * yq) << 16);
+        // Ey of row y for visibilities 2 qa and 2 qa + 1 of the group: computed here, shared by shuffles
+        const float Yv = (float)(8 * yq + ylo - SL / 2);
+        const float ty = g.sep[SL + 8 * yq + ylo];
+        // B entries: x = 8 (warp & 3) + lane % 8, visibility j = 4 jh + lane / 8 of group i, where
+        // (i, jh) = (combo / 2, combo % 2) for combo = 2 (warp / 4) + t, t = 0, 1
+        const int xb = 8 * (warp & 3) + (lane & 7), jl = lane >> 3;
         const float Xv = (float)(xb - SL / 2);
         const float sx = g.sep[xb];
         const float csig = g.c_scale;
-        const int n0 = 2 * xb + cb;
-        const uint32_t off_h0 = kmaj_off(n0, 2 * jb), off_h1 = kmaj_off(64 + n0, 2 * jb);
-        const uint32_t off_l0 = kmaj_off(128 + n0, 2 * jb);
 
         // staging: visibility tid of batch b, loaded into registers one batch ahead
         float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
@@ -226,50 +210,57 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 }
             }
         };
+        // coefficients and raw V of the batch; the batch's largest |component| into s_red[bb]
         auto store_batch = [&](int bb) {
             float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 v[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             if (pin) {
                 cf.x = (float)((pu * psc - d.u0) * g.k_uv);
                 cf.y = (float)((pv * psc - d.v0) * g.k_uv);
                 cf.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
                 if (!pflag) {
-                    v[0] = make_float2(pa.x * scale, pa.y * scale);
-                    v[1] = make_float2(pa.z * scale, pa.w * scale);
-                    v[2] = make_float2(pb.x * scale, pb.y * scale);
-                    v[3] = make_float2(pb.z * scale, pb.w * scale);
+                    a = pa;
+                    b = pb;
                 }
             }
             s_coef[bb * VB + tid] = cf;
             float4 *dv = (float4 *)(s_vis + (size_t)(bb * VB + tid) * 4);
-            dv[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-            dv[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+            dv[0] = a;
+            dv[1] = b;
+            float m = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w))),
+                            fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)), fmaxf(fabsf(b.z), fabsf(b.w))));
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (lane == 0) s_red[bb][warp] = m;
         };
+        float inv_sc0 = 1.0f, inv_sc1 = 1.0f;        // 1 / scale of the last even and odd batch
 
         auto fold = [&](int P) {
-            const int p = P & 1;
-            wait_or_fail(smem_u32(&s_foldbar[p]), (uint32_t)((P >> 1) & 1), failed);
+            wait_or_fail(smem_u32(&s_foldbar), (uint32_t)(P & 1), failed);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // this thread's row (q, y = lane), columns of x in [8 sl, 8 sl + 8): sums at s_fold[c][tid]
-            uint32_t r[16], rc[16];
-            const uint32_t base = lane_base + ACC_STRIDE * (uint32_t)p + 16u * (uint32_t)sl;
-            tmem_ld16(base, r);                      // main, m = 0
-            tmem_ld16(base + 128u, rc);              // correction, m = 0
+            // this thread's row, columns 16 sl .. of the m = 0 block (main + correction) and of m = 1;
+            // the accumulator is released right after the loads
+            uint32_t r[16], rc[16], r1[16];
+            const uint32_t base = lane_base + 16u * (uint32_t)sl;
+            tmem_ld16(base, r);
+            tmem_ld16(base + 128u, rc);
+            tmem_ld16(base + 64u, r1);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_folded));
+            const float is = (P & 1) ? inv_sc1 : inv_sc0;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const float v = __uint_as_float(r[c]) + __uint_as_float(rc[c]);
+                const float v = (__uint_as_float(r[c]) + __uint_as_float(rc[c])) * is;
                 float &f = s_fold[c * NP + tid];
                 f = P ? f + v : v;
             }
-            tmem_ld16(base + 64u, r);                // main, m = 1
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
+                const float v = __uint_as_float(r1[c]) * is;
                 float &f = s_fold[(16 + c) * NP + tid];
-                f = P ? f + __uint_as_float(r[c]) : __uint_as_float(r[c]);
+                f = P ? f + v : v;
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&s_folded[p]));
         };
 
         load_batch(0);
@@ -278,6 +269,15 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         int next_fold = 0;
         for (int b = 0; b < n_batches; ++b) {
             const int bb = b & 1;
+            // this batch's power-of-two scale: largest |component| of V in [2^9, 2^10)
+            float m = 0.0f;
+#pragma unroll
+            for (int w = 0; w < NPW; ++w) m = fmaxf(m, s_red[bb][w]);
+            int e2 = 0;
+            if (m > 0.0f) frexpf(m, &e2);
+            const float scale = ldexpf(1.0f, 10 - e2);
+            if (bb) inv_sc1 = ldexpf(1.0f, e2 - 10);
+            else inv_sc0 = ldexpf(1.0f, e2 - 10);
             if (b + 1 < n_batches) load_batch(b + 1);
             const float4 *coef = s_coef + bb * VB;
             const float2 *vb = s_vis + (size_t)bb * VB * 4;
@@ -286,73 +286,96 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 const int st = b * (GB / SG) + si;
                 const int s = st % STAGES;
                 if (st >= STAGES) wait_or_fail(smem_u32(&s_empty[s]), (uint32_t)(((st / STAGES) - 1) & 1), failed);
-                // B entry pairs, one per group: beta = Ex_k(x) (m = 0, hi and lo) and c_k sigma Ex_k(x) (m = 1, hi)
+                // the MMAs of stage st - STAGES are done: when that was the last stage of period
+                // next_fold, read it out now (the next period's first MMA waits for it)
+                if (next_fold < n_batches - 1 && st - STAGES == (next_fold + 1) * (FOLD / SG) - 1) {
+                    fold(next_fold);
+                    ++next_fold;
+                }
+                // A entries of group ga: scale V_kq Ey_k(y) for its 8 visibilities
+                {
+                    const int kb = 8 * (SG * si + ga);
+                    float ec[2], es[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float4 cf = coef[kb + 2 * qa + h];
+                        float sn, cs;
+                        __sincosf(fmaf(cf.z, ty, cf.y * Yv), &sn, &cs);
+                        ec[h] = cs * scale;
+                        es[h] = sn * scale;
+                    }
+                    uint32_t e[16];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int src = 8 * (j >> 1) + ylo;
+                        const float cs = __shfl_sync(0xffffffffu, (j & 1) ? ec[1] : ec[0], src);
+                        const float sn = __shfl_sync(0xffffffffu, (j & 1) ? es[1] : es[0], src);
+                        const float2 v = vb[(kb + j) * 4 + qa];
+                        split_e(fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs), e[j], e[8 + j]);
+                    }
+                    tmem_st16(lane_base + A_COL + 64u * (uint32_t)s + 16u * (uint32_t)ga, e);
+                }
+                // B entries: beta = Ex_k(x) (m = 0: hi and lo) and c_k sigma Ex_k(x) (m = 1: hi), rows
+                // (m, re, x) = (Re beta, -Im beta) and (m, im, x) = (Im beta, Re beta)
                 uint8_t *Bs = sB + s * B_STAGE;
 #pragma unroll
-                for (int i = 0; i < SG; ++i) {
-                    const float4 cf = coef[8 * (SG * si + i) + jb];
+                for (int t = 0; t < 2; ++t) {
+                    const int combo = 2 * (warp >> 2) + t, i = combo >> 1, j = 4 * (combo & 1) + jl;
+                    const float4 cf = coef[8 * (SG * si + i) + j];
                     float sn, cs;
                     __sincosf(fmaf(cf.z, sx, cf.x * Xv), &sn, &cs);
-                    const float vx = cb ? sn : cs, vy = cb ? cs : -sn;
-                    uint32_t h0, l0;
-                    split_e(vx, vy, h0, l0);
+                    uint32_t hr, lr, hi_, li_;
+                    split_e(cs, -sn, hr, lr);
+                    split_e(sn, cs, hi_, li_);
                     const float cz = cf.z * csig;
-                    const uint32_t h1 = pack_f16x2(cz * vx, cz * vy);
-                    *(uint32_t *)(Bs + i * B_GROUP + off_h0) = h0;
-                    *(uint32_t *)(Bs + i * B_GROUP + off_h1) = h1;
-                    *(uint32_t *)(Bs + i * B_GROUP + off_l0) = l0;
+                    const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn), h1i = pack_f16x2(cz * sn, cz * cs);
+                    uint8_t *Bg = Bs + i * B_GROUP;
+                    const uint32_t kc = (uint32_t)(j >> 2) * kLBO + (uint32_t)(xb & 7) * 16 + (uint32_t)(j & 3) * 4;
+                    const uint32_t rg = (uint32_t)(xb >> 3) * kSBO;        // row group of x within a 32-row block
+                    *(uint32_t *)(Bg + rg + kc) = hr;                      // rows   0 + x: m = 0, re
+                    *(uint32_t *)(Bg + 4 * kSBO + rg + kc) = hi_;          // rows  32 + x: m = 0, im
+                    *(uint32_t *)(Bg + 8 * kSBO + rg + kc) = h1r;          // rows  64 + x: m = 1, re
+                    *(uint32_t *)(Bg + 12 * kSBO + rg + kc) = h1i;         // rows  96 + x: m = 1, im
+                    *(uint32_t *)(Bg + 16 * kSBO + rg + kc) = lr;          // rows 128 + x: m = 0, re, lo
+                    *(uint32_t *)(Bg + 20 * kSBO + rg + kc) = li_;         // rows 160 + x: m = 0, im, lo
                 }
-                // A entries of group ga: V_kq Ey_k(y) for its 8 visibilities
-                uint32_t e[16];
-                const int kb = 8 * (SG * si + ga);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 cf = coef[kb + j];
-                    float sn, cs;
-                    __sincosf(fmaf(cf.z, ty, cf.y * Yv), &sn, &cs);
-                    const float2 v = vb[(kb + j) * 4 + q];
-                    split_e(fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs), e[j], e[8 + j]);
-                }
-                tmem_st16(lane_base + A_COL + 64u * (uint32_t)s + 16u * (uint32_t)ga, e);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&s_full[s]));
-                // fold period next_fold half-way through the following one
-                if (next_fold < n_per - 1 && (st + 1) * SG == (next_fold + 1) * FOLD + FOLD / 2) {
-                    fold(next_fold);
-                    ++next_fold;
-                }
             }
             if (b + 1 < n_batches) {
                 store_batch(bb ^ 1);
                 producers_sync();
             }
         }
-        while (next_fold < n_per) {
+        while (next_fold < n_batches) {
             fold(next_fold);
             ++next_fold;
         }
         if (failed && lane == 0) atomicExch(&g_sep_error, 1);
-        producers_sync();      // every producer is past the stage and batch buffers
+        producers_sync();      // every producer is past the stage and batch buffers and has folded
         if (!failed) {
-            // I = S0 + i r S1 / sigma, unscaled, into the polarisation planes
+            // I = S0 + i r S1 / sigma into the polarisation planes.  Column slice sl holds the
+            // re (sl < 2) or im (sl >= 2) part of x in [16 (sl & 1), + 16); the thread with
+            // slice sl takes 8 of those x, reading the re and im parts of both slices.
+            const int x0 = 16 * (sl & 1) + 8 * (sl >> 1);
+            const int tre = tid & ~256, tim = tid | 256;     // threads holding re and im of this row and x range
             const float rs = 1.0f / csig;
+            const int y = 8 * yq + ylo;
 #pragma unroll
             for (int xi = 0; xi < 8; ++xi) {
-                const int x = 8 * sl + xi;
-                const float rr = g.sep[2 * SL + lane * SL + x] * rs;
+                const int x = x0 + xi, c = x & 15;
                 float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f;
-                if (n_per) {
-                    s0r = s_fold[(2 * xi) * NP + tid];
-                    s0i = s_fold[(2 * xi + 1) * NP + tid];
-                    s1r = s_fold[(16 + 2 * xi) * NP + tid];
-                    s1i = s_fold[(17 + 2 * xi) * NP + tid];
+                if (n_batches) {
+                    s0r = s_fold[c * NP + tre];
+                    s0i = s_fold[c * NP + tim];
+                    s1r = s_fold[(16 + c) * NP + tre];
+                    s1i = s_fold[(16 + c) * NP + tim];
                 }
-                const float re = fmaf(-rr, s1i, s0r) * inv_scale;
-                const float im = fmaf(rr, s1r, s0i) * inv_scale;
-                s_fft[(q * SL + lane) * FFT_P + x] = make_float2(re, im);
+                const float rr = g.sep[2 * SL + y * SL + x] * rs;
+                s_fft[(qa * SL + y) * FFT_P + x] = make_float2(fmaf(-rr, s1i, s0r), fmaf(rr, s1r, s0i));
             }
         }
     }
