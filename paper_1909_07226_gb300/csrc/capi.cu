@@ -157,6 +157,7 @@ idg::Geometry idg_plan::geometry() const {
     g.sep = d_nprime + (size_t)L * L;
     g.separable = stats.separable;
     g.c_scale = c_scale;
+    g.r_scale = r_scale;
     g.ds = ds;
     g.recurrence = opts.precision_mode == IDG_PHASOR_RECURRENCE ? 1 : 0;
     g.anchor = 8;
@@ -399,6 +400,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         p->sep_theta = c_max * r_max;
         p->c_scale = 1.0f;
         if (c_max > 1.0) p->c_scale = (float)std::ldexp(1.0, -(int)std::ceil(std::log2(c_max)));
+        p->r_scale = r_max > 0.0 ? (float)std::ldexp(1.0, std::min(100, (int)std::floor(std::log2(1.0 / r_max)))) : 1.0f;
         p->stats.separable = (L == 32 && p->sep_theta <= kSepThetaMax) ? 1 : 0;
         p->stats.sep_phase = p->sep_theta;
     }
@@ -644,7 +646,8 @@ static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int
     const SubgridSet all = order_of(p, o, first, count);
     if (fused_degrid(p, all)) {
         ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, count, o));
-        return launch_degridder_tcw_fused(g, all, grid, flags, aterms, taper, vis_out, s);
+        return g.separable ? launch_degridder_sep_fused(g, all, grid, flags, aterms, taper, vis_out, s)
+                           : launch_degridder_tcw_fused(g, all, grid, flags, aterms, taper, vis_out, s);
     }
     idg_status st = IDG_OK;
     for (int64_t f = first; f < first + count && st == IDG_OK; f += chunk) {

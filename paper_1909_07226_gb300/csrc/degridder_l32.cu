@@ -36,7 +36,29 @@ idg_status launch_tcw_auto(const Geometry &g, const SubgridSet &set, const void 
     return launch_tcw(g, set, sub, flags, aterms, taper, vis_out, s);
 }
 
-const DegridVariant kD32[] = {{"tcgen05_tmemA_ws_nt288_auto512", launch_tcw_auto<512>},
+// separable tensor-core form where the plan allows it (by the same K_p rule), else the above
+idg_status launch_sep_auto(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
+                           const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
+    if (!g.separable) return launch_tcw_auto<512>(g, set, sub, flags, aterms, taper, vis_out, s);
+    if (!set.kp_host) return fail(IDG_ERR_INVALID_ARG, "degridder: K_p of the subgrid set is required");
+    int64_t small = 0, all = 0;
+    for (int64_t i = 0; i < set.count; ++i) {
+        all += set.kp_host[i];
+        if (set.kp_host[i] < 512) small += set.kp_host[i];
+    }
+    if (2 * small > all) return degrid_f2_launch_static<32, 4, 128, 3>(g, set, sub, flags, aterms, taper, vis_out, s);
+    return launch_degridder_sep(g, set, sub, flags, aterms, taper, vis_out, (void *)s);
+}
+
+idg_status launch_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
+                      const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
+    if (!g.separable) return launch_tcw(g, set, sub, flags, aterms, taper, vis_out, s);
+    return launch_degridder_sep(g, set, sub, flags, aterms, taper, vis_out, (void *)s);
+}
+
+const DegridVariant kD32[] = {{"tcgen05_separable_auto512", launch_sep_auto},
+                              {"tcgen05_separable", launch_sep},
+                              {"tcgen05_tmemA_ws_nt288_auto512", launch_tcw_auto<512>},
                               DV_F2(32, 4, 128, 3),      {"tcgen05_tmemA_ws_nt288", launch_tcw},
                               DV_RT(32, 4, 256),         DV_ST(32, 4, 256, 3),
                               DV_ST(32, 4, 128, 5),      DV_ST(32, 4, 128, 6), DV_ST(32, 2, 256, 4),

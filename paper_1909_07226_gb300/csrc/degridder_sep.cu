@@ -1,0 +1,427 @@
+// Separable degridder on the tensor cores (tcgen05), L = 32.
+//
+// The visibilities of Algorithm 2 from the corrected subgrid image P_q(x, y)
+// (taper and A_p P A_q^H applied) are
+//   y_kq = sum_{x,y} P_q(x, y) exp(-i (a_k X + b_k Y + c_k n'(x, y))).
+// With the split n' = s(x) + t(y) + r(x, y) used by the separable gridder and
+// exp(-i c r) = 1 - i c r + O(theta^2 / 2) (theta = max |c| max |r|, checked
+// by the plan),
+//   y_kq = sum_y Ey*_k(y) [T0_kq(y) - i c_k T1_kq(y)],
+//   T_mkq(y) = sum_x Ex*_k(x) Q_mq(x, y),  Q0 = P, Q1 = P r,
+//   Ex*_k(x) = exp(-i (a_k X + c_k s(x))),  Ey*_k(y) = exp(-i (b_k Y + c_k t(y))).
+// The contraction over x is a complex matrix product on the tensor cores: rows
+// (visibility, re/im) of a tile of 64 visibilities, columns (m, q, y), 256 of
+// them, K = (x, re/im), 64.  The sum over y with the visibility's own phasors
+// runs on the CUDA cores (FP32, round to nearest), one thread per tile row.
+//
+// GEMM.  A holds the real 2 x 2 embedding of E = Ex*_k(x): row (k, re) =
+// (Re E, -Im E), row (k, im) = (Im E, Re E) over K = (x, re/im); B[(m, q, y)]
+// = (Re, Im) of Q_mq(x, y) over the same K, scaled by a power of two per
+// subgrid (and Q1 by rho, a power of two with max |r| rho <= 1).  Both are
+// split into FP16 hi + lo; the m = 0 block takes A_hi B_hi + A_hi B_lo +
+// A_lo B_hi, the m = 1 block (at most theta relative) A_hi B_hi.  Per K step
+// of 16: N = 256 (A_hi, [B0_hi | B1_hi]), N = 128 (A_hi, B0_lo), N = 128
+// (A_lo, B0_hi).  The accumulation is 12 MMAs long, so no folds are needed.
+//
+// Schedule.  One CTA per subgrid, one CTA per SM.  All warps first form the
+// image (split from the grid and inverse transform in shared memory when
+// FUSED), the corrections, the scale and B (shared memory, fixed for the
+// subgrid).  Then per tile: eight producer warps stage the coefficients and
+// write A (shared memory, one core matrix per warp store) and the Ey* table;
+// the MMA warp issues the 12 MMAs into one of two accumulators; eight consumer
+// warps read their rows' columns, sum over y, pair the re/im rows by a shuffle
+// and write the visibilities.  Tensor memory: accumulator b at 256 b.
+// Every wait is bounded; after a failed wait a thread skips every later wait,
+// the error word is set and no output is written.
+#include "batch_jobs.cuh"
+#include "device_common.cuh"
+#include "fft_impl.cuh"
+#include "tc_common.cuh"
+
+namespace idg {
+
+// device error word of the separable degridder (0 = ok); read and cleared by
+// idg_device_errors
+__device__ int g_sepd_error = 0;
+
+namespace {
+
+using namespace dev;
+using namespace tc;
+
+constexpr int SL = 32;
+constexpr int SPIX = SL * SL;
+constexpr int NPW = 8, NCW = 8;                 // producer and consumer warps
+constexpr int NP = NPW * 32, NC = NCW * 32;
+constexpr int MMA_WARP = NPW + NCW;
+constexpr int NT = NP + NC + 32;
+constexpr int TV = 64;                          // visibilities per tile (rows 2 k + re/im)
+constexpr int AST = 2;                          // A, Ey* and coefficient stages
+constexpr int KT = 4;                           // K steps of 16 (8 x, re/im) over the 32 x
+constexpr int T4K = 128 * 32;                   // 128 rows x 16 K FP16
+constexpr int BH_OFF = 0;                       // B hi: [KT][256 rows: m = 0 (q, y), then m = 1]
+constexpr int BL_OFF = BH_OFF + KT * 2 * T4K;   // B lo (m = 0): [KT][128 rows]
+constexpr int A_OFF = BL_OFF + KT * T4K;        // A: [AST][hi, lo][KT][128 rows]
+constexpr int A_STAGE = 2 * KT * T4K;
+constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [AST][32 y][TV] float2
+constexpr int EY_STAGE = SL * TV * 8;
+constexpr int CF_OFF = EY_OFF + AST * EY_STAGE; // coefficients: [AST][TV] float4 (a, b, c, 0)
+constexpr int SEPD_SMEM = CF_OFF + AST * TV * 16;
+constexpr int FFT_P = SL + 1;
+constexpr uint32_t IDESC_N256 = idesc_m128(256), IDESC_N128 = idesc_m128(128);
+static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
+static_assert(AST == 2, "stage and accumulator indices coincide");
+
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
+
+// Visibilities of subgrid d of geometry g from its image src[L][L][4], or with
+// FUSED from the grid src[layer][N][N][4]: split and transformed in shared memory
+// first (Algorithm 2: split from the master grid, "IFFT", image-domain kernel, sum).
+template <bool FUSED>
+__device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevSubgrid d,
+                                                   const float4 *__restrict__ src, const uint8_t *__restrict__ flags,
+                                                   const float4 *__restrict__ aterms, const float *__restrict__ taper,
+                                                   float4 *__restrict__ vis_out) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    float2 *s_fft = (float2 *)(smem + A_OFF);       // [4][L][L + 1] during the prologue
+    float4 *s_coef = (float4 *)(smem + CF_OFF);
+    float2 *s_ey = (float2 *)(smem + EY_OFF);
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyempty[AST], s_dfull[2], s_dempty[2], s_drain;
+    __shared__ float s_red[NT / 32];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_tiles = (d.kp + TV - 1) / TV;
+
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&s_tmem)), "n"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < AST; ++s) {
+            mbar_init(smem_u32(&s_afull[s]), NPW);
+            mbar_init(smem_u32(&s_aempty[s]), 1);
+            mbar_init(smem_u32(&s_eyempty[s]), NCW);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&s_dfull[b]), 1);
+            mbar_init(smem_u32(&s_dempty[b]), NCW);
+        }
+        mbar_init(smem_u32(&s_drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+
+    // ---- prologue: the corrected image P = taper A_p I A_q^H into the planes
+    if (FUSED) {
+        const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
+        for (int pix = tid; pix < SPIX; pix += NT) {
+            const int i = pix / SL, j = pix % SL;
+            const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
+            const float sg = ((i + j) & 1) ? -1.0f : 1.0f;
+            const float4 a = gsrc[2 * gp], b = gsrc[2 * gp + 1];
+            s_fft[(0 * SL + i) * FFT_P + j] = make_float2(sg * a.x, sg * a.y);
+            s_fft[(1 * SL + i) * FFT_P + j] = make_float2(sg * a.z, sg * a.w);
+            s_fft[(2 * SL + i) * FFT_P + j] = make_float2(sg * b.x, sg * b.y);
+            s_fft[(3 * SL + i) * FFT_P + j] = make_float2(sg * b.z, sg * b.w);
+        }
+        __syncthreads();
+        fft2_planar<SL, +1>(s_fft, tid, NT);
+    }
+    float m = 0.0f;
+    for (int pix = tid; pix < SPIX; pix += NT) {
+        const int y = pix >> 5, x = pix & (SL - 1);
+        M22 P;
+        if (FUSED) {      // (-1)^(x+y) / L^2 of the transform
+            const float sg = ((x + y) & 1) ? -1.0f / SPIX : 1.0f / SPIX;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 v = s_fft[(q * SL + y) * FFT_P + x];
+                P.m[q] = make_float2(sg * v.x, sg * v.y);
+            }
+        } else {
+            P = load_m22(src + 2 * pix);
+        }
+        if (aterms) {
+            const size_t base = ((size_t)d.slot * g.n_stations) * SPIX;
+            const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * SPIX + pix));
+            const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * SPIX + pix));
+            P = mul_mul_herm(Ap, P, Aq);
+        }
+        const float tw = taper[pix];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 v = make_float2(tw * P.m[q].x, tw * P.m[q].y);
+            s_fft[(q * SL + y) * FFT_P + x] = v;
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) s_red[warp] = m;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    m = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) m = fmaxf(m, s_red[w]);
+    int e2 = 0;
+    if (m > 0.0f) frexpf(m, &e2);
+    const float scale = ldexpf(1.0f, 10 - e2);
+    const float inv_scale = ldexpf(1.0f, e2 - 10);
+    // B: Q0 = scale P (hi to rows 32 q + y, lo), Q1 = scale rho r P (hi to rows 128 + 32 q + y); one
+    // core matrix (8 rows y, 4 x) per warp store: warp-task wt = (q, y block, x chunk of 4)
+    if (warp < MMA_WARP) {
+        const float rs = g.r_scale;
+        for (int wt = warp; wt < 128; wt += MMA_WARP) {
+            const int q = wt >> 5, yb = (wt >> 3) & 3, xc = wt & 7;
+            const int y = 8 * yb + (lane >> 2), x = 4 * xc + (lane & 3);
+            const float2 p = s_fft[(q * SL + y) * FFT_P + x];
+            const float rr = g.sep[2 * SL + y * SL + x] * rs;
+            uint32_t h0, l0;
+            split_e(p.x * scale, p.y * scale, h0, l0);
+            const uint32_t h1 = pack_f16x2(p.x * rr * scale, p.y * rr * scale);
+            const uint32_t off = (uint32_t)(4 * q + yb) * kSBO + (uint32_t)(xc & 1) * kLBO + (uint32_t)(lane >> 2) * 16 +
+                                 (uint32_t)(lane & 3) * 4;
+            const int kk = xc >> 1;
+            *(uint32_t *)(smem + BH_OFF + kk * 2 * T4K + off) = h0;
+            *(uint32_t *)(smem + BH_OFF + kk * 2 * T4K + T4K + off) = h1;
+            *(uint32_t *)(smem + BL_OFF + kk * T4K + off) = l0;
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();      // B complete; the planes (over the A stages) are free
+
+    bool failed = false;
+    if (warp == MMA_WARP) {
+        if (lane == 0) {
+            const uint64_t da0 = smem_desc(smem_u32(smem + A_OFF));
+            const uint64_t dbh0 = smem_desc(smem_u32(smem + BH_OFF)), dbl0 = smem_desc(smem_u32(smem + BL_OFF));
+            for (int t = 0; t < n_tiles; ++t) {
+                const int s = t & 1;
+                wait_or_fail(smem_u32(&s_afull[s]), (uint32_t)((t >> 1) & 1), failed);
+                if (t >= 2) wait_or_fail(smem_u32(&s_dempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dt = tmem + 256u * (uint32_t)s;
+#pragma unroll
+                for (int kk = 0; kk < KT; ++kk) {
+                    const uint64_t dah = da0 + (uint64_t)((s * A_STAGE + kk * T4K) >> 4);
+                    const uint64_t dal = dah + (uint64_t)((KT * T4K) >> 4);
+                    const uint64_t dbh = dbh0 + (uint64_t)((kk * 2 * T4K) >> 4);
+                    const uint64_t dbl = dbl0 + (uint64_t)((kk * T4K) >> 4);
+                    mma_ss_i(dt, dah, dbh, IDESC_N256, kk > 0 ? 1u : 0u);
+                    mma_ss_i(dt, dah, dbl, IDESC_N128, 1u);
+                    mma_ss_i(dt, dal, dbh, IDESC_N128, 1u);
+                }
+                commit(smem_u32(&s_aempty[s]));
+                commit(smem_u32(&s_dfull[s]));
+            }
+            commit(smem_u32(&s_drain));
+            bool drained = false;
+            wait_or_fail(smem_u32(&s_drain), 0u, drained);     // bounded: let own MMAs finish before the free
+        }
+        failed = __shfl_sync(0xffffffffu, failed, 0);
+    } else if (warp < NPW) {
+        // ---- producers: coefficients, A (2 x 2 embedding of Ex*) and the Ey* table per tile
+        double pu = 0.0, pv = 0.0, pw = 0.0, psc = 0.0;
+        bool pin = false;
+        auto load_coef = [&](int t) {      // threads < TV: the raw coordinates of visibility t TV + tid
+            const int k = t * TV + tid;
+            pin = k < d.kp;
+            if (pin) {
+                int tt, c;
+                vis_index(g, d, k, tt, c);
+                const double *xw = g.uvw + ((size_t)d.bl * g.n_t + tt) * 3;
+                pu = xw[0];
+                pv = xw[1];
+                pw = xw[2];
+                psc = g.scale[c];
+            }
+        };
+        if (tid < TV) load_coef(0);
+        for (int t = 0; t < n_tiles; ++t) {
+            const int s = t & 1;
+            if (t >= 2) {
+                wait_or_fail(smem_u32(&s_aempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
+                wait_or_fail(smem_u32(&s_eyempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
+            }
+            if (tid < TV) {
+                float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (pin) {
+                    cf.x = (float)((pu * psc - d.u0) * g.k_uv);
+                    cf.y = (float)((pv * psc - d.v0) * g.k_uv);
+                    cf.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
+                }
+                s_coef[s * TV + tid] = cf;
+                if (t + 1 < n_tiles) load_coef(t + 1);
+            }
+            producers_sync();
+            const float4 *cf = s_coef + s * TV;
+            uint8_t *As = smem + A_OFF + s * A_STAGE;
+            // A: warp-task wt = warp + 8 i: row group rg = wt % 16 (visibilities 4 rg ..), x chunk kc = wt / 16;
+            // lane: row 8 rg + lane / 4 = 2 k + re/im, x = 4 kc + lane % 4
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const int wt = warp + NPW * i, rg = wt & 15, kc = wt >> 4;
+                const int k = 4 * rg + (lane >> 3), ci = (lane >> 2) & 1, x = 4 * kc + (lane & 3);
+                const float4 c = cf[k];
+                float sn, cs;
+                __sincosf(fmaf(c.z, g.sep[x], c.x * (float)(x - SL / 2)), &sn, &cs);
+                // E = cs - i sn: row re = (cs, sn), row im = (-sn, cs)
+                uint32_t h, l;
+                split_e(ci ? -sn : cs, ci ? cs : sn, h, l);
+                const uint32_t off = (uint32_t)(kc >> 1) * T4K + (uint32_t)rg * kSBO + (uint32_t)(kc & 1) * kLBO +
+                                     (uint32_t)(lane >> 2) * 16 + (uint32_t)(lane & 3) * 4;
+                *(uint32_t *)(As + off) = h;
+                *(uint32_t *)(As + KT * T4K + off) = l;
+            }
+            // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))): entry e = y TV + k
+            float2 *ey = s_ey + s * (SL * TV);
+#pragma unroll 4
+            for (int j = 0; j < SL * TV / NP; ++j) {
+                const int e = tid + NP * j, y = e / TV, k = e % TV;
+                const float4 c = cf[k];
+                float sn, cs;
+                __sincosf(fmaf(c.z, g.sep[SL + y], c.y * (float)(y - SL / 2)), &sn, &cs);
+                ey[e] = make_float2(cs, -sn);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_afull[s]));
+        }
+        if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
+    } else {
+        // ---- consumers: row 32 (warp % 4) + lane = 2 k + re/im of the tile, polarisations 2 h, 2 h + 1
+        const int qq = warp & 3, h = (warp - NPW) >> 2;
+        const int kl = 16 * qq + (lane >> 1), ci = lane & 1;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * qq) << 16);
+        for (int t = 0; t < n_tiles; ++t) {
+            const int s = t & 1;
+            wait_or_fail(smem_u32(&s_afull[s]), (uint32_t)((t >> 1) & 1), failed);
+            wait_or_fail(smem_u32(&s_dfull[s]), (uint32_t)((t >> 1) & 1), failed);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float2 *ey = s_ey + s * (SL * TV);
+            float acc[2][2][2];      // [m][q'][ (sum er T, sum ei T) ]
+#pragma unroll
+            for (int a = 0; a < 8; ++a) (&acc[0][0][0])[a] = 0.0f;
+#pragma unroll 1
+            for (int yc = 0; yc < 4; ++yc) {         // rows y in [8 yc, 8 yc + 8)
+                uint32_t r[4][8];
+#pragma unroll
+                for (int mq = 0; mq < 4; ++mq)       // (m, q') = (mq / 2, mq % 2): columns 128 m + 32 (2 h + q') + y
+                    tmem_ld8_nowait(lane_base + 256u * (uint32_t)s +
+                                        (uint32_t)(128 * (mq >> 1) + 64 * h + 32 * (mq & 1) + 8 * yc), r[mq]);
+                float2 e[8];
+#pragma unroll
+                for (int y = 0; y < 8; ++y) e[y] = ey[(8 * yc + y) * TV + kl];
+#pragma unroll
+                for (int mq = 0; mq < 4; ++mq) {
+                    tmem_wait_ld8(r[mq]);
+                    const int mm = mq >> 1, qp = mq & 1;
+#pragma unroll
+                    for (int y = 0; y < 8; ++y) {
+                        const float v = __uint_as_float(r[mq][y]);
+                        acc[mm][qp][0] = fmaf(e[y].x, v, acc[mm][qp][0]);
+                        acc[mm][qp][1] = fmaf(e[y].y, v, acc[mm][qp][1]);
+                    }
+                }
+            }
+            const float c1 = s_coef[s * TV + kl].z / g.r_scale;     // c_k / rho (Q1 holds rho r P)
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_u32(&s_dempty[s]));
+                mbar_arrive(smem_u32(&s_eyempty[s]));
+            }
+            // rows re (holds Re T) and im (Im T) of visibility kl: Re(E T) = er Tr - ei Ti, Im = er Ti + ei Tr
+            float o[2][2][2];
+#pragma unroll
+            for (int mm = 0; mm < 2; ++mm)
+#pragma unroll
+                for (int qp = 0; qp < 2; ++qp) {
+                    const float pa = __shfl_xor_sync(0xffffffffu, acc[mm][qp][0], 1);
+                    const float pb = __shfl_xor_sync(0xffffffffu, acc[mm][qp][1], 1);
+                    o[mm][qp][0] = acc[mm][qp][0] - pb;      // on the re row: er Tr - ei Ti
+                    o[mm][qp][1] = pa + acc[mm][qp][1];      // er Ti + ei Tr
+                }
+            const int k = t * TV + kl;
+            if (ci == 0 && k < d.kp && !failed) {
+                // y = T0 - i c_k T1 with T1 computed from rho r P
+                int tt, c;
+                const size_t vi = vis_index(g, d, k, tt, c);
+                float4 out;
+                out.x = (o[0][0][0] + c1 * o[1][0][1]) * inv_scale;
+                out.y = (o[0][0][1] - c1 * o[1][0][0]) * inv_scale;
+                out.z = (o[0][1][0] + c1 * o[1][1][1]) * inv_scale;
+                out.w = (o[0][1][1] - c1 * o[1][1][0]) * inv_scale;
+                if (flags && flags[vi]) out = make_float4(0.f, 0.f, 0.f, 0.f);
+                vis_out[2 * vi + h] = out;
+            }
+        }
+        if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(512));
+}
+
+// one CTA per subgrid of one plan (plan index idx[b] or first + b; image b of sub)
+__global__ void __launch_bounds__(NT, 1)
+degridder_sep_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ sub,
+                     const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                     const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    degridder_sep_body<false>(g, g.sub[sid], sub + (size_t)blockIdx.x * SPIX * 2, flags, aterms, taper, vis_out);
+}
+
+// fused: one CTA per subgrid, read from the grid
+__global__ void __launch_bounds__(NT, 1)
+degridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
+                           const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
+                           const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
+    degridder_sep_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
+}
+
+}  // namespace
+
+idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
+                                const void *aterms, const float *taper, void *vis_out, void *stream) {
+    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 and a separable plan");
+    if (set.count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(degridder_sep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "separable degridder smem attribute");
+    degridder_sep_kernel<<<(unsigned)set.count, NT, SEPD_SMEM, s>>>(g, set.idx, set.first, (const float4 *)sub, flags,
+                                                                    (const float4 *)aterms, taper, (float4 *)vis_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "separable degridder launch");
+    return IDG_OK;
+}
+
+idg_status launch_degridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                      const void *aterms, const float *taper, void *vis_out, void *stream) {
+    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 and a separable plan");
+    if (set.count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaFuncSetAttribute(degridder_sep_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "separable degridder smem attribute");
+    degridder_sep_fused_kernel<<<(unsigned)set.count, NT, SEPD_SMEM, s>>>(g, set.idx, set.first, (const float4 *)grid,
+                                                                          flags, (const float4 *)aterms, taper,
+                                                                          (float4 *)vis_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "separable fused degridder launch");
+    return IDG_OK;
+}
+
+idg_status read_sepd_error(int *code) {
+    int zero = 0, v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_sepd_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_sepd_error, &zero, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the separable degridder error word");
+    *code = v;
+    return IDG_OK;
+}
+
+}  // namespace idg

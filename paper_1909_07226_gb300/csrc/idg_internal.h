@@ -39,6 +39,7 @@ struct Geometry {
     const float *sep;
     int separable;             // 1: max |c_k| max |r| is small enough for the first-order w remainder
     float c_scale;             // power of two with max |c_k| c_scale <= 1 (c_k = 2 pi (w - w0))
+    float r_scale;             // power of two with max |r(x, y)| r_scale <= 1
 };
 
 // Host planner output.
@@ -81,6 +82,7 @@ struct idg_plan {
     float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
     double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
     float c_scale = 1.0f;
+    float r_scale = 1.0f;
     bool any_dropped = false;
     double ds = 0.0;                        // uniform channel scale step (0 if not uniform)
     std::vector<int64_t> kp_prefix_plan;    // [n_sub + 1], sum of K_p in plan order
@@ -165,6 +167,13 @@ idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const vo
 idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status read_sep_error(int *code);
+// separable tensor-core degridder (L = 32, g.separable): from subgrid images, or
+// fused with the splitter and the inverse transform from grid
+idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
+                                const void *aterms, const float *taper, void *vis_out, void *stream);
+idg_status launch_degridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                      const void *aterms, const float *taper, void *vis_out, void *stream);
+idg_status read_sepd_error(int *code);
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *subgrids, void *stream);
 idg_status read_device_errors(int *code, void *stream);

@@ -224,16 +224,16 @@ def test_tc_transform_rejected_by_batches():
 # ---------------------------------------------------------------------------
 # tensor-core degridder
 
-TCD = "tcgen05_tmemA_ws_nt288"
+TCD_VARIANTS = ["tcgen05_separable", "tcgen05_tmemA_ws_nt288"]
 
 
-@pytest.fixture
-def tcd_selected():
+@pytest.fixture(params=TCD_VARIANTS)
+def tcd_selected(request):
     names = idg.kernel_variants("degridder", 32)
-    assert TCD in names
+    assert request.param in names
     prev = idg.get_kernel_variant("degridder", 32)
-    idg.set_kernel_variant("degridder", 32, names.index(TCD))
-    yield TCD
+    idg.set_kernel_variant("degridder", 32, names.index(request.param))
+    yield request.param
     idg.set_kernel_variant("degridder", 32, prev)
 
 
