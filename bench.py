@@ -58,6 +58,12 @@ ISSUE_PER_VISPIX_TC = 9
 # dirty in L2 when the launch ends), degridder 28.6 + 91.9 MB (grid lines in,
 # model visibilities out).
 FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
+SEP_VARIANT = "tcgen05_separable_fused"
+# Tensor-core work of the separable kernels (kind::f16, M = 128, K = 16 per MMA, 2 FLOP
+# per multiply-add): the gridder issues N = 192 + 64 per group of 8 visibilities, the
+# degridder 4 K steps of N = 256 + 128 + 128 per tile of 64 visibilities.
+SEP_GRID_FLOP_PER_GROUP = 2 * 128 * 16 * (192 + 64)
+SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (256 + 128 + 128)
 KERNEL_TRAFFIC = {
     "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
                 "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9,
@@ -386,6 +392,11 @@ def run_gb300(args, world, rank, local):
                  f"per visibility-pixel")
     tc_basis = (f"{n_sm} SMs x {LANES_PER_SM} issue slots x {f_max_mhz:.0f} MHz / {ISSUE_PER_VISPIX_TC} "
                 f"phasor-generation instructions per visibility-pixel (multiply-adds on the tensor cores)")
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    bf16_src = "measured burst" if "bf16_tflops" in peaks else "fallback"
+    kp = plan.export()[:, 9].astype(np.int64)                 # K_p per subgrid (descriptor field 9)
+    sep_flop = {"gridder": float(((kp + 7) // 8).sum()) * SEP_GRID_FLOP_PER_GROUP,
+                "degridder": float(((kp + 63) // 64).sum()) * SEP_DEGRID_FLOP_PER_TILE}
     kernels = {}
     for k, d in prof.items():
         if d["launches"] == 0:
@@ -395,14 +406,20 @@ def run_gb300(args, world, rank, local):
         if k in ("gridder", "degridder"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
             var = idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)]
-            # a step without adder (splitter) launches ran the fused tensor-core gridder
-            # (degridder): transform and adder (splitter) inside the same kernel
+            # a step without adder (splitter) launches ran a fused tensor-core kernel: the separable
+            # one where the plan allows it, else the direct one (transform and adder in the same CTA)
             if prof["adder" if k == "gridder" else "splitter"]["launches"] == 0:
-                var = FUSED_VARIANT
-            tc = var.startswith("tcgen05")
-            pk = tc_peak if tc else alu_peak
-            ent.update(bound="alu", achieved=ach, peak=pk, unit="Gvispix/s", frac=ach / pk, variant=var,
-                       peak_basis=tc_basis if tc else fma_basis, frac_of_fp32_fma_peak=ach / alu_peak)
+                var = SEP_VARIANT if plan.stats.separable else FUSED_VARIANT
+            if var == SEP_VARIANT:
+                tfl = sep_flop[k] * args.steps / (d["ms"] * 1e-3) / 1e12
+                ent.update(bound="tensor", achieved=tfl, peak=bf16_peak, unit="TFLOP/s", frac=tfl / bf16_peak,
+                           variant=var, peak_basis=f"dense bf16 tensor rate ({bf16_src}); FP16 runs at the same rate",
+                           achieved_vispix=ach, vispix_unit="Gvispix/s", frac_of_fp32_fma_peak=ach / alu_peak)
+            else:
+                tc = var.startswith("tcgen05")
+                pk = tc_peak if tc else alu_peak
+                ent.update(bound="alu", achieved=ach, peak=pk, unit="Gvispix/s", frac=ach / pk, variant=var,
+                           peak_basis=tc_basis if tc else fma_basis, frac_of_fp32_fma_peak=ach / alu_peak)
         elif k in ("adder", "splitter"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
             ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
@@ -413,13 +430,17 @@ def run_gb300(args, world, rank, local):
     per_vispix = KERNEL_TRAFFIC.get(dom, {}).get(kernels[dom]["variant"]) if L == 32 else None
     if per_vispix is not None:
         traffic = per_vispix * prof[dom]["work"] / prof[dom]["launches"]
-    roof = {"kernel": dom, "variant": kernels[dom]["variant"], "bound": "alu",
+    roof = {"kernel": dom, "variant": kernels[dom]["variant"], "bound": kernels[dom]["bound"],
             "achieved": kernels[dom]["achieved"], "peak": kernels[dom]["peak"],
-            "unit": "Gvispix/s", "frac": kernels[dom]["frac"], "traffic": traffic,
+            "unit": kernels[dom]["unit"], "frac": kernels[dom]["frac"], "traffic": traffic,
             "traffic_basis": "ncu dram bytes per visibility-pixel of the slice capture x visibility-pixels per launch"
             if traffic is not None else None,
             "peak_basis": kernels[dom]["peak_basis"], "frac_of_fp32_fma_peak": kernels[dom]["frac_of_fp32_fma_peak"],
             "hbm_peak_basis": hbm_src}
+    if "achieved_vispix" in kernels[dom]:
+        roof["achieved_vispix"] = kernels[dom]["achieved_vispix"]
+        roof["flop_basis"] = ("MMA FLOP issued: gridder 2*128*16*(192+64) per group of 8 visibilities, degridder "
+                              "4*2*128*16*(256+128+128) per tile of 64 (FP16 hi/lo split products included)")
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 
     # end to end through the host-buffer C-ABI calls

@@ -21,5 +21,7 @@ struct JobDev {
 // sets the shared-memory size of the tensor-core batch kernels (once, before any graph capture)
 cudaError_t prepare_tcw_batch_kernels();
 cudaError_t prepare_gridder_tcw_batch();
+cudaError_t prepare_sep_batch_kernels();
+cudaError_t prepare_gridder_sep_batch();
 
 }  // namespace idg

@@ -384,7 +384,31 @@ degridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t 
     degridder_sep_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
 }
 
+// fused, one CTA per work item (job, subgrid) of a batch: split from the job's grid
+__global__ void __launch_bounds__(NT, 1)
+degridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    degridder_sep_body<true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
+}
+
 }  // namespace
+
+cudaError_t prepare_sep_batch_kernels() {
+    cudaError_t e = prepare_gridder_sep_batch();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(degridder_sep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
+    return e;
+}
+
+// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
+idg_status launch_degridder_sep_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
+    if (count <= 0) return IDG_OK;
+    degridder_sep_batch_kernel<<<(unsigned)count, NT, SEPD_SMEM, (cudaStream_t)stream>>>(jobs, items);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "separable batch degridder launch");
+    return IDG_OK;
+}
 
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {

@@ -372,6 +372,7 @@ idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, 
 
 cudaError_t prepare_tcw_batch_kernels() {
     cudaError_t e = prepare_gridder_tcw_batch();
+    if (e == cudaSuccess) e = prepare_sep_batch_kernels();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(degridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM);
     return e;

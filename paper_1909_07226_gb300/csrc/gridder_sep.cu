@@ -441,7 +441,28 @@ gridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t fi
     gridder_sep_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
 }
 
+// fused, one CTA per work item (job, subgrid) of a batch: added into the job's grid
+__global__ void __launch_bounds__(NT, 1)
+gridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const JobDev &J = jobs[it.x];
+    gridder_sep_body<true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
+}
+
 }  // namespace
+
+cudaError_t prepare_gridder_sep_batch() {
+    return cudaFuncSetAttribute(gridder_sep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEP_SMEM);
+}
+
+// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
+idg_status launch_gridder_sep_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
+    if (count <= 0) return IDG_OK;
+    gridder_sep_batch_kernel<<<(unsigned)count, NT, SEP_SMEM, (cudaStream_t)stream>>>(jobs, items);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "separable batch gridder launch");
+    return IDG_OK;
+}
 
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {

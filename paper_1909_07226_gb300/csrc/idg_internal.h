@@ -193,6 +193,9 @@ idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, 
 struct JobDev;
 idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+// the separable kernels over work items of jobs whose plans are separable
+idg_status launch_gridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+idg_status launch_degridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);

@@ -119,3 +119,35 @@ def test_batch_tensor_core_class_matches_the_oracle(graph):
         idg.device_errors()
         for i, (w, op, j, m) in enumerate(zip(wls, ops, djobs, models)):
             parity(j["vis_out"].cpu().numpy(), O.degrid(w, op, m), f"tc batch degrid job {i} pass {rep}")
+
+
+def test_batch_separable_and_direct_l32_classes():
+    # two L = 32 jobs: one whose plan takes the separable kernels and one wide-field job over
+    # the remainder bound (the direct tensor-core kernels); each forms its own class
+    import torch
+    wls = [_big_l32_jobs()[0],
+           syn.make_small(seed=777, n_st=4, n_t=128, n_chan=16, L=32, N=512, max_t=128, n_slots=1, flag_p=0.05,
+                          diameter_m=800.0, cell=1e-3, df=0.25e6)]
+    plans = [idg.plan_from_workload(w) for w in wls]
+    assert [p.stats.separable for p in plans] == [1, 0]
+    ops = [O.plan(w) for w in wls]
+    rng = np.random.default_rng(23)
+    jobs, models = [], []
+    for w, p in zip(wls, plans):
+        d = workload_to_device(w)
+        models.append(syn.random_grid(rng, p.n_w_layers, w.grid_size))
+        jobs.append(dict(vis=d["vis"], flags=d["flags"], aterms=d["aterms"], taper=d["taper"],
+                         grid=torch.zeros((p.n_w_layers, w.grid_size, w.grid_size, 4), dtype=torch.complex64,
+                                          device="cuda"),
+                         vis_out=torch.zeros(w.vis.shape, dtype=torch.complex64, device="cuda")))
+    b = idg.Batch(plans, jobs)
+    assert b.info()["n_launches"] == 2
+    b.grid()
+    idg.device_errors()
+    for i, (w, op, j) in enumerate(zip(wls, ops, jobs)):
+        parity(j["grid"].cpu().numpy(), O.grid(w, op), f"l32 classes grid job {i}")
+    bd = idg.Batch(plans, [dict(j, grid=dev(m), vis=None) for j, m in zip(jobs, models)])
+    bd.degrid()
+    idg.device_errors()
+    for i, (w, op, j, m) in enumerate(zip(wls, ops, jobs, models)):
+        parity(j["vis_out"].cpu().numpy(), O.degrid(w, op, m), f"l32 classes degrid job {i}")
