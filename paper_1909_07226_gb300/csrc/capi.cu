@@ -401,7 +401,9 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         p->c_scale = 1.0f;
         if (c_max > 1.0) p->c_scale = (float)std::ldexp(1.0, -(int)std::ceil(std::log2(c_max)));
         p->r_scale = r_max > 0.0 ? (float)std::ldexp(1.0, std::min(100, (int)std::floor(std::log2(1.0 / r_max)))) : 1.0f;
-        p->stats.separable = (L == 32 && p->sep_theta <= kSepThetaMax) ? 1 : 0;
+        // (the separable degridder stages visibility indices in 31 bits)
+        const bool fits = (int64_t)n_bl * n_t * n_chan < 0x7FFFFFFFll;
+        p->stats.separable = (L == 32 && p->sep_theta <= kSepThetaMax && fits) ? 1 : 0;
         p->stats.sep_phase = p->sep_theta;
     }
 

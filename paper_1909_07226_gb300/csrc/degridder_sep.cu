@@ -14,8 +14,8 @@
 // them, K = (x, re/im), 64.  The sum over y with the visibility's own phasors
 // runs on the CUDA cores (FP32, round to nearest), one thread per tile row.
 //
-// GEMM.  A holds the real 2 x 2 embedding of E = Ex*_k(x): row (k, re) =
-// (Re E, -Im E), row (k, im) = (Im E, Re E) over K = (x, re/im); B[(m, q, y)]
+// GEMM.  A holds the real 2 x 2 embedding of E = Ex*_k(x): row k (re) =
+// (Re E, -Im E), row 64 + k (im) = (Im E, Re E) over K = (x, re/im); B[(m, q, y)]
 // = (Re, Im) of Q_mq(x, y) over the same K, scaled by a power of two per
 // subgrid (and Q1 by rho, a power of two with max |r| rho <= 1).  Both are
 // split into FP16 hi + lo; the m = 0 block takes A_hi B_hi + A_hi B_lo +
@@ -29,8 +29,9 @@
 // subgrid).  Then per tile: eight producer warps stage the coefficients and
 // write A (shared memory, one core matrix per warp store) and the Ey* table;
 // the MMA warp issues the 12 MMAs into one of two accumulators; eight consumer
-// warps read their rows' columns, sum over y, pair the re/im rows by a shuffle
-// and write the visibilities.  Tensor memory: accumulator b at 256 b.
+// warps read their rows' columns, sum over y, pair the re and im rows of each
+// visibility through shared memory and write the visibilities.  Tensor memory:
+// accumulator b at 256 b.
 // Every wait is bounded; after a failed wait a thread skips every later wait,
 // the error word is set and no output is written.
 #include "batch_jobs.cuh"
@@ -66,13 +67,15 @@ constexpr int A_STAGE = 2 * KT * T4K;
 constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [AST][32 y][TV] float2
 constexpr int EY_STAGE = SL * TV * 8;
 constexpr int CF_OFF = EY_OFF + AST * EY_STAGE; // coefficients: [AST][TV] float4 (a, b, c, 0)
-constexpr int SEPD_SMEM = CF_OFF + AST * TV * 16;
+constexpr int PART_OFF = CF_OFF + AST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][8][TV] float
+constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 8 * TV * 4;
 constexpr int FFT_P = SL + 1;
 constexpr uint32_t IDESC_N256 = idesc_m128(256), IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
 static_assert(AST == 2, "stage and accumulator indices coincide");
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
 
 // Visibilities of subgrid d of geometry g from its image src[L][L][4], or with
 // FUSED from the grid src[layer][N][N][4]: split and transformed in shared memory
@@ -86,6 +89,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     float2 *s_fft = (float2 *)(smem + A_OFF);       // [4][L][L + 1] during the prologue
     float4 *s_coef = (float4 *)(smem + CF_OFF);
     float2 *s_ey = (float2 *)(smem + EY_OFF);
+    float *s_part = (float *)(smem + PART_OFF);
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyempty[AST], s_dfull[2], s_dempty[2], s_drain;
     __shared__ float s_red[NT / 32];
@@ -223,23 +227,53 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         }
         failed = __shfl_sync(0xffffffffu, failed, 0);
     } else if (warp < NPW) {
-        // ---- producers: coefficients, A (2 x 2 embedding of Ex*) and the Ey* table per tile
+        // ---- producers: coefficients, A (2 x 2 embedding of Ex*) and the Ey* table per tile.
+        // A rows are (re/im, k): row k = (Re E, -Im E), row 64 + k = (Im E, Re E).  Lane = 4 k_lo + x_lo:
+        // warp w owns x = 4 w + x_lo (K step w / 2, chunk w % 2) and writes visibilities 8 kg + k_lo
+        const int klo = lane >> 2, xlo = lane & 3, x = 4 * warp + xlo;
+        const float Xv = (float)(x - SL / 2), sx = g.sep[x];
+        const uint32_t a_off = (uint32_t)(warp >> 1) * T4K + (uint32_t)(warp & 1) * kLBO + (uint32_t)klo * 16 +
+                               (uint32_t)xlo * 4;
+        // Ey* entries e = tid + NP j: k = tid % TV, y = tid / TV + 4 j
+        const int ke = tid & (TV - 1), y0 = tid >> 6;
+        float tys[SL * TV / NP];
+#pragma unroll
+        for (int j = 0; j < SL * TV / NP; ++j) tys[j] = g.sep[SL + y0 + 4 * j];
+        // coefficients of the next tile: threads < TV load one visibility's coordinates, then form
+        // (a, b, c) and its output index (flag in bit 31) one tile ahead of use
         double pu = 0.0, pv = 0.0, pw = 0.0, psc = 0.0;
-        bool pin = false;
-        auto load_coef = [&](int t) {      // threads < TV: the raw coordinates of visibility t TV + tid
+        uint32_t pvi = 0;
+        bool pin = false, pflag = false;
+        float4 cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto load_coef = [&](int t) {
             const int k = t * TV + tid;
             pin = k < d.kp;
+            pflag = false;
             if (pin) {
                 int tt, c;
-                vis_index(g, d, k, tt, c);
+                const size_t vi = vis_index(g, d, k, tt, c);
                 const double *xw = g.uvw + ((size_t)d.bl * g.n_t + tt) * 3;
                 pu = xw[0];
                 pv = xw[1];
                 pw = xw[2];
                 psc = g.scale[c];
+                pvi = (uint32_t)vi;
+                pflag = flags && flags[vi];
             }
         };
-        if (tid < TV) load_coef(0);
+        auto form_coef = [&]() {
+            cf_next = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));   // beyond K_p: no output
+            if (pin) {
+                cf_next.x = (float)((pu * psc - d.u0) * g.k_uv);
+                cf_next.y = (float)((pv * psc - d.v0) * g.k_uv);
+                cf_next.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
+                cf_next.w = __uint_as_float(pvi | (pflag ? 0x80000000u : 0u));
+            }
+        };
+        if (tid < TV) {
+            load_coef(0);
+            form_coef();
+        }
         for (int t = 0; t < n_tiles; ++t) {
             const int s = t & 1;
             if (t >= 2) {
@@ -247,54 +281,50 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                 wait_or_fail(smem_u32(&s_eyempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
             }
             if (tid < TV) {
-                float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (pin) {
-                    cf.x = (float)((pu * psc - d.u0) * g.k_uv);
-                    cf.y = (float)((pv * psc - d.v0) * g.k_uv);
-                    cf.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
-                }
-                s_coef[s * TV + tid] = cf;
+                s_coef[s * TV + tid] = cf_next;
                 if (t + 1 < n_tiles) load_coef(t + 1);
             }
             producers_sync();
             const float4 *cf = s_coef + s * TV;
             uint8_t *As = smem + A_OFF + s * A_STAGE;
-            // A: warp-task wt = warp + 8 i: row group rg = wt % 16 (visibilities 4 rg ..), x chunk kc = wt / 16;
-            // lane: row 8 rg + lane / 4 = 2 k + re/im, x = 4 kc + lane % 4
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int wt = warp + NPW * i, rg = wt & 15, kc = wt >> 4;
-                const int k = 4 * rg + (lane >> 3), ci = (lane >> 2) & 1, x = 4 * kc + (lane & 3);
-                const float4 c = cf[k];
+#pragma unroll 2
+            for (int kg = 0; kg < TV / 8; ++kg) {
+                const float4 c = cf[8 * kg + klo];
                 float sn, cs;
-                __sincosf(fmaf(c.z, g.sep[x], c.x * (float)(x - SL / 2)), &sn, &cs);
+                __sincosf(fmaf(c.z, sx, c.x * Xv), &sn, &cs);
                 // E = cs - i sn: row re = (cs, sn), row im = (-sn, cs)
-                uint32_t h, l;
-                split_e(ci ? -sn : cs, ci ? cs : sn, h, l);
-                const uint32_t off = (uint32_t)(kc >> 1) * T4K + (uint32_t)rg * kSBO + (uint32_t)(kc & 1) * kLBO +
-                                     (uint32_t)(lane >> 2) * 16 + (uint32_t)(lane & 3) * 4;
-                *(uint32_t *)(As + off) = h;
-                *(uint32_t *)(As + KT * T4K + off) = l;
+                uint32_t hr, lr, hm, lm;
+                split_e(cs, sn, hr, lr);
+                split_e(-sn, cs, hm, lm);
+                const uint32_t o_re = a_off + (uint32_t)kg * kSBO, o_im = o_re + 8 * kSBO;
+                *(uint32_t *)(As + o_re) = hr;
+                *(uint32_t *)(As + o_im) = hm;
+                *(uint32_t *)(As + KT * T4K + o_re) = lr;
+                *(uint32_t *)(As + KT * T4K + o_im) = lm;
             }
-            // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))): entry e = y TV + k
-            float2 *ey = s_ey + s * (SL * TV);
-#pragma unroll 4
-            for (int j = 0; j < SL * TV / NP; ++j) {
-                const int e = tid + NP * j, y = e / TV, k = e % TV;
-                const float4 c = cf[k];
-                float sn, cs;
-                __sincosf(fmaf(c.z, g.sep[SL + y], c.y * (float)(y - SL / 2)), &sn, &cs);
-                ey[e] = make_float2(cs, -sn);
+            // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))): entry y TV + k
+            {
+                float2 *ey = s_ey + s * (SL * TV);
+                const float4 c = cf[ke];
+#pragma unroll
+                for (int j = 0; j < SL * TV / NP; ++j) {
+                    const int y = y0 + 4 * j;
+                    float sn, cs;
+                    __sincosf(fmaf(c.z, tys[j], c.y * (float)(y - SL / 2)), &sn, &cs);
+                    ey[y * TV + ke] = make_float2(cs, -sn);
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_afull[s]));
+            if (tid < TV && t + 1 < n_tiles) form_coef();
         }
         if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
     } else {
-        // ---- consumers: row 32 (warp % 4) + lane = 2 k + re/im of the tile, polarisations 2 h, 2 h + 1
+        // ---- consumers: row 32 (warp % 4) + lane = (re/im = row / 64, k = row % 64) of the tile,
+        // polarisations 2 h, 2 h + 1; the re and im rows of a visibility meet through s_part
         const int qq = warp & 3, h = (warp - NPW) >> 2;
-        const int kl = 16 * qq + (lane >> 1), ci = lane & 1;
+        const int ci = qq >> 1, kl = 32 * (qq & 1) + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * qq) << 16);
         for (int t = 0; t < n_tiles; ++t) {
             const int s = t & 1;
@@ -304,7 +334,9 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             const float2 *ey = s_ey + s * (SL * TV);
             float acc[2][2][2];      // [m][q'][ (sum er T, sum ei T) ]
 #pragma unroll
-            for (int a = 0; a < 8; ++a) (&acc[0][0][0])[a] = 0.0f;
+            for (int mm = 0; mm < 2; ++mm)
+#pragma unroll
+                for (int q2 = 0; q2 < 2; ++q2) acc[mm][q2][0] = acc[mm][q2][1] = 0.0f;
 #pragma unroll 1
             for (int yc = 0; yc < 4; ++yc) {         // rows y in [8 yc, 8 yc + 8)
                 uint32_t r[4][8];
@@ -327,36 +359,48 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                     }
                 }
             }
-            const float c1 = s_coef[s * TV + kl].z / g.r_scale;     // c_k / rho (Q1 holds rho r P)
+            const float4 cfk = s_coef[s * TV + kl];
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(smem_u32(&s_dempty[s]));
                 mbar_arrive(smem_u32(&s_eyempty[s]));
             }
-            // rows re (holds Re T) and im (Im T) of visibility kl: Re(E T) = er Tr - ei Ti, Im = er Ti + ei Tr
-            float o[2][2][2];
+            // exchange with the other row of the visibility: the re row holds (er Tr, ei Tr),
+            // the im row (er Ti, ei Ti); Re(E T) = er Tr - ei Ti, Im(E T) = er Ti + ei Tr
+            float *part = s_part + (size_t)(s * 2 + ci) * (2 * 8 * TV) + (size_t)h * 8 * TV;
 #pragma unroll
             for (int mm = 0; mm < 2; ++mm)
 #pragma unroll
-                for (int qp = 0; qp < 2; ++qp) {
-                    const float pa = __shfl_xor_sync(0xffffffffu, acc[mm][qp][0], 1);
-                    const float pb = __shfl_xor_sync(0xffffffffu, acc[mm][qp][1], 1);
-                    o[mm][qp][0] = acc[mm][qp][0] - pb;      // on the re row: er Tr - ei Ti
-                    o[mm][qp][1] = pa + acc[mm][qp][1];      // er Ti + ei Tr
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    part[(4 * mm + 2 * q2) * TV + kl] = acc[mm][q2][0];
+                    part[(4 * mm + 2 * q2 + 1) * TV + kl] = acc[mm][q2][1];
                 }
-            const int k = t * TV + kl;
-            if (ci == 0 && k < d.kp && !failed) {
+            consumers_sync();
+            const float *other = s_part + (size_t)(s * 2 + (ci ^ 1)) * (2 * 8 * TV) + (size_t)h * 8 * TV;
+            // this thread writes polarisation q' = ci of the pair
+            const int qp = ci;
+            float o[2][2];
+#pragma unroll
+            for (int mm = 0; mm < 2; ++mm) {
+                const float own0 = ci ? acc[mm][1][0] : acc[mm][0][0];
+                const float own1 = ci ? acc[mm][1][1] : acc[mm][0][1];
+                const float oth0 = other[(4 * mm + 2 * qp) * TV + kl];
+                const float oth1 = other[(4 * mm + 2 * qp + 1) * TV + kl];
+                const float a0 = ci ? oth0 : own0, a1 = ci ? oth1 : own1;     // er Tr, ei Tr
+                const float b0 = ci ? own0 : oth0, b1 = ci ? own1 : oth1;     // er Ti, ei Ti
+                o[mm][0] = a0 - b1;
+                o[mm][1] = b0 + a1;
+            }
+            const uint32_t vw = __float_as_uint(cfk.w);       // index (< 2^31 - 1), bit 31 = flagged
+            if (!(vw & 0x80000000u) && !failed) {
                 // y = T0 - i c_k T1 with T1 computed from rho r P
-                int tt, c;
-                const size_t vi = vis_index(g, d, k, tt, c);
-                float4 out;
-                out.x = (o[0][0][0] + c1 * o[1][0][1]) * inv_scale;
-                out.y = (o[0][0][1] - c1 * o[1][0][0]) * inv_scale;
-                out.z = (o[0][1][0] + c1 * o[1][1][1]) * inv_scale;
-                out.w = (o[0][1][1] - c1 * o[1][1][0]) * inv_scale;
-                if (flags && flags[vi]) out = make_float4(0.f, 0.f, 0.f, 0.f);
-                vis_out[2 * vi + h] = out;
+                const float c1 = cfk.z / g.r_scale;
+                const size_t vi = vw;
+                float2 out = make_float2((o[0][0] + c1 * o[1][1]) * inv_scale, (o[0][1] - c1 * o[1][0]) * inv_scale);
+                ((float2 *)vis_out)[4 * vi + 2 * h + qp] = out;
+            } else if (vw != 0xFFFFFFFFu && !failed) {
+                ((float2 *)vis_out)[4 * (vw & 0x7FFFFFFFu) + 2 * h + qp] = make_float2(0.f, 0.f);   // flagged
             }
         }
         if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
