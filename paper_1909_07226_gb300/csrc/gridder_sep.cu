@@ -210,20 +210,24 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 }
             }
         };
+        // phase coefficients of the staged visibility (FP64 offsets, rounded once to FP32)
+        float4 cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        auto form_coef = [&]() {
+            cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (pin) {
+                cf_next.x = (float)((pu * psc - d.u0) * g.k_uv);
+                cf_next.y = (float)((pv * psc - d.v0) * g.k_uv);
+                cf_next.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
+            }
+        };
         // coefficients and raw V of the batch; the batch's largest |component| into s_red[bb]
         auto store_batch = [&](int bb) {
-            float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-            if (pin) {
-                cf.x = (float)((pu * psc - d.u0) * g.k_uv);
-                cf.y = (float)((pv * psc - d.v0) * g.k_uv);
-                cf.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
-                if (!pflag) {
-                    a = pa;
-                    b = pb;
-                }
+            if (pin && !pflag) {
+                a = pa;
+                b = pb;
             }
-            s_coef[bb * VB + tid] = cf;
+            s_coef[bb * VB + tid] = cf_next;
             float4 *dv = (float4 *)(s_vis + (size_t)(bb * VB + tid) * 4);
             dv[0] = a;
             dv[1] = b;
@@ -264,6 +268,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         };
 
         load_batch(0);
+        form_coef();
         store_batch(0);
         producers_sync();
         int next_fold = 0;
@@ -324,11 +329,15 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     const float4 cf = coef[8 * (SG * si + i) + j];
                     float sn, cs;
                     __sincosf(fmaf(cf.z, sx, cf.x * Xv), &sn, &cs);
-                    uint32_t hr, lr, hi_, li_;
+                    // the im row (sn, cs) is the re row (cs, -sn) with its halves swapped and the new
+                    // low half negated: exact, as FP16 rounding is symmetric
+                    uint32_t hr, lr;
                     split_e(cs, -sn, hr, lr);
-                    split_e(sn, cs, hi_, li_);
+                    const uint32_t hi_ = __byte_perm(hr, 0u, 0x1032u) ^ 0x8000u;
+                    const uint32_t li_ = __byte_perm(lr, 0u, 0x1032u) ^ 0x8000u;
                     const float cz = cf.z * csig;
-                    const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn), h1i = pack_f16x2(cz * sn, cz * cs);
+                    const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn);
+                    const uint32_t h1i = __byte_perm(h1r, 0u, 0x1032u) ^ 0x8000u;
                     uint8_t *Bg = Bs + i * B_GROUP;
                     const uint32_t kc = (uint32_t)(j >> 2) * kLBO + (uint32_t)(xb & 7) * 16 + (uint32_t)(j & 3) * 4;
                     const uint32_t rg = (uint32_t)(xb >> 3) * kSBO;        // row group of x within a 32-row block
@@ -346,6 +355,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 if (lane == 0) mbar_arrive(smem_u32(&s_full[s]));
             }
             if (b + 1 < n_batches) {
+                form_coef();
                 store_batch(bb ^ 1);
                 producers_sync();
             }
