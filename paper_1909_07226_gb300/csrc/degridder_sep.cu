@@ -9,29 +9,32 @@
 //   y_kq = sum_y Ey*_k(y) [T0_kq(y) - i c_k T1_kq(y)],
 //   T_mkq(y) = sum_x Ex*_k(x) Q_mq(x, y),  Q0 = P, Q1 = P r,
 //   Ex*_k(x) = exp(-i (a_k X + c_k s(x))),  Ey*_k(y) = exp(-i (b_k Y + c_k t(y))).
-// The contraction over x is a complex matrix product on the tensor cores: rows
-// (visibility, re/im) of a tile of 64 visibilities, columns (m, q, y), 256 of
-// them, K = (x, re/im), 64.  The sum over y with the visibility's own phasors
-// runs on the CUDA cores (FP32, round to nearest), one thread per tile row.
+// Both terms are one complex matrix product on the tensor cores,
+//   T_kq(y) = sum_x Ex*_k(x) Q0_q(x, y) + sum_x (-i c_k Ex*_k(x)) Q1_q(x, y),
+// with rows (re/im, visibility) of a tile of 64 visibilities, columns (q, y),
+// 128 of them, and K = (x, re/im) twice (m = 0, then m = 1).  The sum over y
+// with the visibility's own phasors, y_kq = sum_y Ey*_k(y) T_kq(y), runs on
+// the CUDA cores (FP32, round to nearest), one thread per tile row.
 //
-// GEMM.  A holds the real 2 x 2 embedding of E = Ex*_k(x): row k (re) =
-// (Re E, -Im E), row 64 + k (im) = (Im E, Re E) over K = (x, re/im); B[(m, q, y)]
-// = (Re, Im) of Q_mq(x, y) over the same K, scaled by a power of two per
-// subgrid (and Q1 by rho, a power of two with max |r| rho <= 1).  Both are
-// split into FP16 hi + lo; the m = 0 block takes A_hi B_hi + A_hi B_lo +
-// A_lo B_hi, the m = 1 block (at most theta relative) A_hi B_hi.  Per K step
-// of 16: N = 256 (A_hi, [B0_hi | B1_hi]), N = 128 (A_hi, B0_lo), N = 128
-// (A_lo, B0_hi).  The accumulation is 12 MMAs long, so no folds are needed.
+// GEMM.  A holds the real 2 x 2 embedding of a = Ex*_k(x) (m = 0) and of
+// a = -i c_k sigma Ex*_k(x) (m = 1, sigma a power of two with max |c| sigma
+// <= 1): row k (re) = (Re a, -Im a), row 64 + k (im) = (Im a, Re a) over
+// K = (x, re/im).  B[(q, y)] = (Re, Im) of Q0 = s P and of Q1 = s r P / sigma
+// (s a power of two per subgrid), so both products carry the same scale.  The
+// m = 0 operands are split into FP16 hi + lo and take A_hi B_hi + A_hi B_lo +
+// A_lo B_hi; the m = 1 term (at most theta relative) takes A_hi B_hi.  Per K
+// step of 16 (8 x): four MMAs of N = 128.  The accumulation is 16 MMAs long,
+// so no folds are needed.
 //
 // Schedule.  One CTA per subgrid, one CTA per SM.  All warps first form the
 // image (split from the grid and inverse transform in shared memory when
 // FUSED), the corrections, the scale and B (shared memory, fixed for the
 // subgrid).  Then per tile: eight producer warps stage the coefficients and
 // write A (shared memory, one core matrix per warp store) and the Ey* table;
-// the MMA warp issues the 12 MMAs into one of two accumulators; eight consumer
+// the MMA warp issues the 16 MMAs into one of two accumulators; eight consumer
 // warps read their rows' columns, sum over y, pair the re and im rows of each
 // visibility through shared memory and write the visibilities.  Tensor memory:
-// accumulator b at 256 b.
+// accumulator b at 128 b.
 // Every wait is bounded; after a failed wait a thread skips every later wait,
 // the error word is set and no output is written.
 #include "batch_jobs.cuh"
@@ -60,17 +63,17 @@ constexpr int TV = 64;                          // visibilities per tile (rows 2
 constexpr int AST = 2;                          // A, Ey* and coefficient stages
 constexpr int KT = 4;                           // K steps of 16 (8 x, re/im) over the 32 x
 constexpr int T4K = 128 * 32;                   // 128 rows x 16 K FP16
-constexpr int BH_OFF = 0;                       // B hi: [KT][256 rows: m = 0 (q, y), then m = 1]
-constexpr int BL_OFF = BH_OFF + KT * 2 * T4K;   // B lo (m = 0): [KT][128 rows]
-constexpr int A_OFF = BL_OFF + KT * T4K;        // A: [AST][hi, lo][KT][128 rows]
-constexpr int A_STAGE = 2 * KT * T4K;
+// B (fixed per subgrid), each [KT][128 rows (q, y)]: Q0 hi, Q0 lo, Q1 hi
+constexpr int B0H_OFF = 0, B0L_OFF = B0H_OFF + KT * T4K, B1H_OFF = B0L_OFF + KT * T4K;
+constexpr int A_OFF = B1H_OFF + KT * T4K;       // A: [AST][m = 0 hi, m = 0 lo, m = 1 hi][KT][128 rows]
+constexpr int A_STAGE = 3 * KT * T4K;
 constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [AST][32 y][TV] float2
 constexpr int EY_STAGE = SL * TV * 8;
 constexpr int CF_OFF = EY_OFF + AST * EY_STAGE; // coefficients: [AST][TV] float4 (a, b, c, 0)
-constexpr int PART_OFF = CF_OFF + AST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][8][TV] float
-constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 8 * TV * 4;
+constexpr int PART_OFF = CF_OFF + AST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
+constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 4 * TV * 4;
 constexpr int FFT_P = SL + 1;
-constexpr uint32_t IDESC_N256 = idesc_m128(256), IDESC_N128 = idesc_m128(128);
+constexpr uint32_t IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
 static_assert(AST == 2, "stage and accumulator indices coincide");
 
@@ -99,7 +102,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
 
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&s_tmem)), "n"(512));
+                     :: "r"(smem_u32(&s_tmem)), "n"(256));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -174,10 +177,10 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     if (m > 0.0f) frexpf(m, &e2);
     const float scale = ldexpf(1.0f, 10 - e2);
     const float inv_scale = ldexpf(1.0f, e2 - 10);
-    // B: Q0 = scale P (hi to rows 32 q + y, lo), Q1 = scale rho r P (hi to rows 128 + 32 q + y); one
-    // core matrix (8 rows y, 4 x) per warp store: warp-task wt = (q, y block, x chunk of 4)
+    // B: Q0 = scale P (hi and lo), Q1 = scale r P / sigma (hi), rows 32 q + y; one core matrix
+    // (8 rows y, 4 x) per warp store: warp-task wt = (q, y block, x chunk of 4)
     if (warp < MMA_WARP) {
-        const float rs = g.r_scale;
+        const float rs = scale / g.c_scale;
         for (int wt = warp; wt < 128; wt += MMA_WARP) {
             const int q = wt >> 5, yb = (wt >> 3) & 3, xc = wt & 7;
             const int y = 8 * yb + (lane >> 2), x = 4 * xc + (lane & 3);
@@ -185,13 +188,13 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             const float rr = g.sep[2 * SL + y * SL + x] * rs;
             uint32_t h0, l0;
             split_e(p.x * scale, p.y * scale, h0, l0);
-            const uint32_t h1 = pack_f16x2(p.x * rr * scale, p.y * rr * scale);
+            const uint32_t h1 = pack_f16x2(p.x * rr, p.y * rr);
             const uint32_t off = (uint32_t)(4 * q + yb) * kSBO + (uint32_t)(xc & 1) * kLBO + (uint32_t)(lane >> 2) * 16 +
                                  (uint32_t)(lane & 3) * 4;
             const int kk = xc >> 1;
-            *(uint32_t *)(smem + BH_OFF + kk * 2 * T4K + off) = h0;
-            *(uint32_t *)(smem + BH_OFF + kk * 2 * T4K + T4K + off) = h1;
-            *(uint32_t *)(smem + BL_OFF + kk * T4K + off) = l0;
+            *(uint32_t *)(smem + B0H_OFF + kk * T4K + off) = h0;
+            *(uint32_t *)(smem + B0L_OFF + kk * T4K + off) = l0;
+            *(uint32_t *)(smem + B1H_OFF + kk * T4K + off) = h1;
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -201,22 +204,22 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     if (warp == MMA_WARP) {
         if (lane == 0) {
             const uint64_t da0 = smem_desc(smem_u32(smem + A_OFF));
-            const uint64_t dbh0 = smem_desc(smem_u32(smem + BH_OFF)), dbl0 = smem_desc(smem_u32(smem + BL_OFF));
+            const uint64_t db0 = smem_desc(smem_u32(smem + B0H_OFF));
             for (int t = 0; t < n_tiles; ++t) {
                 const int s = t & 1;
                 wait_or_fail(smem_u32(&s_afull[s]), (uint32_t)((t >> 1) & 1), failed);
                 if (t >= 2) wait_or_fail(smem_u32(&s_dempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t dt = tmem + 256u * (uint32_t)s;
+                const uint32_t dt = tmem + 128u * (uint32_t)s;
 #pragma unroll
                 for (int kk = 0; kk < KT; ++kk) {
-                    const uint64_t dah = da0 + (uint64_t)((s * A_STAGE + kk * T4K) >> 4);
-                    const uint64_t dal = dah + (uint64_t)((KT * T4K) >> 4);
-                    const uint64_t dbh = dbh0 + (uint64_t)((kk * 2 * T4K) >> 4);
-                    const uint64_t dbl = dbl0 + (uint64_t)((kk * T4K) >> 4);
-                    mma_ss_i(dt, dah, dbh, IDESC_N256, kk > 0 ? 1u : 0u);
-                    mma_ss_i(dt, dah, dbl, IDESC_N128, 1u);
-                    mma_ss_i(dt, dal, dbh, IDESC_N128, 1u);
+                    const uint64_t da = da0 + (uint64_t)((s * A_STAGE + kk * T4K) >> 4);     // m = 0 hi
+                    const uint64_t db = db0 + (uint64_t)((kk * T4K) >> 4);                  // Q0 hi
+                    mma_ss_i(dt, da, db, IDESC_N128, kk > 0 ? 1u : 0u);
+                    mma_ss_i(dt, da, db + (uint64_t)((KT * T4K) >> 4), IDESC_N128, 1u);        // Q0 lo
+                    mma_ss_i(dt, da + (uint64_t)((KT * T4K) >> 4), db, IDESC_N128, 1u);        // m = 0 lo
+                    mma_ss_i(dt, da + (uint64_t)((2 * KT * T4K) >> 4), db + (uint64_t)((2 * KT * T4K) >> 4),
+                             IDESC_N128, 1u);                                                // m = 1 hi x Q1 hi
                 }
                 commit(smem_u32(&s_aempty[s]));
                 commit(smem_u32(&s_dfull[s]));
@@ -231,7 +234,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         // A rows are (re/im, k): row k = (Re E, -Im E), row 64 + k = (Im E, Re E).  Lane = 4 k_lo + x_lo:
         // warp w owns x = 4 w + x_lo (K step w / 2, chunk w % 2) and writes visibilities 8 kg + k_lo
         const int klo = lane >> 2, xlo = lane & 3, x = 4 * warp + xlo;
-        const float Xv = (float)(x - SL / 2), sx = g.sep[x];
+        const float Xv = (float)(x - SL / 2), sx = g.sep[x], csig = g.c_scale;
         const uint32_t a_off = (uint32_t)(warp >> 1) * T4K + (uint32_t)(warp & 1) * kLBO + (uint32_t)klo * 16 +
                                (uint32_t)xlo * 4;
         // Ey* entries e = tid + NP j: k = tid % TV, y = tid / TV + 4 j
@@ -292,15 +295,23 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                 const float4 c = cf[8 * kg + klo];
                 float sn, cs;
                 __sincosf(fmaf(c.z, sx, c.x * Xv), &sn, &cs);
-                // E = cs - i sn: row re = (cs, sn), row im = (-sn, cs)
-                uint32_t hr, lr, hm, lm;
+                // m = 0: a = E = cs - i sn: row re = (cs, sn), row im = (-sn, cs); the im row is the re
+                // row with halves swapped and the new low half negated (exact for FP16 parts)
+                uint32_t hr, lr;
                 split_e(cs, sn, hr, lr);
-                split_e(-sn, cs, hm, lm);
+                const uint32_t hm = __byte_perm(hr, 0u, 0x1032u) ^ 0x8000u;
+                const uint32_t lm = __byte_perm(lr, 0u, 0x1032u) ^ 0x8000u;
+                // m = 1: a = -i c sigma E = -c sigma (sn + i cs): row re = (-c sigma sn, c sigma cs)
+                const float cz = c.z * csig;
+                const uint32_t h1r = pack_f16x2(-cz * sn, cz * cs);
+                const uint32_t h1m = __byte_perm(h1r, 0u, 0x1032u) ^ 0x8000u;
                 const uint32_t o_re = a_off + (uint32_t)kg * kSBO, o_im = o_re + 8 * kSBO;
                 *(uint32_t *)(As + o_re) = hr;
                 *(uint32_t *)(As + o_im) = hm;
                 *(uint32_t *)(As + KT * T4K + o_re) = lr;
                 *(uint32_t *)(As + KT * T4K + o_im) = lm;
+                *(uint32_t *)(As + 2 * KT * T4K + o_re) = h1r;
+                *(uint32_t *)(As + 2 * KT * T4K + o_im) = h1m;
             }
             // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))): entry y TV + k
             {
@@ -332,30 +343,26 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             wait_or_fail(smem_u32(&s_dfull[s]), (uint32_t)((t >> 1) & 1), failed);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const float2 *ey = s_ey + s * (SL * TV);
-            float acc[2][2][2];      // [m][q'][ (sum er T, sum ei T) ]
+            float acc[2][2];         // [q'][ (sum er T, sum ei T) ]
 #pragma unroll
-            for (int mm = 0; mm < 2; ++mm)
-#pragma unroll
-                for (int q2 = 0; q2 < 2; ++q2) acc[mm][q2][0] = acc[mm][q2][1] = 0.0f;
+            for (int q2 = 0; q2 < 2; ++q2) acc[q2][0] = acc[q2][1] = 0.0f;
 #pragma unroll 1
             for (int yc = 0; yc < 4; ++yc) {         // rows y in [8 yc, 8 yc + 8)
-                uint32_t r[4][8];
+                uint32_t r[2][8];
 #pragma unroll
-                for (int mq = 0; mq < 4; ++mq)       // (m, q') = (mq / 2, mq % 2): columns 128 m + 32 (2 h + q') + y
-                    tmem_ld8_nowait(lane_base + 256u * (uint32_t)s +
-                                        (uint32_t)(128 * (mq >> 1) + 64 * h + 32 * (mq & 1) + 8 * yc), r[mq]);
+                for (int qp = 0; qp < 2; ++qp)       // columns 32 (2 h + q') + y
+                    tmem_ld8_nowait(lane_base + 128u * (uint32_t)s + (uint32_t)(64 * h + 32 * qp + 8 * yc), r[qp]);
                 float2 e[8];
 #pragma unroll
                 for (int y = 0; y < 8; ++y) e[y] = ey[(8 * yc + y) * TV + kl];
 #pragma unroll
-                for (int mq = 0; mq < 4; ++mq) {
-                    tmem_wait_ld8(r[mq]);
-                    const int mm = mq >> 1, qp = mq & 1;
+                for (int qp = 0; qp < 2; ++qp) {
+                    tmem_wait_ld8(r[qp]);
 #pragma unroll
                     for (int y = 0; y < 8; ++y) {
-                        const float v = __uint_as_float(r[mq][y]);
-                        acc[mm][qp][0] = fmaf(e[y].x, v, acc[mm][qp][0]);
-                        acc[mm][qp][1] = fmaf(e[y].y, v, acc[mm][qp][1]);
+                        const float v = __uint_as_float(r[qp][y]);
+                        acc[qp][0] = fmaf(e[y].x, v, acc[qp][0]);
+                        acc[qp][1] = fmaf(e[y].y, v, acc[qp][1]);
                     }
                 }
             }
@@ -368,46 +375,33 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             }
             // exchange with the other row of the visibility: the re row holds (er Tr, ei Tr),
             // the im row (er Ti, ei Ti); Re(E T) = er Tr - ei Ti, Im(E T) = er Ti + ei Tr
-            float *part = s_part + (size_t)(s * 2 + ci) * (2 * 8 * TV) + (size_t)h * 8 * TV;
+            float *part = s_part + (size_t)(s * 2 + ci) * (2 * 4 * TV) + (size_t)h * 4 * TV;
 #pragma unroll
-            for (int mm = 0; mm < 2; ++mm)
-#pragma unroll
-                for (int q2 = 0; q2 < 2; ++q2) {
-                    part[(4 * mm + 2 * q2) * TV + kl] = acc[mm][q2][0];
-                    part[(4 * mm + 2 * q2 + 1) * TV + kl] = acc[mm][q2][1];
-                }
+            for (int q2 = 0; q2 < 2; ++q2) {
+                part[(2 * q2) * TV + kl] = acc[q2][0];
+                part[(2 * q2 + 1) * TV + kl] = acc[q2][1];
+            }
             consumers_sync();
-            const float *other = s_part + (size_t)(s * 2 + (ci ^ 1)) * (2 * 8 * TV) + (size_t)h * 8 * TV;
+            const float *other = s_part + (size_t)(s * 2 + (ci ^ 1)) * (2 * 4 * TV) + (size_t)h * 4 * TV;
             // this thread writes polarisation q' = ci of the pair
             const int qp = ci;
-            float o[2][2];
-#pragma unroll
-            for (int mm = 0; mm < 2; ++mm) {
-                const float own0 = ci ? acc[mm][1][0] : acc[mm][0][0];
-                const float own1 = ci ? acc[mm][1][1] : acc[mm][0][1];
-                const float oth0 = other[(4 * mm + 2 * qp) * TV + kl];
-                const float oth1 = other[(4 * mm + 2 * qp + 1) * TV + kl];
-                const float a0 = ci ? oth0 : own0, a1 = ci ? oth1 : own1;     // er Tr, ei Tr
-                const float b0 = ci ? own0 : oth0, b1 = ci ? own1 : oth1;     // er Ti, ei Ti
-                o[mm][0] = a0 - b1;
-                o[mm][1] = b0 + a1;
-            }
+            const float own0 = ci ? acc[1][0] : acc[0][0];
+            const float own1 = ci ? acc[1][1] : acc[0][1];
+            const float oth0 = other[(2 * qp) * TV + kl], oth1 = other[(2 * qp + 1) * TV + kl];
+            const float a0 = ci ? oth0 : own0, a1 = ci ? oth1 : own1;     // er Tr, ei Tr
+            const float b0 = ci ? own0 : oth0, b1 = ci ? own1 : oth1;     // er Ti, ei Ti
             const uint32_t vw = __float_as_uint(cfk.w);       // index (< 2^31 - 1), bit 31 = flagged
             if (!(vw & 0x80000000u) && !failed) {
-                // y = T0 - i c_k T1 with T1 computed from rho r P
-                const float c1 = cfk.z / g.r_scale;
-                const size_t vi = vw;
-                float2 out = make_float2((o[0][0] + c1 * o[1][1]) * inv_scale, (o[0][1] - c1 * o[1][0]) * inv_scale);
-                ((float2 *)vis_out)[4 * vi + 2 * h + qp] = out;
+                ((float2 *)vis_out)[4 * (size_t)vw + 2 * h + qp] = make_float2((a0 - b1) * inv_scale, (b0 + a1) * inv_scale);
             } else if (vw != 0xFFFFFFFFu && !failed) {
-                ((float2 *)vis_out)[4 * (vw & 0x7FFFFFFFu) + 2 * h + qp] = make_float2(0.f, 0.f);   // flagged
+                ((float2 *)vis_out)[4 * (size_t)(vw & 0x7FFFFFFFu) + 2 * h + qp] = make_float2(0.f, 0.f);   // flagged
             }
         }
         if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(512));
+    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(256));
 }
 
 // one CTA per subgrid of one plan (plan index idx[b] or first + b; image b of sub)
