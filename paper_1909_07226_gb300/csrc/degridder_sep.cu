@@ -30,11 +30,14 @@
 // image (split from the grid and inverse transform in shared memory when
 // FUSED), the corrections, the scale and B (shared memory, fixed for the
 // subgrid).  Then per tile: eight producer warps stage the coefficients and
-// write A (shared memory, one core matrix per warp store) and the Ey* table;
+// write A (shared memory, one core matrix per warp store); the consumers form
+// the tile's Ey* table while its MMAs run;
 // the MMA warp issues the 16 MMAs into one of two accumulators; eight consumer
 // warps read their rows' columns, sum over y, pair the re and im rows of each
-// visibility through shared memory and write the visibilities.  Tensor memory:
-// accumulator b at 128 b.
+// visibility through shared memory and write the visibilities.  The A stages
+// (two, freed by the MMAs) and the coefficient and accumulator stages (four,
+// freed by the consumers) are separate, so producers, MMAs and consumers
+// overlap across tiles.  Tensor memory: accumulator e at 128 e.
 // Every wait is bounded; after a failed wait a thread skips every later wait,
 // the error word is set and no output is written.
 #include "batch_jobs.cuh"
@@ -60,22 +63,24 @@ constexpr int NP = NPW * 32, NC = NCW * 32;
 constexpr int MMA_WARP = NPW + NCW;
 constexpr int NT = NP + NC + 32;
 constexpr int TV = 64;                          // visibilities per tile (rows 2 k + re/im)
-constexpr int AST = 2;                          // A, Ey* and coefficient stages
+constexpr int AST = 2;                          // A stages (gated by the MMAs)
+constexpr int EST = 4;                          // Ey*, coefficient stages and accumulators (gated by the consumers)
 constexpr int KT = 4;                           // K steps of 16 (8 x, re/im) over the 32 x
 constexpr int T4K = 128 * 32;                   // 128 rows x 16 K FP16
 // B (fixed per subgrid), each [KT][128 rows (q, y)]: Q0 hi, Q0 lo, Q1 hi
 constexpr int B0H_OFF = 0, B0L_OFF = B0H_OFF + KT * T4K, B1H_OFF = B0L_OFF + KT * T4K;
 constexpr int A_OFF = B1H_OFF + KT * T4K;       // A: [AST][m = 0 hi, m = 0 lo, m = 1 hi][KT][128 rows]
 constexpr int A_STAGE = 3 * KT * T4K;
-constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [AST][32 y][TV] float2
+constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [2][32 y][TV] float2 (written and read by the consumers)
 constexpr int EY_STAGE = SL * TV * 8;
-constexpr int CF_OFF = EY_OFF + AST * EY_STAGE; // coefficients: [AST][TV] float4 (a, b, c, 0)
-constexpr int PART_OFF = CF_OFF + AST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
+constexpr int CF_OFF = EY_OFF + 2 * EY_STAGE;   // coefficients: [EST][TV] float4 (a, b, c, index)
+constexpr int PART_OFF = CF_OFF + EST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
 constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 4 * TV * 4;
 constexpr int FFT_P = SL + 1;
 constexpr uint32_t IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
-static_assert(AST == 2, "stage and accumulator indices coincide");
+static_assert(AST == 2 && EST == 4, "stage arithmetic below");
+static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
@@ -94,7 +99,8 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     float2 *s_ey = (float2 *)(smem + EY_OFF);
     float *s_part = (float *)(smem + PART_OFF);
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyempty[AST], s_dfull[2], s_dempty[2], s_drain;
+    __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyfull[EST], s_eyempty[EST], s_dfull[EST],
+        s_dempty[EST], s_drain;
     __shared__ float s_red[NT / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -102,18 +108,19 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
 
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&s_tmem)), "n"(256));
+                     :: "r"(smem_u32(&s_tmem)), "n"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         for (int s = 0; s < AST; ++s) {
             mbar_init(smem_u32(&s_afull[s]), NPW);
             mbar_init(smem_u32(&s_aempty[s]), 1);
-            mbar_init(smem_u32(&s_eyempty[s]), NCW);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&s_dfull[b]), 1);
-            mbar_init(smem_u32(&s_dempty[b]), NCW);
+        for (int e = 0; e < EST; ++e) {
+            mbar_init(smem_u32(&s_eyfull[e]), NPW);
+            mbar_init(smem_u32(&s_eyempty[e]), NCW);
+            mbar_init(smem_u32(&s_dfull[e]), 1);
+            mbar_init(smem_u32(&s_dempty[e]), NCW);
         }
         mbar_init(smem_u32(&s_drain), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -206,11 +213,11 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             const uint64_t da0 = smem_desc(smem_u32(smem + A_OFF));
             const uint64_t db0 = smem_desc(smem_u32(smem + B0H_OFF));
             for (int t = 0; t < n_tiles; ++t) {
-                const int s = t & 1;
+                const int s = t & 1, e = t & 3;
                 wait_or_fail(smem_u32(&s_afull[s]), (uint32_t)((t >> 1) & 1), failed);
-                if (t >= 2) wait_or_fail(smem_u32(&s_dempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
+                if (t >= EST) wait_or_fail(smem_u32(&s_dempty[e]), (uint32_t)(((t >> 2) - 1) & 1), failed);
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t dt = tmem + 128u * (uint32_t)s;
+                const uint32_t dt = tmem + 128u * (uint32_t)e;
 #pragma unroll
                 for (int kk = 0; kk < KT; ++kk) {
                     const uint64_t da = da0 + (uint64_t)((s * A_STAGE + kk * T4K) >> 4);     // m = 0 hi
@@ -222,7 +229,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                              IDESC_N128, 1u);                                                // m = 1 hi x Q1 hi
                 }
                 commit(smem_u32(&s_aempty[s]));
-                commit(smem_u32(&s_dfull[s]));
+                commit(smem_u32(&s_dfull[e]));
             }
             commit(smem_u32(&s_drain));
             bool drained = false;
@@ -237,11 +244,6 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         const float Xv = (float)(x - SL / 2), sx = g.sep[x], csig = g.c_scale;
         const uint32_t a_off = (uint32_t)(warp >> 1) * T4K + (uint32_t)(warp & 1) * kLBO + (uint32_t)klo * 16 +
                                (uint32_t)xlo * 4;
-        // Ey* entries e = tid + NP j: k = tid % TV, y = tid / TV + 4 j
-        const int ke = tid & (TV - 1), y0 = tid >> 6;
-        float tys[SL * TV / NP];
-#pragma unroll
-        for (int j = 0; j < SL * TV / NP; ++j) tys[j] = g.sep[SL + y0 + 4 * j];
         // coefficients of the next tile: threads < TV load one visibility's coordinates, then form
         // (a, b, c) and its output index (flag in bit 31) one tile ahead of use
         double pu = 0.0, pv = 0.0, pw = 0.0, psc = 0.0;
@@ -278,17 +280,16 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             form_coef();
         }
         for (int t = 0; t < n_tiles; ++t) {
-            const int s = t & 1;
-            if (t >= 2) {
-                wait_or_fail(smem_u32(&s_aempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
-                wait_or_fail(smem_u32(&s_eyempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
-            }
+            const int s = t & 1, e = t & 3;
+            if (t >= AST) wait_or_fail(smem_u32(&s_aempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
+            if (t >= EST) wait_or_fail(smem_u32(&s_eyempty[e]), (uint32_t)(((t >> 2) - 1) & 1), failed);
             if (tid < TV) {
-                s_coef[s * TV + tid] = cf_next;
+                s_coef[e * TV + tid] = cf_next;
                 if (t + 1 < n_tiles) load_coef(t + 1);
             }
             producers_sync();
-            const float4 *cf = s_coef + s * TV;
+            if (lane == 0) mbar_arrive(smem_u32(&s_eyfull[e]));      // the tile's coefficients are in place
+            const float4 *cf = s_coef + e * TV;
             uint8_t *As = smem + A_OFF + s * A_STAGE;
 #pragma unroll 2
             for (int kg = 0; kg < TV / 8; ++kg) {
@@ -313,18 +314,6 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                 *(uint32_t *)(As + 2 * KT * T4K + o_re) = h1r;
                 *(uint32_t *)(As + 2 * KT * T4K + o_im) = h1m;
             }
-            // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))): entry y TV + k
-            {
-                float2 *ey = s_ey + s * (SL * TV);
-                const float4 c = cf[ke];
-#pragma unroll
-                for (int j = 0; j < SL * TV / NP; ++j) {
-                    const int y = y0 + 4 * j;
-                    float sn, cs;
-                    __sincosf(fmaf(c.z, tys[j], c.y * (float)(y - SL / 2)), &sn, &cs);
-                    ey[y * TV + ke] = make_float2(cs, -sn);
-                }
-            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_afull[s]));
@@ -337,12 +326,30 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         const int qq = warp & 3, h = (warp - NPW) >> 2;
         const int ci = qq >> 1, kl = 32 * (qq & 1) + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * qq) << 16);
+        // Ey* entries j: visibility ke = ctid % TV, y = ctid / TV + 4 j (ctid = consumer thread index)
+        const int ctid = tid - NP, ke = ctid & (TV - 1), y0 = ctid >> 6;
+        float tys[SL * TV / NC];
+#pragma unroll
+        for (int j = 0; j < SL * TV / NC; ++j) tys[j] = g.sep[SL + y0 + 4 * j];
         for (int t = 0; t < n_tiles; ++t) {
-            const int s = t & 1;
-            wait_or_fail(smem_u32(&s_afull[s]), (uint32_t)((t >> 1) & 1), failed);
-            wait_or_fail(smem_u32(&s_dfull[s]), (uint32_t)((t >> 1) & 1), failed);
+            const int s = t & 1, e = t & 3;
+            wait_or_fail(smem_u32(&s_eyfull[e]), (uint32_t)((t >> 2) & 1), failed);
+            // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))) of the tile (entry y TV + k), while its MMAs run
+            float2 *eyw = s_ey + s * (SL * TV);
+            {
+                const float4 c = s_coef[e * TV + ke];
+#pragma unroll
+                for (int j = 0; j < SL * TV / NC; ++j) {
+                    const int y = y0 + 4 * j;
+                    float sn, cs;
+                    __sincosf(fmaf(c.z, tys[j], c.y * (float)(y - SL / 2)), &sn, &cs);
+                    eyw[y * TV + ke] = make_float2(cs, -sn);
+                }
+            }
+            consumers_sync();
+            wait_or_fail(smem_u32(&s_dfull[e]), (uint32_t)((t >> 2) & 1), failed);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float2 *ey = s_ey + s * (SL * TV);
+            const float2 *ey = eyw;
             float acc[2][2];         // [q'][ (sum er T, sum ei T) ]
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) acc[q2][0] = acc[q2][1] = 0.0f;
@@ -351,7 +358,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                 uint32_t r[2][8];
 #pragma unroll
                 for (int qp = 0; qp < 2; ++qp)       // columns 32 (2 h + q') + y
-                    tmem_ld8_nowait(lane_base + 128u * (uint32_t)s + (uint32_t)(64 * h + 32 * qp + 8 * yc), r[qp]);
+                    tmem_ld8_nowait(lane_base + 128u * (uint32_t)e + (uint32_t)(64 * h + 32 * qp + 8 * yc), r[qp]);
                 float2 e[8];
 #pragma unroll
                 for (int y = 0; y < 8; ++y) e[y] = ey[(8 * yc + y) * TV + kl];
@@ -366,12 +373,12 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                     }
                 }
             }
-            const float4 cfk = s_coef[s * TV + kl];
+            const float4 cfk = s_coef[e * TV + kl];
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(smem_u32(&s_dempty[s]));
-                mbar_arrive(smem_u32(&s_eyempty[s]));
+                mbar_arrive(smem_u32(&s_dempty[e]));
+                mbar_arrive(smem_u32(&s_eyempty[e]));
             }
             // exchange with the other row of the visibility: the re row holds (er Tr, ei Tr),
             // the im row (er Ti, ei Ti); Re(E T) = er Tr - ei Ti, Im(E T) = er Ti + ei Tr
@@ -401,7 +408,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(256));
+    if (warp == MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(512));
 }
 
 // one CTA per subgrid of one plan (plan index idx[b] or first + b; image b of sub)
