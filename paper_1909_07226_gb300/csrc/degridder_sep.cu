@@ -29,9 +29,10 @@
 // Schedule.  One CTA per subgrid, one CTA per SM.  All warps first form the
 // image (split from the grid and inverse transform in shared memory when
 // FUSED), the corrections, the scale and B (shared memory, fixed for the
-// subgrid).  Then per tile: eight producer warps stage the coefficients and
-// write A (shared memory, one core matrix per warp store); the consumers form
-// the tile's Ey* table while its MMAs run;
+// subgrid).  Then per tile: a coefficient warp stages the visibilities'
+// phase coefficients (FP64 offsets); eight producer warps write A (shared
+// memory, one core matrix per warp store); the consumers form the tile's Ey*
+// table while its MMAs run;
 // the MMA warp issues the 16 MMAs into one of two accumulators; eight consumer
 // warps read their rows' columns, sum over y, pair the re and im rows of each
 // visibility through shared memory and write the visibilities.  The A stages
@@ -61,7 +62,8 @@ constexpr int SPIX = SL * SL;
 constexpr int NPW = 8, NCW = 8;                 // producer and consumer warps
 constexpr int NP = NPW * 32, NC = NCW * 32;
 constexpr int MMA_WARP = NPW + NCW;
-constexpr int NT = NP + NC + 32;
+constexpr int COEF_WARP = MMA_WARP + 1;        // stages the per-visibility coefficients (FP64 offsets)
+constexpr int NT = NP + NC + 64;
 constexpr int TV = 64;                          // visibilities per tile (rows 2 k + re/im)
 constexpr int AST = 2;                          // A stages (gated by the MMAs)
 constexpr int EST = 4;                          // Ey*, coefficient stages and accumulators (gated by the consumers)
@@ -82,7 +84,6 @@ static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over th
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
 
 // Visibilities of subgrid d of geometry g from its image src[L][L][4], or with
@@ -117,7 +118,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             mbar_init(smem_u32(&s_aempty[s]), 1);
         }
         for (int e = 0; e < EST; ++e) {
-            mbar_init(smem_u32(&s_eyfull[e]), NPW);
+            mbar_init(smem_u32(&s_eyfull[e]), 1);
             mbar_init(smem_u32(&s_eyempty[e]), NCW);
             mbar_init(smem_u32(&s_dfull[e]), 1);
             mbar_init(smem_u32(&s_dempty[e]), NCW);
@@ -244,51 +245,10 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         const float Xv = (float)(x - SL / 2), sx = g.sep[x], csig = g.c_scale;
         const uint32_t a_off = (uint32_t)(warp >> 1) * T4K + (uint32_t)(warp & 1) * kLBO + (uint32_t)klo * 16 +
                                (uint32_t)xlo * 4;
-        // coefficients of the next tile: threads < TV load one visibility's coordinates, then form
-        // (a, b, c) and its output index (flag in bit 31) one tile ahead of use
-        double pu = 0.0, pv = 0.0, pw = 0.0, psc = 0.0;
-        uint32_t pvi = 0;
-        bool pin = false, pflag = false;
-        float4 cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
-        auto load_coef = [&](int t) {
-            const int k = t * TV + tid;
-            pin = k < d.kp;
-            pflag = false;
-            if (pin) {
-                int tt, c;
-                const size_t vi = vis_index(g, d, k, tt, c);
-                const double *xw = g.uvw + ((size_t)d.bl * g.n_t + tt) * 3;
-                pu = xw[0];
-                pv = xw[1];
-                pw = xw[2];
-                psc = g.scale[c];
-                pvi = (uint32_t)vi;
-                pflag = flags && flags[vi];
-            }
-        };
-        auto form_coef = [&]() {
-            cf_next = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));   // beyond K_p: no output
-            if (pin) {
-                cf_next.x = (float)((pu * psc - d.u0) * g.k_uv);
-                cf_next.y = (float)((pv * psc - d.v0) * g.k_uv);
-                cf_next.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
-                cf_next.w = __uint_as_float(pvi | (pflag ? 0x80000000u : 0u));
-            }
-        };
-        if (tid < TV) {
-            load_coef(0);
-            form_coef();
-        }
         for (int t = 0; t < n_tiles; ++t) {
             const int s = t & 1, e = t & 3;
             if (t >= AST) wait_or_fail(smem_u32(&s_aempty[s]), (uint32_t)(((t >> 1) - 1) & 1), failed);
-            if (t >= EST) wait_or_fail(smem_u32(&s_eyempty[e]), (uint32_t)(((t >> 2) - 1) & 1), failed);
-            if (tid < TV) {
-                s_coef[e * TV + tid] = cf_next;
-                if (t + 1 < n_tiles) load_coef(t + 1);
-            }
-            producers_sync();
-            if (lane == 0) mbar_arrive(smem_u32(&s_eyfull[e]));      // the tile's coefficients are in place
+            wait_or_fail(smem_u32(&s_eyfull[e]), (uint32_t)((t >> 2) & 1), failed);      // the tile's coefficients
             const float4 *cf = s_coef + e * TV;
             uint8_t *As = smem + A_OFF + s * A_STAGE;
 #pragma unroll 2
@@ -317,7 +277,59 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_afull[s]));
-            if (tid < TV && t + 1 < n_tiles) form_coef();
+        }
+        if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
+    } else if (warp == COEF_WARP) {
+        // ---- coefficients: lane l stages visibilities l and l + 32 of each tile: (a, b, c) from the
+        // FP64 offsets and the output index (flag in bit 31); the coordinates of the next tile are
+        // loaded while this one is formed, and a stage is reused once the consumers release it
+        struct Raw {
+            double u, v, w, sc;
+            uint32_t vi;
+            bool in, flag;
+        };
+        auto load_raw = [&](Raw &r, int k) {
+            r.in = k < d.kp;
+            r.flag = false;
+            if (r.in) {
+                int tt, c;
+                const size_t vi = vis_index(g, d, k, tt, c);
+                const double *xw = g.uvw + ((size_t)d.bl * g.n_t + tt) * 3;
+                r.u = xw[0];
+                r.v = xw[1];
+                r.w = xw[2];
+                r.sc = g.scale[c];
+                r.vi = (uint32_t)vi;
+                r.flag = flags && flags[vi];
+            }
+        };
+        auto form = [&](const Raw &r) {
+            float4 cf = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));   // beyond K_p: no output
+            if (r.in) {
+                cf.x = (float)((r.u * r.sc - d.u0) * g.k_uv);
+                cf.y = (float)((r.v * r.sc - d.v0) * g.k_uv);
+                cf.z = (float)((r.w * r.sc - d.w0) * 6.283185307179586476925286766559);
+                cf.w = __uint_as_float(r.vi | (r.flag ? 0x80000000u : 0u));
+            }
+            return cf;
+        };
+        Raw r0 = {0.0, 0.0, 0.0, 0.0, 0u, false, false}, r1 = r0;
+        if (n_tiles > 0) {
+            load_raw(r0, lane);
+            load_raw(r1, lane + 32);
+        }
+        for (int t = 0; t < n_tiles; ++t) {
+            const int e = t & 3;
+            const float4 c0 = form(r0), c1 = form(r1);
+            if (t + 1 < n_tiles) {
+                load_raw(r0, (t + 1) * TV + lane);
+                load_raw(r1, (t + 1) * TV + lane + 32);
+            }
+            if (t >= EST) wait_or_fail(smem_u32(&s_eyempty[e]), (uint32_t)(((t >> 2) - 1) & 1), failed);
+            s_coef[e * TV + lane] = c0;
+            s_coef[e * TV + lane + 32] = c1;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_eyfull[e]));
         }
         if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
     } else {
