@@ -56,7 +56,9 @@ ISSUE_PER_VISPIX_TC = 9
 # (profiles/gridder_degridder_tcw_fused_lofar_slice.md): gridder 176.3 + 5.5 MB
 # (visibilities in, grid lines read; the atomically updated grid lines are still
 # dirty in L2 when the launch ends), degridder 28.6 + 91.9 MB (grid lines in,
-# model visibilities out).
+# model visibilities out).  The separable kernels on the same slice
+# (profiles/gridder_degridder_sep_fused_lofar_slice.md): gridder 175.9 + 5.7 MB,
+# degridder 28.5 + 93.1 MB.
 FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
 SEP_VARIANT = "tcgen05_separable_fused"
 # Tensor-core work of the separable kernels (kind::f16, M = 128, K = 16 per MMA, 2 FLOP
@@ -67,12 +69,14 @@ SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (4 * 128)
 KERNEL_TRAFFIC = {
     "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
                 "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9,
-                FUSED_VARIANT: (176.3e6 + 5.5e6) / 4.731e9},
+                FUSED_VARIANT: (176.3e6 + 5.5e6) / 4.731e9,
+                SEP_VARIANT: (175.9e6 + 5.7e6) / 4.731e9},
     "degridder": {"f32x2_nv4_nt128_minb3_pg_static": (115.7e6 + 99.7e6) / 4.728e9,
                   "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9,
                   # the per-call choice runs the LOFAR-like workload on the same kernel
                   "tcgen05_tmemA_ws_nt288_auto512": (118.0e6 + 110.1e6) / 4.73e9,
-                  FUSED_VARIANT: (28.6e6 + 91.9e6) / 4.731e9},
+                  FUSED_VARIANT: (28.6e6 + 91.9e6) / 4.731e9,
+                  SEP_VARIANT: (28.5e6 + 93.1e6) / 4.731e9},
 }
 
 
