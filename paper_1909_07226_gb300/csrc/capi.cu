@@ -133,6 +133,30 @@ ProfileScope::~ProfileScope() {
 
 using namespace idg;
 
+static constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// x = hi + lo with hi = x rounded to FP32 and lo the rounded remainder (|x - hi - lo|
+// <= 2^-48 |x| about); the kernels form phase coefficients from such pairs with
+// error-free FP32 products and sums.
+static void split_pair(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// uvw [n][3] (metres) -> pairs [n][8] = (u hi, u lo, v hi, v lo, w hi, w lo, 0, 0)
+__global__ void split_uvw_kernel(const double *__restrict__ uvw, float4 *__restrict__ out, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[3], l[3];
+    for (int j = 0; j < 3; ++j) {
+        const double x = uvw[3 * i + j];
+        h[j] = __double2float_rn(x);
+        l[j] = __double2float_rn(x - (double)h[j]);
+    }
+    out[2 * i] = make_float4(h[0], l[0], h[1], l[1]);
+    out[2 * i + 1] = make_float4(h[2], l[2], 0.0f, 0.0f);
+}
+
 // The separable kernels (L = 32) write the phasor of visibility k at pixel (x, y) as
 // exp(i (a X + c s(x))) exp(i (b Y + c t(y))) exp(i c r(x, y)) and keep the last
 // factor to first order, 1 + i c r; the dropped terms are at most theta^2 / 2 in
@@ -153,6 +177,8 @@ idg::Geometry idg_plan::geometry() const {
     g.order = d_order;
     g.uvw = d_uvw;
     g.scale = d_scale;
+    g.uvw_f2 = d_uvw_f2;
+    g.scale_f2 = d_scale_f2;
     g.nprime = d_nprime;
     g.sep = d_nprime + (size_t)L * L;
     g.separable = stats.separable;
@@ -262,6 +288,8 @@ void idg_plan_destroy(idg_plan *p) {
     cudaFree(p->d_span_order);
     cudaFree(p->d_uvw);
     cudaFree(p->d_scale);
+    cudaFree(p->d_uvw_f2);
+    cudaFree(p->d_scale_f2);
     cudaFree(p->d_nprime);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
@@ -422,6 +450,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
     p->stats.device = p->device;
 
+    const double k_uv = kTwoPi * p->S / (double)L;      // as Geometry::k_uv
     std::vector<DevSubgrid> hsub((size_t)std::max<int64_t>(n_sub, 1));
     for (int64_t s = 0; s < n_sub; ++s) {
         const int32_t *d = &p->desc[s * kDescFields];
@@ -433,7 +462,9 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         g.u0 = ((double)g.q0 + 0.5 * L - 0.5 * N) / p->S;
         g.v0 = ((double)g.r0 + 0.5 * L - 0.5 * N) / p->S;
         g.w0 = w_step > 0.0 ? (double)(g.layer + pr.k_min) * w_step : 0.0;
-        g.pad = 0.0;
+        split_pair(g.u0 * k_uv, g.a0h, g.a0l);
+        split_pair(g.v0 * k_uv, g.b0h, g.b0l);
+        split_pair(g.w0 * kTwoPi, g.c0h, g.c0l);
     }
     std::vector<int32_t> span_order;
     // device work order: most visibilities first (longest-processing-time first
@@ -487,7 +518,12 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         span_order.swap(so);
     }
     std::vector<double> scale(n_chan);
-    for (int c = 0; c < n_chan; ++c) scale[c] = freqs_hz[c] / kSpeedOfLight;
+    std::vector<float> scale_f2((size_t)4 * n_chan);
+    for (int c = 0; c < n_chan; ++c) {
+        scale[c] = freqs_hz[c] / kSpeedOfLight;
+        split_pair(scale[c] * k_uv, scale_f2[4 * c], scale_f2[4 * c + 1]);
+        split_pair(scale[c] * kTwoPi, scale_f2[4 * c + 2], scale_f2[4 * c + 3]);
+    }
     // n' table, then the separable split n' = s(x) + t(y) + r(x, y) with s and t
     // the row and column through the centre pixel (l = 0 at X = 0, m = 0 at Y = 0)
     std::vector<float> nprime((size_t)2 * L * L + 2 * L);
@@ -513,6 +549,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_span_order, span_order.data(), sizeof(int32_t) * span_order.size(), "span order"},
         {(void **)&p->d_uvw, uvw_m, sizeof(double) * n_uvw, "uvw"},
         {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
+        {(void **)&p->d_scale_f2, scale_f2.data(), sizeof(float) * scale_f2.size(), "channel scale pairs"},
         {(void **)&p->d_nprime, nprime.data(), sizeof(float) * nprime.size(), "n' table"},
     };
     for (auto &u : ups) {
@@ -525,6 +562,20 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             idg_status st = cuda_fail(e, (std::string("cudaMemcpy(") + u.what + ")").c_str());
+            idg_plan_destroy(p);
+            return st;
+        }
+    }
+    {
+        const size_t n_bt = (size_t)n_bl * n_t;
+        e = cudaMalloc((void **)&p->d_uvw_f2, sizeof(float) * 8 * std::max<size_t>(n_bt, 1));
+        if (e == cudaSuccess && n_bt > 0) {
+            split_uvw_kernel<<<(unsigned)((n_bt + 255) / 256), 256>>>(p->d_uvw, (float4 *)p->d_uvw_f2, n_bt);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e != cudaSuccess) {
+            idg_status st = cuda_fail(e, "uvw pairs");
             idg_plan_destroy(p);
             return st;
         }

@@ -280,25 +280,29 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         }
         if (failed && lane == 0) atomicExch(&g_sepd_error, 1);
     } else if (warp == COEF_WARP) {
-        // ---- coefficients: lane l stages visibilities l and l + 32 of each tile: (a, b, c) from the
-        // FP64 offsets and the output index (flag in bit 31); the coordinates of the next tile are
-        // loaded while this one is formed, and a stage is reused once the consumers release it
+        // ---- coefficients: lane l stages visibilities l and l + 32 of each tile: (a, b, c) from
+        // float pairs (error-free FP32 products and sums, rounded once) and the output index (flag
+        // in bit 31); the coordinates of the next tile are loaded while this one is formed, and a
+        // stage is reused once the consumers release it
         struct Raw {
-            double u, v, w, sc;
+            float4 uv, sc;
+            float2 w;
             uint32_t vi;
             bool in, flag;
         };
+        const float4 *uvw2 = (const float4 *)g.uvw_f2;
+        const float4 *sc2 = (const float4 *)g.scale_f2;
         auto load_raw = [&](Raw &r, int k) {
             r.in = k < d.kp;
             r.flag = false;
             if (r.in) {
                 int tt, c;
                 const size_t vi = vis_index(g, d, k, tt, c);
-                const double *xw = g.uvw + ((size_t)d.bl * g.n_t + tt) * 3;
-                r.u = xw[0];
-                r.v = xw[1];
-                r.w = xw[2];
-                r.sc = g.scale[c];
+                const size_t bt = (size_t)d.bl * g.n_t + tt;
+                r.uv = uvw2[2 * bt];
+                const float4 w4 = uvw2[2 * bt + 1];
+                r.w = make_float2(w4.x, w4.y);
+                r.sc = sc2[c];
                 r.vi = (uint32_t)vi;
                 r.flag = flags && flags[vi];
             }
@@ -306,14 +310,16 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         auto form = [&](const Raw &r) {
             float4 cf = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));   // beyond K_p: no output
             if (r.in) {
-                cf.x = (float)((r.u * r.sc - d.u0) * g.k_uv);
-                cf.y = (float)((r.v * r.sc - d.v0) * g.k_uv);
-                cf.z = (float)((r.w * r.sc - d.w0) * 6.283185307179586476925286766559);
+                cf.x = pair_coef(r.uv.x, r.uv.y, r.sc.x, r.sc.y, d.a0h, d.a0l);
+                cf.y = pair_coef(r.uv.z, r.uv.w, r.sc.x, r.sc.y, d.b0h, d.b0l);
+                cf.z = pair_coef(r.w.x, r.w.y, r.sc.z, r.sc.w, d.c0h, d.c0l);
                 cf.w = __uint_as_float(r.vi | (r.flag ? 0x80000000u : 0u));
             }
             return cf;
         };
-        Raw r0 = {0.0, 0.0, 0.0, 0.0, 0u, false, false}, r1 = r0;
+        Raw r0 = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float2(0.f, 0.f), 0u,
+                  false, false},
+            r1 = r0;
         if (n_tiles > 0) {
             load_raw(r0, lane);
             load_raw(r1, lane + 32);

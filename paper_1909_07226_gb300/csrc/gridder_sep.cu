@@ -188,9 +188,11 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         const float csig = g.c_scale;
 
         // staging: visibility tid of batch b, loaded into registers one batch ahead
-        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
-        double pu = 0.0, pv = 0.0, pw = 0.0, psc = 0.0;
+        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, puv = pa, pws = pa;
+        float2 pw = make_float2(0.f, 0.f);
         bool pin = false, pflag = false;
+        const float4 *uvw2 = (const float4 *)g.uvw_f2;
+        const float4 *sc2 = (const float4 *)g.scale_f2;
         auto load_batch = [&](int b) {
             const int k = b * VB + tid;
             pin = k < d.kp;
@@ -198,11 +200,11 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             if (pin) {
                 int t, c;
                 const size_t vi = vis_index(g, d, k, t, c);
-                const double *xw = g.uvw + ((size_t)d.bl * g.n_t + t) * 3;
-                pu = xw[0];
-                pv = xw[1];
-                pw = xw[2];
-                psc = g.scale[c];
+                const size_t bt = (size_t)d.bl * g.n_t + t;
+                puv = uvw2[2 * bt];
+                const float4 w4 = uvw2[2 * bt + 1];
+                pw = make_float2(w4.x, w4.y);
+                pws = sc2[c];
                 pflag = flags && flags[vi];
                 if (!pflag) {
                     pa = vis[2 * vi];
@@ -210,14 +212,15 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 }
             }
         };
-        // phase coefficients of the staged visibility (FP64 offsets, rounded once to FP32)
+        // phase coefficients of the staged visibility: u (f/c) k_uv - u0 k_uv and so on, from
+        // float pairs with error-free products and sums, rounded once to FP32
         float4 cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
         auto form_coef = [&]() {
             cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
             if (pin) {
-                cf_next.x = (float)((pu * psc - d.u0) * g.k_uv);
-                cf_next.y = (float)((pv * psc - d.v0) * g.k_uv);
-                cf_next.z = (float)((pw * psc - d.w0) * 6.283185307179586476925286766559);
+                cf_next.x = pair_coef(puv.x, puv.y, pws.x, pws.y, d.a0h, d.a0l);
+                cf_next.y = pair_coef(puv.z, puv.w, pws.x, pws.y, d.b0h, d.b0l);
+                cf_next.z = pair_coef(pw.x, pw.y, pws.z, pws.w, d.c0h, d.c0l);
             }
         };
         // coefficients and raw V of the batch; the batch's largest |component| into s_red[bb]

@@ -12,13 +12,15 @@ namespace idg {
 constexpr double kSpeedOfLight = 299792458.0;   // m/s
 constexpr int kDescFields = IDG_DESC_FIELDS;
 
-// Work description of one subgrid on the device (80 B, 16-B aligned).
+// Work description of one subgrid on the device (96 B, 16-B aligned).
 struct alignas(16) DevSubgrid {
     int32_t bl, slot, t0, nt, c0, nc, q0, r0, layer, kp, st_p, st_q;
     double u0, v0, w0;     // centre of the subgrid in wavelengths (Sect. 3.3)
-    double pad;
+    // the phase offsets of the centre as float pairs (hi + lo = the FP64 value to
+    // about 2^-48): u0 k_uv, v0 k_uv and 2 pi w0
+    float a0h, a0l, b0h, b0l, c0h, c0l;
 };
-static_assert(sizeof(DevSubgrid) == 80, "DevSubgrid layout");
+static_assert(sizeof(DevSubgrid) == 96, "DevSubgrid layout");
 
 // Geometry and pointers the kernels read; passed by value to every launch.
 struct Geometry {
@@ -29,6 +31,12 @@ struct Geometry {
     const int32_t *order;      // [n_sub], device work order (plan indices)
     const double *uvw;         // [n_bl][n_t][3] metres
     const double *scale;       // [n_chan] f / c
+    // float-pair copies (hi + lo = the FP64 value to about 2^-48) for coefficient
+    // arithmetic without FP64 instructions, 16-B aligned: uvw_f2[8 (bl n_t + t) ..]
+    // = (u hi, u lo, v hi, v lo, w hi, w lo, 0, 0) in metres; scale_f2[4 c ..] =
+    // (k_uv f/c hi, lo, 2 pi f/c hi, lo)
+    const float *uvw_f2;
+    const float *scale_f2;
     const float *nprime;       // [L][L] n' = sqrt(1 - l^2 - m^2) - 1
     double ds;                 // channel scale step (f_{c+1} - f_c)/c for uniformly spaced channels
     int recurrence;            // 1: phasors by channel recurrence (IDG_PHASOR_RECURRENCE)
@@ -79,6 +87,8 @@ struct idg_plan {
     int32_t *d_order = nullptr;
     double *d_uvw = nullptr;
     double *d_scale = nullptr;
+    float *d_uvw_f2 = nullptr;             // float-pair copies for the coefficient arithmetic
+    float *d_scale_f2 = nullptr;
     float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
     double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
     float c_scale = 1.0f;

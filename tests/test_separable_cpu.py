@@ -87,3 +87,55 @@ def test_plan_reports_the_remainder_phase(kw):
     want = _theta_definition(wl)
     assert p.stats.sep_phase == pytest.approx(want, rel=1e-9, abs=1e-15)
     assert p.stats.separable == (1 if want <= 1.38e-3 else 0)
+
+
+def _fma32(a, b, c):
+    # fused multiply-add rounded once to FP32: a b of two FP32 values is exact in FP64,
+    # and here the sum with c is too (the operands lie within 2^29 of each other)
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _pair(x):
+    hi = np.float32(x)
+    return hi, np.float32(x - np.float64(hi))
+
+
+def _pair_coef(xh, xl, sh, sl, oh, ol):
+    # restatement of the kernels' float-pair coefficient: two-product by fma, then
+    # Knuth's two-sum of p and -oh, the small terms added, one final rounding
+    f = np.float32
+    p = f(xh * sh)
+    e = _fma32(xh, sh, -p)
+    e = _fma32(xh, sl, e)
+    e = _fma32(xl, sh, e)
+    s = f(p - oh)
+    bb = f(s - p)
+    err = f(f(p - f(s - bb)) + f(-oh - bb))
+    return f(s + f(err + f(e - ol)))
+
+
+def test_float_pair_coefficients_match_fp64_rounded_once():
+    """The kernels form a = u (f/c) k_uv - u0 k_uv without FP64 instructions, from
+    float pairs.  Over LOFAR-scale magnitudes (|u (f/c) k_uv| up to ~300 rad on a
+    4096-pixel grid with 32-pixel subgrids, |a| <= pi) the result is the FP64 value
+    correctly rounded to FP32 (within half an ulp, up to the ~2^-48 terms left out),
+    where a single FP32 product and difference would be off by up to ~1e-4 rad."""
+    rng = np.random.default_rng(7)
+    k_uv = 2 * np.pi * 0.05 / 32
+    worst_ulps, worst_naive = 0.0, 0.0
+    for _ in range(4000):
+        u = rng.uniform(-1.0e5, 1.0e5)                     # metres
+        fc = rng.uniform(120e6, 190e6) / 299792458.0       # f / c
+        u_lambda = u * fc
+        u0 = np.round(u_lambda * k_uv / 0.1) * 0.1 / k_uv + rng.uniform(-1, 1) / k_uv
+        exact = u_lambda * k_uv - u0 * k_uv
+        uh, ul = _pair(u)
+        sh, sl = _pair(fc * k_uv)
+        oh, ol = _pair(u0 * k_uv)
+        got = _pair_coef(uh, ul, sh, sl, oh, ol)
+        ulp = np.spacing(np.float32(abs(exact))) if exact != 0 else np.float32(1e-45)
+        worst_ulps = max(worst_ulps, abs(np.float64(got) - exact) / np.float64(ulp))
+        naive = np.float32(np.float32(np.float32(u) * np.float32(fc * k_uv)) - np.float32(u0 * k_uv))
+        worst_naive = max(worst_naive, abs(np.float64(naive) - exact))
+    assert worst_ulps <= 0.51, worst_ulps
+    assert worst_naive > 1e-5          # the plain FP32 route would not do
