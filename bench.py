@@ -144,6 +144,52 @@ def whole_job_rate(world, seconds_local: float, units_local: float) -> float:
     return sum_over_ranks(world, units_local) / max_over_ranks(world, seconds_local)
 
 
+def _cpulist(text: str) -> set:
+    cpus = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        lo, _, hi = part.partition("-")
+        cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
+class near_gpu_memory:
+    """Within the block, run on the CPUs next to the GPU (its PCI device's
+    local_cpulist in sysfs) so that page-locked host buffers allocated and filled
+    there sit on the GPU's own host memory node (first-touch placement); the
+    previous CPU set comes back on exit.  No-op where sysfs or affinity is not
+    available.  Records the CPUs used in .cpus."""
+
+    def __init__(self, device: int):
+        self.device, self.saved, self.cpus = device, None, None
+
+    def __enter__(self):
+        import torch
+        try:
+            pr = torch.cuda.get_device_properties(self.device)
+            bdf = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+            with open(f"/sys/bus/pci/devices/{bdf}/local_cpulist") as f:
+                local = _cpulist(f.read())
+            self.saved = os.sched_getaffinity(0)
+            use = local & self.saved
+            if use and use != self.saved:
+                os.sched_setaffinity(0, use)
+                self.cpus = f"{len(use)} of {len(self.saved)} allowed CPUs, local to {bdf}"
+            else:
+                self.cpus = (f"all {len(use)} allowed CPUs are local to {bdf}" if use else
+                             f"none of the {len(self.saved)} allowed CPUs is local to {bdf}")
+                self.saved = None
+        except Exception:          # no sysfs entry, no affinity support, no device properties
+            self.saved = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
+        return False
+
+
 def make_workload(name):
     from paper_1909_07226_gb300 import synthetic as syn
     if name == "tiny":
@@ -448,12 +494,15 @@ def run_gb300(args, world, rank, local):
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 
     # end to end through the host-buffer C-ABI calls
-    vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
-    vis_h.copy_(torch.from_numpy(wl.vis))
-    model_p = torch.empty(model.shape, dtype=torch.complex64, pin_memory=True)
-    model_p.copy_(torch.from_numpy(model_h))
-    grid_h = torch.empty(grid.shape, dtype=torch.complex64, pin_memory=True)
-    visout_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+    with near_gpu_memory(local) as placement:
+        vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+        vis_h.copy_(torch.from_numpy(wl.vis))
+        model_p = torch.empty(model.shape, dtype=torch.complex64, pin_memory=True)
+        model_p.copy_(torch.from_numpy(model_h))
+        grid_h = torch.empty(grid.shape, dtype=torch.complex64, pin_memory=True)
+        grid_h.zero_()
+        visout_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+        visout_h.zero_()
     aterms_h = torch.from_numpy(wl.aterms)
     taper_h = torch.from_numpy(wl.taper)
     flags_h = None if wl.flags is None else torch.from_numpy(wl.flags)
@@ -494,7 +543,8 @@ def run_gb300(args, world, rank, local):
             "data": "synthetic", "config": workload_config(wl, args.config),
             "roofline": roof, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                    "host_buffers_placed_from_cpus": placement.cpus},
             "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu,
             "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
             "parallelism": "replicas" if world > 1 else "single GPU",

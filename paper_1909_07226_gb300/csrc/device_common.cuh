@@ -12,28 +12,60 @@ namespace idg {
 namespace dev {
 
 // ---------------------------------------------------------------------------
+// x s - o for float pairs x = xh + xl, s = sh + sl, o = oh + ol, rounded once to FP32.
+// The product xh sh is split exactly by an fma (Dekker's two-product, with fma), the
+// difference with oh exactly by Knuth's two-sum; the terms left out (xl sl and the
+// roundings of the small corrections) are about 2^-48 |x s|.  No FP64 instruction:
+// FP64 issues at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ float pair_coef(float xh, float xl, float sh, float sl, float oh, float ol) {
+    const float p = __fmul_rn(xh, sh);
+    float e = __fmaf_rn(xh, sh, -p);
+    e = __fmaf_rn(xh, sl, e);
+    e = __fmaf_rn(xl, sh, e);
+    const float s = __fsub_rn(p, oh);
+    const float bb = __fsub_rn(s, p);
+    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(-oh, bb));
+    return __fadd_rn(s, __fadd_rn(err, __fsub_rn(e, ol)));
+}
+
 // phase coefficients of one visibility relative to its subgrid
 //
 // The subgrid-image phasor of Eq. (ShiftedDirectImaging) at pixel (y, x) is
 //   phi = 2 pi ((u - u0) l + (v - v0) m + (w - w0) n'),  l = X S/L, m = Y S/L,
-// with X = x - L/2, Y = y - L/2.  u = u_m * f/c and the offsets are formed in
-// FP64 (the coordinates are large, the differences small); the three
-// coefficients of phi = a X + b Y + c n' are then rounded once to FP32.
+// with X = x - L/2, Y = y - L/2.  u = u_m * f/c; the coordinates are large and the
+// differences small, so a = u_m (f/c) k_uv - u0 k_uv (and b, c alike) is formed from
+// float pairs (hi + lo, FP64 accurate) with error-free products and sums and
+// rounded once to FP32, as an FP64 evaluation rounded to FP32 would be.
 struct PhaseCoef {
     float a, b, c;
 };
 
-__device__ __forceinline__ PhaseCoef phase_coef(const Geometry &g, const DevSubgrid &d, int t, int c) {
-    const double *x = g.uvw + ((size_t)d.bl * g.n_t + t) * 3;
-    const double sc = g.scale[c];
-    const double du = x[0] * sc - d.u0;
-    const double dv = x[1] * sc - d.v0;
-    const double dw = x[2] * sc - d.w0;
-    PhaseCoef r;
-    r.a = (float)(du * g.k_uv);
-    r.b = (float)(dv * g.k_uv);
-    r.c = (float)(dw * 6.283185307179586476925286766559);
+// the plan's float-pair coordinates of (baseline, timestep) and channel scales
+struct PairCoords {
+    float4 uv, sc;
+    float2 w;
+};
+
+__device__ __forceinline__ PairCoords pair_coords(const Geometry &g, const DevSubgrid &d, int t, int c) {
+    const float4 *x = (const float4 *)g.uvw_f2 + 2 * ((size_t)d.bl * g.n_t + t);
+    PairCoords r;
+    r.uv = x[0];
+    const float4 w4 = x[1];
+    r.w = make_float2(w4.x, w4.y);
+    r.sc = ((const float4 *)g.scale_f2)[c];
     return r;
+}
+
+__device__ __forceinline__ PhaseCoef pair_phase_coef(const DevSubgrid &d, const PairCoords &x) {
+    PhaseCoef r;
+    r.a = pair_coef(x.uv.x, x.uv.y, x.sc.x, x.sc.y, d.a0h, d.a0l);
+    r.b = pair_coef(x.uv.z, x.uv.w, x.sc.x, x.sc.y, d.b0h, d.b0l);
+    r.c = pair_coef(x.w.x, x.w.y, x.sc.z, x.sc.w, d.c0h, d.c0l);
+    return r;
+}
+
+__device__ __forceinline__ PhaseCoef phase_coef(const Geometry &g, const DevSubgrid &d, int t, int c) {
+    return pair_phase_coef(d, pair_coords(g, d, t, c));
 }
 
 __device__ __forceinline__ size_t vis_index(const Geometry &g, const DevSubgrid &d, int k, int &t, int &c) {

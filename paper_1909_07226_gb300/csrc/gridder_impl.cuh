@@ -12,7 +12,7 @@ namespace dev {
 
 struct RawVis {
     float4 v01, v23;
-    double u, v, w, sc;
+    PairCoords x;
     int ok;
 };
 
@@ -20,11 +20,7 @@ __device__ __forceinline__ void fetch_raw(const Geometry &g, const DevSubgrid &d
                                           const uint8_t *flags, RawVis &r) {
     int t, c;
     const size_t vi = vis_index(g, d, k, t, c);
-    const double *x = g.uvw + ((size_t)d.bl * g.n_t + t) * 3;
-    r.u = x[0];
-    r.v = x[1];
-    r.w = x[2];
-    r.sc = g.scale[c];
+    r.x = pair_coords(g, d, t, c);
     r.v01 = vis[2 * vi];
     r.v23 = vis[2 * vi + 1];
     r.ok = !(flags && flags[vi]);
@@ -32,11 +28,8 @@ __device__ __forceinline__ void fetch_raw(const Geometry &g, const DevSubgrid &d
 
 __device__ __forceinline__ void store_raw(const Geometry &g, const DevSubgrid &d, const RawVis &r, float4 *s_coef,
                                           float4 *s_v01, float4 *s_v23, int i) {
-    const double du = r.u * r.sc - d.u0;
-    const double dv = r.v * r.sc - d.v0;
-    const double dw = r.w * r.sc - d.w0;
-    s_coef[i] = make_float4((float)(du * g.k_uv), (float)(dv * g.k_uv),
-                            (float)(dw * 6.283185307179586476925286766559), 0.0f);
+    const PhaseCoef pc = pair_phase_coef(d, r.x);
+    s_coef[i] = make_float4(pc.a, pc.b, pc.c, 0.0f);
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     s_v01[i] = r.ok ? r.v01 : z;     // flagged: weight 0
     s_v23[i] = r.ok ? r.v23 : z;

@@ -147,20 +147,5 @@ __device__ __forceinline__ void split_e(float x, float y, uint32_t &hi, uint32_t
         "}" : "=r"(hi), "=r"(lo) : "f"(x), "f"(y));
 }
 
-// x s - o for float pairs x = xh + xl, s = sh + sl, o = oh + ol, rounded once to FP32.
-// The product xh sh is split exactly by an fma (Dekker's two-product, with fma), the
-// difference with oh exactly by Knuth's two-sum; the terms left out (xl sl and the
-// roundings of the small corrections) are about 2^-48 |x s|.
-__device__ __forceinline__ float pair_coef(float xh, float xl, float sh, float sl, float oh, float ol) {
-    const float p = __fmul_rn(xh, sh);
-    float e = __fmaf_rn(xh, sh, -p);
-    e = __fmaf_rn(xh, sl, e);
-    e = __fmaf_rn(xl, sh, e);
-    const float s = __fsub_rn(p, oh);
-    const float bb = __fsub_rn(s, p);
-    const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(-oh, bb));
-    return __fadd_rn(s, __fadd_rn(err, __fsub_rn(e, ol)));
-}
-
 }  // namespace tc
 }  // namespace idg
