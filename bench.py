@@ -44,21 +44,14 @@ LANES_PER_SM = 128
 # An SM issues 4 x 32 thread-instructions per clock.
 ISSUE_PER_VISPIX_TC = 9
 # DRAM bytes (read + write) per visibility-pixel of one launch, from the ncu
-# captures of the packed-FP32 L=32 kernels on the LOFAR-like slice
-# (profiles/gridder_degridder_f32x2_lofar_slice.md: 159.1 + 54.4 MB for 4.73e9
-# visibility-pixels).  The traffic is the visibilities and the subgrid writes,
-# proportional to the work, so it scales to a full launch by the units it processes.
-# The same for the default L=32 degridder: its pixel-group-1 launch on the slice moved
-# 115.7 + 99.7 MB for ~4.728e9 visibility-pixels (all but 18 small subgrids of the slice).
-# The tensor-core kernels on the same slice (one launch of all 3206 subgrids, 4.73e9 visibility-pixels):
-# gridder 159.2 + 56.0 MB, degridder 118.0 + 110.1 MB (profiles/*_tcw_lofar_slice.md).
-# The fused tensor-core kernels of the composite calls, same slice and launch
-# (profiles/gridder_degridder_tcw_fused_lofar_slice.md): gridder 176.3 + 5.5 MB
-# (visibilities in, grid lines read; the atomically updated grid lines are still
-# dirty in L2 when the launch ends), degridder 28.6 + 91.9 MB (grid lines in,
-# model visibilities out).  The separable kernels on the same slice
-# (profiles/gridder_degridder_sep_fused_lofar_slice.md): gridder 175.9 + 5.7 MB,
-# degridder 28.5 + 93.1 MB.
+# capture of the separable kernels (the default at L = 32 where the plan is
+# separable) on the LOFAR-like slice, one launch of all 3206 subgrids, 4.731e9
+# visibility-pixels (profiles/gridder_degridder_sep_fused_lofar_slice.md):
+# gridder 178.7 + 5.7 MB (visibilities and coordinates in; the atomically updated
+# grid lines are still dirty in L2 when the launch ends), degridder 31.1 + 93.5 MB
+# (grid lines and coordinates in, model visibilities out).  The traffic is
+# proportional to the work, so it scales to a full launch by the units processed.
+# Kernels without a capture of their current code report no traffic.
 FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
 SEP_VARIANT = "tcgen05_separable_fused"
 # Tensor-core work of the separable kernels (kind::f16, M = 128, K = 16 per MMA, 2 FLOP
@@ -67,16 +60,8 @@ SEP_VARIANT = "tcgen05_separable_fused"
 SEP_GRID_FLOP_PER_GROUP = 2 * 128 * 16 * (192 + 64)
 SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (4 * 128)
 KERNEL_TRAFFIC = {
-    "gridder": {"f32x2_npx4_vb128_minb2": (159.1e6 + 54.4e6) / 4.73e9,
-                "tcgen05_tmemA_ws_nt288": (159.2e6 + 56.0e6) / 4.73e9,
-                FUSED_VARIANT: (176.3e6 + 5.5e6) / 4.731e9,
-                SEP_VARIANT: (175.9e6 + 5.7e6) / 4.731e9},
-    "degridder": {"f32x2_nv4_nt128_minb3_pg_static": (115.7e6 + 99.7e6) / 4.728e9,
-                  "tcgen05_tmemA_ws_nt288": (118.0e6 + 110.1e6) / 4.73e9,
-                  # the per-call choice runs the LOFAR-like workload on the same kernel
-                  "tcgen05_tmemA_ws_nt288_auto512": (118.0e6 + 110.1e6) / 4.73e9,
-                  FUSED_VARIANT: (28.6e6 + 91.9e6) / 4.731e9,
-                  SEP_VARIANT: (28.5e6 + 93.1e6) / 4.731e9},
+    "gridder": {SEP_VARIANT: (178.7e6 + 5.7e6) / 4.731e9},
+    "degridder": {SEP_VARIANT: (31.1e6 + 93.5e6) / 4.731e9},
 }
 
 
