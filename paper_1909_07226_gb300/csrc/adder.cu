@@ -3,7 +3,7 @@
 // from master grid").  A pixel of a grid or subgrid is 32 contiguous bytes (4
 // complex64 polarisations); consecutive threads move consecutive pixels of a
 // subgrid row, so every warp touches a contiguous 32*L-byte run of a grid row.
-// The adder uses 16-byte vector atomics because subgrids overlap.
+// The adder uses 16-byte vector reductions because subgrids overlap.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,8 +26,8 @@ adder_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const f
     for (int pix = threadIdx.x; pix < L * L; pix += kThreads) {
         const int i = pix / L, j = pix - (pix / L) * L;
         const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
-        atomicAdd(dst + 2 * gp, src[2 * pix]);
-        atomicAdd(dst + 2 * gp + 1, src[2 * pix + 1]);
+        dev::red_add_f4(dst + 2 * gp, src[2 * pix]);
+        dev::red_add_f4(dst + 2 * gp + 1, src[2 * pix + 1]);
     }
 }
 

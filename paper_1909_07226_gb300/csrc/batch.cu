@@ -116,8 +116,8 @@ batch_grid_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ item
             const float2 p0 = s_fft[(0 * L + i) * P + j], p1 = s_fft[(1 * L + i) * P + j];
             const float2 p2 = s_fft[(2 * L + i) * P + j], p3 = s_fft[(3 * L + i) * P + j];
             const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
-            atomicAdd(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
-            atomicAdd(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
+            red_add_f4(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
+            red_add_f4(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
         }
         __syncthreads();
     }

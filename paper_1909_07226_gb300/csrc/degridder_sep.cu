@@ -79,8 +79,13 @@ constexpr int CF_OFF = EY_OFF + 2 * EY_STAGE;   // coefficients: [EST][TV] float
 constexpr int PART_OFF = CF_OFF + EST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
 constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 4 * TV * 4;
 constexpr int FFT_P = SL + 1;
+// the subgrid's A-terms (A_p, A_q: [2][L^2] 2 x 2 complex, 64 KB), fetched by bulk copies at the
+// start of the prologue beside the transform planes (A stages and Ey* table are free until the tiles)
+constexpr int AT_OFF = A_OFF + 4 * SL * FFT_P * 8;
+constexpr uint32_t AT_BYTES = SPIX * 32;       // one station
 constexpr uint32_t IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
+static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
@@ -101,7 +106,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     float *s_part = (float *)(smem + PART_OFF);
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyfull[EST], s_eyempty[EST], s_dfull[EST],
-        s_dempty[EST], s_drain;
+        s_dempty[EST], s_drain, s_atbar;
     __shared__ float s_red[NT / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -124,7 +129,15 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             mbar_init(smem_u32(&s_dempty[e]), NCW);
         }
         mbar_init(smem_u32(&s_drain), 1);
+        mbar_init(smem_u32(&s_atbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (aterms) {
+            const float4 *base = aterms + 2 * ((size_t)d.slot * g.n_stations) * SPIX;
+            mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
+            bulk_g2s(smem_u32(smem + AT_OFF), base + 2 * (size_t)d.st_p * SPIX, AT_BYTES, smem_u32(&s_atbar));
+            bulk_g2s(smem_u32(smem + AT_OFF + AT_BYTES), base + 2 * (size_t)d.st_q * SPIX, AT_BYTES,
+                     smem_u32(&s_atbar));
+        }
     }
 
     // ---- prologue: the corrected image P = taper A_p I A_q^H into the planes
@@ -141,7 +154,13 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             s_fft[(3 * SL + i) * FFT_P + j] = make_float2(sg * b.z, sg * b.w);
         }
         __syncthreads();
-        fft2_planar<SL, +1>(s_fft, tid, NT);
+        fft2_planar_pairs32<+1>(s_fft, tid);
+    }
+    if (!FUSED) __syncthreads();    // (FUSED: the transform's barriers) the copies' barrier is initialised
+    if (aterms) {
+        bool late = false;
+        wait_or_fail(smem_u32(&s_atbar), 0u, late);
+        if (late) atomicExch(&g_sepd_error, 1);
     }
     float m = 0.0f;
     for (int pix = tid; pix < SPIX; pix += NT) {
@@ -158,9 +177,9 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             P = load_m22(src + 2 * pix);
         }
         if (aterms) {
-            const size_t base = ((size_t)d.slot * g.n_stations) * SPIX;
-            const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * SPIX + pix));
-            const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * SPIX + pix));
+            const float4 *at = (const float4 *)(smem + AT_OFF);
+            const M22 Ap = load_m22(at + 2 * pix);
+            const M22 Aq = load_m22(at + 2 * (SPIX + pix));
             P = mul_mul_herm(Ap, P, Aq);
         }
         const float tw = taper[pix];

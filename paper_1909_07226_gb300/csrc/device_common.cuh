@@ -68,6 +68,13 @@ __device__ __forceinline__ PhaseCoef phase_coef(const Geometry &g, const DevSubg
     return pair_phase_coef(d, pair_coords(g, d, t, c));
 }
 
+// *p += v as one 16-byte reduction without a return value (relaxed, GPU scope; each
+// component rounded to nearest like atomicAdd)
+__device__ __forceinline__ void red_add_f4(float4 *p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ size_t vis_index(const Geometry &g, const DevSubgrid &d, int k, int &t, int &c) {
     const int tt = k / d.nc;
     t = d.t0 + tt;

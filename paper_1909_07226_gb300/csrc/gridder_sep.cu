@@ -326,30 +326,35 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 // B entries: beta = Ex_k(x) (m = 0: hi and lo) and c_k sigma Ex_k(x) (m = 1: hi), rows
                 // (m, re, x) = (Re beta, -Im beta) and (m, im, x) = (Im beta, Re beta)
                 uint8_t *Bs = sB + s * B_STAGE;
+                {
+                    // visibilities j0 = 2 jl and j0 + 1 of group i = warp / 4 sit in adjacent K slots of
+                    // each row: one 8-byte store per row
+                    const int i = warp >> 2, j0 = 2 * jl;
+                    uint32_t w[6][2];
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int combo = 2 * (warp >> 2) + t, i = combo >> 1, j = 4 * (combo & 1) + jl;
-                    const float4 cf = coef[8 * (SG * si + i) + j];
-                    float sn, cs;
-                    __sincosf(fmaf(cf.z, sx, cf.x * Xv), &sn, &cs);
-                    // the im row (sn, cs) is the re row (cs, -sn) with its halves swapped and the new
-                    // low half negated: exact, as FP16 rounding is symmetric
-                    uint32_t hr, lr;
-                    split_e(cs, -sn, hr, lr);
-                    const uint32_t hi_ = __byte_perm(hr, 0u, 0x1032u) ^ 0x8000u;
-                    const uint32_t li_ = __byte_perm(lr, 0u, 0x1032u) ^ 0x8000u;
-                    const float cz = cf.z * csig;
-                    const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn);
-                    const uint32_t h1i = __byte_perm(h1r, 0u, 0x1032u) ^ 0x8000u;
-                    uint8_t *Bg = Bs + i * B_GROUP;
-                    const uint32_t kc = (uint32_t)(j >> 2) * kLBO + (uint32_t)(xb & 7) * 16 + (uint32_t)(j & 3) * 4;
-                    const uint32_t rg = (uint32_t)(xb >> 3) * kSBO;        // row group of x within a 32-row block
-                    *(uint32_t *)(Bg + rg + kc) = hr;                      // rows   0 + x: m = 0, re
-                    *(uint32_t *)(Bg + 4 * kSBO + rg + kc) = hi_;          // rows  32 + x: m = 0, im
-                    *(uint32_t *)(Bg + 8 * kSBO + rg + kc) = h1r;          // rows  64 + x: m = 1, re
-                    *(uint32_t *)(Bg + 12 * kSBO + rg + kc) = h1i;         // rows  96 + x: m = 1, im
-                    *(uint32_t *)(Bg + 16 * kSBO + rg + kc) = lr;          // rows 128 + x: m = 0, re, lo
-                    *(uint32_t *)(Bg + 20 * kSBO + rg + kc) = li_;         // rows 160 + x: m = 0, im, lo
+                    for (int t = 0; t < 2; ++t) {
+                        const float4 cf = coef[8 * (SG * si + i) + j0 + t];
+                        float sn, cs;
+                        __sincosf(fmaf(cf.z, sx, cf.x * Xv), &sn, &cs);
+                        // the im row (sn, cs) is the re row (cs, -sn) with its halves swapped and the
+                        // new low half negated: exact, as FP16 rounding is symmetric
+                        uint32_t hr, lr;
+                        split_e(cs, -sn, hr, lr);
+                        const float cz = cf.z * csig;
+                        const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn);
+                        w[0][t] = hr;
+                        w[1][t] = __byte_perm(hr, 0u, 0x1032u) ^ 0x8000u;
+                        w[2][t] = h1r;
+                        w[3][t] = __byte_perm(h1r, 0u, 0x1032u) ^ 0x8000u;
+                        w[4][t] = lr;
+                        w[5][t] = __byte_perm(lr, 0u, 0x1032u) ^ 0x8000u;
+                    }
+                    uint8_t *Bg = Bs + i * B_GROUP + (uint32_t)(xb >> 3) * kSBO + (uint32_t)(jl >> 1) * kLBO +
+                                  (uint32_t)(xb & 7) * 16 + (uint32_t)(jl & 1) * 8;
+                    // row blocks of 32 (4 kSBO): m = 0 re, m = 0 im, m = 1 re, m = 1 im, then the lo
+                    // parts of m = 0 re and im (rows 128 + x, 160 + x)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) *(uint2 *)(Bg + 4 * q * kSBO) = make_uint2(w[q][0], w[q][1]);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -427,8 +432,8 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 const float2 p0 = s_fft[(0 * SL + i) * FFT_P + j], p1 = s_fft[(1 * SL + i) * FFT_P + j];
                 const float2 p2 = s_fft[(2 * SL + i) * FFT_P + j], p3 = s_fft[(3 * SL + i) * FFT_P + j];
                 const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
-                atomicAdd(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
-                atomicAdd(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
+                red_add_f4(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
+                red_add_f4(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
             }
         }
     }

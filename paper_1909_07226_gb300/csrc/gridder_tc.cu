@@ -334,8 +334,8 @@ __device__ __forceinline__ void gridder_tcw_body(const Geometry &g, const DevSub
                 const float2 p0 = s_fft[(0 * TC_L + i) * FFT_P + j], p1 = s_fft[(1 * TC_L + i) * FFT_P + j];
                 const float2 p2 = s_fft[(2 * TC_L + i) * FFT_P + j], p3 = s_fft[(3 * TC_L + i) * FFT_P + j];
                 const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
-                atomicAdd(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
-                atomicAdd(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
+                red_add_f4(dst + 2 * gp, make_float4(sg * p0.x, sg * p0.y, sg * p1.x, sg * p1.y));
+                red_add_f4(dst + 2 * gp + 1, make_float4(sg * p2.x, sg * p2.y, sg * p3.x, sg * p3.y));
             }
         }
     }

@@ -124,6 +124,18 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
                  : "memory");
 }
 
+// arrive on bar and raise its expected transaction count by bytes
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+
+// bulk copy of bytes (16-B aligned addresses, a multiple of 16) from global to shared
+// memory, completing on bar's transaction count
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
 // FP16 pair (x in the low half, y in the high half), round to nearest
 __device__ __forceinline__ uint32_t pack_f16x2(float x, float y) {
     uint32_t r;
