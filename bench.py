@@ -47,8 +47,8 @@ ISSUE_PER_VISPIX_TC = 9
 # capture of the separable kernels (the default at L = 32 where the plan is
 # separable) on the LOFAR-like slice, one launch of all 3206 subgrids, 4.731e9
 # visibility-pixels (profiles/gridder_degridder_sep_fused_lofar_slice.md):
-# gridder 178.7 + 5.7 MB (visibilities and coordinates in; the atomically updated
-# grid lines are still dirty in L2 when the launch ends), degridder 31.1 + 93.5 MB
+# gridder 178.3 + 5.7 MB (visibilities and coordinates in; the atomically updated
+# grid lines are still dirty in L2 when the launch ends), degridder 31.0 + 93.4 MB
 # (grid lines and coordinates in, model visibilities out).  The traffic is
 # proportional to the work, so it scales to a full launch by the units processed.
 # Kernels without a capture of their current code report no traffic.
@@ -60,8 +60,8 @@ SEP_VARIANT = "tcgen05_separable_fused"
 SEP_GRID_FLOP_PER_GROUP = 2 * 128 * 16 * (192 + 64)
 SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (4 * 128)
 KERNEL_TRAFFIC = {
-    "gridder": {SEP_VARIANT: (178.7e6 + 5.7e6) / 4.731e9},
-    "degridder": {SEP_VARIANT: (31.1e6 + 93.5e6) / 4.731e9},
+    "gridder": {SEP_VARIANT: (178.3e6 + 5.7e6) / 4.731e9},
+    "degridder": {SEP_VARIANT: (31.0e6 + 93.4e6) / 4.731e9},
 }
 
 
