@@ -390,6 +390,35 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
  */
 idg_status idg_device_errors(idg_stream stream);
 
+/*
+ * Anti-aliasing windows (Sect. 4.1-4.3 and the appendix; host, FP64, no GPU).
+ *
+ * The taper passed to the gridding calls is c[y][x] = a_y a_x with a 1D window a
+ * of L samples; sample x sits at offset x - L/2 from the subgrid centre and the
+ * main lobe (the image) spans samples [0, L).
+ *
+ * idg_taper_window(L, beta, kind, a_out, eps_out) writes the window
+ * a_out[L] (host, may be NULL), normalised so that a_out[L/2] = 1, and its
+ * aliasing level *eps_out (may be NULL; not both):
+ *   IDG_TAPER_PSWF: a_x = psi_0(c = pi beta / 2, eta = 2 (x - L/2) / L), the zeroth
+ *     prolate spheroidal wave function (Sect. 4.1); *eps_out = sqrt(1 - lambda_0),
+ *     its side-lobe level as a classical-gridding window of support beta
+ *     (Table 1, "Classical PSWF").  In FP64, 1 - lambda_0 loses digits for
+ *     beta > 9 (eps < 1e-6).
+ *   IDG_TAPER_IDG_OPTIMAL: the window that minimises the mean side-lobe energy
+ *     of the effective window of image domain gridding over the allowed sample
+ *     positions |s| <= (L - beta + 1) / 2 (Sect. 4.3, Eq. a_opt): the eigenvector
+ *     of the smallest eigenvalue of Rbar = Qbar (Hadamard) Sbar (appendix);
+ *     *eps_out = the square root of that eigenvalue.
+ * idg_taper_aliasing(L, beta, a, eps_out) writes the side-lobe level of any
+ * window a[L] in image domain gridding: sqrt(a^T Rbar a / a^T a).
+ * Both fail with IDG_ERR_INVALID_ARG for odd L, L outside 2 .. 512, beta outside
+ * (0, L + 1), an unknown kind, or missing pointers.
+ */
+enum { IDG_TAPER_PSWF = 0, IDG_TAPER_IDG_OPTIMAL = 1 };
+idg_status idg_taper_window(int subgrid_size, double beta, int kind, double *a_out, double *eps_out);
+idg_status idg_taper_aliasing(int subgrid_size, double beta, const double *a, double *eps_out);
+
 /* Text of a status code, and the last error message of the calling thread. */
 const char *idg_status_string(idg_status status);
 const char *idg_last_error(void);

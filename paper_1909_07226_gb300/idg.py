@@ -35,7 +35,7 @@ EXPORTED = [
     "idg_profile_enable", "idg_profile_read", "idg_grid_no_alloc",
     "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
     "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
-    "idg_batch_destroy", "idg_device_errors",
+    "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
@@ -107,6 +107,8 @@ def load(path: str = LIB_PATH):
         "idg_batch_info": (I32, [P, P, P, P]),
         "idg_batch_destroy": (None, [P]),
         "idg_device_errors": (I32, [P]),
+        "idg_taper_window": (I32, [I32, D, I32, P, P]),
+        "idg_taper_aliasing": (I32, [I32, D, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -133,6 +135,32 @@ def supported_subgrid_sizes():
     buf = (ctypes.c_int32 * 16)()
     n = lib.idg_supported_subgrid_sizes(buf, 16)
     return [int(buf[i]) for i in range(min(n, 16))]
+
+
+TAPER_PSWF, TAPER_IDG_OPTIMAL = 0, 1
+
+
+def taper_window(subgrid_size: int, beta: float, kind: int = TAPER_IDG_OPTIMAL):
+    """1D anti-aliasing window a[L] (a[L/2] = 1) and its aliasing level eps
+    (idg_taper_window, host FP64): kind TAPER_PSWF is psi_0(pi beta / 2, .) with
+    eps = sqrt(1 - lambda_0) (Sect. 4.1); TAPER_IDG_OPTIMAL is the optimal window of
+    image domain gridding with eps = sqrt(smallest eigenvalue of Rbar) (Sect. 4.3)."""
+    a = np.zeros(subgrid_size, dtype=np.float64)
+    eps = ctypes.c_double(0.0)
+    _check(load().idg_taper_window(int(subgrid_size), float(beta), int(kind), a.ctypes.data, ctypes.byref(eps)),
+           "idg_taper_window")
+    return a, eps.value
+
+
+def taper_aliasing(subgrid_size: int, beta: float, a) -> float:
+    """Side-lobe level of window a[L] in image domain gridding (idg_taper_aliasing)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (subgrid_size,):
+        raise ValueError(f"a must have shape ({subgrid_size},)")
+    eps = ctypes.c_double(0.0)
+    _check(load().idg_taper_aliasing(int(subgrid_size), float(beta), a.ctypes.data, ctypes.byref(eps)),
+           "idg_taper_aliasing")
+    return eps.value
 
 
 def profile_enable(on: bool = True):

@@ -300,8 +300,15 @@ def test_tc_degridder_lofar_slice_sampled(tcd_selected):
 # (splitter, transform and degridder) when most of its visibilities lie in
 # subgrids of K_p >= 512.  The launch counters show which path ran.
 
+def _no_aterms(wl):
+    wl.aterms = None
+    return wl
+
+
 FUSED_CASES = {
     "long_kp": CASES["long_kp"],
+    # no A-terms: the separable degridder fetches none and waits for none
+    "long_kp_no_aterms": lambda: _no_aterms(CASES["long_kp"]()),
     # four w layers, K_p 96 .. 2048: fused degridder
     "long_kp_w_layers": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6, w_step=50.0),
     # two A-term slots and two w layers, K_p 8 .. 768: fused degridder, ragged groups
