@@ -478,6 +478,35 @@ def run_gb300(args, world, rank, local):
                               "4*2*128*16*(4*128) per tile of 64 (FP16 hi/lo split products included)")
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 
+    # image-side steps, outside the grid + degrid step: the whole grid to the image and
+    # back (idg_image_from_grid / idg_grid_from_image, PSWF window of the taper).  Each call
+    # reads and writes the N x N x 4 complex64 image twice (row pass, column pass) per w-layer.
+    image_steps = None
+    if wl.grid_size in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
+        win, _ = idg.taper_window(wl.subgrid_size, float(wl.kernel_size), idg.TAPER_PSWF)
+        img = torch.empty((wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
+        im_ms = {}
+        for name, fn in (("image_from_grid", lambda: idg.image_from_grid(plan, grid, win, img, stream)),
+                         ("grid_from_image", lambda: idg.grid_from_image(plan, img, win, grid, stream))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            im_ms[name] = e0.elapsed_time(e1) / 5
+        idg.device_errors(stream)
+        im_bytes = 4.0 * plan.n_w_layers * wl.grid_size ** 2 * 32
+        image_steps = {name: {"ms": ms, "achieved": im_bytes / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": im_bytes / (ms * 1e-3) / 1e9 / hbm_peak} for name, ms in im_ms.items()}
+        image_steps["bytes_per_call"] = im_bytes
+        image_steps["basis"] = ("4 x n_w x N^2 x 32 B per call (row and column pass, read and write), "
+                                f"against the {hbm_src} copy bandwidth")
+
     # end to end through the host-buffer C-ABI calls
     with near_gpu_memory(local) as placement:
         vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
@@ -530,7 +559,7 @@ def run_gb300(args, world, rank, local):
             "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                     "host_buffers_placed_from_cpus": placement.cpus},
-            "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu,
+            "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu, "image_steps": image_steps,
             "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
             "parallelism": "replicas" if world > 1 else "single GPU",
         }

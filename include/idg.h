@@ -419,6 +419,34 @@ enum { IDG_TAPER_PSWF = 0, IDG_TAPER_IDG_OPTIMAL = 1 };
 idg_status idg_taper_window(int subgrid_size, double beta, int kind, double *a_out, double *eps_out);
 idg_status idg_taper_aliasing(int subgrid_size, double beta, const double *a, double *eps_out);
 
+/*
+ * Image-side steps (Alg. 1 last line, Alg. 2 first lines; Sect. 3.5, 4.2), device
+ * buffers, stream-ordered on `stream`:
+ *
+ * idg_image_from_grid(plan, d_grid, h_window, d_image, stream):
+ *   d_image[y][x][pol] (complex64, N x N x 4, overwritten) =
+ *     sum_k exp(+2 pi i w0_k n'(x, y)) sum_{q,r} d_grid[k][r][q][pol]
+ *       exp(+2 pi i ((q - N/2)(x - N/2) + (r - N/2)(y - N/2)) / N) / (cbar(x) cbar(y)),
+ *   over the plan's w-layers k (w0_k = (k + w_layer_min) w_step, 0 without layers),
+ *   with l = (x - N/2) S / N, m = (y - N/2) S / N, n' = sqrt(1 - l^2 - m^2) - 1.
+ *   cbar is the effective window at zero shift of the 1D window h_window[L] (host,
+ *   the window of the taper c[y][x] = a_y a_x):
+ *     cbar(x) = L^-1 sum_j a_j sum_{m=-L/2}^{L/2-1} exp(2 pi i m ((x - N/2)/N - (j - L/2)/L)),
+ *   which makes a sample at a subgrid centre image to its exact fringe.  h_window
+ *   NULL: no division.
+ * idg_grid_from_image(plan, d_image, h_window, d_grid, stream): its adjoint,
+ *   d_grid[k] (overwritten) = the centred forward transform (sign -) of
+ *   d_image exp(-2 pi i w0_k n') / (conj cbar(x) conj cbar(y)).
+ * Both take a scratch image (32 N^2 bytes) from the stream-ordered pool, need N a
+ * power of two in 16 .. 4096 (IDG_ERR_UNSUPPORTED otherwise) and fail with
+ * IDG_ERR_INVALID_ARG for missing buffers, a window that is not finite or whose
+ * cbar vanishes on the image, or a plan of another device.
+ */
+idg_status idg_image_from_grid(const idg_plan *plan, const void *d_grid, const double *h_window, void *d_image,
+                               idg_stream stream);
+idg_status idg_grid_from_image(const idg_plan *plan, const void *d_image, const double *h_window, void *d_grid,
+                               idg_stream stream);
+
 /* Text of a status code, and the last error message of the calling thread. */
 const char *idg_status_string(idg_status status);
 const char *idg_last_error(void);

@@ -36,6 +36,7 @@ EXPORTED = [
     "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
     "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
+    "idg_image_from_grid", "idg_grid_from_image",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
         "idg_device_errors": (I32, [P]),
         "idg_taper_window": (I32, [I32, D, I32, P, P]),
         "idg_taper_aliasing": (I32, [I32, D, P, P]),
+        "idg_image_from_grid": (I32, [P, P, P, P, P]),
+        "idg_grid_from_image": (I32, [P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -161,6 +164,38 @@ def taper_aliasing(subgrid_size: int, beta: float, a) -> float:
     _check(load().idg_taper_aliasing(int(subgrid_size), float(beta), a.ctypes.data, ctypes.byref(eps)),
            "idg_taper_aliasing")
     return eps.value
+
+
+def _window_ptr(window, L):
+    if window is None:
+        return None, None
+    w = np.ascontiguousarray(window, dtype=np.float64)
+    if w.shape != (L,):
+        raise ValueError(f"the window must have shape ({L},)")
+    return w, w.ctypes.data
+
+
+def image_from_grid(plan: Plan, grid, window, image_out, stream=None):
+    """idg_image_from_grid: grid [n_w][N][N][4] -> image [N][N][4] (CUDA complex64 tensors);
+    window: the taper's 1D window a[L] (numpy, host) or None."""
+    import torch
+    sh = _shapes(plan)
+    N = plan.stats.grid_size
+    w, wp = _window_ptr(window, plan.stats.subgrid_size)
+    _check(load().idg_image_from_grid(plan.handle, _dptr(grid, "grid", torch.complex64, sh["grid"]), wp,
+                                      _dptr(image_out, "image", torch.complex64, (N, N, 4)), _stream(stream)),
+           "idg_image_from_grid")
+
+
+def grid_from_image(plan: Plan, image, window, grid_out, stream=None):
+    """idg_grid_from_image: image [N][N][4] -> grid [n_w][N][N][4], the adjoint."""
+    import torch
+    sh = _shapes(plan)
+    N = plan.stats.grid_size
+    w, wp = _window_ptr(window, plan.stats.subgrid_size)
+    _check(load().idg_grid_from_image(plan.handle, _dptr(image, "image", torch.complex64, (N, N, 4)), wp,
+                                      _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)),
+           "idg_grid_from_image")
 
 
 def profile_enable(on: bool = True):

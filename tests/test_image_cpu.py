@@ -1,0 +1,112 @@
+"""Image-side steps (Alg. 1 last line, Alg. 2 first lines): pins of the oracle
+(``oracle/image.py``), no GPU.
+
+- the centred transform is its definition (the double sum);
+- a subgrid built by the definition of the gridder's transform (L^-2 times the centred
+  DFT of the subgrid image of a sample at the subgrid centre, which is the taper, since
+  the subgrid phasors are relative to the centre) images to the sample's fringe times
+  cbar(x) cbar(y) exactly, on the whole image: this pins cbar's form, phase and
+  normalisation;
+- one grid pixel at the centre of a w-layer images to exp(+2 pi i w0 n') (closed form);
+- grid_from_image is the adjoint of image_from_grid;
+- the whole oracle chain (grid, then image) matches direct imaging of the same
+  visibilities within the aliasing level of the taper (Table 1: ~1e-4 at beta = 7) on
+  the inner image, with and without w-layers.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import image as OI
+from oracle import oracle as O
+from oracle import taper as OT
+from paper_1909_07226_gb300 import synthetic as syn
+
+C = 299792458.0
+
+
+def test_centred_transform_is_the_double_sum():
+    rng = np.random.default_rng(1)
+    N = 16
+    G = rng.standard_normal((N, N, 4)) + 1j * rng.standard_normal((N, N, 4))
+    x = np.arange(N) - N / 2
+    E = np.exp(2j * np.pi * np.outer(x, x) / N)
+    direct = np.einsum("yr,rqp,xq->yxp", E, G, E)
+    assert np.max(np.abs(OI.centred_idft2(G) - direct)) < 1e-12 * np.max(np.abs(direct))
+    back = np.einsum("yr,rqp,xq->yxp", np.conj(E), G, np.conj(E))
+    assert np.max(np.abs(OI.centred_dft2(G) - back)) < 1e-12 * np.max(np.abs(back))
+
+
+@pytest.mark.parametrize("L,N,q0,r0", [(8, 64, 20, 36), (16, 128, 40, 56), (32, 256, 96, 80)])
+def test_subgrid_centre_sample_images_to_its_fringe(L, N, q0, r0):
+    S = 0.05
+    a = OT.pswf_window(L, 7.0)
+    xs = np.arange(L) - L / 2
+    u0, v0 = (q0 + L / 2 - N / 2) / S, (r0 + L / 2 - N / 2) / S
+    # the subgrid phasors are relative to the subgrid centre: a sample there gives the taper
+    P = np.outer(a, a)
+    # the gridder's transform: L^-2 times the centred DFT of the subgrid image
+    E = np.exp(-2j * np.pi * np.outer(xs, xs) / L)
+    Vp = E @ P @ E.T / L ** 2
+    G = np.zeros((1, N, N, 4), dtype=np.complex128)
+    G[0, r0:r0 + L, q0:q0 + L, 0] = Vp
+    # compared before the division (cbar nearly vanishes at the edges of a beta = 7 PSWF)
+    img = OI.image_from_grid(G, S, [0.0], None, L)[:, :, 0]
+    l = (np.arange(N) - N / 2) * S / N
+    cb = OI.effective_window(a, L, N)
+    ref = np.exp(2j * np.pi * (u0 * l[None, :] + v0 * l[:, None])) * cb[None, :] * cb[:, None]
+    assert np.max(np.abs(img - ref)) < 1e-12
+    # and after it, on the inner image
+    inner = (np.abs(l)[None, :] < 0.3 * S) & (np.abs(l)[:, None] < 0.3 * S)
+    div = OI.image_from_grid(G, S, [0.0], a, L)[:, :, 0]
+    assert np.max(np.abs(div - ref / (cb[None, :] * cb[:, None]))[inner]) < 1e-10
+
+
+def test_w_layer_phase_of_a_centre_pixel():
+    N, S, w0 = 64, 0.2, 123.0
+    G = np.zeros((1, N, N, 4), dtype=np.complex128)
+    G[0, N // 2, N // 2, :] = [1.0, 2.0, -1.0, 0.5j]
+    img = OI.image_from_grid(G, S, [w0], None, 16)
+    l = (np.arange(N) - N / 2) * S / N
+    npr = np.sqrt(1 - l[None, :] ** 2 - l[:, None] ** 2) - 1
+    ref = np.exp(2j * np.pi * w0 * npr)[:, :, None] * G[0, N // 2, N // 2][None, None, :]
+    assert np.max(np.abs(img - ref)) < 1e-12
+
+
+def test_grid_from_image_is_the_adjoint():
+    rng = np.random.default_rng(2)
+    N, L, S = 32, 8, 0.3
+    w0s = [-40.0, 0.0, 40.0]
+    a = OT.pswf_window(L, 5.0)
+    G = rng.standard_normal((3, N, N, 4)) + 1j * rng.standard_normal((3, N, N, 4))
+    I = rng.standard_normal((N, N, 4)) + 1j * rng.standard_normal((N, N, 4))
+    lhs = np.vdot(OI.image_from_grid(G, S, w0s, a, L), I)
+    rhs = np.vdot(G, OI.grid_from_image(I, S, w0s, a, L))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("w_step", [0.0, 40.0])
+def test_oracle_chain_matches_direct_imaging(w_step):
+    L, beta = 32, 7.0
+    wl = syn.make_small(seed=5, n_st=5, n_t=24, n_chan=4, L=L, N=256, aterms="identity", max_t=8, flag_p=0.0,
+                        diameter_m=3000.0 if w_step == 0 else 20000.0, w_step=w_step, beta=beta)
+    a = OT.pswf_window(L, beta)
+    wl.taper = np.outer(a, a)
+    p = O.plan(wl)
+    N, S = wl.grid_size, wl.grid_size * wl.cell_size
+    w0s = [(k + p.k_min) * wl.w_step for k in range(p.n_w)] if wl.w_step > 0 else [0.0]
+    img = OI.image_from_grid(O.grid(wl, p), S, w0s, a, L)[:, :, 0]
+    lx = (np.arange(N) - N / 2) * S / N
+    npr = OI.nprime(N, S)
+    sc = wl.freqs_hz / C
+    D = np.zeros((N, N), complex)
+    for d in p.desc:
+        b = d[0]
+        for t in range(d[2], d[2] + d[3]):
+            for c in range(d[4], d[4] + d[5]):
+                u, v, w = wl.uvw_m[b, t] * sc[c]
+                D += wl.vis[b, t, c, 0] * np.exp(2j * np.pi * (u * lx[None, :] + v * lx[:, None] + w * npr))
+    inner = (np.abs(lx)[None, :] < 0.35 * S) & (np.abs(lx)[:, None] < 0.35 * S)
+    rel = np.sqrt(np.mean(np.abs(img - D)[inner] ** 2) / np.mean(np.abs(D[inner]) ** 2))
+    assert rel < 2e-4, rel
