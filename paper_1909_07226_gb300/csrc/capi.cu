@@ -58,7 +58,8 @@ static cudaMemPool_t scratch_pool(int device) {
     return pools[device];
 }
 
-static idg_status scratch_alloc(int device, size_t bytes, cudaStream_t s, void **p) {
+idg_status scratch_alloc(int device, size_t bytes, void *stream, void **p) {
+    cudaStream_t s = (cudaStream_t)stream;
     cudaMemPool_t pool = scratch_pool(device);
     if (!pool) return fail(IDG_ERR_CUDA, "cannot create the scratch memory pool");
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);

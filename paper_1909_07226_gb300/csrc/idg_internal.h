@@ -114,6 +114,10 @@ struct idg_plan {
 
 namespace idg {
 
+// device memory from the library's stream-ordered pool (kept across calls); free with
+// cudaFreeAsync on the same stream
+idg_status scratch_alloc(int device, size_t bytes, void *stream, void **p);
+
 // thread-local error text
 void set_error(const std::string &msg);
 idg_status fail(idg_status st, const std::string &msg);
