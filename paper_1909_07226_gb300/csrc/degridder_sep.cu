@@ -28,12 +28,13 @@
 //
 // Schedule.  One CTA per subgrid, one CTA per SM.  All warps first form the
 // image (split from the grid and inverse transform in shared memory when
-// FUSED), the corrections, the scale and B (shared memory, fixed for the
-// subgrid).  Then per tile: a coefficient warp stages the visibilities'
-// phase coefficients (FP64 offsets); eight producer warps write A (shared
+// FUSED, while two bulk copies bring the subgrid's A-terms), the corrections,
+// the scale and B (shared memory, fixed for the subgrid).  Then per tile: a
+// coefficient warp stages the visibilities' phase coefficients (float pairs,
+// error-free FP32 products and sums); eight producer warps write A (shared
 // memory, one core matrix per warp store); the consumers form the tile's Ey*
 // table while its MMAs run;
-// the MMA warp issues the 16 MMAs into one of two accumulators; eight consumer
+// the MMA warp issues the 16 MMAs into one of four accumulators; eight consumer
 // warps read their rows' columns, sum over y, pair the re and im rows of each
 // visibility through shared memory and write the visibilities.  The A stages
 // (two, freed by the MMAs) and the coefficient and accumulator stages (four,
@@ -62,7 +63,7 @@ constexpr int SPIX = SL * SL;
 constexpr int NPW = 8, NCW = 8;                 // producer and consumer warps
 constexpr int NP = NPW * 32, NC = NCW * 32;
 constexpr int MMA_WARP = NPW + NCW;
-constexpr int COEF_WARP = MMA_WARP + 1;        // stages the per-visibility coefficients (FP64 offsets)
+constexpr int COEF_WARP = MMA_WARP + 1;        // stages the per-visibility coefficients (float pairs)
 constexpr int NT = NP + NC + 64;
 constexpr int TV = 64;                          // visibilities per tile (rows 2 k + re/im)
 constexpr int AST = 2;                          // A stages (gated by the MMAs)

@@ -37,11 +37,16 @@
 // cover the round trip MMA -> producers -> MMA).
 //
 // Schedule.  One CTA per subgrid, one CTA per SM: sixteen producer warps and
-// one MMA warp.  A stage is four groups of 8 visibilities: per stage each
-// producer writes the 8 A entries of its row (q = warp % 4, y = lane) for
-// group warp / 4 into tensor memory (one 16-column store) and one B entry pair
-// (x, re/im, j) per group into shared memory (one core matrix per warp and
-// store, no bank conflicts), twelve independent phasor chains per thread.
+// one MMA warp.  A stage is four groups of 8 visibilities.  Per stage each
+// producer:
+//   - writes the 8 A entries of its row (polarisation lane / 8, pixel row
+//     8 (warp % 4) + lane % 8) for group warp / 4 into tensor memory, one
+//     16-column store.  It forms Ey for two of the visibilities and takes the
+//     others from the lanes of the same row by shuffles;
+//   - forms the B entries of pixel column 8 (warp % 4) + lane % 8 for the
+//     adjacent visibilities 2 (lane / 8) and 2 (lane / 8) + 1 of the same
+//     group, and writes them as one 8-byte store per row block (a warp's store
+//     covers 256 contiguous bytes, free of bank conflicts).
 // Visibilities are staged 512 at a time; the next batch is loaded into
 // registers while the current one is processed.
 // Tensor memory (512 columns):
