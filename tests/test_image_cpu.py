@@ -110,3 +110,33 @@ def test_oracle_chain_matches_direct_imaging(w_step):
     inner = (np.abs(lx)[None, :] < 0.35 * S) & (np.abs(lx)[:, None] < 0.35 * S)
     rel = np.sqrt(np.mean(np.abs(img - D)[inner] ** 2) / np.mean(np.abs(D[inner]) ** 2))
     assert rel < 2e-4, rel
+
+
+@pytest.mark.parametrize("L,seed", [(32, 5), (24, 5)])
+def test_optimal_window_lowers_the_image_error(L, seed):
+    # Sect. 4.3: the optimal window minimises the side-lobe energy averaged over the
+    # image and the sample positions.  Through the oracle chain (grid, image, divide by
+    # cbar) its error against direct imaging over 90 % of the image is below the PSWF's
+    # (by 20-27 % in these cases; near the centre the two are on a par).
+    beta = 7.0
+    wl = syn.make_small(seed=seed, n_st=6, n_t=32, n_chan=4, L=L, N=256, aterms="identity", max_t=8, flag_p=0.0,
+                        diameter_m=3000.0, beta=beta)
+    p = O.plan(wl)
+    N, S = wl.grid_size, wl.grid_size * wl.cell_size
+    lx = (np.arange(N) - N / 2) * S / N
+    npr = OI.nprime(N, S)
+    sc = wl.freqs_hz / C
+    D = np.zeros((N, N), complex)
+    for d in p.desc:
+        b = d[0]
+        for t in range(d[2], d[2] + d[3]):
+            for c in range(d[4], d[4] + d[5]):
+                u, v, w = wl.uvw_m[b, t] * sc[c]
+                D += wl.vis[b, t, c, 0] * np.exp(2j * np.pi * (u * lx[None, :] + v * lx[:, None] + w * npr))
+    region = (np.abs(lx)[None, :] < 0.45 * S) & (np.abs(lx)[:, None] < 0.45 * S)
+    err = {}
+    for name, a in (("pswf", OT.pswf_window(L, beta)), ("optimal", OT.optimal_window(L, beta)[0])):
+        wl.taper = np.outer(a, a)
+        img = OI.image_from_grid(O.grid(wl, p), S, [0.0], a, L)[:, :, 0]
+        err[name] = np.sqrt(np.mean(np.abs(img - D)[region] ** 2) / np.mean(np.abs(D[region]) ** 2))
+    assert err["optimal"] < 0.95 * err["pswf"], err
