@@ -81,6 +81,26 @@ def pswf_window(L: int, beta: float, n: int = 200) -> np.ndarray:
     return psi / psi[L // 2]
 
 
+def pswf_eval(beta: float, eta, n: int = 200) -> np.ndarray:
+    """psi_0(c = pi beta / 2, eta) at arbitrary eta in [-1, 1], normalised psi_0(0) = 1
+    (the Nystrom eigenvector, interpolated with the integral equation)."""
+    c = np.pi * beta / 2.0
+    t, w = np.polynomial.legendre.leggauss(n)
+    d = t[:, None] - t[None, :]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        K = np.where(d == 0.0, c / np.pi, np.sin(c * d) / (np.pi * d))
+    sw = np.sqrt(w)
+    lam, U = np.linalg.eigh(sw[:, None] * K * sw[None, :])
+    psi_nodes = U[:, -1] / sw
+    def interp(e):
+        e = np.atleast_1d(np.asarray(e, dtype=np.float64))
+        de = e[:, None] - t[None, :]
+        with np.errstate(invalid="ignore", divide="ignore"):
+            Ke = np.where(de == 0.0, c / np.pi, np.sin(c * de) / (np.pi * de))
+        return (Ke * w[None, :]) @ psi_nodes / lam[-1]
+    return interp(eta) / interp(0.0)[0]
+
+
 # ---------------------------------------------------------------------------
 # Sect. 4.2-4.3 and the appendix: the optimal window of image domain gridding
 

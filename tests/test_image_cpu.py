@@ -140,3 +140,55 @@ def test_optimal_window_lowers_the_image_error(L, seed):
         img = OI.image_from_grid(O.grid(wl, p), S, [0.0], a, L)[:, :, 0]
         err[name] = np.sqrt(np.mean(np.abs(img - D)[region] ** 2) / np.mean(np.abs(D[region]) ** 2))
     assert err["optimal"] < 0.95 * err["pswf"], err
+
+
+def test_classical_gridding_reaches_the_same_aliasing_level():
+    # Sect. 4 (Table 1): classical gridding with the PSWF kernel of support beta and image
+    # domain gridding with a taper of the same beta reach comparable accuracy.  Classical
+    # gridding here is the textbook form, for the comparison only: each visibility is
+    # spread over the grid pixels within beta / 2 of it with psi_0(c, 2 Delta / beta)
+    # evaluated exactly, the grid is transformed, and the image is divided by the kernel's
+    # continuous transform.  No w term (w is zeroed on both sides).
+    L, beta, N = 32, 7.0, 256
+    wl = syn.make_small(seed=5, n_st=6, n_t=32, n_chan=4, L=L, N=N, aterms="identity", max_t=8, flag_p=0.0,
+                        diameter_m=3000.0, beta=beta)
+    wl.uvw_m = wl.uvw_m.copy()
+    wl.uvw_m[..., 2] = 0.0
+    a = OT.pswf_window(L, beta)
+    wl.taper = np.outer(a, a)
+    p = O.plan(wl)
+    S = N * wl.cell_size
+    sc = wl.freqs_hz / C
+    lx = (np.arange(N) - N / 2) * S / N
+    half = beta / 2
+    us, vs, Vs = [], [], []
+    for d in p.desc:
+        for t in range(d[2], d[2] + d[3]):
+            for c in range(d[4], d[4] + d[5]):
+                u, v, _ = wl.uvw_m[d[0], t] * sc[c]
+                us.append(u); vs.append(v); Vs.append(wl.vis[d[0], t, c, 0])
+    us, vs, Vs = np.array(us), np.array(vs), np.array(Vs)
+    D = (Vs[:, None, None] * np.exp(2j * np.pi * (us[:, None, None] * lx[None, None, :] +
+                                                  vs[:, None, None] * lx[None, :, None]))).sum(axis=0)
+    pu, pv = us * S + N / 2, vs * S + N / 2
+    m = int(np.ceil(beta)) + 1
+    q = np.floor(pu - half).astype(int)[:, None] + np.arange(1, m + 1)[None, :]
+    r = np.floor(pv - half).astype(int)[:, None] + np.arange(1, m + 1)[None, :]
+    dq, dr = q - pu[:, None], r - pv[:, None]
+    ok_q, ok_r = np.abs(dq) <= half, np.abs(dr) <= half
+    psi = OT.pswf_eval(beta, np.clip(2 * np.concatenate([dq.ravel(), dr.ravel()]) / beta, -1, 1))
+    Cq = np.where(ok_q, psi[:dq.size].reshape(dq.shape), 0.0)
+    Cr = np.where(ok_r, psi[dq.size:].reshape(dr.shape), 0.0)
+    G = np.zeros((N, N), complex)
+    for k in range(Vs.size):
+        G[np.ix_(r[k], q[k])] += Vs[k] * np.outer(Cr[k], Cq[k])
+    tg, wg = np.polynomial.legendre.leggauss(120)
+    W = (np.exp(2j * np.pi * np.outer((np.arange(N) - N / 2) / N, tg * half)) *
+         (wg * half * OT.pswf_eval(beta, tg))[None, :]).sum(axis=1)
+    classical = OI.centred_idft2(G[:, :, None])[:, :, 0] / np.outer(W, W)
+    idg_img = OI.image_from_grid(O.grid(wl, p), S, [0.0], a, L)[:, :, 0]
+    inner = (np.abs(lx)[None, :] < 0.35 * S) & (np.abs(lx)[:, None] < 0.35 * S)
+    rel = lambda img: np.sqrt(np.mean(np.abs(img - D)[inner] ** 2) / np.mean(np.abs(D[inner]) ** 2))
+    e_cl, e_idg = rel(classical), rel(idg_img)
+    assert e_cl < 3e-4 and e_idg < 3e-4, (e_cl, e_idg)
+    assert 0.25 < e_idg / e_cl < 4.0, (e_cl, e_idg)
