@@ -567,7 +567,7 @@ def run_gb300(args, world, rank, local):
 
 
 def run_batched(args, world, rank, local):
-    """The uneven batch (SURVEY config B): the same jobs gridded and degridded
+    """The uneven batch (config B): the same jobs gridded and degridded
     (a) one after another with idg_grid / idg_degrid (plain per-job form) and
     (b) as one batch: one persistent launch per subgrid size, subgrids kept in
     shared memory, the launch sequence replayed from a CUDA graph."""
@@ -649,7 +649,7 @@ def run_batched(args, world, rank, local):
 
 
 def run_serving(args, world, rank, local):
-    """Serving (SURVEY config S): a Poisson stream of requests drawn from the
+    """Serving (config S): a Poisson stream of requests drawn from the
     batched distribution ("cycle": 5 major cycles of degrid -> residual -> grid,
     "grid", "degrid"), served by the continuous-batching engine, and the same
     trace served one job at a time by the plain per-job form."""
@@ -694,7 +694,7 @@ def run_serving(args, world, rank, local):
 
 
 def run_precision(args, world, rank, local):
-    """Precision forms (SURVEY config P): the LOFAR-like workload with A-terms
+    """Precision forms (config P): the LOFAR-like workload with A-terms
     refreshed every 16 timesteps.  For every form: grid+degrid MVis/s on the
     full workload, and the error against the FP64 oracle of the full grid and of
     all visibilities on the first 256 timesteps (which the oracle redoes)."""
