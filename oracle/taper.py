@@ -7,7 +7,9 @@ methods other than the library's, so that the two check each other:
 
 - lambda_0 of the PSWF comes from a Nystrom discretisation of the time-frequency
   limiting operator (sin c(x - t)) / (pi (x - t)) on [-1, 1] with Gauss-Legendre nodes,
-  not from a Legendre expansion;
+  not from a Legendre expansion.  This holds for beta <= 12: beyond it the operator's
+  top eigenvalues are all 1 to FP64 precision, the eigenvector is no longer psi_0, and
+  the PSWF functions here refuse such beta;
 - Qbar comes from the orthonormality of shifted sincs (the integral of
   sinc(x - k) sinc(x - l) over the whole line is delta_kl), as delta_kl minus the
   main-lobe integral over [0, L) by Gauss-Legendre quadrature, not from the cosine
@@ -44,10 +46,18 @@ def _gauss_pieces(lo: float, hi: float, n_per_unit: int = 24):
 # ---------------------------------------------------------------------------
 # Sect. 4.1: the PSWF
 
+_PSWF_BETA_MAX = 12.0
+
+
+def _check_beta(beta: float):
+    if not beta <= _PSWF_BETA_MAX:
+        raise ValueError(f"the Nystrom PSWF is reliable for beta <= {_PSWF_BETA_MAX}, got {beta}")
+
 
 def pswf_lambda0(beta: float, n: int = 200) -> float:
     """First eigenvalue lambda_0(c), c = pi beta / 2, of the operator
     (K psi)(x) = int_{-1}^{1} sin(c (x - t)) / (pi (x - t)) psi(t) dt (Nystrom)."""
+    _check_beta(beta)
     c = np.pi * beta / 2.0
     x, w = np.polynomial.legendre.leggauss(n)
     d = x[:, None] - x[None, :]
@@ -65,6 +75,7 @@ def pswf_eps(beta: float) -> float:
 def pswf_window(L: int, beta: float, n: int = 200) -> np.ndarray:
     """psi_0(c, eta) at eta = 2 (x - L/2) / L, x = 0 .. L-1, normalised at x = L/2: the
     Nystrom eigenvector, interpolated with the integral equation itself."""
+    _check_beta(beta)
     c = np.pi * beta / 2.0
     t, w = np.polynomial.legendre.leggauss(n)
     d = t[:, None] - t[None, :]
@@ -84,6 +95,7 @@ def pswf_window(L: int, beta: float, n: int = 200) -> np.ndarray:
 def pswf_eval(beta: float, eta, n: int = 200) -> np.ndarray:
     """psi_0(c = pi beta / 2, eta) at arbitrary eta in [-1, 1], normalised psi_0(0) = 1
     (the Nystrom eigenvector, interpolated with the integral equation)."""
+    _check_beta(beta)
     c = np.pi * beta / 2.0
     t, w = np.polynomial.legendre.leggauss(n)
     d = t[:, None] - t[None, :]

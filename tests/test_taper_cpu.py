@@ -143,3 +143,14 @@ def test_library_rejects_bad_arguments(lib):
             idg.taper_window(L, beta, kind)
     with pytest.raises(idg.IDGError):
         idg.taper_aliasing(16, 5.0, np.zeros(16))
+
+
+def test_library_pswf_beyond_the_oracle_range(lib):
+    # beyond beta ~ 12 the Nystrom oracle cannot separate psi_0 (it refuses); the library's
+    # Legendre expansion stays consistent: the window decays monotonically from the centre
+    # and its classical level 1 - lambda_0 is below FP64 resolution
+    with pytest.raises(ValueError):
+        OT.pswf_window(64, 15.0)
+    a, eps = idg.taper_window(64, 15.0, idg.TAPER_PSWF)
+    assert a[32] == 1.0 and np.all(np.diff(a[:33]) > 0) and np.all(np.diff(a[32:]) < 0)
+    assert 0.0 <= eps < 1e-7
