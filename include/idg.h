@@ -409,7 +409,9 @@ idg_status idg_device_errors(idg_stream stream);
  *     of the effective window of image domain gridding over the allowed sample
  *     positions |s| <= (L - beta + 1) / 2 (Sect. 4.3, Eq. a_opt): the eigenvector
  *     of the smallest eigenvalue of Rbar = Qbar (Hadamard) Sbar (appendix);
- *     *eps_out = the square root of that eigenvalue.
+ *     *eps_out = the square root of that eigenvalue.  Where that eigenvalue is
+ *     below 1e-14 of the largest (eps below about 1e-7, beta >~ 12) the window
+ *     is not determined in FP64: IDG_ERR_UNSUPPORTED.
  * idg_taper_aliasing(L, beta, a, eps_out) writes the side-lobe level of any
  * window a[L] in image domain gridding: sqrt(a^T Rbar a / a^T a).
  * Both fail with IDG_ERR_INVALID_ARG for odd L, L outside 2 .. 512, beta outside

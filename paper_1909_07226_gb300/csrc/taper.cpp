@@ -242,8 +242,15 @@ idg_status idg_taper_window(int L, double beta, int kind, double *a_out, double 
         std::vector<double> R = rbar(L, beta), w, V;
         jacobi_eigh(L, R, w, V);
         int imin = 0;
-        for (int i = 1; i < L; ++i)
+        double wmax = 0.0;
+        for (int i = 0; i < L; ++i) {
             if (w[i] < w[imin]) imin = i;
+            wmax = std::fmax(wmax, std::fabs(w[i]));
+        }
+        // below this the smallest eigenvalue, and so the window, is not determined in FP64
+        // (eps below about 1e-7 of the largest eigenvalue's square root; beta >~ 12)
+        if (!(w[imin] >= 1e-14 * wmax))
+            return fail(IDG_ERR_UNSUPPORTED, "the optimal window is below FP64 resolution for this beta (eps < ~1e-7)");
         if (a_out) {
             const double centre = V[(size_t)(L / 2) * L + imin];
             if (centre == 0.0) return fail(IDG_ERR_INVALID_ARG, "degenerate window (zero at the centre)");

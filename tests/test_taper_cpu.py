@@ -143,6 +143,11 @@ def test_library_rejects_bad_arguments(lib):
             idg.taper_window(L, beta, kind)
     with pytest.raises(idg.IDGError):
         idg.taper_aliasing(16, 5.0, np.zeros(16))
+    # beyond FP64 resolution the optimal window is refused, not returned arbitrary
+    with pytest.raises(idg.IDGError):
+        idg.taper_window(128, 15.0, idg.TAPER_IDG_OPTIMAL)
+    for L in (16, 24, 32, 48, 64):          # beta = 11 (Table 1's last FP64 row) is still served
+        idg.taper_window(L, 11.0, idg.TAPER_IDG_OPTIMAL)
 
 
 def test_library_pswf_beyond_the_oracle_range(lib):
