@@ -439,8 +439,8 @@ idg_status idg_taper_aliasing(int subgrid_size, double beta, const double *a, do
  * idg_grid_from_image(plan, d_image, h_window, d_grid, stream): its adjoint,
  *   d_grid[k] (overwritten) = the centred forward transform (sign -) of
  *   d_image exp(-2 pi i w0_k n') / (conj cbar(x) conj cbar(y)).
- * Both take a scratch image (32 N^2 bytes) from the stream-ordered pool, need N a
- * power of two in 16 .. 4096 (IDG_ERR_UNSUPPORTED otherwise) and fail with
+ * Both take two scratch images (32 N^2 bytes each) from the stream-ordered pool, need N
+ * a power of two in 32 .. 4096 (IDG_ERR_UNSUPPORTED otherwise) and fail with
  * IDG_ERR_INVALID_ARG for missing buffers, a window that is not finite or whose
  * cbar vanishes on the image, or a plan of another device.
  */

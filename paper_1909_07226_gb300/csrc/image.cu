@@ -25,7 +25,7 @@
 // shared memory (2 N complex values and N / 2 twiddles, about 80 KB at N = 4096, two CTAs
 // per SM): bit-reversed loads into a padded layout (one slot per 128, free of bank
 // conflicts), then log2 N radix-2 stages.  The input factor is applied on the first
-// row pass.  N is a power of two, 16 .. 4096.
+// row pass.  N is a power of two, 32 .. 4096.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,7 +43,7 @@ constexpr int kLines = 2;                 // polarisations per CTA of a row tran
 constexpr int kTile = 32;                 // transpose tile (pixels)
 constexpr int kPer = 4096 / kImgThreads;  // line elements per thread at the largest N
 
-// pointwise factor of pixel (x, y) before (row pass) or after (column pass) a transform
+// pointwise factor of pixel (x, y): on the way into the first row pass, or in the final transpose
 struct PixOp {
     int mode;            // 0: (-1)^(x+y) only (uv side); 1: the image-side factor; 2: none
     int accumulate;      // column pass: add into the output instead of overwriting
@@ -213,7 +213,7 @@ cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, float4 *s2, i
 // With t = xi_x - xi_j, e^{i pi t} = e^{i pi xi_x} e^{-i pi xi_j} and sin(pi L t) =
 // (-1)^(j - L/2) sin(pi L xi_x), so only N + L exponentials are evaluated.  |t| < 2, so t
 // is an integer only for N L t = -N L, 0 or N L (checked in integers); there the limit
-// D = L (-1)^(t (L - 1)) e^{i pi t} is taken.
+// D = L (-1)^(t (L - 1)) e^{-i pi t} is taken.
 std::vector<float> effective_window_eval(const double *a, int L, int N) {
     std::vector<float> cb(2 * (size_t)N);
     const double pi = 3.14159265358979323846;
