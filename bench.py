@@ -59,6 +59,13 @@ SEP_VARIANT = "tcgen05_separable_fused"
 # degridder 4 K steps of 4 x N = 128 per tile of 64 visibilities.
 SEP_GRID_FLOP_PER_GROUP = 2 * 128 * 16 * (192 + 64)
 SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (4 * 128)
+# Half of those products are the FP16 hi/lo split that keeps FP32 accuracy: the
+# gridder's N = 256 columns are A_hi x [B_hi (128) | B0_lo (64)] and A_lo x B0_hi (64);
+# the degridder's four N = 128 products per K step are hi x hi of the m = 0 and the
+# first-order w term plus the two lo corrections of the m = 0 term.  The method's own
+# contraction (hi x hi) is the other half.
+SEP_USEFUL_SHARE = 0.5
+DTYPE_SEP = "f32 (fp16 hi/lo split tensor-core products, fp32 accumulate)"
 KERNEL_TRAFFIC = {
     "gridder": {SEP_VARIANT: (178.3e6 + 5.7e6) / 4.731e9},
     "degridder": {SEP_VARIANT: (31.0e6 + 93.4e6) / 4.731e9},
@@ -440,7 +447,7 @@ def run_gb300(args, world, rank, local):
                "share": d["ms"] / ms_total if ms_total > 0 else None}
         if k in ("gridder", "degridder"):
             ach = d["work"] / (d["ms"] * 1e-3) / 1e9
-            var = idg.kernel_variants(k, wl.subgrid_size)[idg.get_kernel_variant(k, wl.subgrid_size)]
+            var = idg.kernel_variants(k, wl.subgrid_size)[idg.plan_get_kernel_variant(plan, k)]
             # a step without adder (splitter) launches ran a fused tensor-core kernel: the separable
             # one where the plan allows it, else the direct one (transform and adder in the same CTA)
             if prof["adder" if k == "gridder" else "splitter"]["launches"] == 0:
@@ -449,6 +456,9 @@ def run_gb300(args, world, rank, local):
                 tfl = sep_flop[k] * args.steps / (d["ms"] * 1e-3) / 1e12
                 ent.update(bound="tensor", achieved=tfl, peak=bf16_peak, unit="TFLOP/s", frac=tfl / bf16_peak,
                            variant=var, peak_basis=f"dense bf16 tensor rate ({bf16_src}); FP16 runs at the same rate",
+                           useful_frac=SEP_USEFUL_SHARE * tfl / bf16_peak,
+                           useful_basis="hi x hi products only (the method's contraction); the rest is the FP16 "
+                                        "hi/lo split for FP32 accuracy",
                            achieved_vispix=ach, vispix_unit="Gvispix/s", frac_of_fp32_fma_peak=ach / alu_peak)
             else:
                 tc = var.startswith("tcgen05")
@@ -472,6 +482,9 @@ def run_gb300(args, world, rank, local):
             if traffic is not None else None,
             "peak_basis": kernels[dom]["peak_basis"], "frac_of_fp32_fma_peak": kernels[dom]["frac_of_fp32_fma_peak"],
             "hbm_peak_basis": hbm_src}
+    if "useful_frac" in kernels[dom]:
+        roof["useful_frac"] = kernels[dom]["useful_frac"]
+        roof["useful_basis"] = kernels[dom]["useful_basis"]
     if "achieved_vispix" in kernels[dom]:
         roof["achieved_vispix"] = kernels[dom]["achieved_vispix"]
         roof["flop_basis"] = ("MMA FLOP issued: gridder 2*128*16*(192+64) per group of 8 visibilities, degridder "
@@ -553,7 +566,8 @@ def run_gb300(args, world, rank, local):
         rec = {
             "metric": "grid+degrid MVis/s", "value": value, "unit": "MVis/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_SEP if plan.stats.separable else "f32",
             "data": "synthetic", "config": workload_config(wl, args.config),
             "roofline": roof, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),

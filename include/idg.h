@@ -37,10 +37,13 @@
  *
  * Ownership: the caller owns every data buffer; device pointers are plain CUDA
  * device (or managed) addresses, host pointers plain host memory.  A plan owns
- * its own host and device metadata and is immutable after creation; it may be
- * used from several host threads and streams at once.  Device calls are
- * asynchronous and stream-ordered on the stream given (NULL = legacy default
- * stream); a call returns after enqueueing.  Host-buffer variants synchronise.
+ * its own host and device metadata and is immutable after creation, except for
+ * its kernel choice (idg_plan_set_kernel_variant, idg_autotune), which each call
+ * reads once when it starts; it may be used from several host threads and
+ * streams at once, and one plan's kernel choice does not affect another plan.
+ * Device calls are asynchronous and stream-ordered on the stream given (NULL =
+ * legacy default stream); a call returns after enqueueing.  Host-buffer
+ * variants synchronise.
  *
  * Errors: every entry point returns an idg_status; nothing crosses the ABI as
  * an exception.  idg_last_error() returns a thread-local description of the
@@ -174,7 +177,10 @@ void idg_plan_destroy(idg_plan *plan);
  * d_vis     device complex64 [n_bl][n_t][n_chan][4]
  * d_flags   device uint8 [n_bl][n_t][n_chan], nonzero = flagged (weight 0), or NULL
  * d_aterms  device complex64 [n_slots][n_stations][L][L][4], or NULL = identity
- * d_taper   device float32 [L][L] (required)
+ * d_taper   device float32 [L][L], or NULL for the plan's default taper
+ *           c[y][x] = a_y a_x, a the PSWF window of the plan's kernel_size as
+ *           idg_taper_window(L, kernel_size, IDG_TAPER_PSWF) gives it (Sect. 4.1),
+ *           rounded to float32 and kept on the plan's device
  * d_grid    device complex64 [n_w][N][N][4]; the result is ADDED (Alg. 1 starts
  *           from V = 0: zero it first), so several plans may sum into one grid.
  * Summation order on the grid is not fixed (atomic adds): results agree with
@@ -205,6 +211,29 @@ idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d
                       idg_stream stream);
 
 /*
+ * The composite operations restricted to the plan's subgrids [first, first +
+ * count) in plan order (0 <= first, first + count <= n_subgrids; count 0 does
+ * nothing).  They run the kernels idg_grid / idg_degrid would choose for these
+ * subgrids (fused where those are fused).  This is the unit of a partition of
+ * the subgrids over several devices or processes (Sect. 3.2: subgrids are
+ * independent, only their sum into the grid couples them): every part grids
+ * its range into a grid of its own and the parts' grids are summed; for
+ * degridding the ranges' visibilities are disjoint.
+ * idg_grid_range   ADDS the range's subgrids into d_grid (as idg_grid).
+ * idg_degrid_range writes the visibilities of the range's subgrids (flagged
+ *                  ones as 0) and leaves every other element of d_vis_out as
+ *                  it was (dropped visibilities included).
+ * Arguments otherwise as for idg_grid / idg_degrid; IDG_ERR_INVALID_ARG for a
+ * range outside the plan.
+ */
+idg_status idg_grid_range(const idg_plan *plan, int64_t first, int64_t count, const void *d_vis,
+                          const uint8_t *d_flags, const void *d_aterms, const float *d_taper, void *d_grid,
+                          idg_stream stream);
+idg_status idg_degrid_range(const idg_plan *plan, int64_t first, int64_t count, const void *d_grid,
+                            const uint8_t *d_flags, const void *d_aterms, const float *d_taper, void *d_vis_out,
+                            idg_stream stream);
+
+/*
  * The same two operations on HOST buffers (layouts as above): inputs are copied
  * to device memory taken from the library's stream-ordered pool, the operation
  * runs on `stream`, the result is copied back and the call returns when it is
@@ -215,7 +244,8 @@ idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d
  * out behind), ordered by events.  Page-locked host memory gives the full copy
  * bandwidth and the overlap; pageable memory works with staged copies.
  * h_grid is OVERWRITTEN with the grid of these visibilities (the device grid
- * starts from zero); h_vis_out is overwritten as in idg_degrid.  Host buffers
+ * starts from zero); h_vis_out is overwritten as in idg_degrid.  h_taper NULL
+ * selects the plan's default taper (as d_taper NULL in idg_grid).  Host buffers
  * must not be touched by the caller until the call returns.
  */
 idg_status idg_grid_host(const idg_plan *plan, const void *h_vis, const uint8_t *h_flags,
@@ -239,8 +269,17 @@ idg_status idg_degrid_host(const idg_plan *plan, const void *h_grid, const uint8
  *     larger plan is rejected with IDG_ERR_INVALID_ARG and a message giving
  *     the need and the limit, before any work is enqueued.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture on the device.
+ *     (cudaGetSymbolAddress, with that device current) and caches it.  Under
+ *     CUDA's lazy module loading that lookup also loads the array (64 MiB)
+ *     onto the device, so the first call may fail for lack of memory or
+ *     synchronise the device: make it before reserving the rest of the
+ *     device's memory and before any stream capture on the device.  A call
+ *     with a plan of no subgrids does only the lookup and serves as the
+ *     warm-up.  The cached address stays valid while the device's context
+ *     lives: calls after cudaDeviceReset are not supported.
+ *   - Only the plain atomic adder runs here.  A plan created with
+ *     IDG_ADDER_COMPENSATED needs a grid-sized compensation buffer and is
+ *     refused with IDG_ERR_UNSUPPORTED before any work is enqueued.
  *   - All calls on one device share the array.  Calls whose work overlaps on
  *     the GPU (different streams without ordering between them) race on it:
  *     order them on one stream or with events.  The array keeps the last
@@ -303,7 +342,8 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  * idg_job_buffers per job (device pointers, layouts as above):
  *   vis      gridding input (may be NULL for a degrid-only batch)
  *   vis_out  degridding output (may be NULL for a grid-only batch)
- *   flags    or NULL;  aterms  or NULL (identity);  taper (required)
+ *   flags    or NULL;  aterms  or NULL (identity);  taper  or NULL (the plan's
+ *            default taper, as in idg_grid)
  *   grid     gridding output (accumulated) / degridding input
  * idg_batch_info returns the planned visibilities, work items and launches per
  * direction (1 per class).
@@ -360,7 +400,8 @@ idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int res
  *                              d_vis_scratch is given) the degridder on a
  *                              strided sample of at most max_subgrids (<= 0:
  *                              4096) of the plan's subgrids, on `stream`, and
- *                              selects the fastest for the plan's L.  Mean
+ *                              selects the fastest for this plan (its own
+ *                              kernel choice; other plans keep theirs).  Mean
  *                              milliseconds per launch of variant v go to
  *                              gridder_ms[v] / degridder_ms[v] for v < cap
  *                              (arrays may be NULL).  d_vis_scratch is a
@@ -373,6 +414,14 @@ int idg_kernel_variant_count(int kernel, int subgrid_size);
 const char *idg_kernel_variant_name(int kernel, int subgrid_size, int variant);
 idg_status idg_set_kernel_variant(int kernel, int subgrid_size, int variant);
 int idg_get_kernel_variant(int kernel, int subgrid_size);
+/* The kernel choice of one plan (IDG_KERNEL_GRIDDER or IDG_KERNEL_DEGRIDDER):
+ * variant -1 (the default of a new plan) follows the process-wide choice for the
+ * plan's L; 0 .. count-1 fixes the plan's own.  Calls made with the plan read
+ * it once when they start.  idg_autotune stores its pick in the plan, not
+ * process-wide.  idg_plan_get_kernel_variant returns the variant the plan's
+ * calls use (-1 for a NULL plan or an unknown kernel). */
+idg_status idg_plan_set_kernel_variant(idg_plan *plan, int kernel, int variant);
+int idg_plan_get_kernel_variant(const idg_plan *plan, int kernel);
 idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags, const void *d_aterms,
                         const float *d_taper, void *d_vis_scratch, int64_t max_subgrids, double *gridder_ms,
                         double *degridder_ms, int cap, idg_stream stream);
@@ -389,6 +438,18 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
  * The words are per device and per process.
  */
 idg_status idg_device_errors(idg_stream stream);
+
+/*
+ * Self-test of that failure path (no counterpart in the paper): enqueues on
+ * `stream` one CTA that allocates tensor memory as the tensor-core kernels do,
+ * waits on a shared-memory barrier that nothing arrives on, with a limit of
+ * max_polls polls (1 .. 2^20, a few milliseconds at most), records the timeout
+ * in its device error word and releases the tensor memory.  The next
+ * idg_device_errors then returns IDG_ERR_TIMEOUT (and clears the word); the
+ * device stays usable.  No matrix operation or copy is involved.
+ * IDG_ERR_INVALID_ARG for max_polls out of range.
+ */
+idg_status idg_selftest_wait_timeout(int64_t max_polls, idg_stream stream);
 
 /*
  * Anti-aliasing windows (Sect. 4.1-4.3 and the appendix; host, FP64, no GPU).

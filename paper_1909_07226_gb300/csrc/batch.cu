@@ -480,7 +480,8 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         KernelShape a, c;
         if (!shapes_for(p->L, &a, &c))
             return fail(IDG_ERR_UNSUPPORTED, "batches support subgrid sizes 8, 16, 24 and 32 (job " + std::to_string(j) + ")");
-        if (!bufs[j].taper) return fail(IDG_ERR_INVALID_ARG, "job " + std::to_string(j) + " has no taper");
+        if (!p->taper_or_default(bufs[j].taper))
+            return fail(IDG_ERR_INVALID_ARG, "job " + std::to_string(j) + " has no taper and its plan no default");
     }
     idg_batch *b = new idg_batch();
     b->device = dev;
@@ -498,7 +499,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         J.vis_out = (float4 *)bufs[j].vis_out;
         J.flags = bufs[j].flags;
         J.aterms = (const float4 *)bufs[j].aterms;
-        J.taper = bufs[j].taper;
+        J.taper = p->taper_or_default(bufs[j].taper);
         J.grid = (float4 *)bufs[j].grid;
         b->n_vis += p->stats.n_vis_planned;
         if (p->any_dropped && bufs[j].vis_out)

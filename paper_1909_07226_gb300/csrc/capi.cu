@@ -191,6 +191,12 @@ idg::Geometry idg_plan::geometry() const {
     return g;
 }
 
+int idg_plan::kernel_variant(int kernel) const {
+    if (kernel < 0 || kernel >= IDG_KERNEL_COUNT) return 0;
+    const int v = variant[kernel].load(std::memory_order_relaxed);
+    return v >= 0 ? v : idg::get_variant(kernel, L);
+}
+
 extern "C" {
 
 void idg_plan_options_default(idg_plan_options *o) {
@@ -292,6 +298,7 @@ void idg_plan_destroy(idg_plan *p) {
     cudaFree(p->d_uvw_f2);
     cudaFree(p->d_scale_f2);
     cudaFree(p->d_nprime);
+    cudaFree(p->d_taper);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
 }
@@ -543,6 +550,20 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         nprime[(size_t)L * L + L + i] = (float)n1(L / 2, i);
     }
 
+    // the default taper (calls with a NULL taper): c[y][x] = a_y a_x with a the PSWF
+    // window of the plan's beta (Sect. 4.1), as idg_taper_window gives it
+    std::vector<float> taper_def;
+    {
+        std::vector<double> a((size_t)L);
+        const std::string saved = g_last_error;
+        if (idg_taper_window(L, o.kernel_size, IDG_TAPER_PSWF, a.data(), nullptr) == IDG_OK) {
+            taper_def.resize((size_t)L * L);
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) taper_def[(size_t)y * L + x] = (float)(a[y] * a[x]);
+        }
+        g_last_error = saved;
+    }
+
     struct Up { void **dst; const void *src; size_t bytes; const char *what; };
     Up ups[] = {
         {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
@@ -552,8 +573,10 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
         {(void **)&p->d_scale_f2, scale_f2.data(), sizeof(float) * scale_f2.size(), "channel scale pairs"},
         {(void **)&p->d_nprime, nprime.data(), sizeof(float) * nprime.size(), "n' table"},
+        {(void **)&p->d_taper, taper_def.data(), sizeof(float) * taper_def.size(), "default taper"},
     };
     for (auto &u : ups) {
+        if (u.bytes == 0) continue;
         e = cudaMalloc(u.dst, u.bytes);
         if (e != cudaSuccess) {
             idg_status st = cuda_fail(e, (std::string("cudaMalloc(") + u.what + ")").c_str());
@@ -596,6 +619,10 @@ idg_status idg_plan_export(const idg_plan *p, int32_t *desc, int64_t cap) {
     if (cap < p->stats.n_subgrids) return fail(IDG_ERR_INVALID_ARG, "desc capacity is smaller than n_subgrids");
     std::copy(p->desc.begin(), p->desc.end(), desc);
     return IDG_OK;
+}
+
+static idg_status no_default_taper() {
+    return fail(IDG_ERR_INVALID_ARG, "the taper is NULL and the plan has no default taper");
 }
 
 static idg_status check_call(const idg_plan *p, const void *a, const char *an, const void *b, const char *bn) {
@@ -646,11 +673,11 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
 // lie in subgrids of at least 512 (as the default per-call choice does).
 static bool fused_grid(const idg_plan *p) {
     return p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
-           p->opts.adder_mode == IDG_ADDER_ATOMIC && get_variant(IDG_KERNEL_GRIDDER, 32) == 0;
+           p->opts.adder_mode == IDG_ADDER_ATOMIC && p->kernel_variant(IDG_KERNEL_GRIDDER) == 0;
 }
 static bool fused_degrid(const idg_plan *p, const SubgridSet &set) {
     if (!(p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
-          get_variant(IDG_KERNEL_DEGRIDDER, 32) == 0))
+          p->kernel_variant(IDG_KERNEL_DEGRIDDER) == 0))
         return false;
     int64_t small = 0, all = 0;
     for (int64_t i = 0; i < set.count; ++i) {
@@ -678,7 +705,7 @@ static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64
         const SubgridSet set = order_of(p, o, f, cnt);
         {
             ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, f, cnt, o));
-            st = launch_gridder(g, set, -1, vis, flags, aterms, taper, scratch, s);
+            st = launch_gridder(g, set, p->kernel_variant(IDG_KERNEL_GRIDDER), vis, flags, aterms, taper, scratch, s);
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
@@ -717,21 +744,21 @@ static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, f, cnt, o));
-            st = launch_degridder(g, set, -1, scratch, flags, aterms, taper, vis_out, s);
+            st = launch_degridder(g, set, p->kernel_variant(IDG_KERNEL_DEGRIDDER), scratch, flags, aterms, taper, vis_out, s);
         }
     }
     return st;
 }
 
-idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
-                    const float *taper, void *grid, idg_stream stream) {
-    idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
-    if (st != IDG_OK) return st;
-    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
-    const int64_t n = p->stats.n_subgrids;
-    if (n == 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int64_t chunk = chunk_subgrids(p);
+// The composite calls over the positions [first, first + count) of order o
+// (the whole plan in work order for idg_grid / idg_degrid, a plan-order range
+// for the range calls).
+static idg_status grid_call(const idg_plan *p, Order o, int64_t first, int64_t count, const void *vis,
+                            const uint8_t *flags, const void *aterms, const float *taper, void *grid,
+                            cudaStream_t s) {
+    if (count == 0) return IDG_OK;
+    idg_status st = IDG_OK;
+    const int64_t chunk = std::min(chunk_subgrids(p), count);
     const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     void *scratch = nullptr;     // the subgrid scratch, unless one fused launch takes the call
     if (comp || !fused_grid(p)) st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
@@ -746,7 +773,7 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
             if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(compensation)");
         }
     }
-    if (st == IDG_OK) st = grid_span(p, g, Order::Work, 0, n, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
+    if (st == IDG_OK) st = grid_span(p, g, o, first, count, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
     if (comp && cbuf) {
         if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
         cudaFreeAsync(cbuf, s);
@@ -756,27 +783,60 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
     return st;
 }
 
+static idg_status degrid_call(const idg_plan *p, Order o, int64_t first, int64_t count, const void *grid,
+                              const uint8_t *flags, const void *aterms, const float *taper, void *vis_out,
+                              cudaStream_t s) {
+    if (count == 0) return IDG_OK;
+    idg_status st = IDG_OK;
+    const int64_t chunk = std::min(chunk_subgrids(p), count);
+    void *scratch = nullptr;
+    if (!fused_degrid(p, order_of(p, o, first, count)))
+        st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    if (st != IDG_OK) return st;
+    st = degrid_span(p, p->geometry(), o, first, count, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
+    cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
+    return st;
+}
+
+idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
+                    const float *taper, void *grid, idg_stream stream) {
+    idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
+    if (st != IDG_OK) return st;
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
+    return grid_call(p, Order::Work, 0, p->stats.n_subgrids, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+}
+
 idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags, const void *aterms,
                       const float *taper, void *vis_out, idg_stream stream) {
     idg_status st = check_call(p, grid, "d_grid", vis_out, "d_vis_out");
     if (st != IDG_OK) return st;
-    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = p->stats.n_subgrids;
     if (p->any_dropped || n == 0) {
         cudaError_t e = cudaMemsetAsync(vis_out, 0, (size_t)p->n_bl * p->n_t * p->n_chan * 32, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(vis_out)");
     }
-    if (n == 0) return IDG_OK;
-    const int64_t chunk = chunk_subgrids(p);
-    void *scratch = nullptr;
-    if (!fused_degrid(p, order_of(p, Order::Work, 0, n)))
-        st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    return degrid_call(p, Order::Work, 0, n, grid, flags, aterms, taper, vis_out, s);
+}
+
+idg_status idg_grid_range(const idg_plan *p, int64_t first, int64_t count, const void *vis, const uint8_t *flags,
+                          const void *aterms, const float *taper, void *grid, idg_stream stream) {
+    idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
     if (st != IDG_OK) return st;
-    st = degrid_span(p, p->geometry(), Order::Work, 0, n, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
-    cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
-    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
-    return st;
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
+    if ((st = check_range(p, first, count)) != IDG_OK) return st;
+    return grid_call(p, Order::Plan, first, count, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+}
+
+idg_status idg_degrid_range(const idg_plan *p, int64_t first, int64_t count, const void *grid, const uint8_t *flags,
+                            const void *aterms, const float *taper, void *vis_out, idg_stream stream) {
+    idg_status st = check_call(p, grid, "d_grid", vis_out, "d_vis_out");
+    if (st != IDG_OK) return st;
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
+    if ((st = check_range(p, first, count)) != IDG_OK) return st;
+    return degrid_call(p, Order::Plan, first, count, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -837,7 +897,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
                          const float *h_taper, void *h_grid, idg_stream stream) {
     idg_status st = check_call(p, h_vis, "h_vis", h_grid, "h_grid");
     if (st != IDG_OK) return st;
-    if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
+    if (!h_taper && !p->d_taper) return no_default_taper();
     cudaStream_t s = (cudaStream_t)stream, cs = nullptr;
     if ((st = copy_stream(p->device, &cs)) != IDG_OK) return st;
     const size_t per_bl = (size_t)p->n_t * p->n_chan;      // visibilities per baseline
@@ -847,7 +907,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
     const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
-    const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, (size_t)p->L * p->L * 4, grid_bytes,
+    const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0, grid_bytes,
                              comp || !fused_grid(p) ? (size_t)chunk * p->L * p->L * 32 : 0};
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
@@ -879,7 +939,8 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
         if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
         if (st == IDG_OK && sf[k + 1] > sf[k])
             st = grid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
-                           (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], b.ptr[6], s);
+                           (const uint8_t *)b.ptr[1], b.ptr[2], h_taper ? (const float *)b.ptr[3] : p->d_taper, b.ptr[4],
+                           b.ptr[6], s);
     }
     if (st == IDG_OK && comp) st = launch_fold_compensation(b.ptr[4], b.ptr[6], grid_f4, s);
     // the copy stream's work ends before the buffers are released on s
@@ -898,7 +959,7 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
                            const float *h_taper, void *h_vis_out, idg_stream stream) {
     idg_status st = check_call(p, h_grid, "h_grid", h_vis_out, "h_vis_out");
     if (st != IDG_OK) return st;
-    if (!h_taper) return fail(IDG_ERR_INVALID_ARG, "h_taper is NULL");
+    if (!h_taper && !p->d_taper) return no_default_taper();
     cudaStream_t s = (cudaStream_t)stream, cs = nullptr;
     if ((st = copy_stream(p->device, &cs)) != IDG_OK) return st;
     const size_t per_bl = (size_t)p->n_t * p->n_chan;
@@ -907,7 +968,7 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
     const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
-    const size_t sizes[6] = {grid_bytes, h_flags ? nvis : 0, at_bytes, (size_t)p->L * p->L * 4, nvis * 32,
+    const size_t sizes[6] = {grid_bytes, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0, nvis * 32,
                              (size_t)chunk * p->L * p->L * 32};
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
@@ -934,7 +995,8 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
         if (sf[k + 1] > sf[k])
             st = degrid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
-                             (const uint8_t *)b.ptr[1], b.ptr[2], (const float *)b.ptr[3], b.ptr[4], s);
+                             (const uint8_t *)b.ptr[1], b.ptr[2], h_taper ? (const float *)b.ptr[3] : p->d_taper,
+                             b.ptr[4], s);
         cudaEvent_t e_done;
         if (st == IDG_OK && (e = ev.add(&e_done)) == cudaSuccess && (e = cudaEventRecord(e_done, s)) == cudaSuccess)
             e = cudaStreamWaitEvent(cs, e_done, 0);
@@ -963,10 +1025,11 @@ idg_status idg_grid_subgrids(const idg_plan *p, int64_t first, int64_t count, co
                              idg_stream stream) {
     idg_status st = check_call(p, vis, "d_vis", sub, "d_subgrids");
     if (st != IDG_OK) return st;
-    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_GRIDDER, stream, vispix(p, first, count, Order::Plan));
-    return launch_gridder(p->geometry(), plan_set(p, first, count), -1, vis, flags, aterms, taper, sub, stream);
+    return launch_gridder(p->geometry(), plan_set(p, first, count), p->kernel_variant(IDG_KERNEL_GRIDDER), vis,
+                          flags, aterms, taper, sub, stream);
 }
 
 idg_status idg_fft_subgrids(const idg_plan *p, int64_t count, int direction, void *sub, idg_stream stream) {
@@ -1002,11 +1065,11 @@ idg_status idg_degrid_subgrids(const idg_plan *p, int64_t first, int64_t count, 
                                idg_stream stream) {
     idg_status st = check_call(p, sub, "d_subgrids", vis_out, "d_vis_out");
     if (st != IDG_OK) return st;
-    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_DEGRIDDER, stream, vispix(p, first, count, Order::Plan));
-    return launch_degridder(p->geometry(), plan_set(p, first, count), -1, sub, flags, aterms, taper, vis_out,
-                            stream);
+    return launch_degridder(p->geometry(), plan_set(p, first, count), p->kernel_variant(IDG_KERNEL_DEGRIDDER), sub,
+                            flags, aterms, taper, vis_out, stream);
 }
 
 }  // extern "C"
@@ -1058,11 +1121,28 @@ idg_status idg_set_kernel_variant(int kernel, int L, int v) {
 
 int idg_get_kernel_variant(int kernel, int L) { return get_variant(kernel, L); }
 
+idg_status idg_plan_set_kernel_variant(idg_plan *p, int kernel, int v) {
+    if (!p) return fail(IDG_ERR_INVALID_ARG, "plan is NULL");
+    if (kernel != IDG_KERNEL_GRIDDER && kernel != IDG_KERNEL_DEGRIDDER)
+        return fail(IDG_ERR_INVALID_ARG, "a plan holds a choice for the gridder and the degridder only");
+    const int n = idg_kernel_variant_count(kernel, p->L);
+    if (n == 0) return fail(IDG_ERR_INVALID_ARG, "no such kernel for the plan's subgrid size");
+    if (v < -1 || v >= n) return fail(IDG_ERR_INVALID_ARG, "variant out of range");
+    p->variant[kernel].store(v, std::memory_order_relaxed);
+    return IDG_OK;
+}
+
+int idg_plan_get_kernel_variant(const idg_plan *p, int kernel) {
+    if (!p || kernel < 0 || kernel >= IDG_KERNEL_COUNT) return -1;
+    return p->kernel_variant(kernel);
+}
+
 idg_status idg_autotune(const idg_plan *p, const void *vis, const uint8_t *flags, const void *aterms,
                         const float *taper, void *vis_scratch, int64_t max_subgrids, double *gridder_ms,
                         double *degridder_ms, int cap, idg_stream stream) {
-    idg_status st = check_call(p, vis, "d_vis", taper, "d_taper");
+    idg_status st = check_call(p, vis, "d_vis", vis, "d_vis");
     if (st != IDG_OK) return st;
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
     const int64_t n = p->stats.n_subgrids;
     if (n == 0) return IDG_OK;
     const int64_t m = std::min<int64_t>(n, max_subgrids > 0 ? max_subgrids : 4096);
@@ -1105,7 +1185,7 @@ idg_status idg_autotune(const idg_plan *p, const void *vis, const uint8_t *flags
             if (out_ms && v < cap) out_ms[v] = t;
             if (t < best_ms) { best_ms = t; best = v; }
         }
-        if (st == IDG_OK) set_variant(kernel, p->L, best);
+        if (st == IDG_OK) p->variant[kernel].store(best, std::memory_order_relaxed);
         return best;
     };
     if (st == IDG_OK)

@@ -1,6 +1,7 @@
 // Private declarations shared by the library's translation units.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -108,8 +109,22 @@ struct idg_plan {
     int32_t *d_span_order = nullptr;
     std::vector<int32_t> kp_span_order;
     std::vector<int64_t> kp_prefix_span;
+    // default taper c[y][x] = a_y a_x of the PSWF window a of the plan's beta (device,
+    // float32 [L][L]); used where a call passes a NULL taper
+    float *d_taper = nullptr;
+    // the plan's own kernel choice per kernel (-1: the process-wide choice for its L);
+    // the one part of a plan that may change after creation (idg_plan_set_kernel_variant,
+    // idg_autotune), read once per call
+    mutable std::atomic<int> variant[IDG_KERNEL_COUNT];
 
+    idg_plan() {
+        for (auto &v : variant) v.store(-1, std::memory_order_relaxed);
+    }
     idg::Geometry geometry() const;
+    // effective kernel variant of this plan for `kernel`
+    int kernel_variant(int kernel) const;
+    // the taper a call uses: its own, else the plan's default (NULL if the plan has none)
+    const float *taper_or_default(const float *t) const { return t ? t : d_taper; }
 };
 
 namespace idg {
@@ -195,6 +210,8 @@ idg_status read_device_errors(int *code, void *stream);
 idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *subgrids, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream);
 idg_status read_tcd_error(int *code);
+// error word of the bounded-wait self-test kernel (selftest.cu)
+idg_status read_selftest_error(int *code);
 // fused forms (L = 32): the gridder transforms each subgrid in shared memory and adds it
 // into `grid` (accumulated); the degridder splits and transforms from `grid`
 idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,

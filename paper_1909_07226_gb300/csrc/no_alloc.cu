@@ -12,7 +12,18 @@
 // GPU on which the library's module is loaded holds it until the process
 // exits.  Host code cannot use the array's name as a device address, so its
 // address is looked up once per device with cudaGetSymbolAddress, with that
-// device current, and cached.
+// device current, and cached.  With CUDA's lazy module loading that first
+// lookup is also what loads this module, and with it the 64 MiB array, on the
+// device: the first call on each device may therefore fail for lack of memory
+// or synchronise the device, and belongs before the caller reserves its memory
+// and before any stream capture.  A call with a plan of no subgrids does only
+// this lookup, so it serves as the warm-up.  The cached address assumes the
+// device's context lives as long as the process: after cudaDeviceReset the
+// cached address is stale, and the call is not supported.
+//
+// Only the plain atomic adder can run here: the compensated adder needs a
+// grid-sized compensation buffer, which this call cannot allocate, so plans
+// with IDG_ADDER_COMPENSATED are refused.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -55,7 +66,12 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
     if (!p) return fail(IDG_ERR_INVALID_ARG, "plan is NULL");
     if (!vis) return fail(IDG_ERR_INVALID_ARG, "d_vis is NULL");
     if (!grid) return fail(IDG_ERR_INVALID_ARG, "d_grid is NULL");
-    if (!taper) return fail(IDG_ERR_INVALID_ARG, "d_taper is NULL");
+    if (!(taper = p->taper_or_default(taper)) && p->device >= 0)
+        return fail(IDG_ERR_INVALID_ARG, "the taper is NULL and the plan has no default taper");
+    if (p->opts.adder_mode == IDG_ADDER_COMPENSATED)
+        return fail(IDG_ERR_UNSUPPORTED,
+                    "idg_grid_no_alloc: the compensated adder needs a grid-sized buffer that this call cannot "
+                    "allocate; use a plan with IDG_ADDER_ATOMIC or idg_grid");
     if (!gridder_supported(p->L))
         return fail(IDG_ERR_UNSUPPORTED, "subgrid size " + std::to_string(p->L) + " is not compiled in");
     if (p->device < 0) return fail(IDG_ERR_INVALID_ARG, "the plan was created without a CUDA device");
@@ -74,16 +90,15 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
                         "x" + std::to_string(p->L) + " need " + std::to_string(need) +
                         " bytes of scratch; the built-in scratch holds " + std::to_string(kStaticScratchBytes) +
                         " bytes (" + std::to_string(kStaticScratchBytes / per) + " subgrids of this size)");
-    if (n == 0) return IDG_OK;
     void *scratch = nullptr;
     idg_status st = static_scratch_address(dev, &scratch);
-    if (st != IDG_OK) return st;
+    if (st != IDG_OK || n == 0) return st;
     // The gridder writes every pixel of every subgrid slot it uses before the
     // FFT and the adder read it, so nothing in the scratch has to start at zero.
     cudaStream_t s = (cudaStream_t)stream;
     const Geometry g = p->geometry();
     const SubgridSet all{p->d_order, 0, n, p->kp_order.data()};
-    st = launch_gridder(g, all, -1, vis, flags, aterms, taper, scratch, s);
+    st = launch_gridder(g, all, p->kernel_variant(IDG_KERNEL_GRIDDER), vis, flags, aterms, taper, scratch, s);
     if (st == IDG_OK) st = launch_subgrid_fft(p, n, -1, scratch, s);
     if (st == IDG_OK) st = launch_adder(g, all, scratch, grid, s);
     return st;

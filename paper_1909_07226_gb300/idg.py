@@ -36,7 +36,8 @@ EXPORTED = [
     "idg_kernel_variant_count", "idg_kernel_variant_name", "idg_set_kernel_variant", "idg_get_kernel_variant",
     "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
-    "idg_image_from_grid", "idg_grid_from_image",
+    "idg_image_from_grid", "idg_grid_from_image", "idg_plan_set_kernel_variant", "idg_plan_get_kernel_variant",
+    "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
         "idg_grid": (I32, [P, P, P, P, P, P, P]),
         "idg_degrid": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_host": (I32, [P, P, P, P, P, P, P]),
+        "idg_grid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
+        "idg_degrid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_degrid_host": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_fft_subgrids": (I32, [P, I64, I32, P, P]),
@@ -101,6 +104,8 @@ def load(path: str = LIB_PATH):
         "idg_kernel_variant_name": (ctypes.c_char_p, [I32, I32, I32]),
         "idg_set_kernel_variant": (I32, [I32, I32, I32]),
         "idg_get_kernel_variant": (I32, [I32, I32]),
+        "idg_plan_set_kernel_variant": (I32, [P, I32, I32]),
+        "idg_plan_get_kernel_variant": (I32, [P, I32]),
         "idg_autotune": (I32, [P, P, P, P, P, P, I64, P, P, I32, P]),
         "idg_batch_create": (I32, [P, P, I32, I32, P]),
         "idg_batch_grid": (I32, [P, P]),
@@ -108,6 +113,7 @@ def load(path: str = LIB_PATH):
         "idg_batch_info": (I32, [P, P, P, P]),
         "idg_batch_destroy": (None, [P]),
         "idg_device_errors": (I32, [P]),
+        "idg_selftest_wait_timeout": (I32, [I64, P]),
         "idg_taper_window": (I32, [I32, D, I32, P, P]),
         "idg_taper_aliasing": (I32, [I32, D, P, P]),
         "idg_image_from_grid": (I32, [P, P, P, P, P]),
@@ -233,15 +239,31 @@ def get_kernel_variant(kernel: str, L: int) -> int:
     return int(load().idg_get_kernel_variant(KERNEL_ID[kernel], L))
 
 
+def plan_set_kernel_variant(plan, kernel: str, variant: int):
+    """The plan's own kernel choice (-1: follow the process-wide choice for its L)."""
+    _check(load().idg_plan_set_kernel_variant(plan.handle, KERNEL_ID[kernel], int(variant)),
+           "idg_plan_set_kernel_variant")
+
+
+def plan_get_kernel_variant(plan, kernel: str) -> int:
+    """The variant the plan's calls use for `kernel`."""
+    return int(load().idg_plan_get_kernel_variant(plan.handle, KERNEL_ID[kernel]))
+
+
 def device_errors(stream=None):
     """idg_device_errors: synchronise the stream and raise IDGError if a bounded
     device wait (tensor-core gridder) gave up since the last call."""
     _check(load().idg_device_errors(_stream(stream)), "idg_device_errors")
 
 
+def selftest_wait_timeout(max_polls: int = 4096, stream=None):
+    """idg_selftest_wait_timeout: enqueue a kernel whose bounded wait runs out on purpose."""
+    _check(load().idg_selftest_wait_timeout(int(max_polls), _stream(stream)), "idg_selftest_wait_timeout")
+
+
 def autotune(plan, vis, flags, aterms, taper, vis_scratch=None, max_subgrids: int = 4096, stream=None) -> dict:
     """idg_autotune: time every gridder (and degridder) variant on a sample of the
-    plan's subgrids and select the fastest for its L.  Returns the timings."""
+    plan's subgrids and select the fastest for this plan.  Returns the timings."""
     import torch
     L = plan.stats.subgrid_size
     sh = _shapes(plan)
@@ -251,14 +273,15 @@ def autotune(plan, vis, flags, aterms, taper, vis_scratch=None, max_subgrids: in
     _check(load().idg_autotune(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
                                _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                                _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                               _dptr(taper, "taper", torch.float32, sh["taper"]),
+                               _dptr(taper, "taper", torch.float32, sh["taper"], True),
                                _dptr(vis_scratch, "vis_scratch", torch.complex64, sh["vis"], True),
                                int(max_subgrids), gms, dms, cap, _stream(stream)), "idg_autotune")
     g_names, d_names = kernel_variants("gridder", L), kernel_variants("degridder", L)
     return {"L": L,
-            "gridder": {"ms": {n: gms[i] for i, n in enumerate(g_names)}, "chosen": get_kernel_variant("gridder", L)},
+            "gridder": {"ms": {n: gms[i] for i, n in enumerate(g_names)},
+                        "chosen": plan_get_kernel_variant(plan, "gridder")},
             "degridder": {"ms": {n: dms[i] for i, n in enumerate(d_names) if dms[i] >= 0},
-                          "chosen": get_kernel_variant("degridder", L)}}
+                          "chosen": plan_get_kernel_variant(plan, "degridder")}}
 
 
 def _device_key() -> str:
@@ -401,7 +424,7 @@ def grid(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
     _check(load().idg_grid(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
                            _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                            _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                           _dptr(taper, "taper", torch.float32, sh["taper"]),
+                           _dptr(taper, "taper", torch.float32, sh["taper"], True),
                            _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)), "idg_grid")
 
 
@@ -411,8 +434,33 @@ def degrid(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None):
     _check(load().idg_degrid(plan.handle, _dptr(grid_in, "grid", torch.complex64, sh["grid"]),
                              _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                              _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                             _dptr(taper, "taper", torch.float32, sh["taper"]),
+                             _dptr(taper, "taper", torch.float32, sh["taper"], True),
                              _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)), "idg_degrid")
+
+
+def grid_range(plan: Plan, first: int, count: int, vis, flags, aterms, taper, grid_out, stream=None):
+    """idg_grid_range: the subgrids [first, first + count) (plan order) added into grid_out."""
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_grid_range(plan.handle, int(first), int(count), _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                                 _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                 _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                 _dptr(taper, "taper", torch.float32, sh["taper"], True),
+                                 _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)),
+           "idg_grid_range")
+
+
+def degrid_range(plan: Plan, first: int, count: int, grid_in, flags, aterms, taper, vis_out, stream=None):
+    """idg_degrid_range: the visibilities of subgrids [first, first + count) written to vis_out."""
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_degrid_range(plan.handle, int(first), int(count),
+                                   _dptr(grid_in, "grid", torch.complex64, sh["grid"]),
+                                   _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                   _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                   _dptr(taper, "taper", torch.float32, sh["taper"], True),
+                                   _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)),
+           "idg_degrid_range")
 
 
 def grid_no_alloc(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
@@ -423,7 +471,7 @@ def grid_no_alloc(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
     _check(load().idg_grid_no_alloc(plan.handle, _dptr(vis, "vis", torch.complex64, sh["vis"]),
                                     _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                                     _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                                    _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                    _dptr(taper, "taper", torch.float32, sh["taper"], True),
                                     _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)),
            "idg_grid_no_alloc")
 
@@ -435,7 +483,7 @@ def grid_subgrids(plan: Plan, first: int, count: int, vis, flags, aterms, taper,
     _check(load().idg_grid_subgrids(plan.handle, first, count, _dptr(vis, "vis", torch.complex64, sh["vis"]),
                                     _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                                     _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                                    _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                    _dptr(taper, "taper", torch.float32, sh["taper"], True),
                                     _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
                                     _stream(stream)), "idg_grid_subgrids")
 
@@ -474,7 +522,7 @@ def degrid_subgrids(plan: Plan, first: int, count: int, subgrids, flags, aterms,
                                       _dptr(subgrids, "subgrids", torch.complex64, (count, L, L, 4)),
                                       _dptr(flags, "flags", torch.uint8, sh["flags"], True),
                                       _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
-                                      _dptr(taper, "taper", torch.float32, sh["taper"]),
+                                      _dptr(taper, "taper", torch.float32, sh["taper"], True),
                                       _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)),
            "idg_degrid_subgrids")
 
@@ -502,7 +550,7 @@ def grid_host(plan: Plan, vis, flags, aterms, taper, grid_out, stream=None):
     _check(load().idg_grid_host(plan.handle, _hptr(vis, "vis", np.complex64, sh["vis"]),
                                 _hptr(flags, "flags", np.uint8, sh["flags"], True),
                                 _hptr(aterms, "aterms", np.complex64, sh["aterms"], True),
-                                _hptr(taper, "taper", np.float32, sh["taper"]),
+                                _hptr(taper, "taper", np.float32, sh["taper"], True),
                                 _hptr(grid_out, "grid", np.complex64, sh["grid"]), _stream(stream)),
            "idg_grid_host")
 
@@ -512,7 +560,7 @@ def degrid_host(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None)
     _check(load().idg_degrid_host(plan.handle, _hptr(grid_in, "grid", np.complex64, sh["grid"]),
                                   _hptr(flags, "flags", np.uint8, sh["flags"], True),
                                   _hptr(aterms, "aterms", np.complex64, sh["aterms"], True),
-                                  _hptr(taper, "taper", np.float32, sh["taper"]),
+                                  _hptr(taper, "taper", np.float32, sh["taper"], True),
                                   _hptr(vis_out, "vis_out", np.complex64, sh["vis"]), _stream(stream)),
            "idg_degrid_host")
 
@@ -541,7 +589,7 @@ class Batch:
             bufs[i].vis_out = _dptr(j.get("vis_out"), "vis_out", torch.complex64, sh["vis"], True)
             bufs[i].flags = _dptr(j.get("flags"), "flags", torch.uint8, sh["flags"], True)
             bufs[i].aterms = _dptr(j.get("aterms"), "aterms", torch.complex64, sh["aterms"], True)
-            bufs[i].taper = _dptr(j.get("taper"), "taper", torch.float32, sh["taper"])
+            bufs[i].taper = _dptr(j.get("taper"), "taper", torch.float32, sh["taper"], True)
             bufs[i].grid = _dptr(j.get("grid"), "grid", torch.complex64, sh["grid"], True)
         arr = (ctypes.c_void_p * n)(*[p.handle for p in plans])
         h = ctypes.c_void_p()

@@ -153,3 +153,36 @@ def test_tensor_core_transform_only_for_subgrid_size_32(lib):
     wl = syn.make_small(seed=1, n_st=4, n_t=8, n_chan=2, L=32, N=128, with_vis=False, aterms="identity")
     p = idg.plan_from_workload(wl, fft_mode=idg.FFT_TC_SPLIT)
     assert p.stats.subgrid_size == 32
+
+
+def test_no_alloc_refuses_the_compensated_adder(lib):
+    # the compensated adder needs a grid-sized buffer that the no-allocation call
+    # cannot take: refused before anything is enqueued (and before device checks)
+    p = _create(adder_mode=idg.ADDER_COMPENSATED)
+    st = lib.idg_grid_no_alloc(p.handle, ctypes.c_void_p(16), None, None, None, ctypes.c_void_p(16), None)
+    assert st == 6
+    assert b"compensated" in lib.idg_last_error()
+
+
+def test_kernel_choice_is_per_plan(lib):
+    wl = syn.make_small(seed=1, n_st=4, n_t=8, n_chan=2, L=32, N=128, with_vis=False, aterms="identity")
+    a, b = idg.plan_from_workload(wl), idg.plan_from_workload(wl)
+    n = len(idg.kernel_variants("gridder", 32))
+    assert n >= 2
+    assert idg.plan_get_kernel_variant(a, "gridder") == idg.get_kernel_variant("gridder", 32) == 0
+    idg.plan_set_kernel_variant(a, "gridder", 1)
+    assert idg.plan_get_kernel_variant(a, "gridder") == 1
+    assert idg.plan_get_kernel_variant(b, "gridder") == 0          # the other plan keeps its choice
+    assert idg.get_kernel_variant("gridder", 32) == 0              # and so does the process
+    try:
+        idg.set_kernel_variant("gridder", 32, n - 1)                # process-wide default moves b, not a
+        assert idg.plan_get_kernel_variant(b, "gridder") == n - 1
+        assert idg.plan_get_kernel_variant(a, "gridder") == 1
+        idg.plan_set_kernel_variant(a, "gridder", -1)                # back to following the process
+        assert idg.plan_get_kernel_variant(a, "gridder") == n - 1
+    finally:
+        idg.set_kernel_variant("gridder", 32, 0)
+    with pytest.raises(idg.IDGError):
+        idg.plan_set_kernel_variant(a, "gridder", n)
+    with pytest.raises(idg.IDGError):
+        idg.plan_set_kernel_variant(a, "adder", 0)

@@ -161,3 +161,22 @@ def test_lofar_recurrence_form_sampled(lofar):
     for dsc in op.desc[ids]:
         mask[dsc[0], dsc[2]:dsc[2] + dsc[3], dsc[4]:dsc[4] + dsc[5]] = True
     parity(v.cpu().numpy()[mask], ref[mask], "lofar recurrence degrid (sampled subgrids)")
+
+
+def test_lofar_fused_grid_on_sampled_ranges(lofar):
+    # the fused separable gridder the benchmark times, on sampled plan-order
+    # ranges of the full plan (idg_grid_range runs the same kernel), every pixel
+    # of the resulting grid against the oracle's grid of the same subgrids
+    import torch
+    wl, p, op, d, ids = lofar["wl"], lofar["p"], lofar["op"], lofar["d"], lofar["ids"]
+    assert p.stats.separable == 1
+    g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+    i = 0
+    while i < len(ids):
+        j = i
+        while j + 1 < len(ids) and ids[j + 1] == ids[j] + 1:
+            j += 1
+        idg.grid_range(p, int(ids[i]), j - i + 1, d["vis"], d["flags"], d["aterms"], d["taper"], g)
+        i = j + 1
+    idg.device_errors()
+    parity(g.cpu().numpy(), O.grid(wl, op, ids=ids), "lofar fused grid (sampled ranges, every pixel)")

@@ -55,3 +55,29 @@ def test_serving_matches_plain_per_job():
                    tol=1e-6)
         if a.kind in ("cycle", "degrid"):
             parity(a.data.work.cpu().numpy(), b.data.work.cpu().numpy(), f"serving vs plain vis job {a.id}", tol=1e-6)
+
+
+def test_served_cycle_job_matches_the_oracle():
+    # A "cycle" job served inside a mix, checked against the FP64 oracle's
+    # composition of the residual formulation (Sect. 2): after 3 major cycles the
+    # model is m2 = 0.75 truth (m0 = 0, m <- m + (truth - m) / 2), the residual
+    # visibilities are observed - degrid(m2) (flagged and dropped ones: the model
+    # is 0 there) and the residual grid is grid(residual) over unflagged samples.
+    from oracle import oracle as O
+    wls = syn.make_batched_jobs(6, seed=23, scale_t=0.1)
+    trace = serving.make_trace(wls, 1e5, ("cycle",), seed=5, n_cycles=3)
+    eng = serving.Engine(budget_bytes=64 << 30, keep=True)
+    eng.run(trace)
+    assert max(n for n, _ in eng.launch_sets) > 1          # the job shared launches with others
+    job = min(trace, key=lambda j: j.wl.n_vis)               # the smallest keeps the oracle quick
+    wl, dd = job.wl, job.data
+    observed = dd.observed.cpu().numpy().astype(np.complex128)
+    flags = dd.flags.cpu().numpy()
+    m2 = 0.75 * dd.truth.cpu().numpy().astype(np.complex128)
+    op = O.plan(wl)
+    assert np.array_equal(job.plan.export(), op.desc)
+    model_vis = O.degrid(wl, op, m2, flags=flags)
+    resid = observed - model_vis
+    parity(dd.work.cpu().numpy(), resid, f"served job {job.id}: residual visibilities vs oracle")
+    ref_grid = O.grid(wl, op, vis=resid.astype(np.complex64), flags=flags)
+    parity(dd.residual.cpu().numpy(), ref_grid, f"served job {job.id}: residual grid vs oracle")

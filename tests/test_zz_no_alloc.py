@@ -31,9 +31,9 @@ def built():
     idg.load()
 
 
-def _reference_and_no_alloc(wl):
+def _reference_and_no_alloc(wl, **opt):
     import torch
-    p = idg.plan_from_workload(wl)
+    p = idg.plan_from_workload(wl, **opt)
     assert p.n_subgrids * wl.subgrid_size ** 2 * 32 <= SCRATCH_BYTES
     d = workload_to_device(wl)
     shape = (p.n_w_layers, wl.grid_size, wl.grid_size, 4)
@@ -93,3 +93,38 @@ def test_no_alloc_rejects_plans_beyond_the_scratch():
     assert st == 1
     msg = lib.idg_last_error().decode()
     assert "scratch" in msg and str(SCRATCH_BYTES) in msg and "2048 subgrids" in msg
+
+
+def test_no_alloc_precision_forms_near_the_limit():
+    # the channel-recurrence gridder and the split tensor-core transform on the
+    # static array, with a plan that fills most of it (the LOFAR-like workload's
+    # first 128 timesteps: 1601 subgrids of 32 x 32, 78 % of the 64 MiB)
+    wl = syn.make_lofar(n_t=128)
+    p, ref, out = _reference_and_no_alloc(wl, precision_mode=idg.PHASOR_RECURRENCE, fft_mode=idg.FFT_TC_SPLIT)
+    assert p.n_subgrids * 32 * 32 * 32 > SCRATCH_BYTES // 2
+    parity(out, ref, "no-alloc recurrence + tensor-core transform vs idg_grid")
+
+
+def test_no_alloc_warm_up_call_and_compensated_plans():
+    import torch
+    lib = idg.load()
+    # a plan without subgrids (every visibility off the grid) only resolves the
+    # array's address: the warm-up call
+    wl = syn.make_small(seed=1, n_st=4, n_t=4, n_chan=2, L=16, N=64, cell=0.02, diameter_m=20000.0)
+    p = idg.plan_from_workload(wl)
+    assert p.n_subgrids == 0
+    d = workload_to_device(wl)
+    g = torch.zeros((1, 64, 64, 4), dtype=torch.complex64, device="cuda")
+    idg.grid_no_alloc(p, d["vis"], None, None, None, g)
+    torch.cuda.synchronize()
+    assert float(g.abs().max()) == 0.0
+    # the compensated adder would need a grid-sized buffer: refused, grid untouched
+    wl = syn.make_tiny()
+    p = idg.plan_from_workload(wl, adder_mode=idg.ADDER_COMPENSATED)
+    d = workload_to_device(wl)
+    g = torch.zeros((1, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+    with pytest.raises(idg.IDGError) as ei:
+        idg.grid_no_alloc(p, d["vis"], None, d["aterms"], d["taper"], g)
+    assert ei.value.status == 6 and "compensated" in str(ei.value)
+    torch.cuda.synchronize()
+    assert float(g.abs().max()) == 0.0
