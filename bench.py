@@ -520,6 +520,51 @@ def run_gb300(args, world, rank, local):
         image_steps["basis"] = ("4 x n_w x N^2 x 32 B per call (row and column pass, read and write), "
                                 f"against the {hbm_src} copy bandwidth")
 
+    # calibration (the residuals, cost and A-term gradient of the model grid against the
+    # observed visibilities, idg_aterm_gradient) on the same workload: one call is a
+    # degrid and a grid pass of every visibility plus the residual and gradient kernels
+    calib = None
+    resid = torch.empty_like(vis)
+    agrad = torch.zeros(aterms.shape, dtype=torch.complex64, device=dev)
+    cost = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def calib_call():
+        idg.aterm_gradient(plan, model, vis, flags, aterms, taper, resid, agrad, cost, stream)
+
+    for _ in range(3):
+        calib_call()
+    torch.cuda.synchronize()
+    idg.profile_enable(True)
+    idg.profile_read(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n_cal = 5
+    e0.record(stream)
+    for _ in range(n_cal):
+        calib_call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cprof = idg.profile_read(reset=True)
+    idg.profile_enable(False)
+    idg.device_errors(stream)
+    cal_ms = e0.elapsed_time(e1) / n_cal
+    calib = {"ms": cal_ms, "mvis_per_s": wl.n_vis / (cal_ms * 1e-3) / 1e6,
+             "launches": int(sum(d["launches"] for d in cprof.values())) // n_cal, "kernels": {}}
+    for k, d in cprof.items():
+        if d["launches"] == 0:
+            continue
+        ent = {"ms_per_call": d["ms"] / n_cal, "launches": d["launches"] // n_cal}
+        if k in ("calib_residual", "calib_gradient", "splitter"):
+            ach = d["work"] / (d["ms"] * 1e-3) / 1e9
+            ent.update(bound="hbm", achieved=ach, peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak)
+        elif k in ("gridder", "degridder"):
+            ent.update(achieved_vispix=d["work"] / (d["ms"] * 1e-3) / 1e9, vispix_unit="Gvispix/s")
+        calib["kernels"][k] = ent
+    calib["basis"] = ("one idg_aterm_gradient call: splitter, inverse transform and degridder (stage kernels), "
+                      "residual kernel (64 B per visibility), gridder of the residuals, gradient kernel (256 B per "
+                      "subgrid pixel); MVis/s = visibilities per call / call time")
+    del resid, agrad
+
     # end to end through the host-buffer C-ABI calls
     with near_gpu_memory(local) as placement:
         vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
@@ -574,6 +619,7 @@ def run_gb300(args, world, rank, local):
                     "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                     "host_buffers_placed_from_cpus": placement.cpus},
             "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu, "image_steps": image_steps,
+            "calibration": calib,
             "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
             "parallelism": "replicas" if world > 1 else "single GPU",
         }

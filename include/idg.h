@@ -211,6 +211,33 @@ idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d
                       idg_stream stream);
 
 /*
+ * Residuals, cost and A-term gradient for calibration (Sect. 6: image domain
+ * gridding computes the residuals and derivatives of a fit whose free
+ * parameters are the A-terms, with a full image -- here its grid -- as model).
+ * With y_k the model visibilities of d_grid under d_aterms (as idg_degrid):
+ *   d_residual[k] = d_vis[k] - y_k for planned, unflagged k; 0 for flagged and
+ *                   dropped k (OVERWRITTEN, layout of d_vis)
+ *   *d_cost      += J = sum_k sum_pol |d_residual[k][pol]|^2 (one FP64 value in
+ *                   device memory, ADDED; NULL: not computed)
+ *   d_gradient   += dJ/dRe(A) + i dJ/dIm(A) for every A-term entry, complex64
+ *                   [n_slots][n_stations][L][L][4] like d_aterms (ADDED: zero it
+ *                   first, or sum several plans into one gradient).  For a
+ *                   complex direction E, d/dh J(A + h E) = Re sum conj(G) E.
+ *   Per subgrid of baseline (p, q) in slot a and pixel: G[a][p] += -2 R A_q B^H
+ *   and G[a][q] += -2 R^H A_p B, with B = taper * (the model's subgrid image)
+ *   and R = sum_k r_k exp(+2 pi i phi_k) (the gridder's direct sum of the
+ *   residuals, without taper and A-terms).
+ * d_aterms NULL differentiates at identity A-terms; d_taper NULL is the plan's
+ * default taper.  Runs the plan's splitter, inverse transform, degridder and
+ * gridder kernels (the stage forms, not the fused ones) plus a residual and a
+ * gradient kernel, per chunk of subgrids with up to 512 MiB of stream-ordered
+ * scratch.  Summation order is not fixed (atomic adds).
+ */
+idg_status idg_aterm_gradient(const idg_plan *plan, const void *d_grid, const void *d_vis, const uint8_t *d_flags,
+                              const void *d_aterms, const float *d_taper, void *d_residual, void *d_gradient,
+                              double *d_cost, idg_stream stream);
+
+/*
  * The composite operations restricted to the plan's subgrids [first, first +
  * count) in plan order (0 <= first, first + count <= n_subgrids; count 0 does
  * nothing).  They run the kernels idg_grid / idg_degrid would choose for these
@@ -376,12 +403,17 @@ void idg_batch_destroy(idg_batch *batch);
  *                (sum of K_p * L^2) for the gridder, the degridder and the two
  *                fused batch kernels (IDG_KERNEL_BATCH_*), bytes moved
  *                for the adder (read subgrid + read and write grid, 96 B per
- *                pixel) and the splitter (64 B per pixel), subgrids for the FFT.
+ *                pixel), the splitter (64 B per pixel), the calibration's
+ *                residual kernel (64 B per planned visibility: model and
+ *                observed read, residual written, flags aside) and gradient
+ *                kernel (256 B per subgrid pixel: R, P, A_p, A_q read, two
+ *                gradient entries read and written), subgrids for the FFT.
  * Arrays have IDG_KERNEL_COUNT entries; any of them may be NULL.  Do not enable
  * timing while a stream is being captured into a CUDA graph.
  */
 enum { IDG_KERNEL_GRIDDER = 0, IDG_KERNEL_FFT, IDG_KERNEL_ADDER, IDG_KERNEL_SPLITTER, IDG_KERNEL_DEGRIDDER,
-       IDG_KERNEL_BATCH_GRID, IDG_KERNEL_BATCH_DEGRID, IDG_KERNEL_COUNT };
+       IDG_KERNEL_BATCH_GRID, IDG_KERNEL_BATCH_DEGRID, IDG_KERNEL_CALIB_RESIDUAL, IDG_KERNEL_CALIB_GRADIENT,
+       IDG_KERNEL_COUNT };
 void idg_profile_enable(int on);
 idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset);
 

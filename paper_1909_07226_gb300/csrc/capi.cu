@@ -299,6 +299,7 @@ void idg_plan_destroy(idg_plan *p) {
     cudaFree(p->d_scale_f2);
     cudaFree(p->d_nprime);
     cudaFree(p->d_taper);
+    cudaFree(p->d_ones);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
 }
@@ -564,6 +565,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         g_last_error = saved;
     }
 
+    const std::vector<float> ones((size_t)L * L, 1.0f);
+
     struct Up { void **dst; const void *src; size_t bytes; const char *what; };
     Up ups[] = {
         {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
@@ -574,6 +577,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_scale_f2, scale_f2.data(), sizeof(float) * scale_f2.size(), "channel scale pairs"},
         {(void **)&p->d_nprime, nprime.data(), sizeof(float) * nprime.size(), "n' table"},
         {(void **)&p->d_taper, taper_def.data(), sizeof(float) * taper_def.size(), "default taper"},
+        {(void **)&p->d_ones, ones.data(), sizeof(float) * ones.size(), "unit taper"},
     };
     for (auto &u : ups) {
         if (u.bytes == 0) continue;
@@ -795,6 +799,63 @@ static idg_status degrid_call(const idg_plan *p, Order o, int64_t first, int64_t
     if (st != IDG_OK) return st;
     st = degrid_span(p, p->geometry(), o, first, count, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
     cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
+    return st;
+}
+
+idg_status idg_aterm_gradient(const idg_plan *p, const void *grid, const void *vis, const uint8_t *flags,
+                              const void *aterms, const float *taper, void *residual, void *gradient, double *cost,
+                              idg_stream stream) {
+    idg_status st = check_call(p, grid, "d_grid", vis, "d_vis");
+    if (st != IDG_OK) return st;
+    if (!residual) return fail(IDG_ERR_INVALID_ARG, "d_residual is NULL");
+    if (!gradient) return fail(IDG_ERR_INVALID_ARG, "d_gradient is NULL");
+    if (!(taper = p->taper_or_default(taper))) return no_default_taper();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = p->stats.n_subgrids;
+    if (p->any_dropped || n == 0) {
+        cudaError_t e = cudaMemsetAsync(residual, 0, (size_t)p->n_bl * p->n_t * p->n_chan * 32, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(residual)");
+    }
+    if (n == 0) return IDG_OK;
+    // two scratch areas of `chunk` subgrid images: the model's P and the residuals' R
+    const int64_t chunk = std::max<int64_t>(1, chunk_subgrids(p) / 2);
+    const size_t img = (size_t)p->L * p->L * 32;
+    void *scratch = nullptr;
+    if ((st = scratch_alloc(p->device, 2 * (size_t)chunk * img, s, &scratch)) != IDG_OK) return st;
+    void *P = scratch, *R = (char *)scratch + (size_t)chunk * img;
+    const Geometry g = p->geometry();
+    const int vd = p->kernel_variant(IDG_KERNEL_DEGRIDDER), vg = p->kernel_variant(IDG_KERNEL_GRIDDER);
+    for (int64_t f = 0; f < n && st == IDG_OK; f += chunk) {
+        const int64_t cnt = std::min(chunk, n - f);
+        const SubgridSet set = order_set(p, f, cnt);
+        {
+            ProfileScope ps(IDG_KERNEL_SPLITTER, s, 64.0 * pixels(p, cnt));
+            st = launch_splitter(g, set, grid, P, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_FFT, s, (double)cnt);
+            st = launch_subgrid_fft(p, cnt, +1, P, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, f, cnt, Order::Work));
+            st = launch_degridder(g, set, vd, P, flags, aterms, taper, residual, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_CALIB_RESIDUAL, s,
+                            64.0 * (double)(p->kp_prefix_order[f + cnt] - p->kp_prefix_order[f]));
+            st = launch_calib_residual(g, set, vis, flags, residual, cost, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, f, cnt, Order::Work));
+            st = launch_gridder(g, set, vg, residual, flags, nullptr, p->d_ones, R, s);
+        }
+        if (st == IDG_OK) {
+            ProfileScope ps(IDG_KERNEL_CALIB_GRADIENT, s, 256.0 * pixels(p, cnt));
+            st = launch_calib_gradient(g, set, R, P, aterms, taper, gradient, s);
+        }
+    }
+    cudaError_t e = cudaFreeAsync(scratch, s);
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "cudaFreeAsync(scratch)");
     return st;
 }

@@ -112,6 +112,7 @@ struct idg_plan {
     // default taper c[y][x] = a_y a_x of the PSWF window a of the plan's beta (device,
     // float32 [L][L]); used where a call passes a NULL taper
     float *d_taper = nullptr;
+    float *d_ones = nullptr;               // [L][L] of 1.0f: the unit taper of the calibration's residual sums
     // the plan's own kernel choice per kernel (-1: the process-wide choice for its L);
     // the one part of a plan that may change after creation (idg_plan_set_kernel_variant,
     // idg_autotune), read once per call
@@ -227,6 +228,14 @@ idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *ite
 // the separable kernels over work items of jobs whose plans are separable
 idg_status launch_gridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 idg_status launch_degridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+
+// calibration (calibration.cu): residuals and cost over the visibilities of a subgrid
+// set (res holds the model visibilities on entry), and the A-term gradient from the
+// residual images R and the model images P of the set (chunk positions)
+idg_status launch_calib_residual(const Geometry &g, const SubgridSet &set, const void *obs, const uint8_t *flags,
+                                 void *res, double *cost, void *stream);
+idg_status launch_calib_gradient(const Geometry &g, const SubgridSet &set, const void *R, const void *P,
+                                 const void *aterms, const float *taper, void *grad, void *stream);
 
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);

@@ -37,10 +37,11 @@ EXPORTED = [
     "idg_autotune", "idg_batch_create", "idg_batch_grid", "idg_batch_degrid", "idg_batch_info",
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
     "idg_image_from_grid", "idg_grid_from_image", "idg_plan_set_kernel_variant", "idg_plan_get_kernel_variant",
-    "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout",
+    "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout", "idg_aterm_gradient",
 ]
 BATCH_GRAPH = 1
-KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid"]
+KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid", "calib_residual",
+           "calib_gradient"]
 
 
 class IDGError(RuntimeError):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "idg_degrid": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_host": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
+        "idg_aterm_gradient": (I32, [P, P, P, P, P, P, P, P, P, P]),
         "idg_degrid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_degrid_host": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
@@ -436,6 +438,23 @@ def degrid(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None):
                              _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
                              _dptr(taper, "taper", torch.float32, sh["taper"], True),
                              _dptr(vis_out, "vis_out", torch.complex64, sh["vis"]), _stream(stream)), "idg_degrid")
+
+
+def aterm_gradient(plan: Plan, grid_in, vis, flags, aterms, taper, residual_out, gradient, cost=None, stream=None):
+    """idg_aterm_gradient: residuals (overwritten), the A-term gradient (added into
+    `gradient`, shaped like the A-terms) and, if `cost` (a one-element float64 CUDA
+    tensor) is given, the cost added into it."""
+    import torch
+    sh = _shapes(plan)
+    _check(load().idg_aterm_gradient(plan.handle, _dptr(grid_in, "grid", torch.complex64, sh["grid"]),
+                                     _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                                     _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                     _dptr(aterms, "aterms", torch.complex64, sh["aterms"], True),
+                                     _dptr(taper, "taper", torch.float32, sh["taper"], True),
+                                     _dptr(residual_out, "residual", torch.complex64, sh["vis"]),
+                                     _dptr(gradient, "gradient", torch.complex64, sh["aterms"]),
+                                     _dptr(cost, "cost", torch.float64, (1,), True), _stream(stream)),
+           "idg_aterm_gradient")
 
 
 def grid_range(plan: Plan, first: int, count: int, vis, flags, aterms, taper, grid_out, stream=None):
