@@ -81,10 +81,12 @@ def parse():
     ap.add_argument("--config", default="lofar",
                     choices=["lofar", "lofar-slice", "tiny", "batched", "serving", "precision"])
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (jobs/s)")
-    ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched configuration")
+    ap.add_argument("--jobs", type=int, default=None,
+                    help="jobs of the batched (default 256) or serving (default 64) configuration")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the forms block of the default line")
     return ap.parse_args()
 
 
@@ -565,6 +567,26 @@ def run_gb300(args, world, rank, local):
                       "subgrid pixel); MVis/s = visibilities per call / call time")
     del resid, agrad
 
+    # classical gridding with oversampled A/W-projection kernels rebuilt per subgrid (the
+    # paper's comparison, Sect. 2) beside image domain gridding, on the precision
+    # workload's A-term cadence (slots of 16 timesteps), first 256 timesteps
+    classical = classical_comparison(idg, syn, torch, dev, stream, hbm_peak) if args.config == "lofar" else None
+
+    # the adder and the splitter as their own launches over every subgrid (the fused
+    # kernels above do not launch them)
+    stages = stage_rates(idg, torch, dev, plan, vis, flags, aterms, taper, grid, stream, hbm_peak) \
+        if args.config == "lofar" else None
+
+    # the deployment forms on small fixed cases: batched against per-job calls on 16 jobs,
+    # serving against per-job FIFO at 50 jobs/s, errors of the precision forms
+    forms = None
+    if args.config == "lofar" and not args.no_forms:
+        b16 = batched_compare(idg, syn, torch, dev, 16, 3, 3, seed=1916)
+        forms = {"batched_16_jobs": {k: b16[k] for k in ("n_vis", "plain_mvis_per_s", "batched_mvis_per_s",
+                                                         "batched_over_plain", "classes")},
+                 "serving_50_per_s": serving_point(idg, syn, torch),
+                 "precision_errors": precision_errors(idg, syn, torch, dev, stream)}
+
     # end to end through the host-buffer C-ABI calls
     with near_gpu_memory(local) as placement:
         vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
@@ -619,37 +641,169 @@ def run_gb300(args, world, rank, local):
                     "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                     "host_buffers_placed_from_cpus": placement.cpus},
             "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu, "image_steps": image_steps,
-            "calibration": calib,
+            "calibration": calib, "classical": classical, "stages": stages, "forms": forms,
             "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
             "parallelism": "replicas" if world > 1 else "single GPU",
         }
         print(json.dumps(rec))
 
 
-def run_batched(args, world, rank, local):
-    """The uneven batch (config B): the same jobs gridded and degridded
-    (a) one after another with idg_grid / idg_degrid (plain per-job form) and
-    (b) as one batch: one persistent launch per subgrid size, subgrids kept in
-    shared memory, the launch sequence replayed from a CUDA graph."""
-    import torch
-    from paper_1909_07226_gb300 import build as lib_build
-    from paper_1909_07226_gb300 import idg
-    from paper_1909_07226_gb300 import synthetic as syn
+def stage_rates(idg, torch, dev, plan, vis, flags, aterms, taper, grid, stream, hbm_peak):
+    """The adder and the splitter as separate launches over every subgrid of the
+    plan (chunks of 16384 subgrid images, 512 MiB at L = 32): algorithmic bytes
+    96 B per subgrid pixel for the adder (subgrid read, grid read and written)
+    and 64 B for the splitter (grid read, subgrid written), per CUDA events."""
+    L = plan.stats.subgrid_size
+    n = plan.n_subgrids
+    chunk = min(n, 16384)
+    sub = torch.zeros((chunk, L, L, 4), dtype=torch.complex64, device=dev)
+    idg.grid_subgrids(plan, 0, chunk, vis, flags, aterms, taper, sub, stream)
+    out = {}
+    for name, fn in (("adder", lambda f, c: idg.add_subgrids(plan, f, c, sub[:c], grid, stream)),
+                     ("splitter", lambda f, c: idg.split_subgrids(plan, f, c, grid, sub[:c], stream))):
+        def one_pass():
+            for f in range(0, n, chunk):
+                fn(f, min(chunk, n - f))
+        one_pass()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            one_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        byts = (96.0 if name == "adder" else 64.0) * n * L * L
+        out[name] = {"ms": ms, "launches": (n + chunk - 1) // chunk, "bytes": byts, "bound": "hbm",
+                     "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": byts / (ms * 1e-3) / 1e9 / hbm_peak}
+    out["basis"] = (f"all {n} subgrids of the workload through idg_add_subgrids / idg_split_subgrids in chunks of "
+                    f"{chunk}; adder 96 B and splitter 64 B per subgrid pixel (algorithmic), against the measured copy "
+                    "bandwidth; overlapping subgrids share grid lines in L2")
+    return out
 
-    torch.cuda.set_device(local)
-    lib_build.build()
-    idg.load()
-    jobs = syn.make_batched_jobs(args.jobs)
+
+def precision_errors(idg, syn, torch, dev, stream, n_t=32):
+    """Error of every precision form against the FP64 oracle on the precision
+    workload's first n_t timesteps (the whole grid and every visibility)."""
+    from oracle import oracle as O
+    O.build()
+    forms = {"direct_sincos": dict(),
+             "channel_recurrence": dict(precision_mode=idg.PHASOR_RECURRENCE),
+             "compensated_adder": dict(adder_mode=idg.ADDER_COMPENSATED),
+             "tc_split_transform": dict(fft_mode=idg.FFT_TC_SPLIT)}
+    sl = syn.make_lofar(with_vis=True, n_t=n_t, slot_len=16, name="precision")
+    op = O.plan(sl)
+    ref_grid = O.grid(sl, op)
+    model_h = syn.random_grid(np.random.default_rng(7), op.n_w, sl.grid_size)
+    ref_vis = O.degrid(sl, op, model_h)
+    d = dict(vis=torch.from_numpy(sl.vis).to(dev), at=torch.from_numpy(sl.aterms).to(dev),
+             tp=torch.from_numpy(sl.taper).to(dev), model=torch.from_numpy(model_h).to(dev))
+    out = {"workload": f"precision workload (A-terms every 16 timesteps), first {n_t} timesteps: {op.n_sub} "
+                       f"subgrids, {sl.n_vis} visibilities, every pixel and visibility against the oracle"}
+    for name, kw in forms.items():
+        p = idg.plan_from_workload(sl, **kw)
+        g = torch.zeros(ref_grid.shape, dtype=torch.complex64, device=dev)
+        idg.grid(p, d["vis"], None, d["at"], d["tp"], g, stream)
+        v = torch.zeros(sl.vis.shape, dtype=torch.complex64, device=dev)
+        idg.degrid(p, d["model"], None, d["at"], d["tp"], v, stream)
+        gg = g.cpu().numpy().astype(np.complex128)
+        vv = v.cpu().numpy().astype(np.complex128)
+        out[name] = {"grid_rel_rms": float(np.linalg.norm(gg - ref_grid) / np.linalg.norm(ref_grid)),
+                     "grid_max_err_rel": float(np.max(np.abs(gg - ref_grid)) / np.max(np.abs(ref_grid))),
+                     "vis_rel_rms": float(np.linalg.norm(vv - ref_vis) / np.linalg.norm(ref_vis)),
+                     "vis_max_err_rel": float(np.max(np.abs(vv - ref_vis)) / np.max(np.abs(ref_vis)))}
+        p.destroy()
+    return out
+
+
+def serving_point(idg, syn, torch, n_jobs=16, rate=50.0):
+    """Serving engine vs per-job FIFO on one Poisson trace (latency and MVis/s)."""
+    from paper_1909_07226_gb300 import serving
+    wls = syn.make_batched_jobs(n_jobs, seed=1913, scale_t=0.25)
+    kinds = ("cycle", "grid", "degrid")
+    serving.Engine(budget_bytes=150 << 30).run(serving.make_trace(
+        syn.make_batched_jobs(3, seed=7, scale_t=0.1), 1000.0, kinds, seed=7))
+    torch.cuda.synchronize()
+    srv = serving.Engine(budget_bytes=150 << 30, max_slots=32, graph=False).run(
+        serving.make_trace(wls, rate, kinds))
+    fifo = serving.run_plain_fifo(serving.make_trace(wls, rate, kinds))
+    keep = ("grid_degrid_mvis_per_s", "latency_p50_s", "latency_p99_s", "makespan_s")
+    return {"rate_jobs_per_s": rate, "jobs": n_jobs, "serving": {k: srv[k] for k in keep},
+            "plain_fifo": {k: fifo[k] for k in keep},
+            "workload": f"{n_jobs} requests from the batched distribution (timesteps scaled by 0.25), kinds "
+                        f"cycle (5 major cycles) / grid / degrid"}
+
+
+CLASSICAL_SUPPORT, CLASSICAL_OVERSAMPLE = 8, 16
+# W-projection plane spacing: half a plane of w error is 2 pi (dw / 2) |n'| <= 0.07 rad
+# at the corner of the LOFAR-like image (|n'| = 4.2e-4)
+CLASSICAL_W_PLANE = 50.0
+
+
+def classical_comparison(idg, syn, torch, dev, stream, hbm_peak):
+    wl = syn.make_lofar(n_t=256, slot_len=16, name="precision")
+    plan = idg.plan_from_workload(wl)
+    M, O_ = CLASSICAL_SUPPORT, CLASSICAL_OVERSAMPLE
+    S = wl.grid_size * wl.cell_size
+    vis = torch.from_numpy(wl.vis).to(dev)
+    at = torch.from_numpy(wl.aterms).to(dev)
+    at_m = torch.from_numpy(syn.aterms_on_subgrid(wl.screens, M, S).astype(np.complex64)).to(dev)
+    tap = torch.from_numpy(wl.taper).to(dev)
+    g = torch.zeros((plan.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
+    out = {"workload": f"LOFAR-like, first 256 timesteps, A-terms every 16 timesteps ({plan.n_subgrids} subgrids, "
+                       f"{wl.n_vis} visibilities)",
+           "support": M, "oversample": O_, "w_plane_step": CLASSICAL_W_PLANE}
+    for name, fn in (("idg_grid", lambda: idg.grid(plan, vis, None, at, tap, g, stream)),
+                     ("classical_grid", lambda: idg.classical_grid(plan, M, O_, CLASSICAL_W_PLANE, vis, None, at_m,
+                                                                  None, g, stream))):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        idg.profile_enable(True)
+        idg.profile_read(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = idg.profile_read(reset=True)
+        idg.profile_enable(False)
+        idg.device_errors(stream)
+        ms = e0.elapsed_time(e1) / 3
+        ent = {"ms": ms, "mvis_per_s": wl.n_vis / (ms * 1e-3) / 1e6}
+        if name == "classical_grid":
+            kb = prof["classical_kernels"]
+            ent["kernel_build_ms"] = kb["ms"] / 3
+            ent["kernel_bytes_per_call"] = kb["work"] / 3
+            ent["kernel_build"] = {"bound": "hbm", "achieved": kb["work"] / (kb["ms"] * 1e-3) / 1e9, "peak": hbm_peak,
+                                   "unit": "GB/s", "frac": kb["work"] / (kb["ms"] * 1e-3) / 1e9 / hbm_peak}
+            ent["gridding_ms"] = prof["classical_grid"]["ms"] / 3
+            ent["kernel_build_share"] = kb["ms"] / max(kb["ms"] + prof["classical_grid"]["ms"], 1e-9)
+            ent["launches"] = (kb["launches"] + prof["classical_grid"]["launches"]) // 3
+        out[name] = ent
+    out["classical_over_idg_time"] = out["classical_grid"]["ms"] / out["idg_grid"]["ms"]
+    return out
+
+
+def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
+    """The same uneven jobs gridded and degridded (a) one after another with
+    idg_grid / idg_degrid (plain per-job form) and (b) as one batch (one persistent
+    launch per subgrid size, subgrids kept in shared memory, graph replay).
+    Returns (rec, n_vis, ms_plain, ms_batch, info)."""
+    jobs = syn.make_batched_jobs(n_jobs, seed=seed)
     t0 = time.perf_counter()
     plans = [idg.plan_from_workload(w) for w in jobs]
     plan_s = time.perf_counter() - t0
-    dev = torch.device("cuda", local)
     gen = torch.Generator(device=dev)
     gen.manual_seed(1912)
     bufs = []
     for w, p in zip(jobs, plans):
-        vis = torch.randn(w.vis_shape if hasattr(w, "vis_shape") else (w.n_bl, w.n_t, w.n_chan, 4),
-                          dtype=torch.complex64, device=dev, generator=gen)
+        vis = torch.randn((w.n_bl, w.n_t, w.n_chan, 4), dtype=torch.complex64, device=dev, generator=gen)
         flags = (torch.rand((w.n_bl, w.n_t, w.n_chan), device=dev, generator=gen) < w.flag_p).to(torch.uint8)
         grid = torch.zeros((p.n_w_layers, w.grid_size, w.grid_size, 4), dtype=torch.complex64, device=dev)
         bufs.append(dict(vis=vis, vis_out=vis, flags=flags, aterms=None, taper=torch.from_numpy(w.taper).to(dev),
@@ -671,39 +825,66 @@ def run_batched(args, world, rank, local):
         batch.grid(stream)
         batch.degrid(stream)
 
-    def timed(fn, steps):
-        for _ in range(max(3, args.warmup)):
+    def timed(fn, n):
+        for _ in range(max(3, warmup)):
             fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(n):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / n
 
+    ms_plain = timed(plain_step, max(1, steps // 2))
+    ms_batch = timed(batch_step, steps)
+    info = batch.info()
+    classes = {}
+    for w, p in zip(jobs, plans):
+        c = classes.setdefault(f"L{w.subgrid_size}", {"jobs": 0, "vis": 0})
+        c["jobs"] += 1
+        c["vis"] += int(w.n_vis)
+    batch.destroy()
+    return {"n_vis": int(n_vis), "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
+            "plain_mvis_per_s": n_vis / ms_plain / 1e3, "batched_mvis_per_s": n_vis / ms_batch / 1e3,
+            "plain_ms": ms_plain, "batched_ms": ms_batch, "batched_over_plain": ms_plain / ms_batch,
+            "classes": classes, "plan_seconds": plan_s}
+
+
+def run_batched(args, world, rank, local):
+    """The uneven batch (config B): the same jobs gridded and degridded
+    (a) one after another with idg_grid / idg_degrid (plain per-job form) and
+    (b) as one batch: one persistent launch per subgrid size, subgrids kept in
+    shared memory, the launch sequence replayed from a CUDA graph."""
+    import torch
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    dev = torch.device("cuda", local)
     sampler = ClockSampler(local)
     sampler.start()
-    ms_plain = timed(plain_step, max(1, args.steps // 2))
-    ms_batch = timed(batch_step, args.steps)
+    args.jobs = args.jobs or 256
+    r = batched_compare(idg, syn, torch, dev, args.jobs, args.steps, args.warmup)
     clocks = sampler.stop()
-    info = batch.info()
     rec = {
-        "metric": "grid+degrid MVis/s (batched form vs plain per-job form)", "value": n_vis / ms_batch / 1e3,
+        "metric": "grid+degrid MVis/s (batched form vs plain per-job form)", "value": r["batched_mvis_per_s"],
         "unit": "MVis/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
-        "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"Batched uneven: {args.jobs} snapshot jobs, U{{12..64}} stations, U{{64..1024}} t, "
                                f"U{{4..32}} ch of 0.2 MHz in 100-200 MHz, 0-20% flags, L in {{16,24,32}}, "
-                               f"N in {{1024,2048,4096}}", "jobs": args.jobs, "n_vis": int(n_vis),
-                   "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
+                               f"N in {{1024,2048,4096}}", "jobs": args.jobs, "n_vis": r["n_vis"],
+                   "subgrids": r["subgrids"], "persistent_launches_per_direction": r["persistent_launches_per_direction"],
                    "graph": True, "l2": "inputs larger than L2, no flush"},
-        "plain_per_job": {"value": n_vis / ms_plain / 1e3, "unit": "MVis/s", "ms_per_step": ms_plain,
-                          "launches_per_step": None},
-        "batched_over_plain": ms_plain / ms_batch,
-        "clocks": clocks, "plan_seconds": plan_s,
+        "plain_per_job": {"value": r["plain_mvis_per_s"], "unit": "MVis/s", "ms_per_step": r["plain_ms"]},
+        "batched_over_plain": r["batched_over_plain"], "classes": r["classes"],
+        "clocks": clocks, "plan_seconds": r["plan_seconds"],
     }
     print(json.dumps(rec))
 
@@ -721,6 +902,7 @@ def run_serving(args, world, rank, local):
     torch.cuda.set_device(local)
     lib_build.build()
     idg.load()
+    args.jobs = args.jobs or 64
     wls = syn.make_batched_jobs(args.jobs, seed=1913)
     kinds = ("cycle", "grid", "degrid")
     sampler = ClockSampler(local)

@@ -211,6 +211,41 @@ idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d
                       idg_stream stream);
 
 /*
+ * Classical gridding with oversampled A/W-projection kernels (Sect. 2: the
+ * convolutional gridding the paper compares image domain gridding against),
+ * on the plan's subgrids, visibilities and grid layout, so the two can be set
+ * side by side on the same data.  For every subgrid p (baseline (p, q), A-term
+ * slot a) and W-projection plane j the call builds the kernel
+ *   window  c[(i,j),(a,b)](y, x) = b[y][x] exp(2 pi i j w_plane_step n') conj(A_p[a][i]) A_q[b][j]
+ *           on the support x support lattice l = (x - M/2) S / M (the gridding
+ *           direction's A_p^H X A_q as a 4 x 4 operator on XX, XY, YX, YY),
+ *   kernel  the window zero-padded to (M O)^2 and Fourier transformed:
+ *           C(dv, du) = M^-2 sum c[y][x] exp(-2 pi i (du (x - M/2) + dv (y - M/2)) / M),
+ *           tabulated at offsets d - M/2 + 1 - o / O (o = 0 .. O-1),
+ * and grids each unflagged visibility: position pu = (u f/c) S + N/2 (pv
+ * alike), support pixels floor(pu) - M/2 + 1 .. floor(pu) + M/2, table phase
+ * o = floor(frac(pu) O + 1/2) (o = O moves the support one pixel on), plane
+ * j = floor((w f/c - w0) / w_plane_step + 1/2) with w0 the subgrid's W-layer
+ * offset; grid[layer][r][q] += C . y_k, support pixels outside the grid are
+ * dropped.  Kernels are rebuilt for every subgrid, i.e. every A-term slot.
+ * support         M, even, 2 .. 32 (with the subgrid size: (L + M + 3)^2 x 32
+ *                 bytes of shared memory at most 200 KiB)
+ * oversample      O, 1 .. 128; one kernel (O^2 M^2 x 16 complex64) <= 256 MiB
+ * w_plane_step    >= 0 wavelengths; 0: no w-term in the kernels
+ * d_aterms        complex64 [n_slots][n_stations][M][M][4], the Jones matrices on
+ *                 the kernel lattice, or NULL (identity)
+ * d_taper         float32 [M][M] window b, or NULL for the PSWF window of width
+ *                 M: a_y a_x with a = idg_taper_window(M, M, IDG_TAPER_PSWF)
+ * d_grid          ADDED into, as idg_grid.
+ * Kernel tables take up to 2 GiB of stream-ordered scratch (chunks of subgrids);
+ * with w_plane_step > 0 the call first reads each subgrid's plane range back to
+ * the host (it synchronises `stream` once).
+ */
+idg_status idg_classical_grid(const idg_plan *plan, int support, int oversample, double w_plane_step,
+                              const void *d_vis, const uint8_t *d_flags, const void *d_aterms, const float *d_taper,
+                              void *d_grid, idg_stream stream);
+
+/*
  * Residuals, cost and A-term gradient for calibration (Sect. 6: image domain
  * gridding computes the residuals and derivatives of a fit whose free
  * parameters are the A-terms, with a full image -- here its grid -- as model).
@@ -407,13 +442,16 @@ void idg_batch_destroy(idg_batch *batch);
  *                residual kernel (64 B per planned visibility: model and
  *                observed read, residual written, flags aside) and gradient
  *                kernel (256 B per subgrid pixel: R, P, A_p, A_q read, two
- *                gradient entries read and written), subgrids for the FFT.
+ *                gradient entries read and written), subgrids for the FFT,
+ *                bytes of kernel tables written for the classical kernel
+ *                builder, visibility-support-pixel products (visibilities x M^2)
+ *                for the classical gridder.
  * Arrays have IDG_KERNEL_COUNT entries; any of them may be NULL.  Do not enable
  * timing while a stream is being captured into a CUDA graph.
  */
 enum { IDG_KERNEL_GRIDDER = 0, IDG_KERNEL_FFT, IDG_KERNEL_ADDER, IDG_KERNEL_SPLITTER, IDG_KERNEL_DEGRIDDER,
        IDG_KERNEL_BATCH_GRID, IDG_KERNEL_BATCH_DEGRID, IDG_KERNEL_CALIB_RESIDUAL, IDG_KERNEL_CALIB_GRADIENT,
-       IDG_KERNEL_COUNT };
+       IDG_KERNEL_CLASSICAL_KERNELS, IDG_KERNEL_CLASSICAL_GRID, IDG_KERNEL_COUNT };
 void idg_profile_enable(int on);
 idg_status idg_profile_read(int64_t *launches, double *ms, double *work, int reset);
 
@@ -466,8 +504,10 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
  * in a device word, waits (bounded) for its own operations in flight, releases
  * its tensor memory and leaves its outputs unwritten.  idg_device_errors
  * synchronises `stream`, reads and clears the words, and returns
- * IDG_ERR_TIMEOUT if any wait gave up since the last call (IDG_OK otherwise).
- * The words are per device and per process.
+ * IDG_ERR_TIMEOUT if any wait gave up since the last call, else
+ * IDG_ERR_DEVICE_CHECK if a device-side check failed (the classical gridder
+ * skipped a visibility whose support left its subgrid's tile, which a valid
+ * plan rules out), IDG_OK otherwise.  The words are per device and per process.
  */
 idg_status idg_device_errors(idg_stream stream);
 

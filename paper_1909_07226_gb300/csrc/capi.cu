@@ -228,7 +228,10 @@ idg_status idg_device_errors(idg_stream stream) {
     int code = 0;
     idg_status st = read_device_errors(&code, stream);
     if (st != IDG_OK) return st;
-    if (code) return fail(IDG_ERR_TIMEOUT, "a bounded wait of the tensor-core gridder gave up; its subgrids are invalid");
+    if (code & 1) return fail(IDG_ERR_TIMEOUT, "a bounded wait of a tensor-core kernel gave up; its outputs are invalid");
+    if (code & 2)
+        return fail(IDG_ERR_DEVICE_CHECK, "a device-side consistency check failed (classical gridder: a support "
+                                          "outside its subgrid's tile was skipped)");
     return IDG_OK;
 }
 

@@ -421,14 +421,15 @@ idg_status read_device_errors(int *code, void *stream) {
     e = cudaMemcpyFromSymbol(&mine, g_tc_error, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    int deg = 0, sep = 0, sepd = 0, self = 0;
+    int deg = 0, sep = 0, sepd = 0, self = 0, cl = 0;
     idg_status st = read_dft_error(&dft);
     if (st == IDG_OK) st = read_tcd_error(&deg);
     if (st == IDG_OK) st = read_sep_error(&sep);
     if (st == IDG_OK) st = read_sepd_error(&sepd);
     if (st == IDG_OK) st = read_selftest_error(&self);
+    if (st == IDG_OK) st = read_classical_error(&cl);
     if (st != IDG_OK) return st;
-    *code = mine | dft | deg | sep | sepd | self;
+    *code = mine | dft | deg | sep | sepd | self | cl;     // bit 0: a wait gave up; bit 1: a device check
     return IDG_OK;
 }
 

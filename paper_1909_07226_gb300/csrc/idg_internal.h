@@ -237,6 +237,18 @@ idg_status launch_calib_residual(const Geometry &g, const SubgridSet &set, const
 idg_status launch_calib_gradient(const Geometry &g, const SubgridSet &set, const void *R, const void *P,
                                  const void *aterms, const float *taper, void *grad, void *stream);
 
+// classical gridding with oversampled A/W-projection kernels (classical.cu)
+size_t classical_kernels_smem(int M, int O);
+size_t classical_grid_smem(int L, int M);
+idg_status launch_classical_planes(const Geometry &g, int64_t n_sub, double dw, struct int2 *range, void *stream);
+idg_status launch_classical_kernels(const Geometry &g, int M, int O, double dw, const float *taper,
+                                    const void *aterms, const double *nprime, const struct int2 *sets,
+                                    int64_t n_sets, void *tables, void *stream);
+idg_status launch_classical_grid(const Geometry &g, int M, int O, double dw, const struct int2 *work,
+                                 const int *jmin, int64_t count, const void *tables, const void *vis,
+                                 const uint8_t *flags, void *grid, void *stream);
+idg_status read_classical_error(int *code);
+
 // tensor-core subgrid transform (fft_mode = IDG_FFT_TC_SPLIT; L = 32)
 bool dft_tc_supported(int L);
 idg_status launch_dft_tc(int L, int64_t count, int direction, void *subgrids, void *stream);

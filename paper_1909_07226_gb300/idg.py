@@ -38,10 +38,11 @@ EXPORTED = [
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
     "idg_image_from_grid", "idg_grid_from_image", "idg_plan_set_kernel_variant", "idg_plan_get_kernel_variant",
     "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout", "idg_aterm_gradient",
+    "idg_classical_grid",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid", "calib_residual",
-           "calib_gradient"]
+           "calib_gradient", "classical_kernels", "classical_grid"]
 
 
 class IDGError(RuntimeError):
@@ -89,6 +90,7 @@ def load(path: str = LIB_PATH):
         "idg_grid_host": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_aterm_gradient": (I32, [P, P, P, P, P, P, P, P, P, P]),
+        "idg_classical_grid": (I32, [P, I32, I32, D, P, P, P, P, P, P]),
         "idg_degrid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_degrid_host": (I32, [P, P, P, P, P, P, P]),
         "idg_grid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
@@ -455,6 +457,23 @@ def aterm_gradient(plan: Plan, grid_in, vis, flags, aterms, taper, residual_out,
                                      _dptr(gradient, "gradient", torch.complex64, sh["aterms"]),
                                      _dptr(cost, "cost", torch.float64, (1,), True), _stream(stream)),
            "idg_aterm_gradient")
+
+
+def classical_grid(plan: Plan, support: int, oversample: int, w_plane_step: float, vis, flags, aterms, taper,
+                   grid_out, stream=None):
+    """idg_classical_grid: classical gridding with oversampled A/W-projection kernels
+    rebuilt per subgrid.  aterms: [n_slots][n_stations][M][M][4] on the kernel lattice
+    (or None); taper: [M][M] (or None for the PSWF window of width M)."""
+    import torch
+    sh = _shapes(plan)
+    M = int(support)
+    _check(load().idg_classical_grid(plan.handle, M, int(oversample), float(w_plane_step),
+                                     _dptr(vis, "vis", torch.complex64, sh["vis"]),
+                                     _dptr(flags, "flags", torch.uint8, sh["flags"], True),
+                                     _dptr(aterms, "aterms", torch.complex64, sh["aterms"][:2] + (M, M, 4), True),
+                                     _dptr(taper, "taper", torch.float32, (M, M), True),
+                                     _dptr(grid_out, "grid", torch.complex64, sh["grid"]), _stream(stream)),
+           "idg_classical_grid")
 
 
 def grid_range(plan: Plan, first: int, count: int, vis, flags, aterms, taper, grid_out, stream=None):
