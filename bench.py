@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the forms block of the default line")
+    ap.add_argument("--case", default=None, choices=["image", "classical", "calibration", "stages", "lofar_slice"],
+                    help="run one small profiling case alone (for ncu) instead of the benchmark")
     return ap.parse_args()
 
 
@@ -563,7 +565,7 @@ def run_gb300(args, world, rank, local):
             ent.update(achieved_vispix=d["work"] / (d["ms"] * 1e-3) / 1e9, vispix_unit="Gvispix/s")
         calib["kernels"][k] = ent
     calib["basis"] = ("one idg_aterm_gradient call: splitter, inverse transform and degridder (stage kernels), "
-                      "residual kernel (64 B per visibility), gridder of the residuals, gradient kernel (256 B per "
+                      "residual kernel (96 B per visibility), gridder of the residuals, gradient kernel (256 B per "
                       "subgrid pixel); MVis/s = visibilities per call / call time")
     del resid, agrad
 
@@ -1033,12 +1035,79 @@ def run_precision(args, world, rank, local):
     print(json.dumps(rec))
 
 
+def run_case(args, local):
+    """One small profiling case, run once after one warm-up: the block of the default
+    line named by --case, on a workload sized for an ncu capture (a few GB on the
+    device, inputs larger than L2).  Prints the case's own times."""
+    import torch
+    from paper_1909_07226_gb300 import build as lib_build
+    from paper_1909_07226_gb300 import idg
+    from paper_1909_07226_gb300 import synthetic as syn
+
+    torch.cuda.set_device(local)
+    lib_build.build()
+    idg.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    case = args.case
+    if case == "classical":
+        wl = syn.make_lofar(n_t=256, slot_len=16, name="precision")
+    else:
+        wl = syn.make_lofar(n_t=256)
+    plan = idg.plan_from_workload(wl)
+    vis = torch.from_numpy(wl.vis).to(dev)
+    at = torch.from_numpy(wl.aterms).to(dev)
+    tap = torch.from_numpy(wl.taper).to(dev)
+    shape = (plan.n_w_layers, wl.grid_size, wl.grid_size, 4)
+    model = torch.from_numpy(syn.random_grid(np.random.default_rng(7), plan.n_w_layers, wl.grid_size)).to(dev)
+    grid = torch.zeros(shape, dtype=torch.complex64, device=dev)
+    if case == "image":
+        win, _ = idg.taper_window(wl.subgrid_size, float(wl.kernel_size), idg.TAPER_PSWF)
+        img = torch.empty((wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
+        fns = [lambda: idg.image_from_grid(plan, model, win, img, stream),
+               lambda: idg.grid_from_image(plan, img, win, grid, stream)]
+    elif case == "classical":
+        M = CLASSICAL_SUPPORT
+        at_m = torch.from_numpy(syn.aterms_on_subgrid(wl.screens, M, wl.grid_size * wl.cell_size)
+                                .astype(np.complex64)).to(dev)
+        fns = [lambda: idg.classical_grid(plan, M, CLASSICAL_OVERSAMPLE, CLASSICAL_W_PLANE, vis, None, at_m, None,
+                                          grid, stream)]
+    elif case == "calibration":
+        resid = torch.empty_like(vis)
+        agrad = torch.zeros(at.shape, dtype=torch.complex64, device=dev)
+        fns = [lambda: idg.aterm_gradient(plan, model, vis, None, at, tap, resid, agrad, None, stream)]
+    elif case == "stages":
+        n = plan.n_subgrids
+        sub = torch.zeros((n, wl.subgrid_size, wl.subgrid_size, 4), dtype=torch.complex64, device=dev)
+        idg.grid_subgrids(plan, 0, n, vis, None, at, tap, sub, stream)
+        fns = [lambda: idg.add_subgrids(plan, 0, n, sub, grid, stream),
+               lambda: idg.split_subgrids(plan, 0, n, grid, sub, stream)]
+    else:                                   # lofar_slice: the composite calls the bench times
+        vout = torch.empty_like(vis)
+        fns = [lambda: idg.grid(plan, vis, None, at, tap, grid, stream),
+               lambda: idg.degrid(plan, model, None, at, tap, vout, stream)]
+    out = {}
+    for rep in range(2):
+        for i, fn in enumerate(fns):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[f"call{i}_ms"] = e0.elapsed_time(e1)
+    idg.device_errors(stream)
+    print(json.dumps({"case": case, "n_subgrids": plan.n_subgrids, "n_vis": int(wl.n_vis), **out}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.case:
+            run_case(args, local)
         elif args.config == "batched":
             run_batched(args, world, rank, local)
         elif args.config == "serving":

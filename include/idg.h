@@ -439,7 +439,7 @@ void idg_batch_destroy(idg_batch *batch);
  *                fused batch kernels (IDG_KERNEL_BATCH_*), bytes moved
  *                for the adder (read subgrid + read and write grid, 96 B per
  *                pixel), the splitter (64 B per pixel), the calibration's
- *                residual kernel (64 B per planned visibility: model and
+ *                residual kernel (96 B per planned visibility: model and
  *                observed read, residual written, flags aside) and gradient
  *                kernel (256 B per subgrid pixel: R, P, A_p, A_q read, two
  *                gradient entries read and written), subgrids for the FFT,

@@ -37,7 +37,9 @@ __global__ void __launch_bounds__(kResThreads) residual_kernel(Geometry g, const
                                                                float4 *__restrict__ res, double *cost) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     const DevSubgrid d = g.sub[sid];
-    double acc = 0.0;
+    // a thread's few terms summed in FP32 (at most 2048 / 256 visibilities of 8
+    // components), the block's sums in FP64 (FP64 is slow on this GPU: one use per thread)
+    float accf = 0.0f;
     const int n = d.nt * d.nc;
     for (int i = threadIdx.x; i < n; i += kResThreads) {
         const int t = d.t0 + i / d.nc, c = d.c0 + i % d.nc;
@@ -48,13 +50,14 @@ __global__ void __launch_bounds__(kResThreads) residual_kernel(Geometry g, const
             const float4 y0 = res[2 * v], y1 = res[2 * v + 1];
             r0 = make_float4(o0.x - y0.x, o0.y - y0.y, o0.z - y0.z, o0.w - y0.w);
             r1 = make_float4(o1.x - y1.x, o1.y - y1.y, o1.z - y1.z, o1.w - y1.w);
-            acc += (double)r0.x * r0.x + (double)r0.y * r0.y + (double)r0.z * r0.z + (double)r0.w * r0.w +
-                   (double)r1.x * r1.x + (double)r1.y * r1.y + (double)r1.z * r1.z + (double)r1.w * r1.w;
+            accf += r0.x * r0.x + r0.y * r0.y + r0.z * r0.z + r0.w * r0.w + r1.x * r1.x + r1.y * r1.y +
+                    r1.z * r1.z + r1.w * r1.w;
         }
         res[2 * v] = r0;
         res[2 * v + 1] = r1;
     }
     if (!cost) return;
+    double acc = (double)accf;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     __shared__ double s_acc[kResThreads / 32];
     if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;

@@ -846,7 +846,7 @@ idg_status idg_aterm_gradient(const idg_plan *p, const void *grid, const void *v
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_CALIB_RESIDUAL, s,
-                            64.0 * (double)(p->kp_prefix_order[f + cnt] - p->kp_prefix_order[f]));
+                            96.0 * (double)(p->kp_prefix_order[f + cnt] - p->kp_prefix_order[f]));
             st = launch_calib_residual(g, set, vis, flags, residual, cost, s);
         }
         if (st == IDG_OK) {

@@ -17,15 +17,23 @@
 // n' = sqrt(1 - l^2 - m^2) - 1 = -(l^2 + m^2) / (1 + sqrt(1 - l^2 - m^2)).
 //
 // For even N the centred transform is the plain one between (-1)^(x+y) and (-1)^(q+r)
-// checkerboards.  A 2D transform is four passes whose global accesses are all long
-// contiguous runs: a row transform, a tiled transpose (32 x 32 pixels through shared
-// memory), a second row transform (now along the other axis, in place) and a tiled
-// transpose back, which applies the output factor and the accumulation over layers.  A row
-// transform takes two CTAs per line, each holding two of the line's polarisations in
-// shared memory (2 N complex values and N / 2 twiddles, about 80 KB at N = 4096, two CTAs
-// per SM): bit-reversed loads into a padded layout (one slot per 128, free of bank
-// conflicts), then log2 N radix-2 stages.  The input factor is applied on the first
-// row pass.  N is a power of two, 32 .. 4096.
+// checkerboards.  A 2D transform is three passes over the image, each reading and
+// writing it once with long contiguous runs:
+//   rows      one CTA per image row (all four polarisations): the N-point transform
+//             along x in shared memory, with the input factor applied on the load;
+//   columns   the N-point transform along y as N = N1 N2 (four-step):
+//     A       one CTA per (y2, block of 16 columns): the N1-point transforms over
+//             y1 of the rows y1 N2 + y2, times exp(SIGN 2 pi i y2 k1 / N), written
+//             back to the same rows (k1 N2 + y2);
+//     B       one CTA per (k1, block of 16 columns): the N2-point transforms over
+//             y2 of the contiguous rows k1 N2 + y2, written to rows k1 + N1 k2 with
+//             the output factor (and the accumulation over w-layers).
+// Every line transform is decimation in frequency with radix-16 steps (radix 8, 4
+// or 2 for the last): a thread takes R elements of a line, forms their R-point
+// transform in registers and applies the twiddles, so an N-point transform costs
+// ceil(log16 N) barriers; the result is in digit-reversed order and is read back
+// by index.  Twiddles come from tables of exp(SIGN 2 pi i t / n) built once per CTA
+// with sincospif of exact fractions.  N is a power of two, 32 .. 4096.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,15 +46,14 @@
 namespace idg {
 namespace {
 
-constexpr int kImgThreads = 512;
-constexpr int kLines = 2;                 // polarisations per CTA of a row transform
-constexpr int kTile = 32;                 // transpose tile (pixels)
-constexpr int kPer = 4096 / kImgThreads;  // line elements per thread at the largest N
+constexpr int kRowThreads = 512;
+constexpr int kColThreads = 256;
+constexpr int kColBlock = 16;             // image columns per CTA of a column pass
 
-// pointwise factor of pixel (x, y): on the way into the first row pass, or in the final transpose
+// pointwise factor of pixel (x, y): on the way into the row pass, or out of the last column pass
 struct PixOp {
     int mode;            // 0: (-1)^(x+y) only (uv side); 1: the image-side factor; 2: none
-    int accumulate;      // column pass: add into the output instead of overwriting
+    int accumulate;      // last pass: add into the output instead of overwriting
     float w0_2pi;        // 2 pi w0 of the layer (image side)
     float sign;          // +1 gridding side (exp(+i ...)), -1 degridding side
     float S;             // image size in direction cosines
@@ -84,104 +91,233 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// padded shared-memory slot of element i of a line (one spare slot per 128)
-__device__ __forceinline__ int pad(int i) { return i + (i >> 7); }
+// shared-memory slot of element i of a line: one spare slot per 16 and one per 256, so that
+// the strided and the digit-reversed accesses of the 4096-point transform spread over banks
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4) + (i >> 8); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + (n >> 8) + 1; }
 
-// In-place radix-2 transform of the kLines lines buf[line][pad(N)] (bit-reversed on entry),
-// X[j] = sum_n x[n] exp(SIGN 2 pi i n j / N); tw[t] = exp(SIGN 2 pi i t / N), t < N / 2.
-template <int SIGN>
-__device__ __forceinline__ void fft_lines(float2 *buf, const float2 *tw, int N, int logN, int stride_line) {
-    const int half_n = N >> 1;
-    for (int lh = 0; lh < logN; ++lh) {
-        const int half = 1 << lh;
-        const int stride = half_n >> lh;             // twiddle index step for groups of 2 half
-        for (int t = threadIdx.x; t < kLines * half_n; t += blockDim.x) {
-            const int pol = t >> (logN - 1), b = t & (half_n - 1);
-            const int j = b & (half - 1);
-            const int i0 = ((b - j) << 1) + j, i1 = i0 + half;
-            float2 *line = buf + pol * stride_line;
-            const float2 u = line[pad(i0)], v = cmulf(line[pad(i1)], tw[j * stride]);
-            line[pad(i0)] = make_float2(u.x + v.x, u.y + v.y);
-            line[pad(i1)] = make_float2(u.x - v.x, u.y - v.y);
+// cos(pi m / 8), m = 0 .. 8
+__device__ __forceinline__ float cos16(int m) {
+    switch (m) {
+    case 0: return 1.0f;
+    case 1: return 0.92387953251128675613f;
+    case 2: return 0.70710678118654752440f;
+    case 3: return 0.38268343236508977173f;
+    case 4: return 0.0f;
+    case 5: return -0.38268343236508977173f;
+    case 6: return -0.70710678118654752440f;
+    case 7: return -0.92387953251128675613f;
+    default: return -1.0f;
+    }
+}
+
+// R-point transform of x in registers (R = 2, 4, 8, 16), X[k] = sum_j x[j] exp(SIGN 2 pi i j k / R),
+// in natural order: radix-2 decimation in frequency with constant twiddles, then the
+// bit-reversal as a register renaming
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int b = 0; b < R; b += 2 * h) {
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float2 u = x[b + i], v = x[b + i + h];
+                x[b + i] = make_float2(u.x + v.x, u.y + v.y);
+                const float2 d = make_float2(u.x - v.x, u.y - v.y);
+                const int m = i * (16 / (2 * h));           // angle 2 pi i / (2 h) = pi m / 8
+                if (m == 0) {
+                    x[b + i + h] = d;
+                } else {
+                    // exp(SIGN i pi m / 8): cos(pi m / 8) and sin(pi m / 8) = cos(pi |4 - m| / 8)
+                    const float c = cos16(m), sn = (float)SIGN * cos16(m < 4 ? 4 - m : m - 4);
+                    x[b + i + h] = make_float2(d.x * c - d.y * sn, d.x * sn + d.y * c);
+                }
+            }
         }
+    }
+    float2 y[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        int r = 0;
+#pragma unroll
+        for (int b = 1, q = R >> 1; b < R; b <<= 1, q >>= 1)
+            if (k & b) r |= q;
+        y[k] = x[r];
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = y[k];
+}
+
+__device__ __forceinline__ int radix_of(int len) { return len >= 16 ? 16 : len; }
+
+// one radix-R decimation-in-frequency step over n_lines lines of length n (stride
+// stride_line): sub-transforms of length len, h = len / R; tw[t] = exp(SIGN 2 pi i t / n)
+template <int R>
+__device__ __forceinline__ void dif_step(float2 *buf, int n_lines, int n, int len, int stride_line, const float2 *tw,
+                                         int tid, int nthreads, int sign) {
+    const int h = len / R;
+    const int gpl = n / R;
+    const int step_base = n / len;
+    for (int t = tid; t < n_lines * gpl; t += nthreads) {
+        const int line = t / gpl, g = t - line * gpl;
+        const int b = g / h, i = g - b * h;
+        float2 *L = buf + line * stride_line;
+        const int base = b * len + i;
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = L[pad(base + j * h)];
+        if (sign > 0)
+            dft_reg<R, 1>(v);
+        else
+            dft_reg<R, -1>(v);
+        const int st = i * step_base;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const float2 w = k ? tw[(k * st) & (n - 1)] : make_float2(1.0f, 0.0f);
+            L[pad(base + k * h)] = k ? cmulf(v[k], w) : v[k];
+        }
+    }
+}
+
+// the whole n-point transform of every line (natural order in, digit-reversed out)
+__device__ __forceinline__ void fft_dif_lines(float2 *buf, int n_lines, int n, int stride_line, const float2 *tw,
+                                              int tid, int nthreads, int sign) {
+    for (int len = n; len > 1;) {
+        const int R = radix_of(len);
+        switch (R) {
+        case 16: dif_step<16>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
+        case 8: dif_step<8>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
+        case 4: dif_step<4>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
+        default: dif_step<2>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
+        }
+        len /= R;
         __syncthreads();
     }
 }
 
-template <int SIGN>
-__device__ __forceinline__ void twiddles(float2 *tw, int N) {
-    for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+// position of frequency f in the digit-reversed output of fft_dif_lines
+__device__ __forceinline__ int dif_pos(int f, int n) {
+    int pos = 0;
+    for (int len = n; len > 1;) {
+        const int R = radix_of(len), h = len / R;
+        pos += (f & (R - 1)) * h;
+        f >>= (R == 16 ? 4 : R == 8 ? 3 : R == 4 ? 2 : 1);
+        len = h;
+    }
+    return pos;
+}
+
+__device__ __forceinline__ void twiddle_table(float2 *tw, int n, int sign) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
         float s, c;
-        sincospif(SIGN * 2.0f * (float)t / (float)N, &s, &c);    // t / N exact for N a power of two
+        sincospif((float)sign * 2.0f * (float)t / (float)n, &s, &c);    // t / n exact for n a power of two
         tw[t] = make_float2(c, s);
     }
 }
 
-// CTA 2 y + h (line y, polarisations 2 h, 2 h + 1): out[y][x][2h..] = transform over x of
-// (in[y][x][2h..] * pre(x, y)); in place when in == out (the line is read whole first)
+// row pass: CTA y transforms row y along x (four polarisation lines); in -> out, pre on the load
 template <int SIGN>
-__global__ void __launch_bounds__(kImgThreads)
-image_rows_kernel(const float4 *in, float4 *out, int N, int logN, PixOp pre) {
+__global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *__restrict__ in,
+                                                                 float4 *__restrict__ out, int N, PixOp pre) {
     extern __shared__ float2 img_smem[];
-    const int stride_line = pad(N - 1) + 1;
-    float2 *buf = img_smem, *tw = img_smem + kLines * stride_line;
-    const int y = blockIdx.x >> 1, h = blockIdx.x & 1;
-    twiddles<SIGN>(tw, N);
-    const float4 *row = in + (size_t)y * N * 2 + h;
-    // all of the thread's loads first (up to kPer in flight), then the stores
-    float4 v[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int x = threadIdx.x + i * kImgThreads;
-        if (x < N) v[i] = row[2 * x];
-    }
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int x = threadIdx.x + i * kImgThreads;
-        if (x < N) {
-            const float2 f = pix_factor(pre, x, y, N);
-            const int rx = pad((int)(__brev((unsigned)x) >> (32 - logN)));
-            buf[rx] = cmulf(make_float2(v[i].x, v[i].y), f);
-            buf[stride_line + rx] = cmulf(make_float2(v[i].z, v[i].w), f);
-        }
+    const int sl = padded_len(N);
+    float2 *buf = img_smem, *tw = img_smem + 4 * sl;
+    const int y = blockIdx.x;
+    twiddle_table(tw, N, SIGN);
+    const float4 *row = in + (size_t)y * N * 2;
+    for (int x = threadIdx.x; x < N; x += kRowThreads) {
+        const float4 a = row[2 * x], b = row[2 * x + 1];
+        const float2 f = pix_factor(pre, x, y, N);
+        const int px = pad(x);
+        buf[px] = cmulf(make_float2(a.x, a.y), f);
+        buf[sl + px] = cmulf(make_float2(a.z, a.w), f);
+        buf[2 * sl + px] = cmulf(make_float2(b.x, b.y), f);
+        buf[3 * sl + px] = cmulf(make_float2(b.z, b.w), f);
     }
     __syncthreads();
-    fft_lines<SIGN>(buf, tw, N, logN, stride_line);
-    float4 *orow = out + (size_t)y * N * 2 + h;
-    for (int x = threadIdx.x; x < N; x += blockDim.x) {
-        const float2 p0 = buf[pad(x)], p1 = buf[stride_line + pad(x)];
+    fft_dif_lines(buf, 4, N, sl, tw, threadIdx.x, kRowThreads, SIGN);
+    float4 *orow = out + (size_t)y * N * 2;
+    for (int x = threadIdx.x; x < N; x += kRowThreads) {
+        const int px = pad(dif_pos(x, N));
+        const float2 p0 = buf[px], p1 = buf[sl + px], p2 = buf[2 * sl + px], p3 = buf[3 * sl + px];
         orow[2 * x] = make_float4(p0.x, p0.y, p1.x, p1.y);
+        orow[2 * x + 1] = make_float4(p2.x, p2.y, p3.x, p3.y);
     }
 }
 
-// out[r][c] (+)= post(x = c, y = r) * in[c][r] for 32-byte pixels, one 32 x 32 tile per CTA
-// (32 x 8 threads), staged through shared memory so that reads and writes are contiguous
-__global__ void __launch_bounds__(kTile * 8)
-image_transpose_kernel(const float4 *__restrict__ in, float4 *__restrict__ out, int N, PixOp post) {
-    __shared__ float4 tile[kTile][kTile + 1][2];
-    const int tx = threadIdx.x & (kTile - 1), ty = threadIdx.x >> 5;
-    const int c0 = blockIdx.x * kTile, r0 = blockIdx.y * kTile;      // output tile origin
-    float4 ld[kTile / 8][2];
-#pragma unroll
-    for (int i = 0; i < kTile / 8; ++i) {        // input rows c0 + ty + 8 i, columns r0 + tx
-        const float4 *p = in + ((size_t)(c0 + ty + 8 * i) * N + (r0 + tx)) * 2;
-        ld[i][0] = p[0];
-        ld[i][1] = p[1];
-    }
-#pragma unroll
-    for (int i = 0; i < kTile / 8; ++i) {
-        tile[ty + 8 * i][tx][0] = ld[i][0];
-        tile[ty + 8 * i][tx][1] = ld[i][1];
+// column pass A (four-step, N = N1 N2): CTA (y2, column block) transforms over y1 the
+// rows y1 N2 + y2 of kColBlock columns (4 kColBlock lines of N1 points), multiplies
+// output k1 by exp(SIGN 2 pi i y2 k1 / N) and writes it to row k1 N2 + y2 (in place)
+template <int SIGN>
+__global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__restrict__ img, int N, int N1, int N2) {
+    extern __shared__ float2 img_smem[];
+    const int sl = padded_len(N1);
+    constexpr int NL = 4 * kColBlock;
+    float2 *buf = img_smem, *tw = img_smem + NL * sl;
+    const int nb = N / kColBlock;
+    const int y2 = blockIdx.x / nb, c0 = (blockIdx.x % nb) * kColBlock;
+    twiddle_table(tw, N1, SIGN);
+    for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
+        const int y1 = t / kColBlock, c = t % kColBlock;
+        const float4 *p = img + ((size_t)(y1 * N2 + y2) * N + c0 + c) * 2;
+        const float4 a = p[0], b = p[1];
+        const int py = pad(y1);
+        buf[(4 * c + 0) * sl + py] = make_float2(a.x, a.y);
+        buf[(4 * c + 1) * sl + py] = make_float2(a.z, a.w);
+        buf[(4 * c + 2) * sl + py] = make_float2(b.x, b.y);
+        buf[(4 * c + 3) * sl + py] = make_float2(b.z, b.w);
     }
     __syncthreads();
-#pragma unroll
-    for (int k = ty; k < kTile; k += 8) {        // output row r0 + k, column c0 + tx
-        const int r = r0 + k, c = c0 + tx;
-        const float2 f = pix_factor(post, c, r, N);
-        const float4 a = tile[tx][k][0], b = tile[tx][k][1];
-        const float2 q0 = cmulf(make_float2(a.x, a.y), f), q1 = cmulf(make_float2(a.z, a.w), f);
-        const float2 q2 = cmulf(make_float2(b.x, b.y), f), q3 = cmulf(make_float2(b.z, b.w), f);
-        float4 *o = out + ((size_t)r * N + c) * 2;
+    fft_dif_lines(buf, NL, N1, sl, tw, threadIdx.x, kColThreads, SIGN);
+    for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
+        const int k1 = t / kColBlock, c = t % kColBlock;
+        const int pk = pad(dif_pos(k1, N1));
+        float s, co;
+        sincospif((float)SIGN * 2.0f * (float)((y2 * k1) & (N - 1)) / (float)N, &s, &co);
+        const float2 w = make_float2(co, s);
+        const float2 p0 = cmulf(buf[(4 * c + 0) * sl + pk], w), p1 = cmulf(buf[(4 * c + 1) * sl + pk], w);
+        const float2 p2 = cmulf(buf[(4 * c + 2) * sl + pk], w), p3 = cmulf(buf[(4 * c + 3) * sl + pk], w);
+        float4 *o = img + ((size_t)(k1 * N2 + y2) * N + c0 + c) * 2;
+        o[0] = make_float4(p0.x, p0.y, p1.x, p1.y);
+        o[1] = make_float4(p2.x, p2.y, p3.x, p3.y);
+    }
+}
+
+// column pass B: CTA (k1, column block) transforms over y2 the contiguous rows k1 N2 + y2
+// and writes frequency k = k1 + N1 k2 to row k of out, times post(x, k) (added with
+// accumulate)
+template <int SIGN>
+__global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 *__restrict__ img,
+                                                                   float4 *__restrict__ out, int N, int N1, int N2,
+                                                                   PixOp post) {
+    extern __shared__ float2 img_smem[];
+    const int sl = padded_len(N2);
+    constexpr int NL = 4 * kColBlock;
+    float2 *buf = img_smem, *tw = img_smem + NL * sl;
+    const int nb = N / kColBlock;
+    const int k1 = blockIdx.x / nb, c0 = (blockIdx.x % nb) * kColBlock;
+    twiddle_table(tw, N2, SIGN);
+    for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
+        const int y2 = t / kColBlock, c = t % kColBlock;
+        const float4 *p = img + ((size_t)(k1 * N2 + y2) * N + c0 + c) * 2;
+        const float4 a = p[0], b = p[1];
+        const int py = pad(y2);
+        buf[(4 * c + 0) * sl + py] = make_float2(a.x, a.y);
+        buf[(4 * c + 1) * sl + py] = make_float2(a.z, a.w);
+        buf[(4 * c + 2) * sl + py] = make_float2(b.x, b.y);
+        buf[(4 * c + 3) * sl + py] = make_float2(b.z, b.w);
+    }
+    __syncthreads();
+    if (N2 > 1) fft_dif_lines(buf, NL, N2, sl, tw, threadIdx.x, kColThreads, SIGN);
+    for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
+        const int k2 = t / kColBlock, c = t % kColBlock;
+        const int pk = pad(N2 > 1 ? dif_pos(k2, N2) : 0);
+        const int y = k1 + N1 * k2, x = c0 + c;
+        const float2 f = pix_factor(post, x, y, N);
+        const float2 q0 = cmulf(buf[(4 * c + 0) * sl + pk], f), q1 = cmulf(buf[(4 * c + 1) * sl + pk], f);
+        const float2 q2 = cmulf(buf[(4 * c + 2) * sl + pk], f), q3 = cmulf(buf[(4 * c + 3) * sl + pk], f);
+        float4 *o = out + ((size_t)y * N + x) * 2;
         float4 v0 = make_float4(q0.x, q0.y, q1.x, q1.y), v1 = make_float4(q2.x, q2.y, q3.x, q3.y);
         if (post.accumulate) {
             const float4 u0 = o[0], u1 = o[1];
@@ -193,19 +329,26 @@ image_transpose_kernel(const float4 *__restrict__ in, float4 *__restrict__ out, 
     }
 }
 
+void split_n(int N, int &N1, int &N2) {
+    int logN = 0;
+    while ((1 << logN) < N) ++logN;
+    N1 = 1 << ((logN + 1) / 2);
+    N2 = N / N1;
+}
+
+size_t rows_smem(int N) { return (size_t)(4 * padded_len(N) + N) * sizeof(float2); }
+size_t cols_smem(int n) { return (size_t)(4 * kColBlock * padded_len(n) + n) * sizeof(float2); }
+
 // in -> out: pre on the way in, the 2D transform of sign SIGN, post on the way out
 template <int SIGN>
-cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, float4 *s2, int N, int logN, const PixOp &pre,
-                        const PixOp &post, cudaStream_t s) {
-    const int stride_line = (N - 1) + ((N - 1) >> 7) + 1;
-    const size_t smem = (size_t)(kLines * stride_line + N / 2) * sizeof(float2);
-    const PixOp none = {2, 0, 0.0f, 1.0f, 0.0f, nullptr};
-    const dim3 tiles(N / kTile, N / kTile);
-    PixOp mid = none;
-    image_rows_kernel<SIGN><<<2 * N, kImgThreads, smem, s>>>(in, s1, N, logN, pre);          // along x
-    image_transpose_kernel<<<tiles, kTile * 8, 0, s>>>(s1, s2, N, mid);                      // s2[x][y]
-    image_rows_kernel<SIGN><<<2 * N, kImgThreads, smem, s>>>(s2, s2, N, logN, none);         // along y
-    image_transpose_kernel<<<tiles, kTile * 8, 0, s>>>(s2, out, N, post);                    // out[y][x]
+cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, int N, const PixOp &pre, const PixOp &post,
+                        cudaStream_t s) {
+    int N1, N2;
+    split_n(N, N1, N2);
+    const int nb = N / kColBlock;
+    image_rows_kernel<SIGN><<<N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre);                  // along x
+    image_cols_a_kernel<SIGN><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);          // y1
+    image_cols_b_kernel<SIGN><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);  // y2
     return cudaGetLastError();
 }
 
@@ -272,11 +415,10 @@ std::vector<float> effective_window(const double *a, int L, int N) {
 
 struct ImageBufs {
     cudaStream_t s;
-    void *s1 = nullptr, *s2 = nullptr, *cbar = nullptr;
+    void *s1 = nullptr, *cbar = nullptr;
     explicit ImageBufs(cudaStream_t st) : s(st) {}
     ~ImageBufs() {
         if (s1) cudaFreeAsync(s1, s);
-        if (s2) cudaFreeAsync(s2, s);
         if (cbar) cudaFreeAsync(cbar, s);
     }
 };
@@ -292,17 +434,23 @@ idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev != p->device) return fail(IDG_ERR_INVALID_ARG, "the plan was created on another device");
-    const int stride_line = (N - 1) + ((N - 1) >> 7) + 1;
-    const size_t smem = (size_t)(kLines * stride_line + N / 2) * sizeof(float2);
-    e = cudaFuncSetAttribute(image_rows_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_rows_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "image transform shared-memory attribute");
+    {
+        int N1, N2;
+        split_n(N, N1, N2);
+        const int rs = (int)rows_smem(N), ca = (int)cols_smem(N1), cb = (int)cols_smem(N2);
+        e = cudaFuncSetAttribute(image_rows_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_rows_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+        if (e != cudaSuccess) return cuda_fail(e, "image transform shared-memory attribute");
+    }
     if (h_window) {
         for (int j = 0; j < p->L; ++j)
             if (!std::isfinite(h_window[j])) return fail(IDG_ERR_INVALID_ARG, "the window must be finite");
     }
     idg_status st = scratch_alloc(dev, (size_t)N * N * 32, s, &bufs.s1);
-    if (st == IDG_OK) st = scratch_alloc(dev, (size_t)N * N * 32, s, &bufs.s2);
     if (st != IDG_OK) return st;
     if (h_window) {
         const std::vector<float> cb = effective_window(h_window, p->L, N);
@@ -338,7 +486,7 @@ idg_status idg_image_from_grid(const idg_plan *p, const void *d_grid, const doub
         const PixOp pre = {0, 0, 0.0f, 1.0f, (float)p->S, nullptr};
         const PixOp post = {1, k > 0, (float)(6.283185307179586 * w0), 1.0f, (float)p->S, (const float2 *)bufs.cbar};
         const float4 *g = (const float4 *)d_grid + (size_t)k * N * N * 2;
-        cudaError_t e = transform2d<+1>(g, (float4 *)d_image, (float4 *)bufs.s1, (float4 *)bufs.s2, N, logN, pre, post, s);
+        cudaError_t e = transform2d<+1>(g, (float4 *)d_image, (float4 *)bufs.s1, N, pre, post, s);
         if (e != cudaSuccess) return cuda_fail(e, "image transform launch");
     }
     return IDG_OK;
@@ -357,7 +505,7 @@ idg_status idg_grid_from_image(const idg_plan *p, const void *d_image, const dou
         const PixOp pre = {1, 0, (float)(6.283185307179586 * w0), -1.0f, (float)p->S, (const float2 *)bufs.cbar};
         const PixOp post = {0, 0, 0.0f, -1.0f, (float)p->S, nullptr};
         float4 *g = (float4 *)d_grid + (size_t)k * N * N * 2;
-        cudaError_t e = transform2d<-1>((const float4 *)d_image, g, (float4 *)bufs.s1, (float4 *)bufs.s2, N, logN, pre, post, s);
+        cudaError_t e = transform2d<-1>((const float4 *)d_image, g, (float4 *)bufs.s1, N, pre, post, s);
         if (e != cudaSuccess) return cuda_fail(e, "image transform launch");
     }
     return IDG_OK;

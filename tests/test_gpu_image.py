@@ -101,3 +101,26 @@ def test_image_steps_reject_unsupported_sizes_and_bad_windows():
         idg.image_from_grid(p2, g2, a[:-1], img2)
     with pytest.raises(idg.IDGError):
         idg.image_from_grid(p2, g2, np.full(16, np.nan), img2)
+
+
+@pytest.mark.parametrize("N", [32, 64, 128, 512, 1024, 2048, 4096])
+def test_transform_sizes(N):
+    # every transform size the image steps support (radix-16 line transforms with a
+    # smaller last radix, four-step columns N = N1 N2), both directions, against the
+    # oracle (without the window division: the transform is what is tested here)
+    import torch
+    L = 16 if N < 64 else 32
+    # (an image of width S = 0.5 in direction cosines keeps every pixel inside the unit circle)
+    wl = syn.make_small(seed=7, n_st=4, n_t=4, n_chan=2, L=L, N=N, aterms="identity", max_t=4, with_vis=False,
+                        cell=0.5 / N)
+    a = None
+    p = idg.plan_from_workload(wl)
+    S = N * wl.cell_size
+    rng = np.random.default_rng(N)
+    G = (rng.standard_normal((1, N, N, 4)) + 1j * rng.standard_normal((1, N, N, 4))).astype(np.complex64)
+    img = torch.empty((N, N, 4), dtype=torch.complex64, device="cuda")
+    idg.image_from_grid(p, dev(G), a, img)
+    parity(img.cpu().numpy(), OI.image_from_grid(G, S, [0.0], a, L), f"image_from_grid N={N}")
+    g = torch.empty((1, N, N, 4), dtype=torch.complex64, device="cuda")
+    idg.grid_from_image(p, dev(G[0]), a, g)
+    parity(g.cpu().numpy(), OI.grid_from_image(G[0], S, [0.0], a, L), f"grid_from_image N={N}")
