@@ -421,6 +421,40 @@ def run_gb300(args, world, rank, local):
     ms_step = ms_total / args.steps
     value = whole_job_rate(world, ms_local * 1e-3, float(wl.n_vis) * args.steps) / 1e6
 
+    # end to end through the host-buffer C-ABI calls (measured right after the device-buffer
+    # steps, before the blocks below fill the device with their own buffers)
+    with near_gpu_memory(local) as placement:
+        vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+        vis_h.copy_(torch.from_numpy(wl.vis))
+        model_p = torch.empty(model.shape, dtype=torch.complex64, pin_memory=True)
+        model_p.copy_(torch.from_numpy(model_h))
+        grid_h = torch.empty(grid.shape, dtype=torch.complex64, pin_memory=True)
+        grid_h.zero_()
+        visout_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
+        visout_h.zero_()
+    aterms_h = torch.from_numpy(wl.aterms)
+    taper_h = torch.from_numpy(wl.taper)
+    flags_h = None if wl.flags is None else torch.from_numpy(wl.flags)
+
+    def e2e_step():
+        idg.grid_host(plan, vis_h, flags_h, aterms_h, taper_h, grid_h, stream)
+        idg.degrid_host(plan, model_p, flags_h, aterms_h, taper_h, visout_h, stream)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_value = whole_job_rate(world, time.perf_counter() - t0, float(wl.n_vis) * args.e2e_steps) / 1e6
+    nvis = wl.n_vis
+    fl = 0 if wl.flags is None else wl.flags.nbytes
+    # grid_host: visibilities, flags, A-terms, taper in, grid out;
+    # degrid_host: model grid, flags, A-terms, taper in, visibilities out
+    h2d = (nvis * 32 + fl + wl.aterms.nbytes + wl.taper.nbytes) + (model_h.nbytes + fl + wl.aterms.nbytes + wl.taper.nbytes)
+    d2h = grid_h.numel() * 8 + nvis * 32
+
     # kernels: achieved against their rooflines
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
@@ -588,39 +622,6 @@ def run_gb300(args, world, rank, local):
                                                          "batched_over_plain", "classes")},
                  "serving_50_per_s": serving_point(idg, syn, torch),
                  "precision_errors": precision_errors(idg, syn, torch, dev, stream)}
-
-    # end to end through the host-buffer C-ABI calls
-    with near_gpu_memory(local) as placement:
-        vis_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
-        vis_h.copy_(torch.from_numpy(wl.vis))
-        model_p = torch.empty(model.shape, dtype=torch.complex64, pin_memory=True)
-        model_p.copy_(torch.from_numpy(model_h))
-        grid_h = torch.empty(grid.shape, dtype=torch.complex64, pin_memory=True)
-        grid_h.zero_()
-        visout_h = torch.empty(vis.shape, dtype=torch.complex64, pin_memory=True)
-        visout_h.zero_()
-    aterms_h = torch.from_numpy(wl.aterms)
-    taper_h = torch.from_numpy(wl.taper)
-    flags_h = None if wl.flags is None else torch.from_numpy(wl.flags)
-
-    def e2e_step():
-        idg.grid_host(plan, vis_h, flags_h, aterms_h, taper_h, grid_h, stream)
-        idg.degrid_host(plan, model_p, flags_h, aterms_h, taper_h, visout_h, stream)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_value = whole_job_rate(world, time.perf_counter() - t0, float(wl.n_vis) * args.e2e_steps) / 1e6
-    nvis = wl.n_vis
-    fl = 0 if wl.flags is None else wl.flags.nbytes
-    # grid_host: visibilities, flags, A-terms, taper in, grid out;
-    # degrid_host: model grid, flags, A-terms, taper in, visibilities out
-    h2d = (nvis * 32 + fl + wl.aterms.nbytes + wl.taper.nbytes) + (model_h.nbytes + fl + wl.aterms.nbytes + wl.taper.nbytes)
-    d2h = grid_h.numel() * 8 + nvis * 32
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -820,6 +821,7 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
             idg.degrid(p, b["grid"], b["flags"], None, b["taper"], b["vis_out"], stream)
 
     batch = idg.Batch(plans, bufs, graph=True)
+    trials = batch.autotune(stream)             # the batch's own shapes per class (trials add into the grids)
 
     def batch_step():
         for b in bufs:
@@ -852,7 +854,7 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
     return {"n_vis": int(n_vis), "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
             "plain_mvis_per_s": n_vis / ms_plain / 1e3, "batched_mvis_per_s": n_vis / ms_batch / 1e3,
             "plain_ms": ms_plain, "batched_ms": ms_batch, "batched_over_plain": ms_plain / ms_batch,
-            "classes": classes, "plan_seconds": plan_s}
+            "classes": classes, "plan_seconds": plan_s, "autotune_trial_ms": trials}
 
 
 def run_batched(args, world, rank, local):

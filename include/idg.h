@@ -425,6 +425,15 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
 idg_status idg_batch_grid(idg_batch *batch, idg_stream stream);
 idg_status idg_batch_degrid(idg_batch *batch, idg_stream stream);
 idg_status idg_batch_info(const idg_batch *batch, int64_t *n_vis, int64_t *n_items, int *n_launches);
+/* The batch's own autotuner: for every class that runs a persistent kernel (not
+ * the tensor-core classes) and each direction, times one launch of every compiled
+ * shape (pixels per thread, visibilities per thread, block size, CTAs per SM) on
+ * `stream` and keeps the fastest for this batch; recorded graphs are dropped and
+ * recorded again on the next call.  The trial launches ADD into the jobs' grids
+ * and overwrite their vis_out: zero the grids after tuning.  ms[i] receives the
+ * trial times in order (classes, grid then degrid, shapes) for i < cap (ms may be
+ * NULL).  Synchronises `stream`. */
+idg_status idg_batch_autotune(idg_batch *batch, double *ms, int cap, idg_stream stream);
 void idg_batch_destroy(idg_batch *batch);
 
 /*

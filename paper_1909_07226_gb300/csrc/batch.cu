@@ -591,6 +591,77 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
     return IDG_OK;
 }
 
+// resident CTAs per SM x SMs for a persistent shape, never more than the items
+static idg_status persistent_blocks(const KernelShape &ks, int n_sm, int64_t n_items, int *blocks) {
+    cudaError_t e = cudaFuncSetAttribute(ks.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks.smem);
+    int per_sm = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.fn, ks.threads, ks.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel occupancy");
+    *blocks = (int)std::min<int64_t>(std::max(1, per_sm) * (int64_t)n_sm, std::max<int64_t>(1, n_items));
+    return IDG_OK;
+}
+
+idg_status idg_batch_autotune(idg_batch *b, double *ms, int cap, idg_stream stream) {
+    if (!b) return fail(IDG_ERR_INVALID_ARG, "batch is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != b->device) return fail(IDG_ERR_INVALID_ARG, "the batch belongs to another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+        return cuda_fail(e, "batch autotune events");
+    idg_status st = IDG_OK;
+    int slot = 0;
+    for (size_t c = 0; c < b->classes.size() && st == IDG_OK; ++c) {
+        auto &cl = b->classes[c];
+        for (int dir = 0; dir < 2 && st == IDG_OK; ++dir) {
+            KernelShape &cur = dir ? cl.degrid : cl.grid;
+            int &cur_blocks = dir ? cl.degrid_blocks : cl.grid_blocks;
+            if (cl.n_items == 0 || cur.tc) continue;     // the tensor-core classes have one shape
+            const auto shapes = dir ? degrid_shapes(cl.L) : grid_shapes(cl.L);
+            double best_ms = 1e300;
+            for (const KernelShape &x : shapes) {
+                if (x.tc) continue;
+                int blocks = 0;
+                if ((st = persistent_blocks(x, n_sm, cl.n_items, &blocks)) != IDG_OK) break;
+                const JobDev *jobs = b->d_jobs;
+                const int2 *items = cl.d_items;
+                int n_items = (int)cl.n_items;
+                int *counter = b->d_counters + c;
+                void *args[] = {(void *)&jobs, (void *)&items, (void *)&n_items, (void *)&counter};
+                float t = 0.f;
+                for (int rep = 0; rep < 2 && st == IDG_OK; ++rep) {      // one warm-up, one timed launch
+                    e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+                    if (e == cudaSuccess && rep) e = cudaEventRecord(e0, s);
+                    if (e == cudaSuccess) e = cudaLaunchKernel(x.fn, dim3(blocks), dim3(x.threads), args, x.smem, s);
+                    if (e == cudaSuccess && rep) e = cudaEventRecord(e1, s);
+                    if (e == cudaSuccess && rep) e = cudaEventSynchronize(e1);
+                    if (e == cudaSuccess && rep) e = cudaEventElapsedTime(&t, e0, e1);
+                    if (e != cudaSuccess) st = cuda_fail(e, "batch autotune trial");
+                }
+                if (st != IDG_OK) break;
+                if (ms && slot < cap) ms[slot] = t;
+                ++slot;
+                if (t < best_ms) {
+                    best_ms = t;
+                    cur = x;
+                    cur_blocks = blocks;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // recorded graphs hold the previous shapes
+    if (b->graph_grid) cudaGraphExecDestroy(b->graph_grid);
+    if (b->graph_degrid) cudaGraphExecDestroy(b->graph_degrid);
+    b->graph_grid = b->graph_degrid = nullptr;
+    return st;
+}
+
 idg_status idg_batch_grid(idg_batch *b, idg_stream stream) { return batch_run(b, false, stream); }
 
 idg_status idg_batch_degrid(idg_batch *b, idg_stream stream) { return batch_run(b, true, stream); }

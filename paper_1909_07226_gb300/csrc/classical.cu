@@ -142,30 +142,51 @@ __global__ void __launch_bounds__(kKThreads) classical_kernels_kernel(Geometry g
                 tx[t] = acc;
             }
             __syncthreads();
-            // along y, every phase oy: table[oy][ox][dy][dx][e0 ..]
-            for (int t = threadIdx.x; t < O * MM; t += kKThreads) {
-                const int oy = t / MM, dy = (t / M) % M, dx = t % M;
-                const int n = O * (dy - M / 2 + 1) - oy;
-                int k = tw_start(n, M, MO);
-                const int dk = tw_step(n, MO);
-                float2 acc[EG];
+            // along y, every phase oy: table[oy][ox][dy][dx][e0 ..].  A thread takes 4 phases x
+            // 4 entries of one support pixel, so each window value and twiddle it loads from
+            // shared memory serves 4 multiply-adds (the loop is then bound by the FMA pipe)
+            const int n_o4 = (O + 3) / 4;              // phase quads (the last one partial when 4 does not divide O)
+            for (int t = threadIdx.x; t < n_o4 * MM * (EG / 4); t += kKThreads) {
+                const int e4 = t % (EG / 4), pix = (t / (EG / 4)) % MM, o4 = t / ((EG / 4) * MM);
+                const int dy = pix / M, dx = pix % M;
+                int k[4], dk[4];
 #pragma unroll
-                for (int e = 0; e < EG; ++e) acc[e] = make_float2(0.f, 0.f);
-                for (int y = 0; y < M; ++y) {
-                    const float2 w = tw[k];
-                    k += dk;
-                    k -= k >= MO ? MO : 0;
-#pragma unroll
-                    for (int e = 0; e < EG; ++e) {
-                        const float2 c = tx[(e * M + y) * M + dx];
-                        acc[e].x += c.x * w.x - c.y * w.y;
-                        acc[e].y += c.x * w.y + c.y * w.x;
-                    }
+                for (int a = 0; a < 4; ++a) {
+                    const int n = O * (dy - M / 2 + 1) - (4 * o4 + a);
+                    k[a] = tw_start(n, M, MO);
+                    dk[a] = tw_step(n, MO);
                 }
-                float4 *dst = (float4 *)(out + ((((size_t)oy * O + ox) * MM + dy * M + dx) * 16 + e0));
+                float2 acc[4][4];
 #pragma unroll
-                for (int e = 0; e < EG; e += 2)
-                    dst[e / 2] = make_float4(norm * acc[e].x, norm * acc[e].y, norm * acc[e + 1].x, norm * acc[e + 1].y);
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[a][e] = make_float2(0.f, 0.f);
+                for (int y = 0; y < M; ++y) {
+                    float2 c[4], w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) c[e] = tx[((4 * e4 + e) * M + y) * M + dx];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        w[a] = tw[k[a]];
+                        k[a] += dk[a];
+                        k[a] -= k[a] >= MO ? MO : 0;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            acc[a][e].x += c[e].x * w[a].x - c[e].y * w[a].y;
+                            acc[a][e].y += c[e].x * w[a].y + c[e].y * w[a].x;
+                        }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int oy = 4 * o4 + a;
+                    if (oy >= O) break;
+                    float4 *dst = (float4 *)(out + ((((size_t)oy * O + ox) * MM + pix) * 16 + e0 + 4 * e4));
+                    dst[0] = make_float4(norm * acc[a][0].x, norm * acc[a][0].y, norm * acc[a][1].x, norm * acc[a][1].y);
+                    dst[1] = make_float4(norm * acc[a][2].x, norm * acc[a][2].y, norm * acc[a][3].x, norm * acc[a][3].y);
+                }
             }
         }
     }

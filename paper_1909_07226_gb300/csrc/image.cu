@@ -46,7 +46,7 @@
 namespace idg {
 namespace {
 
-constexpr int kRowThreads = 512;
+constexpr int kRowThreads = 256;
 constexpr int kColThreads = 256;
 constexpr int kColBlock = 16;             // image columns per CTA of a column pass
 
@@ -90,11 +90,6 @@ __device__ __forceinline__ float2 pix_factor(const PixOp &op, int x, int y, int 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-
-// shared-memory slot of element i of a line: one spare slot per 16 and one per 256, so that
-// the strided and the digit-reversed accesses of the 4096-point transform spread over banks
-__device__ __forceinline__ int pad(int i) { return i + (i >> 4) + (i >> 8); }
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + (n >> 8) + 1; }
 
 // cos(pi m / 8), m = 0 .. 8
 __device__ __forceinline__ float cos16(int m) {
@@ -149,48 +144,79 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
     for (int k = 0; k < R; ++k) x[k] = y[k];
 }
 
-__device__ __forceinline__ int radix_of(int len) { return len >= 16 ? 16 : len; }
+__host__ __device__ __forceinline__ int radix_of(int len) { return len >= 16 ? 16 : len; }
 
-// one radix-R decimation-in-frequency step over n_lines lines of length n (stride
-// stride_line): sub-transforms of length len, h = len / R; tw[t] = exp(SIGN 2 pi i t / n)
-template <int R>
-__device__ __forceinline__ void dif_step(float2 *buf, int n_lines, int n, int len, int stride_line, const float2 *tw,
-                                         int tid, int nthreads, int sign) {
+// Shared-memory layout of a CTA's lines: position-major, the NL lines of a position
+// adjacent, so that a thread's polarisations sit together and the threads of a warp
+// (lines fastest) touch consecutive words.  With PAD, position p sits at slot
+// p + p/16 + p/256, which spreads the strided and the digit-reversed accesses of
+// the long row transforms over the banks.
+template <bool PAD>
+__host__ __device__ __forceinline__ int slot(int p) { return PAD ? p + (p >> 4) + (p >> 8) : p; }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + (n >> 8) + 1; }
+
+// Twiddles of every step of an n-point transform, step by step: a step of radix R over
+// sub-transforms of length len (h = len / R) holds exp(SIGN 2 pi i i k / len) for
+// k = 1 .. R - 1 and i = 0 .. h - 1 at (k - 1) h + i, so that the threads of a warp
+// (consecutive i) read consecutive entries.  n - 1 entries in all.
+__device__ __forceinline__ void step_twiddles(float2 *tw, int n, int sign, int tid, int nthreads) {
+    int off = 0;
+    for (int len = n; len > 1;) {
+        const int R = radix_of(len), h = len / R;
+        for (int t = tid; t < (R - 1) * h; t += nthreads) {
+            const int k = t / h + 1, i = t - (k - 1) * h;
+            const int e = (i * k * (n / len)) & (n - 1);        // exp(sign 2 pi i e / n), e / n exact
+            float s, c;
+            sincospif((float)sign * 2.0f * (float)e / (float)n, &s, &c);
+            tw[off + t] = make_float2(c, s);
+        }
+        off += (R - 1) * h;
+        len = h;
+    }
+}
+
+// the step twiddles of an n-point transform into global memory (once per call, read by
+// every CTA of the row pass through the cache)
+__global__ void __launch_bounds__(256) step_twiddles_kernel(float2 *tw, int n, int sign) {
+    step_twiddles(tw, n, sign, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// one radix-R decimation-in-frequency step over the NL lines of length n: sub-transforms
+// of length len, h = len / R; tws: this step's twiddles
+template <int R, int NL, bool PAD>
+__device__ __forceinline__ void dif_step(float2 *buf, int n, int len, const float2 *tws, int sign) {
     const int h = len / R;
     const int gpl = n / R;
-    const int step_base = n / len;
-    for (int t = tid; t < n_lines * gpl; t += nthreads) {
-        const int line = t / gpl, g = t - line * gpl;
+    for (int t = threadIdx.x; t < NL * gpl; t += blockDim.x) {
+        const int line = t % NL, g = t / NL;
         const int b = g / h, i = g - b * h;
-        float2 *L = buf + line * stride_line;
         const int base = b * len + i;
         float2 v[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) v[j] = L[pad(base + j * h)];
+        for (int j = 0; j < R; ++j) v[j] = buf[slot<PAD>(base + j * h) * NL + line];
         if (sign > 0)
             dft_reg<R, 1>(v);
         else
             dft_reg<R, -1>(v);
-        const int st = i * step_base;
 #pragma unroll
-        for (int k = 0; k < R; ++k) {
-            const float2 w = k ? tw[(k * st) & (n - 1)] : make_float2(1.0f, 0.0f);
-            L[pad(base + k * h)] = k ? cmulf(v[k], w) : v[k];
-        }
+        for (int k = 0; k < R; ++k)      // (tws is shared memory in the column passes, global in the row pass)
+            buf[slot<PAD>(base + k * h) * NL + line] = k ? cmulf(v[k], tws[(k - 1) * h + i]) : v[k];
     }
 }
 
-// the whole n-point transform of every line (natural order in, digit-reversed out)
-__device__ __forceinline__ void fft_dif_lines(float2 *buf, int n_lines, int n, int stride_line, const float2 *tw,
-                                              int tid, int nthreads, int sign) {
+// the whole n-point transform of the NL lines (natural order in, digit-reversed out)
+template <int NL, bool PAD>
+__device__ __forceinline__ void fft_dif_lines(float2 *buf, int n, const float2 *tw, int sign) {
+    int off = 0;
     for (int len = n; len > 1;) {
         const int R = radix_of(len);
         switch (R) {
-        case 16: dif_step<16>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
-        case 8: dif_step<8>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
-        case 4: dif_step<4>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
-        default: dif_step<2>(buf, n_lines, n, len, stride_line, tw, tid, nthreads, sign); break;
+        case 16: dif_step<16, NL, PAD>(buf, n, len, tw + off, sign); break;
+        case 8: dif_step<8, NL, PAD>(buf, n, len, tw + off, sign); break;
+        case 4: dif_step<4, NL, PAD>(buf, n, len, tw + off, sign); break;
+        default: dif_step<2, NL, PAD>(buf, n, len, tw + off, sign); break;
         }
+        off += (R - 1) * (len / R);
         len /= R;
         __syncthreads();
     }
@@ -208,42 +234,29 @@ __device__ __forceinline__ int dif_pos(int f, int n) {
     return pos;
 }
 
-__device__ __forceinline__ void twiddle_table(float2 *tw, int n, int sign) {
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        float s, c;
-        sincospif((float)sign * 2.0f * (float)t / (float)n, &s, &c);    // t / n exact for n a power of two
-        tw[t] = make_float2(c, s);
-    }
-}
-
-// row pass: CTA y transforms row y along x (four polarisation lines); in -> out, pre on the load
+// row pass: CTA 2 y + hp transforms row y along x for polarisations 2 hp and 2 hp + 1
+// (half of each 32-byte pixel; the other CTA of the row reads the other half of the
+// same sectors); in -> out, pre on the load.  Two CTAs fit an SM, so one CTA's loads
+// and stores overlap the other's transform.
 template <int SIGN>
 __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *__restrict__ in,
-                                                                 float4 *__restrict__ out, int N, PixOp pre) {
-    extern __shared__ float2 img_smem[];
-    const int sl = padded_len(N);
-    float2 *buf = img_smem, *tw = img_smem + 4 * sl;
-    const int y = blockIdx.x;
-    twiddle_table(tw, N, SIGN);
-    const float4 *row = in + (size_t)y * N * 2;
+                                                                 float4 *__restrict__ out, int N, PixOp pre,
+                                                                 const float2 *__restrict__ tw) {
+    extern __shared__ float4 img_smem4[];
+    float4 *buf4 = img_smem4;                                     // [slot(N)] x (2 polarisations)
+    float2 *buf = (float2 *)img_smem4;
+    const int y = blockIdx.x >> 1, hp = blockIdx.x & 1;
+    const float4 *row = in + (size_t)y * N * 2 + hp;
     for (int x = threadIdx.x; x < N; x += kRowThreads) {
-        const float4 a = row[2 * x], b = row[2 * x + 1];
+        const float4 a = row[2 * x];
         const float2 f = pix_factor(pre, x, y, N);
-        const int px = pad(x);
-        buf[px] = cmulf(make_float2(a.x, a.y), f);
-        buf[sl + px] = cmulf(make_float2(a.z, a.w), f);
-        buf[2 * sl + px] = cmulf(make_float2(b.x, b.y), f);
-        buf[3 * sl + px] = cmulf(make_float2(b.z, b.w), f);
+        const float2 p0 = cmulf(make_float2(a.x, a.y), f), p1 = cmulf(make_float2(a.z, a.w), f);
+        buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
     }
     __syncthreads();
-    fft_dif_lines(buf, 4, N, sl, tw, threadIdx.x, kRowThreads, SIGN);
-    float4 *orow = out + (size_t)y * N * 2;
-    for (int x = threadIdx.x; x < N; x += kRowThreads) {
-        const int px = pad(dif_pos(x, N));
-        const float2 p0 = buf[px], p1 = buf[sl + px], p2 = buf[2 * sl + px], p3 = buf[3 * sl + px];
-        orow[2 * x] = make_float4(p0.x, p0.y, p1.x, p1.y);
-        orow[2 * x + 1] = make_float4(p2.x, p2.y, p3.x, p3.y);
-    }
+    fft_dif_lines<2, true>(buf, N, tw, SIGN);
+    float4 *orow = out + (size_t)y * N * 2 + hp;
+    for (int x = threadIdx.x; x < N; x += kRowThreads) orow[2 * x] = buf4[slot<true>(dif_pos(x, N))];
 }
 
 // column pass A (four-step, N = N1 N2): CTA (y2, column block) transforms over y1 the
@@ -251,33 +264,35 @@ __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *_
 // output k1 by exp(SIGN 2 pi i y2 k1 / N) and writes it to row k1 N2 + y2 (in place)
 template <int SIGN>
 __global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__restrict__ img, int N, int N1, int N2) {
-    extern __shared__ float2 img_smem[];
-    const int sl = padded_len(N1);
+    extern __shared__ float4 img_smem4[];
     constexpr int NL = 4 * kColBlock;
-    float2 *buf = img_smem, *tw = img_smem + NL * sl;
+    float4 *buf4 = img_smem4;                       // [N1][NL]: position-major, 16 pixels of 4 polarisations
+    float2 *buf = (float2 *)img_smem4;
+    float2 *tw = buf + NL * N1;
     const int nb = N / kColBlock;
     const int y2 = blockIdx.x / nb, c0 = (blockIdx.x % nb) * kColBlock;
-    twiddle_table(tw, N1, SIGN);
+    float2 *w4 = tw + N1;                           // exp(SIGN 2 pi i y2 k1 / N), k1 < N1
+    step_twiddles(tw, N1, SIGN, threadIdx.x, blockDim.x);
+    for (int k1 = threadIdx.x; k1 < N1; k1 += blockDim.x) {
+        float s, co;
+        sincospif((float)SIGN * 2.0f * (float)((y2 * k1) & (N - 1)) / (float)N, &s, &co);
+        w4[k1] = make_float2(co, s);
+    }
     for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
         const int y1 = t / kColBlock, c = t % kColBlock;
         const float4 *p = img + ((size_t)(y1 * N2 + y2) * N + c0 + c) * 2;
-        const float4 a = p[0], b = p[1];
-        const int py = pad(y1);
-        buf[(4 * c + 0) * sl + py] = make_float2(a.x, a.y);
-        buf[(4 * c + 1) * sl + py] = make_float2(a.z, a.w);
-        buf[(4 * c + 2) * sl + py] = make_float2(b.x, b.y);
-        buf[(4 * c + 3) * sl + py] = make_float2(b.z, b.w);
+        buf4[(y1 * NL + 4 * c) / 2] = p[0];
+        buf4[(y1 * NL + 4 * c) / 2 + 1] = p[1];
     }
     __syncthreads();
-    fft_dif_lines(buf, NL, N1, sl, tw, threadIdx.x, kColThreads, SIGN);
+    fft_dif_lines<NL, false>(buf, N1, tw, SIGN);
     for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
         const int k1 = t / kColBlock, c = t % kColBlock;
-        const int pk = pad(dif_pos(k1, N1));
-        float s, co;
-        sincospif((float)SIGN * 2.0f * (float)((y2 * k1) & (N - 1)) / (float)N, &s, &co);
-        const float2 w = make_float2(co, s);
-        const float2 p0 = cmulf(buf[(4 * c + 0) * sl + pk], w), p1 = cmulf(buf[(4 * c + 1) * sl + pk], w);
-        const float2 p2 = cmulf(buf[(4 * c + 2) * sl + pk], w), p3 = cmulf(buf[(4 * c + 3) * sl + pk], w);
+        const int q = (dif_pos(k1, N1) * NL + 4 * c) / 2;
+        const float2 w = w4[k1];
+        const float4 a = buf4[q], b = buf4[q + 1];
+        const float2 p0 = cmulf(make_float2(a.x, a.y), w), p1 = cmulf(make_float2(a.z, a.w), w);
+        const float2 p2 = cmulf(make_float2(b.x, b.y), w), p3 = cmulf(make_float2(b.z, b.w), w);
         float4 *o = img + ((size_t)(k1 * N2 + y2) * N + c0 + c) * 2;
         o[0] = make_float4(p0.x, p0.y, p1.x, p1.y);
         o[1] = make_float4(p2.x, p2.y, p3.x, p3.y);
@@ -291,32 +306,30 @@ template <int SIGN>
 __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 *__restrict__ img,
                                                                    float4 *__restrict__ out, int N, int N1, int N2,
                                                                    PixOp post) {
-    extern __shared__ float2 img_smem[];
-    const int sl = padded_len(N2);
+    extern __shared__ float4 img_smem4[];
     constexpr int NL = 4 * kColBlock;
-    float2 *buf = img_smem, *tw = img_smem + NL * sl;
+    float4 *buf4 = img_smem4;
+    float2 *buf = (float2 *)img_smem4;
+    float2 *tw = buf + NL * N2;
     const int nb = N / kColBlock;
     const int k1 = blockIdx.x / nb, c0 = (blockIdx.x % nb) * kColBlock;
-    twiddle_table(tw, N2, SIGN);
+    step_twiddles(tw, N2, SIGN, threadIdx.x, blockDim.x);
     for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
         const int y2 = t / kColBlock, c = t % kColBlock;
         const float4 *p = img + ((size_t)(k1 * N2 + y2) * N + c0 + c) * 2;
-        const float4 a = p[0], b = p[1];
-        const int py = pad(y2);
-        buf[(4 * c + 0) * sl + py] = make_float2(a.x, a.y);
-        buf[(4 * c + 1) * sl + py] = make_float2(a.z, a.w);
-        buf[(4 * c + 2) * sl + py] = make_float2(b.x, b.y);
-        buf[(4 * c + 3) * sl + py] = make_float2(b.z, b.w);
+        buf4[(y2 * NL + 4 * c) / 2] = p[0];
+        buf4[(y2 * NL + 4 * c) / 2 + 1] = p[1];
     }
     __syncthreads();
-    if (N2 > 1) fft_dif_lines(buf, NL, N2, sl, tw, threadIdx.x, kColThreads, SIGN);
+    fft_dif_lines<NL, false>(buf, N2, tw, SIGN);
     for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
         const int k2 = t / kColBlock, c = t % kColBlock;
-        const int pk = pad(N2 > 1 ? dif_pos(k2, N2) : 0);
+        const int q = (dif_pos(k2, N2) * NL + 4 * c) / 2;
         const int y = k1 + N1 * k2, x = c0 + c;
         const float2 f = pix_factor(post, x, y, N);
-        const float2 q0 = cmulf(buf[(4 * c + 0) * sl + pk], f), q1 = cmulf(buf[(4 * c + 1) * sl + pk], f);
-        const float2 q2 = cmulf(buf[(4 * c + 2) * sl + pk], f), q3 = cmulf(buf[(4 * c + 3) * sl + pk], f);
+        const float4 a = buf4[q], b = buf4[q + 1];
+        const float2 q0 = cmulf(make_float2(a.x, a.y), f), q1 = cmulf(make_float2(a.z, a.w), f);
+        const float2 q2 = cmulf(make_float2(b.x, b.y), f), q3 = cmulf(make_float2(b.z, b.w), f);
         float4 *o = out + ((size_t)y * N + x) * 2;
         float4 v0 = make_float4(q0.x, q0.y, q1.x, q1.y), v1 = make_float4(q2.x, q2.y, q3.x, q3.y);
         if (post.accumulate) {
@@ -336,17 +349,18 @@ void split_n(int N, int &N1, int &N2) {
     N2 = N / N1;
 }
 
-size_t rows_smem(int N) { return (size_t)(4 * padded_len(N) + N) * sizeof(float2); }
-size_t cols_smem(int n) { return (size_t)(4 * kColBlock * padded_len(n) + n) * sizeof(float2); }
+size_t rows_smem(int N) { return (size_t)(2 * padded_len(N)) * sizeof(float2); }
+size_t cols_smem(int n) { return (size_t)(4 * kColBlock * n + 2 * n) * sizeof(float2); }
 
 // in -> out: pre on the way in, the 2D transform of sign SIGN, post on the way out
 template <int SIGN>
-cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, int N, const PixOp &pre, const PixOp &post,
-                        cudaStream_t s) {
+cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, float2 *tw, int N, const PixOp &pre,
+                        const PixOp &post, cudaStream_t s) {
     int N1, N2;
     split_n(N, N1, N2);
     const int nb = N / kColBlock;
-    image_rows_kernel<SIGN><<<N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre);                  // along x
+    step_twiddles_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N, SIGN);
+    image_rows_kernel<SIGN><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);          // along x
     image_cols_a_kernel<SIGN><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);          // y1
     image_cols_b_kernel<SIGN><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);  // y2
     return cudaGetLastError();
@@ -415,11 +429,12 @@ std::vector<float> effective_window(const double *a, int L, int N) {
 
 struct ImageBufs {
     cudaStream_t s;
-    void *s1 = nullptr, *cbar = nullptr;
+    void *s1 = nullptr, *cbar = nullptr, *tw = nullptr;
     explicit ImageBufs(cudaStream_t st) : s(st) {}
     ~ImageBufs() {
         if (s1) cudaFreeAsync(s1, s);
         if (cbar) cudaFreeAsync(cbar, s);
+        if (tw) cudaFreeAsync(tw, s);
     }
 };
 
@@ -451,6 +466,7 @@ idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, 
             if (!std::isfinite(h_window[j])) return fail(IDG_ERR_INVALID_ARG, "the window must be finite");
     }
     idg_status st = scratch_alloc(dev, (size_t)N * N * 32, s, &bufs.s1);
+    if (st == IDG_OK) st = scratch_alloc(dev, sizeof(float2) * N, s, &bufs.tw);
     if (st != IDG_OK) return st;
     if (h_window) {
         const std::vector<float> cb = effective_window(h_window, p->L, N);
@@ -486,7 +502,7 @@ idg_status idg_image_from_grid(const idg_plan *p, const void *d_grid, const doub
         const PixOp pre = {0, 0, 0.0f, 1.0f, (float)p->S, nullptr};
         const PixOp post = {1, k > 0, (float)(6.283185307179586 * w0), 1.0f, (float)p->S, (const float2 *)bufs.cbar};
         const float4 *g = (const float4 *)d_grid + (size_t)k * N * N * 2;
-        cudaError_t e = transform2d<+1>(g, (float4 *)d_image, (float4 *)bufs.s1, N, pre, post, s);
+        cudaError_t e = transform2d<+1>(g, (float4 *)d_image, (float4 *)bufs.s1, (float2 *)bufs.tw, N, pre, post, s);
         if (e != cudaSuccess) return cuda_fail(e, "image transform launch");
     }
     return IDG_OK;
@@ -505,7 +521,8 @@ idg_status idg_grid_from_image(const idg_plan *p, const void *d_image, const dou
         const PixOp pre = {1, 0, (float)(6.283185307179586 * w0), -1.0f, (float)p->S, (const float2 *)bufs.cbar};
         const PixOp post = {0, 0, 0.0f, -1.0f, (float)p->S, nullptr};
         float4 *g = (float4 *)d_grid + (size_t)k * N * N * 2;
-        cudaError_t e = transform2d<-1>((const float4 *)d_image, g, (float4 *)bufs.s1, N, pre, post, s);
+        cudaError_t e = transform2d<-1>((const float4 *)d_image, g, (float4 *)bufs.s1, (float2 *)bufs.tw, N, pre,
+                                        post, s);
         if (e != cudaSuccess) return cuda_fail(e, "image transform launch");
     }
     return IDG_OK;

@@ -38,7 +38,7 @@ EXPORTED = [
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
     "idg_image_from_grid", "idg_grid_from_image", "idg_plan_set_kernel_variant", "idg_plan_get_kernel_variant",
     "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout", "idg_aterm_gradient",
-    "idg_classical_grid",
+    "idg_classical_grid", "idg_batch_autotune",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid", "calib_residual",
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
         "idg_batch_grid": (I32, [P, P]),
         "idg_batch_degrid": (I32, [P, P]),
         "idg_batch_info": (I32, [P, P, P, P]),
+        "idg_batch_autotune": (I32, [P, P, I32, P]),
         "idg_batch_destroy": (None, [P]),
         "idg_device_errors": (I32, [P]),
         "idg_selftest_wait_timeout": (I32, [I64, P]),
@@ -640,6 +641,15 @@ class Batch:
 
     def degrid(self, stream=None):
         _check(load().idg_batch_degrid(self.handle, _stream(stream)), "idg_batch_degrid")
+
+    def autotune(self, stream=None):
+        """idg_batch_autotune: keep the fastest persistent shape per class and direction
+        (the trial launches add into the grids: zero them afterwards).  Returns the
+        trial times in milliseconds."""
+        cap = 256
+        ms = (ctypes.c_double * cap)(*([-1.0] * cap))
+        _check(load().idg_batch_autotune(self.handle, ms, cap, _stream(stream)), "idg_batch_autotune")
+        return [ms[i] for i in range(cap) if ms[i] >= 0]
 
     def info(self):
         nv, ni, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()

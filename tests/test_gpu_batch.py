@@ -151,3 +151,29 @@ def test_batch_separable_and_direct_l32_classes():
     idg.device_errors()
     for i, (w, op, j, m) in enumerate(zip(wls, ops, jobs, models)):
         parity(j["vis_out"].cpu().numpy(), O.degrid(w, op, m), f"l32 classes degrid job {i}")
+
+
+def test_batch_autotune_keeps_results():
+    # the batch's autotuner times every persistent shape of every class, keeps the
+    # fastest, and the batch (graph recorded again) still matches the oracle
+    import torch
+    wls = jobs_mix()
+    plans = [idg.plan_from_workload(w) for w in wls]
+    ops = [O.plan(w) for w in wls]
+    jobs = []
+    for w, p in zip(wls, plans):
+        d = workload_to_device(w)
+        jobs.append(dict(vis=d["vis"], flags=d["flags"], aterms=d["aterms"], taper=d["taper"],
+                         grid=torch.zeros((p.n_w_layers, w.grid_size, w.grid_size, 4), dtype=torch.complex64,
+                                          device="cuda"),
+                         vis_out=torch.zeros(w.vis.shape, dtype=torch.complex64, device="cuda")))
+    b = idg.Batch(plans, jobs, graph=True)
+    b.grid()                                 # records the graph with the default shapes
+    trials = b.autotune()
+    assert len(trials) >= 4 and all(t > 0 for t in trials)
+    for j in jobs:
+        j["grid"].zero_()
+    b.grid()
+    torch.cuda.synchronize()
+    for i, (w, op, j) in enumerate(zip(wls, ops, jobs)):
+        parity(j["grid"].cpu().numpy(), O.grid(w, op), f"batch grid job {i} after autotune")

@@ -34,6 +34,10 @@ CASES = {
                                             flag_p=0.15, diameter_m=15000.0), 8, 8, 4.0, True),
     "L16_M6_O32_wlayers": (dict(seed=93, n_st=5, n_t=16, n_chan=3, L=16, N=64, max_t=8, n_slots=2, w_step=20.0,
                                 diameter_m=20000.0), 6, 32, 2.0, True),
+    # the widest support (the builder takes the Mueller entries 4 at a time) and an
+    # oversampling that 4 does not divide
+    "L32_M32_O6": (dict(seed=95, n_st=4, n_t=8, n_chan=2, L=32, N=128, max_t=8, n_slots=1, diameter_m=3000.0),
+                   32, 6, 0.0, True),
     # subgrids on the first grid row: supports reach past the grid and are clipped
     "L32_M16_O4_grid_edge": (dict(seed=94, n_st=5, n_t=12, n_chan=3, L=32, N=96, max_t=12, n_slots=1,
                                   diameter_m=4000.0, cell=3.4529525903487945e-4), 16, 4, 0.0, True),
