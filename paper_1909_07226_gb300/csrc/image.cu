@@ -123,6 +123,16 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
                 const int m = i * (16 / (2 * h));           // angle 2 pi i / (2 h) = pi m / 8
                 if (m == 0) {
                     x[b + i + h] = d;
+                } else if (m == 4) {                        // exp(SIGN i pi / 2) = SIGN i
+                    x[b + i + h] = SIGN > 0 ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+                } else if (m == 2) {                        // (1 + SIGN i) / sqrt 2
+                    const float r = 0.70710678118654752440f;
+                    x[b + i + h] = SIGN > 0 ? make_float2(r * (d.x - d.y), r * (d.y + d.x))
+                                            : make_float2(r * (d.x + d.y), r * (d.y - d.x));
+                } else if (m == 6) {                        // (-1 + SIGN i) / sqrt 2
+                    const float r = 0.70710678118654752440f;
+                    x[b + i + h] = SIGN > 0 ? make_float2(-r * (d.x + d.y), r * (d.x - d.y))
+                                            : make_float2(r * (d.y - d.x), -r * (d.y + d.x));
                 } else {
                     // exp(SIGN i pi m / 8): cos(pi m / 8) and sin(pi m / 8) = cos(pi |4 - m| / 8)
                     const float c = cos16(m), sn = (float)SIGN * cos16(m < 4 ? 4 - m : m - 4);
