@@ -5,8 +5,8 @@ subgrid images, taper and A-terms, subgrid FFT, adder into a zeroed grid)
 followed by idg_degrid (splitter, subgrid IFFT, taper and A-terms, degridder)
 from a model grid.  value = visibilities / (time of grid + degrid) in MVis/s,
 with inputs resident in device memory.  e2e = the same metric through the
-host-buffer C-ABI calls (idg_grid_host, idg_degrid_host) with the copies from
-and to page-locked host memory inside the timed region.
+host-buffer C-ABI call that runs both directions (idg_grid_degrid_host) with the
+copies from and to page-locked host memory inside the timed region.
 
 Default workload: the LOFAR-like configuration (48 stations, 1128 baselines,
 4096 x 1 s, 16 channels 130-146 MHz, 73.9 M visibilities, subgrid 32, grid
@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the forms block of the default line")
+    ap.add_argument("--step-only", action="store_true",
+                    help="the grid + degrid step and its end-to-end number only: skip the image, calibration, "
+                         "classical, stages and forms blocks of the default line")
     ap.add_argument("--shard", action="store_true",
                     help="with several ranks: split one plan's subgrids over them (one all-reduce per direction) "
                          "instead of running replicas")
@@ -450,8 +453,8 @@ def run_gb300(args, world, rank, local):
     flags_h = None if wl.flags is None else torch.from_numpy(wl.flags)
 
     def e2e_step():
-        idg.grid_host(plan, vis_h, flags_h, aterms_h, taper_h, grid_h, stream)
-        idg.degrid_host(plan, model_p, flags_h, aterms_h, taper_h, visout_h, stream)
+        # both directions in one pipelined call: the grid copies overlap the other direction
+        idg.grid_degrid_host(plan, vis_h, model_p, flags_h, aterms_h, taper_h, grid_h, visout_h, stream)
 
     e2e_step()
     torch.cuda.synchronize()
@@ -463,9 +466,8 @@ def run_gb300(args, world, rank, local):
     e2e_value = whole_job_rate(world, time.perf_counter() - t0, float(wl.n_vis) * args.e2e_steps) / 1e6
     nvis = wl.n_vis
     fl = 0 if wl.flags is None else wl.flags.nbytes
-    # grid_host: visibilities, flags, A-terms, taper in, grid out;
-    # degrid_host: model grid, flags, A-terms, taper in, visibilities out
-    h2d = (nvis * 32 + fl + wl.aterms.nbytes + wl.taper.nbytes) + (model_h.nbytes + fl + wl.aterms.nbytes + wl.taper.nbytes)
+    # in: visibilities, model grid, flags, A-terms, taper; out: grid, model visibilities
+    h2d = nvis * 32 + model_h.nbytes + fl + wl.aterms.nbytes + wl.taper.nbytes
     d2h = grid_h.numel() * 8 + nvis * 32
 
     # kernels: achieved against their rooflines
@@ -546,7 +548,7 @@ def run_gb300(args, world, rank, local):
     # back (idg_image_from_grid / idg_grid_from_image, PSWF window of the taper).  Each call
     # reads and writes the N x N x 4 complex64 image twice (row pass, column pass) per w-layer.
     image_steps = None
-    if wl.grid_size in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096):
+    if wl.grid_size in (16, 32, 64, 128, 256, 512, 1024, 2048, 4096) and not args.step_only:
         win, _ = idg.taper_window(wl.subgrid_size, float(wl.kernel_size), idg.TAPER_PSWF)
         img = torch.empty((wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device=dev)
         im_ms = {}
@@ -571,10 +573,63 @@ def run_gb300(args, world, rank, local):
         image_steps["basis"] = ("4 x n_w x N^2 x 32 B per call (row and column pass, read and write), "
                                 f"against the {hbm_src} copy bandwidth")
 
-    # calibration (the residuals, cost and A-term gradient of the model grid against the
-    # observed visibilities, idg_aterm_gradient) on the same workload: one call is a
-    # degrid and a grid pass of every visibility plus the residual and gradient kernels
-    calib = None
+    # calibration (idg_aterm_gradient) on the same workload
+    calib = None if args.step_only else calibration_rate(idg, torch, dev, plan, wl, model, vis, flags, aterms, taper,
+                                                         stream, hbm_peak)
+    extras = args.config == "lofar" and not args.step_only
+
+    # classical gridding with oversampled A/W-projection kernels rebuilt per subgrid (the
+    # paper's comparison, Sect. 2) beside image domain gridding, on the precision
+    # workload's A-term cadence (slots of 16 timesteps), first 256 timesteps
+    classical = classical_comparison(idg, syn, torch, dev, stream, hbm_peak) if extras else None
+
+    # the adder and the splitter as their own launches over every subgrid (the fused
+    # kernels above do not launch them)
+    stages = stage_rates(idg, torch, dev, plan, vis, flags, aterms, taper, grid, stream, hbm_peak) if extras else None
+
+    # the deployment forms on small fixed cases: batched against per-job calls on 16 jobs,
+    # serving against per-job FIFO at 50 jobs/s, errors of the precision forms
+    forms = None
+    if extras and not args.no_forms:
+        b16 = batched_compare(idg, syn, torch, dev, 16, 3, 3, seed=1916)
+        forms = {"batched_16_jobs": {k: b16[k] for k in ("n_vis", "plain_mvis_per_s", "batched_mvis_per_s",
+                                                         "batched_over_plain", "classes")},
+                 "serving_50_per_s": serving_point(idg, syn, torch),
+                 "precision_errors": precision_errors(idg, syn, torch, dev, stream)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        op = O.plan(wl)
+        v, desc, secs = oracle_sample(wl, op, args.cpu_seconds)
+        cpu = {"value": v, "unit": "MVis/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    if rank == 0:
+        rec = {
+            "metric": "grid+degrid MVis/s", "value": value, "unit": "MVis/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+            "dtype": DTYPE_SEP if plan.stats.separable else "f32",
+            "data": "synthetic", "config": workload_config(wl, args.config),
+            "roofline": roof, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                    "host_buffers_placed_from_cpus": placement.cpus},
+            "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu, "image_steps": image_steps,
+            "calibration": calib, "classical": classical, "stages": stages, "forms": forms,
+            "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
+            "parallelism": ("sharded subgrids, one all-reduce per direction" if sharded else "replicas")
+            if world > 1 else "single GPU",
+        }
+        print(json.dumps(rec))
+
+
+def calibration_rate(idg, torch, dev, plan, wl, model, vis, flags, aterms, taper, stream, hbm_peak):
+    """One idg_aterm_gradient call on the workload (the residuals, cost and A-term
+    gradient of the model grid against the observed visibilities): a degrid and a
+    grid pass of every visibility plus the residual and gradient kernels."""
     resid = torch.empty_like(vis)
     agrad = torch.zeros(aterms.shape, dtype=torch.complex64, device=dev)
     cost = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -614,55 +669,7 @@ def run_gb300(args, world, rank, local):
     calib["basis"] = ("one idg_aterm_gradient call: splitter, inverse transform and degridder (stage kernels), "
                       "residual kernel (96 B per visibility), gridder of the residuals, gradient kernel (256 B per "
                       "subgrid pixel); MVis/s = visibilities per call / call time")
-    del resid, agrad
-
-    # classical gridding with oversampled A/W-projection kernels rebuilt per subgrid (the
-    # paper's comparison, Sect. 2) beside image domain gridding, on the precision
-    # workload's A-term cadence (slots of 16 timesteps), first 256 timesteps
-    classical = classical_comparison(idg, syn, torch, dev, stream, hbm_peak) if args.config == "lofar" else None
-
-    # the adder and the splitter as their own launches over every subgrid (the fused
-    # kernels above do not launch them)
-    stages = stage_rates(idg, torch, dev, plan, vis, flags, aterms, taper, grid, stream, hbm_peak) \
-        if args.config == "lofar" else None
-
-    # the deployment forms on small fixed cases: batched against per-job calls on 16 jobs,
-    # serving against per-job FIFO at 50 jobs/s, errors of the precision forms
-    forms = None
-    if args.config == "lofar" and not args.no_forms:
-        b16 = batched_compare(idg, syn, torch, dev, 16, 3, 3, seed=1916)
-        forms = {"batched_16_jobs": {k: b16[k] for k in ("n_vis", "plain_mvis_per_s", "batched_mvis_per_s",
-                                                         "batched_over_plain", "classes")},
-                 "serving_50_per_s": serving_point(idg, syn, torch),
-                 "precision_errors": precision_errors(idg, syn, torch, dev, stream)}
-
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        from oracle import oracle as O
-        O.build()
-        op = O.plan(wl)
-        v, desc, secs = oracle_sample(wl, op, args.cpu_seconds)
-        cpu = {"value": v, "unit": "MVis/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
-               "seconds": secs}
-
-    if rank == 0:
-        rec = {
-            "metric": "grid+degrid MVis/s", "value": value, "unit": "MVis/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
-            "dtype": DTYPE_SEP if plan.stats.separable else "f32",
-            "data": "synthetic", "config": workload_config(wl, args.config),
-            "roofline": roof, "kernels": kernels,
-            "e2e": {"value": e2e_value, "unit": "MVis/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-                    "host_buffers_placed_from_cpus": placement.cpus},
-            "gpu_launches": gpu_launches, "clocks": clocks, "cpu_baseline": cpu, "image_steps": image_steps,
-            "calibration": calib, "classical": classical, "stages": stages, "forms": forms,
-            "plan": {"n_subgrids": plan.n_subgrids, "seconds": plan_s},
-            "parallelism": ("sharded subgrids, one all-reduce per direction" if sharded else "replicas")
-            if world > 1 else "single GPU",
-        }
-        print(json.dumps(rec))
+    return calib
 
 
 def stage_rates(idg, torch, dev, plan, vis, flags, aterms, taper, grid, stream, hbm_peak):

@@ -317,6 +317,21 @@ idg_status idg_degrid_host(const idg_plan *plan, const void *h_grid, const uint8
                            idg_stream stream);
 
 /*
+ * Both directions on HOST buffers in one call: h_vis gridded into h_grid
+ * (OVERWRITTEN, as idg_grid_host) and the model grid h_model [n_w][N][N][4]
+ * degridded into h_vis_out (OVERWRITTEN, as idg_degrid_host), with the same
+ * flags, A-terms and taper (h_taper NULL: the plan's default).  One copy stream
+ * carries the visibility spans ahead of the gridding, the model grid while the
+ * gridding still runs, the gridded grid back while the degridding runs, and the
+ * model visibilities span by span behind the degridding, so that only the first
+ * and last span's copies are exposed.  Device memory: two visibility-sized and
+ * two grid-sized buffers from the stream-ordered pool.  Synchronises `stream`.
+ */
+idg_status idg_grid_degrid_host(const idg_plan *plan, const void *h_vis, const void *h_model, const uint8_t *h_flags,
+                                const void *h_aterms, const float *h_taper, void *h_grid, void *h_vis_out,
+                                idg_stream stream);
+
+/*
  * Gridding that allocates no device memory (the paper has no counterpart: this
  * is a deployment variant of idg_grid).  Some callers cannot allocate device
  * memory when they grid -- a real-time pipeline that reserves its whole memory

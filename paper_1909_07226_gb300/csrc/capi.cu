@@ -924,6 +924,24 @@ struct DevBufs {
     }
 };
 
+// On an early return of a host-buffer call: the compute stream waits for the copy
+// stream's work and the call returns only after both ended, so that no copy still
+// reads the caller's host memory, or writes a buffer freed on the compute stream.
+struct CopyJoin {
+    cudaStream_t s, cs;
+    bool done = false;
+    CopyJoin(cudaStream_t st, cudaStream_t cst) : s(st), cs(cst) {}
+    ~CopyJoin() {
+        if (done) return;
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            if (cudaEventRecord(e, cs) == cudaSuccess) cudaStreamWaitEvent(s, e, 0);
+            cudaEventDestroy(e);
+        }
+        cudaStreamSynchronize(s);
+    }
+};
+
 struct Events {
     std::vector<cudaEvent_t> ev;
     ~Events() {
@@ -970,6 +988,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
     const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
+    CopyJoin join(s, cs);
     const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0, grid_bytes,
                              comp || !fused_grid(p) ? (size_t)chunk * p->L * p->L * 32 : 0};
@@ -1015,6 +1034,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     e = cudaMemcpyAsync(h_grid, b.ptr[4], grid_bytes, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "copy of the grid to the host");
     e = cudaStreamSynchronize(s);
+    join.done = true;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return IDG_OK;
 }
@@ -1032,6 +1052,7 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
     const int64_t chunk = chunk_subgrids(p);
     DevBufs b(s);
+    CopyJoin join(s, cs);
     const size_t sizes[6] = {grid_bytes, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0, nvis * 32,
                              (size_t)chunk * p->L * p->L * 32};
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
@@ -1077,6 +1098,111 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
     if (st != IDG_OK) return st;
     e = cudaStreamSynchronize(s);
+    join.done = true;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return IDG_OK;
+}
+
+// Both directions in one call: the visibilities gridded into h_grid and the model grid
+// degridded into h_vis_out.  One copy stream carries, in order, the shared inputs, the
+// visibility spans (each released to the compute stream as it lands), the model grid
+// (which lands while the gridding still runs), then -- once the gridding is done -- the
+// gridded grid back to the host while the degridding runs, and the model visibilities
+// span by span behind the degridding.
+idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void *h_model, const uint8_t *h_flags,
+                                const void *h_aterms, const float *h_taper, void *h_grid, void *h_vis_out,
+                                idg_stream stream) {
+    idg_status st = check_call(p, h_vis, "h_vis", h_grid, "h_grid");
+    if (st != IDG_OK) return st;
+    if (!h_model) return fail(IDG_ERR_INVALID_ARG, "h_model is NULL");
+    if (!h_vis_out) return fail(IDG_ERR_INVALID_ARG, "h_vis_out is NULL");
+    if (!h_taper && !p->d_taper) return no_default_taper();
+    cudaStream_t s = (cudaStream_t)stream, cs = nullptr;
+    if ((st = copy_stream(p->device, &cs)) != IDG_OK) return st;
+    const size_t per_bl = (size_t)p->n_t * p->n_chan;
+    const size_t nvis = (size_t)p->n_bl * per_bl;
+    const size_t grid_bytes = (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    const size_t at_bytes = h_aterms ? (size_t)p->n_slots * p->n_stations * p->L * p->L * 32 : 0;
+    const int64_t chunk = chunk_subgrids(p);
+    const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
+    DevBufs b(s);
+    // 0 vis, 1 flags, 2 A-terms, 3 taper, 4 grid out, 5 scratch, 6 compensation; model grid and
+    // model visibilities in a second set
+    DevBufs b2(s);
+    CopyJoin join(s, cs);
+    const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0,
+                             grid_bytes, (size_t)chunk * p->L * p->L * 32};
+    for (int k = 0; k < 6 && st == IDG_OK; ++k)
+        if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
+    const size_t grid_f4 = grid_bytes / 16;
+    if (st == IDG_OK && comp) st = scratch_alloc(p->device, grid_f4 * 16, s, &b.ptr[6]);
+    if (st == IDG_OK) st = scratch_alloc(p->device, grid_bytes, s, &b2.ptr[0]);       // model grid
+    if (st == IDG_OK) st = scratch_alloc(p->device, nvis * 32, s, &b2.ptr[1]);        // model visibilities
+    if (st != IDG_OK) return st;
+    const float *taper = h_taper ? (const float *)b.ptr[3] : p->d_taper;
+    Events ev;
+    cudaEvent_t e_alloc, e_model, e_grid_done, e_end;
+    cudaError_t e = ev.add(&e_alloc);
+    if (e == cudaSuccess) e = ev.add(&e_model);
+    if (e == cudaSuccess) e = ev.add(&e_grid_done);
+    if (e == cudaSuccess) e = ev.add(&e_end);
+    if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e_alloc, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
+    if (e == cudaSuccess && comp) e = cudaMemsetAsync(b.ptr[6], 0, grid_f4 * 16, s);
+    if (e == cudaSuccess && p->any_dropped) e = cudaMemsetAsync(b2.ptr[1], 0, nvis * 32, s);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_degrid_host setup");
+    if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
+    if ((st = h2d(b.ptr[1], h_flags, sizes[1], cs, "copy of flags")) != IDG_OK) return st;
+    const auto &sf = p->span_first;
+    const auto &sb = p->span_bl;
+    const Geometry g = p->geometry();
+    // gridding, span by span behind the visibility copies
+    for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
+        const size_t v0 = (size_t)sb[k] * per_bl, nv = (size_t)(sb[k + 1] - sb[k]) * per_bl;
+        st = h2d((char *)b.ptr[0] + v0 * 32, (const char *)h_vis + v0 * 32, nv * 32, cs, "copy of visibilities");
+        cudaEvent_t e_up;
+        if (st == IDG_OK && (e = ev.add(&e_up)) == cudaSuccess && (e = cudaEventRecord(e_up, cs)) == cudaSuccess)
+            e = cudaStreamWaitEvent(s, e_up, 0);
+        if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+        if (st == IDG_OK && sf[k + 1] > sf[k])
+            st = grid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
+                           (const uint8_t *)b.ptr[1], b.ptr[2], taper, b.ptr[4], b.ptr[6], s);
+    }
+    // the model grid lands while the gridding runs
+    if (st == IDG_OK) st = h2d(b2.ptr[0], h_model, grid_bytes, cs, "copy of the model grid");
+    if (st == IDG_OK && (e = cudaEventRecord(e_model, cs)) != cudaSuccess) st = cuda_fail(e, "model event");
+    if (st == IDG_OK && comp) st = launch_fold_compensation(b.ptr[4], b.ptr[6], grid_f4, s);
+    if (st == IDG_OK && (e = cudaEventRecord(e_grid_done, s)) != cudaSuccess) st = cuda_fail(e, "grid event");
+    // the gridded grid goes back while the degridding runs
+    if (st == IDG_OK && (e = cudaStreamWaitEvent(cs, e_grid_done, 0)) == cudaSuccess)
+        e = cudaMemcpyAsync(h_grid, b.ptr[4], grid_bytes, cudaMemcpyDeviceToHost, cs);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "copy of the grid to the host");
+    if (st == IDG_OK && (e = cudaStreamWaitEvent(s, e_model, 0)) != cudaSuccess) st = cuda_fail(e, "model wait");
+    // degridding, span by span ahead of the visibility copies back
+    for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
+        if (sf[k + 1] > sf[k])
+            st = degrid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b2.ptr[0],
+                             (const uint8_t *)b.ptr[1], b.ptr[2], taper, b2.ptr[1], s);
+        cudaEvent_t e_done;
+        if (st == IDG_OK && (e = ev.add(&e_done)) == cudaSuccess && (e = cudaEventRecord(e_done, s)) == cudaSuccess)
+            e = cudaStreamWaitEvent(cs, e_done, 0);
+        if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+        if (st == IDG_OK) {
+            const size_t v0 = (size_t)sb[k] * per_bl, nv = (size_t)(sb[k + 1] - sb[k]) * per_bl;
+            e = cudaMemcpyAsync((char *)h_vis_out + v0 * 32, (const char *)b2.ptr[1] + v0 * 32, nv * 32,
+                                cudaMemcpyDeviceToHost, cs);
+            if (e != cudaSuccess) st = cuda_fail(e, "copy of the visibilities to the host");
+        }
+    }
+    // the copy stream's work ends before the buffers are released on s
+    e = cudaEventRecord(e_end, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_end, 0);
+    if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
+    if (st != IDG_OK) return st;
+    e = cudaStreamSynchronize(s);
+    join.done = true;
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return IDG_OK;
 }

@@ -38,7 +38,7 @@ EXPORTED = [
     "idg_batch_destroy", "idg_device_errors", "idg_taper_window", "idg_taper_aliasing",
     "idg_image_from_grid", "idg_grid_from_image", "idg_plan_set_kernel_variant", "idg_plan_get_kernel_variant",
     "idg_grid_range", "idg_degrid_range", "idg_selftest_wait_timeout", "idg_aterm_gradient",
-    "idg_classical_grid", "idg_batch_autotune",
+    "idg_classical_grid", "idg_batch_autotune", "idg_grid_degrid_host",
 ]
 BATCH_GRAPH = 1
 KERNELS = ["gridder", "fft", "adder", "splitter", "degridder", "batch_grid", "batch_degrid", "calib_residual",
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "idg_classical_grid": (I32, [P, I32, I32, D, P, P, P, P, P, P]),
         "idg_degrid_range": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_degrid_host": (I32, [P, P, P, P, P, P, P]),
+        "idg_grid_degrid_host": (I32, [P, P, P, P, P, P, P, P, P]),
         "idg_grid_subgrids": (I32, [P, I64, I64, P, P, P, P, P, P]),
         "idg_fft_subgrids": (I32, [P, I64, I32, P, P]),
         "idg_add_subgrids": (I32, [P, I64, I64, P, P, P]),
@@ -602,6 +603,20 @@ def degrid_host(plan: Plan, grid_in, flags, aterms, taper, vis_out, stream=None)
                                   _hptr(taper, "taper", np.float32, sh["taper"], True),
                                   _hptr(vis_out, "vis_out", np.complex64, sh["vis"]), _stream(stream)),
            "idg_degrid_host")
+
+
+def grid_degrid_host(plan: Plan, vis, model, flags, aterms, taper, grid_out, vis_out, stream=None):
+    """idg_grid_degrid_host: vis gridded into grid_out and the model grid degridded into
+    vis_out in one pipelined call (host arrays)."""
+    sh = _shapes(plan)
+    _check(load().idg_grid_degrid_host(plan.handle, _hptr(vis, "vis", np.complex64, sh["vis"]),
+                                       _hptr(model, "model", np.complex64, sh["grid"]),
+                                       _hptr(flags, "flags", np.uint8, sh["flags"], True),
+                                       _hptr(aterms, "aterms", np.complex64, sh["aterms"], True),
+                                       _hptr(taper, "taper", np.float32, sh["taper"], True),
+                                       _hptr(grid_out, "grid", np.complex64, sh["grid"]),
+                                       _hptr(vis_out, "vis_out", np.complex64, sh["vis"]), _stream(stream)),
+           "idg_grid_degrid_host")
 
 
 # ---------------------------------------------------------------------------

@@ -148,3 +148,17 @@ def test_bounded_wait_timeout_is_reported_and_the_device_recovers():
     with pytest.raises(idg.IDGError):
         idg.selftest_wait_timeout(0)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_grid_degrid_host_in_one_call(case):
+    # both directions on host buffers in one pipelined call, against the oracle
+    wl = syn.make_small(**CASES[case])
+    p = idg.plan_from_workload(wl)
+    op = O.plan(wl)
+    G = syn.random_grid(np.random.default_rng(21), p.n_w_layers, wl.grid_size).astype(np.complex64)
+    gout = np.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=np.complex64)
+    vout = np.full(wl.vis.shape, 7.0 + 7.0j, dtype=np.complex64)
+    idg.grid_degrid_host(p, wl.vis, G, wl.flags, wl.aterms, wl.taper.astype(np.float32), gout, vout)
+    parity(gout, O.grid(wl, op), f"{case} grid_degrid_host: grid")
+    parity(vout, O.degrid(wl, op, G), f"{case} grid_degrid_host: visibilities")
