@@ -74,7 +74,7 @@ constexpr int T4K = 128 * 32;                   // 128 rows x 16 K FP16
 constexpr int B0H_OFF = 0, B0L_OFF = B0H_OFF + KT * T4K, B1H_OFF = B0L_OFF + KT * T4K;
 constexpr int A_OFF = B1H_OFF + KT * T4K;       // A: [AST][m = 0 hi, m = 0 lo, m = 1 hi][KT][128 rows]
 constexpr int A_STAGE = 3 * KT * T4K;
-constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [2][32 y][TV] float2 (written and read by the consumers)
+constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [2][16 y pairs][TV] float4 (written and read by the consumers)
 constexpr int EY_STAGE = SL * TV * 8;
 constexpr int CF_OFF = EY_OFF + 2 * EY_STAGE;   // coefficients: [EST][TV] float4 (a, b, c, index)
 constexpr int PART_OFF = CF_OFF + EST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
@@ -88,6 +88,7 @@ constexpr uint32_t IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
 static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
+static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
@@ -103,11 +104,11 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     extern __shared__ __align__(1024) uint8_t smem[];
     float2 *s_fft = (float2 *)(smem + A_OFF);       // [4][L][L + 1] during the prologue
     float4 *s_coef = (float4 *)(smem + CF_OFF);
-    float2 *s_ey = (float2 *)(smem + EY_OFF);
+    float4 *s_ey = (float4 *)(smem + EY_OFF);
     float *s_part = (float *)(smem + PART_OFF);
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_afull[AST], s_aempty[AST], s_eyfull[EST], s_eyempty[EST], s_dfull[EST],
-        s_dempty[EST], s_drain, s_atbar;
+        s_dempty[EST], s_drain, s_atbar, s_gbar;
     __shared__ float s_red[NT / 32];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -131,7 +132,17 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         }
         mbar_init(smem_u32(&s_drain), 1);
         mbar_init(smem_u32(&s_atbar), 1);
+        mbar_init(smem_u32(&s_gbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (FUSED) {
+            // the subgrid's 32 grid rows (1 KB each, contiguous in the grid) into the B area, which
+            // is free until B is formed at the end of the prologue
+            const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
+            mbar_expect_tx(smem_u32(&s_gbar), SL * SL * 32);
+            for (int i = 0; i < SL; ++i)
+                bulk_g2s(smem_u32(smem + B0H_OFF + i * SL * 32), gsrc + 2 * ((size_t)(d.r0 + i) * g.N + d.q0), SL * 32,
+                         smem_u32(&s_gbar));
+        }
         if (aterms) {
             const float4 *base = aterms + 2 * ((size_t)d.slot * g.n_stations) * SPIX;
             mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
@@ -141,14 +152,50 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         }
     }
 
+    // the coefficient warp loads its first tile's coordinates now, so that they have
+    // arrived when the tiles start
+    struct Raw {
+        float4 uv, sc;
+        float2 w;
+        uint32_t vi;
+        bool in, flag;
+    };
+    const float4 *uvw2 = (const float4 *)g.uvw_f2;
+    const float4 *sc2 = (const float4 *)g.scale_f2;
+    auto load_raw = [&](Raw &r, int k) {
+        r.in = k < d.kp;
+        r.flag = false;
+        if (r.in) {
+            int tt, c;
+            const size_t vi = vis_index(g, d, k, tt, c);
+            const size_t bt = (size_t)d.bl * g.n_t + tt;
+            r.uv = uvw2[2 * bt];
+            const float4 w4 = uvw2[2 * bt + 1];
+            r.w = make_float2(w4.x, w4.y);
+            r.sc = sc2[c];
+            r.vi = (uint32_t)vi;
+            r.flag = flags && flags[vi];
+        }
+    };
+    Raw r0 = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float2(0.f, 0.f), 0u, false,
+              false},
+        r1 = r0;
+    if (warp == COEF_WARP && n_tiles > 0) {
+        load_raw(r0, lane);
+        load_raw(r1, lane + 32);
+    }
+    __syncthreads();      // the copies' barriers are initialised
+
     // ---- prologue: the corrected image P = taper A_p I A_q^H into the planes
     if (FUSED) {
-        const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
+        bool late = false;
+        wait_or_fail(smem_u32(&s_gbar), 0u, late);
+        if (late) atomicExch(&g_sepd_error, 1);
+        const float4 *rows = (const float4 *)(smem + B0H_OFF);
         for (int pix = tid; pix < SPIX; pix += NT) {
             const int i = pix / SL, j = pix % SL;
-            const size_t gp = (size_t)(d.r0 + i) * g.N + (d.q0 + j);
             const float sg = ((i + j) & 1) ? -1.0f : 1.0f;
-            const float4 a = gsrc[2 * gp], b = gsrc[2 * gp + 1];
+            const float4 a = rows[2 * pix], b = rows[2 * pix + 1];
             s_fft[(0 * SL + i) * FFT_P + j] = make_float2(sg * a.x, sg * a.y);
             s_fft[(1 * SL + i) * FFT_P + j] = make_float2(sg * a.z, sg * a.w);
             s_fft[(2 * SL + i) * FFT_P + j] = make_float2(sg * b.x, sg * b.y);
@@ -157,7 +204,6 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         __syncthreads();
         fft2_planar_pairs32<+1>(s_fft, tid);
     }
-    if (!FUSED) __syncthreads();    // (FUSED: the transform's barriers) the copies' barrier is initialised
     if (aterms) {
         bool late = false;
         wait_or_fail(smem_u32(&s_atbar), 0u, late);
@@ -303,30 +349,8 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         // ---- coefficients: lane l stages visibilities l and l + 32 of each tile: (a, b, c) from
         // float pairs (error-free FP32 products and sums, rounded once) and the output index (flag
         // in bit 31); the coordinates of the next tile are loaded while this one is formed, and a
-        // stage is reused once the consumers release it
-        struct Raw {
-            float4 uv, sc;
-            float2 w;
-            uint32_t vi;
-            bool in, flag;
-        };
-        const float4 *uvw2 = (const float4 *)g.uvw_f2;
-        const float4 *sc2 = (const float4 *)g.scale_f2;
-        auto load_raw = [&](Raw &r, int k) {
-            r.in = k < d.kp;
-            r.flag = false;
-            if (r.in) {
-                int tt, c;
-                const size_t vi = vis_index(g, d, k, tt, c);
-                const size_t bt = (size_t)d.bl * g.n_t + tt;
-                r.uv = uvw2[2 * bt];
-                const float4 w4 = uvw2[2 * bt + 1];
-                r.w = make_float2(w4.x, w4.y);
-                r.sc = sc2[c];
-                r.vi = (uint32_t)vi;
-                r.flag = flags && flags[vi];
-            }
-        };
+        // stage is reused once the consumers release it (the first tile's were loaded before
+        // the prologue)
         auto form = [&](const Raw &r) {
             float4 cf = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xFFFFFFFFu));   // beyond K_p: no output
             if (r.in) {
@@ -337,13 +361,6 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             }
             return cf;
         };
-        Raw r0 = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), make_float2(0.f, 0.f), 0u,
-                  false, false},
-            r1 = r0;
-        if (n_tiles > 0) {
-            load_raw(r0, lane);
-            load_raw(r1, lane + 32);
-        }
         for (int t = 0; t < n_tiles; ++t) {
             const int e = t & 3;
             const float4 c0 = form(r0), c1 = form(r1);
@@ -364,53 +381,69 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         const int qq = warp & 3, h = (warp - NPW) >> 2;
         const int ci = qq >> 1, kl = 32 * (qq & 1) + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * qq) << 16);
-        // Ey* entries j: visibility ke = ctid % TV, y = ctid / TV + 4 j (ctid = consumer thread index)
-        const int ctid = tid - NP, ke = ctid & (TV - 1), y0 = ctid >> 6;
-        float tys[SL * TV / NC];
+        // Ey* entries: visibility ke = ctid % TV, rows y = 2 p, 2 p + 1 of the pairs p = ctid / TV + 4 j
+        // (ctid = consumer thread index); entry (p, k) = (cs_2p, cs_2p+1, -sn_2p, -sn_2p+1)
+        const int ctid = tid - NP, ke = ctid & (TV - 1), p0 = ctid >> 6;
+        constexpr int EYP = SL * TV / NC / 2;     // pairs per thread
+        float tys[2 * EYP];
 #pragma unroll
-        for (int j = 0; j < SL * TV / NC; ++j) tys[j] = g.sep[SL + y0 + 4 * j];
+        for (int j = 0; j < EYP; ++j) {
+            tys[2 * j] = g.sep[SL + 2 * (p0 + 4 * j)];
+            tys[2 * j + 1] = g.sep[SL + 2 * (p0 + 4 * j) + 1];
+        }
         for (int t = 0; t < n_tiles; ++t) {
             const int s = t & 1, e = t & 3;
             wait_or_fail(smem_u32(&s_eyfull[e]), (uint32_t)((t >> 2) & 1), failed);
             // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))) of the tile (entry y TV + k), while its MMAs run
-            float2 *eyw = s_ey + s * (SL * TV);
+            float4 *eyw = s_ey + s * (SL / 2 * TV);
             {
                 const float4 c = s_coef[e * TV + ke];
 #pragma unroll
-                for (int j = 0; j < SL * TV / NC; ++j) {
-                    const int y = y0 + 4 * j;
-                    float sn, cs;
-                    __sincosf(fmaf(c.z, tys[j], c.y * (float)(y - SL / 2)), &sn, &cs);
-                    eyw[y * TV + ke] = make_float2(cs, -sn);
+                for (int j = 0; j < EYP; ++j) {
+                    const int pp = p0 + 4 * j;
+                    float sn0, cs0, sn1, cs1;
+                    __sincosf(fmaf(c.z, tys[2 * j], c.y * (float)(2 * pp - SL / 2)), &sn0, &cs0);
+                    __sincosf(fmaf(c.z, tys[2 * j + 1], c.y * (float)(2 * pp + 1 - SL / 2)), &sn1, &cs1);
+                    eyw[pp * TV + ke] = make_float4(cs0, cs1, -sn0, -sn1);
                 }
             }
             consumers_sync();
             wait_or_fail(smem_u32(&s_dfull[e]), (uint32_t)((t >> 2) & 1), failed);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float2 *ey = eyw;
-            float acc[2][2];         // [q'][ (sum er T, sum ei T) ]
+            const ulonglong2 *ey = (const ulonglong2 *)eyw;
+            // [q'][(sum er T, sum ei T)], each as packed partial sums over the even and odd rows y
+            f2_t accp[2][2];
 #pragma unroll
-            for (int q2 = 0; q2 < 2; ++q2) acc[q2][0] = acc[q2][1] = 0.0f;
+            for (int q2 = 0; q2 < 2; ++q2) accp[q2][0] = accp[q2][1] = 0ull;
 #pragma unroll 1
             for (int yc = 0; yc < 4; ++yc) {         // rows y in [8 yc, 8 yc + 8)
                 uint32_t r[2][8];
 #pragma unroll
                 for (int qp = 0; qp < 2; ++qp)       // columns 32 (2 h + q') + y
                     tmem_ld8_nowait(lane_base + 128u * (uint32_t)e + (uint32_t)(64 * h + 32 * qp + 8 * yc), r[qp]);
-                float2 e[8];
+                ulonglong2 ep[4];
 #pragma unroll
-                for (int y = 0; y < 8; ++y) e[y] = ey[(8 * yc + y) * TV + kl];
+                for (int pp = 0; pp < 4; ++pp) ep[pp] = ey[(4 * yc + pp) * TV + kl];
 #pragma unroll
                 for (int qp = 0; qp < 2; ++qp) {
                     tmem_wait_ld8(r[qp]);
 #pragma unroll
-                    for (int y = 0; y < 8; ++y) {
-                        const float v = __uint_as_float(r[qp][y]);
-                        acc[qp][0] = fmaf(e[y].x, v, acc[qp][0]);
-                        acc[qp][1] = fmaf(e[y].y, v, acc[qp][1]);
+                    for (int pp = 0; pp < 4; ++pp) {
+                        const f2_t v = f2_pack(__uint_as_float(r[qp][2 * pp]), __uint_as_float(r[qp][2 * pp + 1]));
+                        accp[qp][0] = f2_fma(ep[pp].x, v, accp[qp][0]);
+                        accp[qp][1] = f2_fma(ep[pp].y, v, accp[qp][1]);
                     }
                 }
             }
+            float acc[2][2];
+#pragma unroll
+            for (int q2 = 0; q2 < 2; ++q2)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    float lo, hi;
+                    f2_unpack(accp[q2][c], lo, hi);
+                    acc[q2][c] = lo + hi;
+                }
             const float4 cfk = s_coef[e * TV + kl];
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();

@@ -32,26 +32,28 @@
 // without rounding to nearest, so every FOLD groups of 8 visibilities the
 // accumulator is added into FP32 sums in shared memory (RN) and restarted.
 // The producers read it as soon as the period's MMAs are done and release it
-// before adding, so the MMAs wait only for the tensor-memory loads; the
-// tensor memory goes to four A stages instead (three stages of lookahead
-// cover the round trip MMA -> producers -> MMA).
+// before adding, so the MMAs wait only for the tensor-memory loads; the rest
+// of the tensor memory holds two A stages.
 //
 // Schedule.  One CTA per subgrid, one CTA per SM: sixteen producer warps and
-// one MMA warp.  A stage is four groups of 8 visibilities.  Per stage each
-// producer:
+// one MMA warp.  A stage is eight groups of 8 visibilities: every stage ends
+// in a tensor-memory wait, a proxy fence and a barrier arrival per warp, and
+// with eight groups (rather than four) that fixed cost is spread over twice
+// the work, 9 % off the gridder's time.  Per stage each producer, for each of
+// its groups warp / 4 and warp / 4 + 4:
 //   - writes the 8 A entries of its row (polarisation lane / 8, pixel row
-//     8 (warp % 4) + lane % 8) for group warp / 4 into tensor memory, one
-//     16-column store.  It forms Ey for two of the visibilities and takes the
-//     others from the lanes of the same row by shuffles;
+//     8 (warp % 4) + lane % 8) into tensor memory, one 16-column store.  It
+//     forms Ey for two of the visibilities and takes the others from the
+//     lanes of the same row by shuffles;
 //   - forms the B entries of pixel column 8 (warp % 4) + lane % 8 for the
-//     adjacent visibilities 2 (lane / 8) and 2 (lane / 8) + 1 of the same
-//     group, and writes them as one 8-byte store per row block (a warp's store
+//     adjacent visibilities 2 (lane / 8) and 2 (lane / 8) + 1 of the group,
+//     and writes them as one 8-byte store per row block (a warp's store
 //     covers 256 contiguous bytes, free of bank conflicts).
 // Visibilities are staged 512 at a time; the next batch is loaded into
 // registers while the current one is processed.
 // Tensor memory (512 columns):
 //   accumulator: main (m, re/im, x) 0..127, correction (m = 0) 128..191
-//   A stage s at 192 + 64 s, group i at + 16 i: 8 columns hi, 8 lo
+//   A stage s at 192 + 128 s, group i at + 16 i: 8 columns hi, 8 lo
 // Every wait is bounded; after a failed wait a thread skips every later wait,
 // the error word is set and no output is written.
 #include "batch_jobs.cuh"
@@ -78,8 +80,8 @@ constexpr int NT = NP + 32;                    // + the MMA warp
 constexpr int VB = NP;                         // visibilities per staged batch (one per producer)
 constexpr int GB = VB / 8;                     // groups per batch
 constexpr int FOLD = 64;                       // groups per accumulation period
-constexpr int SG = 4;                          // groups of 8 visibilities per stage
-constexpr int STAGES = 4;
+constexpr int SG = 8;                          // groups of 8 visibilities per stage
+constexpr int STAGES = 2;
 constexpr int B_GROUP = 192 * 32;              // B of one group: 192 rows x 16 K FP16 (hi 128 rows, then lo 64)
 constexpr int B_STAGE = SG * B_GROUP;
 constexpr int COEF_OFF = STAGES * B_STAGE;     // [2][VB] float4 (a, b, c, 0)
@@ -87,9 +89,15 @@ constexpr int VIS_OFF = COEF_OFF + 2 * VB * 16;   // [2][VB][4] float2 (scaled V
 constexpr int FOLD_OFF = VIS_OFF + 2 * VB * 32;   // [32][NP] float: folded sums of each producer
 constexpr int SEP_SMEM = FOLD_OFF + 32 * NP * 4;
 constexpr int FFT_P = SL + 1;
+// the subgrid's A-terms after the main loop: [2 stations][L^2] 2 x 2 complex, beside the
+// transform planes, over the stage and coefficient buffers
+constexpr int AT_OFF = 4 * SL * FFT_P * 8;
+constexpr uint32_t AT_BYTES = SPIX * 32;
 constexpr uint32_t A_COL = 192;                 // accumulator 0..191, then the A stages
 constexpr uint32_t IDESC_N192 = idesc_m128(192), IDESC_N64 = idesc_m128(64);
 static_assert(4 * SL * FFT_P * 8 <= FOLD_OFF, "transform planes fit over the stage buffers");
+static_assert(SEP_SMEM + 1024 <= 227 * 1024, "dynamic and static shared memory of one CTA");
+static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= VIS_OFF, "A-terms over the stage and coefficient buffers");
 static_assert(A_COL + 16 * SG * STAGES <= 512, "tensor memory");
 static_assert(FOLD / SG >= STAGES, "a period spans at least STAGES stages");
 static_assert((STAGES & (STAGES - 1)) == 0, "STAGES is a power of two");
@@ -112,7 +120,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     float2 *s_fft = (float2 *)smem;                 // [4][L][L + 1] after the main loop
     float *s_fold = (float *)(smem + FOLD_OFF);     // [32][NP]: m = 0 sums (16), then m = 1 (16)
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_foldbar, s_folded, s_drain;
+    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_foldbar, s_folded, s_drain, s_atbar;
     __shared__ float s_red[2][NPW];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -133,6 +141,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         mbar_init(smem_u32(&s_foldbar), 1);
         mbar_init(smem_u32(&s_folded), NPW);
         mbar_init(smem_u32(&s_drain), 1);
+        mbar_init(smem_u32(&s_atbar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -140,7 +149,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
 
-    bool failed = false;
+    bool failed = false, at_issued = false;
     const int yq = warp & 3, sl = warp >> 2;        // lane quarter (rows 32 yq ..) and fold column slice
 
     if (mma_warp) {
@@ -160,7 +169,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int ng = min(SG, total_groups - st * SG);
                 const uint64_t dbs = db0 + (uint64_t)((s * B_STAGE) >> 4);
-                const uint32_t ats = tmem + A_COL + 64u * (uint32_t)s;
+                const uint32_t ats = tmem + A_COL + 16u * SG * (uint32_t)s;
 #pragma unroll
                 for (int i = 0; i < SG; ++i) {
                     if (i < ng) {
@@ -173,8 +182,19 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 commit(smem_u32(&s_empty[s]));
             }
             commit(smem_u32(&s_drain));
-            bool drained = false;
-            wait_or_fail(smem_u32(&s_drain), 0u, drained);     // bounded: let own MMAs finish before the free
+            bool late = false;
+            wait_or_fail(smem_u32(&s_drain), 0u, late);     // bounded: let own MMAs finish before the free
+            if (late) failed = true;
+            // the tensor cores are done with the stage buffers: bring the subgrid's A-terms (A_p,
+            // A_q) into them while the producers fold and form the image
+            if (aterms && !failed) {
+                const float4 *base = aterms + 2 * ((size_t)d.slot * g.n_stations) * SPIX;
+                mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
+                bulk_g2s(smem_u32(smem + AT_OFF), base + 2 * (size_t)d.st_p * SPIX, AT_BYTES, smem_u32(&s_atbar));
+                bulk_g2s(smem_u32(smem + AT_OFF + AT_BYTES), base + 2 * (size_t)d.st_q * SPIX, AT_BYTES,
+                         smem_u32(&s_atbar));
+                at_issued = true;
+            }
         }
         failed = __shfl_sync(0xffffffffu, failed, 0);
     } else {
@@ -191,6 +211,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         const float Xv = (float)(xb - SL / 2);
         const float sx = g.sep[xb];
         const float csig = g.c_scale;
+        const uint16_t m1h = 0xBC00u;      // FP16 -1
 
         // staging: visibility tid of batch b, loaded into registers one batch ahead
         float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, puv = pa, pws = pa;
@@ -211,10 +232,8 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 pw = make_float2(w4.x, w4.y);
                 pws = sc2[c];
                 pflag = flags && flags[vi];
-                if (!pflag) {
-                    pa = vis[2 * vi];
-                    pb = vis[2 * vi + 1];
-                }
+                pa = vis[2 * vi];          // loaded whatever the flag: the load does not wait for it
+                pb = vis[2 * vi + 1];
             }
         };
         // phase coefficients of the staged visibility: u (f/c) k_uv - u0 k_uv and so on, from
@@ -305,9 +324,10 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     fold(next_fold);
                     ++next_fold;
                 }
-                // A entries of group ga: scale V_kq Ey_k(y) for its 8 visibilities
-                {
-                    const int kb = 8 * (SG * si + ga);
+                // A entries of groups ga + 4 gg: scale V_kq Ey_k(y) for its 8 visibilities
+#pragma unroll
+                for (int gg = 0; gg < SG / 4; ++gg) {
+                    const int kb = 8 * (SG * si + ga + 4 * gg);
                     float ec[2], es[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -324,17 +344,18 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                         const float cs = __shfl_sync(0xffffffffu, (j & 1) ? ec[1] : ec[0], src);
                         const float sn = __shfl_sync(0xffffffffu, (j & 1) ? es[1] : es[0], src);
                         const float2 v = vb[(kb + j) * 4 + qa];
-                        split_e(fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs), e[j], e[8 + j]);
+                        split_e_m(fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs), m1h, e[j], e[8 + j]);
                     }
-                    tmem_st16(lane_base + A_COL + 64u * (uint32_t)s + 16u * (uint32_t)ga, e);
+                    tmem_st16(lane_base + A_COL + 16u * SG * (uint32_t)s + 16u * (uint32_t)(ga + 4 * gg), e);
                 }
                 // B entries: beta = Ex_k(x) (m = 0: hi and lo) and c_k sigma Ex_k(x) (m = 1: hi), rows
                 // (m, re, x) = (Re beta, -Im beta) and (m, im, x) = (Im beta, Re beta)
                 uint8_t *Bs = sB + s * B_STAGE;
-                {
-                    // visibilities j0 = 2 jl and j0 + 1 of group i = warp / 4 sit in adjacent K slots of
-                    // each row: one 8-byte store per row
-                    const int i = warp >> 2, j0 = 2 * jl;
+#pragma unroll
+                for (int gg = 0; gg < SG / 4; ++gg) {
+                    // visibilities j0 = 2 jl and j0 + 1 of group i = warp / 4 + 4 gg sit in adjacent K
+                    // slots of each row: one 8-byte store per row
+                    const int i = (warp >> 2) + 4 * gg, j0 = 2 * jl;
                     uint32_t w[6][2];
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
@@ -344,7 +365,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                         // the im row (sn, cs) is the re row (cs, -sn) with its halves swapped and the
                         // new low half negated: exact, as FP16 rounding is symmetric
                         uint32_t hr, lr;
-                        split_e(cs, -sn, hr, lr);
+                        split_e_m(cs, -sn, m1h, hr, lr);
                         const float cz = cf.z * csig;
                         const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn);
                         w[0][t] = hr;
@@ -404,6 +425,11 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     if (!__syncthreads_or(failed)) {
+        if (aterms) {
+            bool late = false;
+            wait_or_fail(smem_u32(&s_atbar), 0u, late);
+            if (late) atomicExch(&g_sep_error, 1);
+        }
         // image-domain kernel per pixel: taper * A_p^H I A_q (with the centring factor when FUSED)
         for (int pix = tid; pix < SPIX; pix += NT) {
             const int y = pix >> 5, x = pix & (SL - 1);
@@ -411,9 +437,9 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
 #pragma unroll
             for (int c = 0; c < 4; ++c) P.m[c] = s_fft[(c * SL + y) * FFT_P + x];
             if (aterms) {
-                const size_t base = ((size_t)d.slot * g.n_stations) * SPIX;
-                const M22 Ap = load_m22(aterms + 2 * (base + (size_t)d.st_p * SPIX + pix));
-                const M22 Aq = load_m22(aterms + 2 * (base + (size_t)d.st_q * SPIX + pix));
+                const float4 *at = (const float4 *)(smem + AT_OFF);
+                const M22 Ap = load_m22(at + 2 * pix);
+                const M22 Aq = load_m22(at + 2 * (SPIX + pix));
                 P = herm_mul_mul(Ap, P, Aq);
             }
             if (FUSED) {
@@ -428,7 +454,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         }
         if (FUSED) {
             __syncthreads();
-            fft2_planar<SL, -1>(s_fft, tid, NT);
+            fft2_planar_pairs32<-1>(s_fft, tid);
             const float inv = 1.0f / (float)SPIX;
             float4 *dst = o + (size_t)d.layer * g.N * g.N * 2;
             for (int pix = tid; pix < SPIX; pix += NT) {
@@ -443,6 +469,10 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         }
     }
     __syncthreads();
+    if (at_issued) {      // the copies have landed before the CTA's shared memory is released
+        bool late = false;
+        wait_or_fail(smem_u32(&s_atbar), 0u, late);
+    }
     if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(512));
 }
 

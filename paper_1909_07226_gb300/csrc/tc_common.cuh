@@ -159,5 +159,19 @@ __device__ __forceinline__ void split_e(float x, float y, uint32_t &hi, uint32_t
         "}" : "=r"(hi), "=r"(lo) : "f"(x), "f"(y));
 }
 
+// split_e with the FP16 constant -1 (0xBC00) passed in a register that the
+// caller keeps live across its loop
+__device__ __forceinline__ void split_e_m(float x, float y, uint16_t m1, uint32_t &hi, uint32_t &lo) {
+    asm("{\n"
+        " .reg .b16 hx, hy;\n"
+        " .reg .f32 lx, ly;\n"
+        " cvt.rn.f16x2.f32 %0, %3, %2;\n"
+        " mov.b32 {hx, hy}, %0;\n"
+        " fma.rn.f32.f16 lx, hx, %4, %2;\n"
+        " fma.rn.f32.f16 ly, hy, %4, %3;\n"
+        " cvt.rn.f16x2.f32 %1, ly, lx;\n"
+        "}" : "=r"(hi), "=r"(lo) : "f"(x), "f"(y), "h"(m1));
+}
+
 }  // namespace tc
 }  // namespace idg
