@@ -88,6 +88,7 @@ constexpr uint32_t IDESC_N128 = idesc_m128(128);
 static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
 static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
+static_assert(128 % MMA_WARP == 0, "B tasks spread evenly over the warps before the MMA warp");
 static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
@@ -184,6 +185,20 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         load_raw(r0, lane);
         load_raw(r1, lane + 32);
     }
+    // the prologue's other global reads, issued while the copies run: the taper of this
+    // thread's pixels and the remainder r(x, y) of its B entries
+    constexpr int NPIX = (SPIX + NT - 1) / NT;
+    float tw_pre[NPIX];
+#pragma unroll
+    for (int i = 0; i < NPIX; ++i) tw_pre[i] = tid + i * NT < SPIX ? taper[tid + i * NT] : 0.0f;
+    constexpr int NWT = 128 / MMA_WARP;
+    float rr_pre[NWT];
+#pragma unroll
+    for (int i = 0; i < NWT; ++i) {
+        const int wt = warp + MMA_WARP * i;
+        rr_pre[i] = warp < MMA_WARP ? g.sep[2 * SL + (8 * ((wt >> 3) & 3) + (lane >> 2)) * SL + 4 * (wt & 7) + (lane & 3)]
+                                    : 0.0f;
+    }
     __syncthreads();      // the copies' barriers are initialised
 
     // ---- prologue: the corrected image P = taper A_p I A_q^H into the planes
@@ -210,7 +225,10 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         if (late) atomicExch(&g_sepd_error, 1);
     }
     float m = 0.0f;
-    for (int pix = tid; pix < SPIX; pix += NT) {
+#pragma unroll
+    for (int ip = 0; ip < NPIX; ++ip) {
+        const int pix = tid + ip * NT;
+        if (pix >= SPIX) break;
         const int y = pix >> 5, x = pix & (SL - 1);
         M22 P;
         if (FUSED) {      // (-1)^(x+y) / L^2 of the transform
@@ -229,7 +247,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             const M22 Aq = load_m22(at + 2 * (SPIX + pix));
             P = mul_mul_herm(Ap, P, Aq);
         }
-        const float tw = taper[pix];
+        const float tw = tw_pre[ip];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const float2 v = make_float2(tw * P.m[q].x, tw * P.m[q].y);
@@ -255,11 +273,13 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     // (8 rows y, 4 x) per warp store: warp-task wt = (q, y block, x chunk of 4)
     if (warp < MMA_WARP) {
         const float rs = scale / g.c_scale;
-        for (int wt = warp; wt < 128; wt += MMA_WARP) {
+#pragma unroll
+        for (int i = 0; i < NWT; ++i) {
+            const int wt = warp + MMA_WARP * i;
             const int q = wt >> 5, yb = (wt >> 3) & 3, xc = wt & 7;
             const int y = 8 * yb + (lane >> 2), x = 4 * xc + (lane & 3);
             const float2 p = s_fft[(q * SL + y) * FFT_P + x];
-            const float rr = g.sep[2 * SL + y * SL + x] * rs;
+            const float rr = rr_pre[i] * rs;
             uint32_t h0, l0;
             split_e(p.x * scale, p.y * scale, h0, l0);
             const uint32_t h1 = pack_f16x2(p.x * rr, p.y * rr);

@@ -150,6 +150,13 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     const uint32_t tmem = s_tmem;
 
     bool failed = false, at_issued = false;
+    // the taper of this thread's epilogue pixels, loaded at the end of its main loop
+    constexpr int NPIX = (SPIX + NT - 1) / NT;
+    float tw_pre[NPIX];
+    auto load_taper = [&]() {
+#pragma unroll
+        for (int i = 0; i < NPIX; ++i) tw_pre[i] = tid + i * NT < SPIX ? taper[tid + i * NT] : 0.0f;
+    };
     const int yq = warp & 3, sl = warp >> 2;        // lane quarter (rows 32 yq ..) and fold column slice
 
     if (mma_warp) {
@@ -197,6 +204,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             }
         }
         failed = __shfl_sync(0xffffffffu, failed, 0);
+        load_taper();
     } else {
         // A rows: r = 32 yq + lane holds polarisation qa = lane / 8 of pixel row y = 8 yq + lane % 8
         const int qa = lane >> 3, ylo = lane & 7;
@@ -394,6 +402,13 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 producers_sync();
             }
         }
+        // the epilogue's global reads first: taper, and r(x, y) of this thread's x range
+        load_taper();
+        const int x0 = 16 * (sl & 1) + 8 * (sl >> 1);
+        const int y = 8 * yq + ylo;
+        float rr_pre[8];
+#pragma unroll
+        for (int xi = 0; xi < 8; ++xi) rr_pre[xi] = g.sep[2 * SL + y * SL + x0 + xi];
         while (next_fold < n_batches) {
             fold(next_fold);
             ++next_fold;
@@ -404,10 +419,8 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             // I = S0 + i r S1 / sigma into the polarisation planes.  Column slice sl holds the
             // re (sl < 2) or im (sl >= 2) part of x in [16 (sl & 1), + 16); the thread with
             // slice sl takes 8 of those x, reading the re and im parts of both slices.
-            const int x0 = 16 * (sl & 1) + 8 * (sl >> 1);
             const int tre = tid & ~256, tim = tid | 256;     // threads holding re and im of this row and x range
             const float rs = 1.0f / csig;
-            const int y = 8 * yq + ylo;
 #pragma unroll
             for (int xi = 0; xi < 8; ++xi) {
                 const int x = x0 + xi, c = x & 15;
@@ -418,7 +431,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     s1r = s_fold[(16 + c) * NP + tre];
                     s1i = s_fold[(16 + c) * NP + tim];
                 }
-                const float rr = g.sep[2 * SL + y * SL + x] * rs;
+                const float rr = rr_pre[xi] * rs;
                 s_fft[(qa * SL + y) * FFT_P + x] = make_float2(fmaf(-rr, s1i, s0r), fmaf(rr, s1r, s0i));
             }
         }
@@ -431,7 +444,10 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             if (late) atomicExch(&g_sep_error, 1);
         }
         // image-domain kernel per pixel: taper * A_p^H I A_q (with the centring factor when FUSED)
-        for (int pix = tid; pix < SPIX; pix += NT) {
+#pragma unroll
+        for (int ip = 0; ip < NPIX; ++ip) {
+            const int pix = tid + ip * NT;
+            if (pix >= SPIX) break;
             const int y = pix >> 5, x = pix & (SL - 1);
             M22 P;
 #pragma unroll
@@ -443,11 +459,11 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 P = herm_mul_mul(Ap, P, Aq);
             }
             if (FUSED) {
-                const float tw = ((x + y) & 1) ? -taper[pix] : taper[pix];
+                const float tw = ((x + y) & 1) ? -tw_pre[ip] : tw_pre[ip];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) s_fft[(c * SL + y) * FFT_P + x] = make_float2(tw * P.m[c].x, tw * P.m[c].y);
             } else {
-                const float tw = taper[pix];
+                const float tw = tw_pre[ip];
                 o[2 * pix] = make_float4(tw * P.m[0].x, tw * P.m[0].y, tw * P.m[1].x, tw * P.m[1].y);
                 o[2 * pix + 1] = make_float4(tw * P.m[2].x, tw * P.m[2].y, tw * P.m[3].x, tw * P.m[3].y);
             }
