@@ -84,7 +84,10 @@ constexpr int SG = 8;                          // groups of 8 visibilities per s
 constexpr int STAGES = 2;
 constexpr int B_GROUP = 192 * 32;              // B of one group: 192 rows x 16 K FP16 (hi 128 rows, then lo 64)
 constexpr int B_STAGE = SG * B_GROUP;
-constexpr int COEF_OFF = STAGES * B_STAGE;     // [2][VB] float4 (a, b, c, 0)
+// coefficients as two float pairs, [2][VB] (b, c) for the Ey side, then [2][VB] (a, c) for
+// the Ex side: the shared-memory pipe is close to its limit in the main loop and its cost
+// is the bytes each thread reads (a float4 where two floats are used costs twice)
+constexpr int COEF_OFF = STAGES * B_STAGE;
 constexpr int VIS_OFF = COEF_OFF + 2 * VB * 16;   // [2][VB][4] float2 (scaled V)
 constexpr int FOLD_OFF = VIS_OFF + 2 * VB * 32;   // [32][NP] float: folded sums of each producer
 constexpr int SEP_SMEM = FOLD_OFF + 32 * NP * 4;
@@ -115,7 +118,8 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                                                  float4 *__restrict__ o) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
-    float4 *s_coef = (float4 *)(smem + COEF_OFF);
+    float2 *s_cb = (float2 *)(smem + COEF_OFF);          // [2][VB] (b, c)
+    float2 *s_ca = s_cb + 2 * VB;                         // [2][VB] (a, c)
     float2 *s_vis = (float2 *)(smem + VIS_OFF);
     float2 *s_fft = (float2 *)smem;                 // [4][L][L + 1] after the main loop
     float *s_fold = (float *)(smem + FOLD_OFF);     // [32][NP]: m = 0 sums (16), then m = 1 (16)
@@ -262,7 +266,8 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 a = pa;
                 b = pb;
             }
-            s_coef[bb * VB + tid] = cf_next;
+            s_cb[bb * VB + tid] = make_float2(cf_next.y, cf_next.z);
+            s_ca[bb * VB + tid] = make_float2(cf_next.x, cf_next.z);
             float4 *dv = (float4 *)(s_vis + (size_t)(bb * VB + tid) * 4);
             dv[0] = a;
             dv[1] = b;
@@ -319,7 +324,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             if (bb) inv_sc1 = ldexpf(1.0f, e2 - 10);
             else inv_sc0 = ldexpf(1.0f, e2 - 10);
             if (b + 1 < n_batches) load_batch(b + 1);
-            const float4 *coef = s_coef + bb * VB;
+            const float2 *cb = s_cb + bb * VB, *ca = s_ca + bb * VB;
             const float2 *vb = s_vis + (size_t)bb * VB * 4;
             const int nst = (min(GB, total_groups - b * GB) + SG - 1) / SG;
             for (int si = 0; si < nst; ++si) {
@@ -339,9 +344,9 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     float ec[2], es[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float4 cf = coef[kb + 2 * qa + h];
+                        const float2 cf = cb[kb + 2 * qa + h];
                         float sn, cs;
-                        __sincosf(fmaf(cf.z, ty, cf.y * Yv), &sn, &cs);
+                        __sincosf(fmaf(cf.y, ty, cf.x * Yv), &sn, &cs);
                         ec[h] = cs * scale;
                         es[h] = sn * scale;
                     }
@@ -367,14 +372,14 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     uint32_t w[6][2];
 #pragma unroll
                     for (int t = 0; t < 2; ++t) {
-                        const float4 cf = coef[8 * (SG * si + i) + j0 + t];
+                        const float2 cf = ca[8 * (SG * si + i) + j0 + t];
                         float sn, cs;
-                        __sincosf(fmaf(cf.z, sx, cf.x * Xv), &sn, &cs);
+                        __sincosf(fmaf(cf.y, sx, cf.x * Xv), &sn, &cs);
                         // the im row (sn, cs) is the re row (cs, -sn) with its halves swapped and the
                         // new low half negated: exact, as FP16 rounding is symmetric
                         uint32_t hr, lr;
                         split_e_m(cs, -sn, m1h, hr, lr);
-                        const float cz = cf.z * csig;
+                        const float cz = cf.y * csig;
                         const uint32_t h1r = pack_f16x2(cz * cs, -cz * sn);
                         w[0][t] = hr;
                         w[1][t] = __byte_perm(hr, 0u, 0x1032u) ^ 0x8000u;
