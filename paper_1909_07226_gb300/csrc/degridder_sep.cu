@@ -90,6 +90,7 @@ static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
 static_assert(128 % MMA_WARP == 0, "B tasks spread evenly over the warps before the MMA warp");
 static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
+static_assert(SL == 32, "one grid row per lane of warp 0");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
@@ -120,36 +121,38 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                      :: "r"(smem_u32(&s_tmem)), "n"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        for (int s = 0; s < AST; ++s) {
-            mbar_init(smem_u32(&s_afull[s]), NPW);
-            mbar_init(smem_u32(&s_aempty[s]), 1);
+    if (warp == 0) {
+        // barriers by lane 0; the copies are then issued by the whole warp, one per lane: the
+        // subgrid's 32 grid rows (1 KB each, contiguous in the grid) into the B area, which is
+        // free until B is formed at the end of the prologue, and the two stations' A-terms
+        if (lane == 0) {
+            for (int s = 0; s < AST; ++s) {
+                mbar_init(smem_u32(&s_afull[s]), NPW);
+                mbar_init(smem_u32(&s_aempty[s]), 1);
+            }
+            for (int e = 0; e < EST; ++e) {
+                mbar_init(smem_u32(&s_eyfull[e]), 1);
+                mbar_init(smem_u32(&s_eyempty[e]), NCW);
+                mbar_init(smem_u32(&s_dfull[e]), 1);
+                mbar_init(smem_u32(&s_dempty[e]), NCW);
+            }
+            mbar_init(smem_u32(&s_drain), 1);
+            mbar_init(smem_u32(&s_atbar), 1);
+            mbar_init(smem_u32(&s_gbar), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (FUSED) mbar_expect_tx(smem_u32(&s_gbar), SL * SL * 32);
+            if (aterms) mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
         }
-        for (int e = 0; e < EST; ++e) {
-            mbar_init(smem_u32(&s_eyfull[e]), 1);
-            mbar_init(smem_u32(&s_eyempty[e]), NCW);
-            mbar_init(smem_u32(&s_dfull[e]), 1);
-            mbar_init(smem_u32(&s_dempty[e]), NCW);
-        }
-        mbar_init(smem_u32(&s_drain), 1);
-        mbar_init(smem_u32(&s_atbar), 1);
-        mbar_init(smem_u32(&s_gbar), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        __syncwarp();
         if (FUSED) {
-            // the subgrid's 32 grid rows (1 KB each, contiguous in the grid) into the B area, which
-            // is free until B is formed at the end of the prologue
             const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
-            mbar_expect_tx(smem_u32(&s_gbar), SL * SL * 32);
-            for (int i = 0; i < SL; ++i)
-                bulk_g2s(smem_u32(smem + B0H_OFF + i * SL * 32), gsrc + 2 * ((size_t)(d.r0 + i) * g.N + d.q0), SL * 32,
-                         smem_u32(&s_gbar));
+            bulk_g2s(smem_u32(smem + B0H_OFF + lane * SL * 32), gsrc + 2 * ((size_t)(d.r0 + lane) * g.N + d.q0),
+                     SL * 32, smem_u32(&s_gbar));
         }
-        if (aterms) {
+        if (aterms && lane < 2) {
             const float4 *base = aterms + 2 * ((size_t)d.slot * g.n_stations) * SPIX;
-            mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
-            bulk_g2s(smem_u32(smem + AT_OFF), base + 2 * (size_t)d.st_p * SPIX, AT_BYTES, smem_u32(&s_atbar));
-            bulk_g2s(smem_u32(smem + AT_OFF + AT_BYTES), base + 2 * (size_t)d.st_q * SPIX, AT_BYTES,
-                     smem_u32(&s_atbar));
+            bulk_g2s(smem_u32(smem + AT_OFF + lane * AT_BYTES), base + 2 * (size_t)(lane ? d.st_q : d.st_p) * SPIX,
+                     AT_BYTES, smem_u32(&s_atbar));
         }
     }
 
