@@ -339,7 +339,7 @@ using namespace idg;
 struct idg_batch {
     struct Class {
         int L;
-        bool sep = false;              // L = 32 jobs whose plans take the separable kernels
+        bool sep = false;              // L = 32 or 24 jobs whose plans take the separable kernels
         int64_t n_items;
         double vispix;                 // sum of K_p L^2 of its items
         int2 *d_items = nullptr;
@@ -373,8 +373,8 @@ static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
         if (ks.tc) {
             ProfileScope ps(degrid ? IDG_KERNEL_BATCH_DEGRID : IDG_KERNEL_BATCH_GRID, s, cl.vispix);
             const idg_status st =
-                cl.sep ? (degrid ? launch_degridder_sep_batch(b->d_jobs, cl.d_items, cl.n_items, s)
-                                 : launch_gridder_sep_batch(b->d_jobs, cl.d_items, cl.n_items, s))
+                cl.sep ? (degrid ? launch_degridder_sep_batch(cl.L, b->d_jobs, cl.d_items, cl.n_items, s)
+                                 : launch_gridder_sep_batch(cl.L, b->d_jobs, cl.d_items, cl.n_items, s))
                        : (degrid ? launch_degridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s)
                                  : launch_gridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s));
             if (st != IDG_OK) return st;
@@ -505,7 +505,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         if (p->any_dropped && bufs[j].vis_out)
             b->zero_on_degrid.push_back({bufs[j].vis_out, (size_t)p->n_bl * p->n_t * p->n_chan * 32});
         size_t c = 0;
-        const bool sep = p->L == 32 && p->stats.separable;
+        const bool sep = separable_size(p->L) && p->stats.separable;
         while (c < b->classes.size() && (b->classes[c].L != p->L || b->classes[c].sep != sep)) ++c;
         if (c == b->classes.size()) {
             idg_batch::Class cl;
@@ -514,6 +514,8 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
             cl.n_items = 0;
             cl.vispix = 0.0;
             shapes_for(p->L, &cl.grid, &cl.degrid);
+            // L = 24 has tensor-core kernels only in the separable form
+            if (sep && p->L != 32) cl.grid = cl.degrid = kTcShape;
             b->classes.push_back(cl);
             per_class.emplace_back();
         }

@@ -158,7 +158,7 @@ __global__ void split_uvw_kernel(const double *__restrict__ uvw, float4 *__restr
     out[2 * i + 1] = make_float4(h[2], l[2], 0.0f, 0.0f);
 }
 
-// The separable kernels (L = 32) write the phasor of visibility k at pixel (x, y) as
+// The separable kernels (L = 32, 24) write the phasor of visibility k at pixel (x, y) as
 // exp(i (a X + c s(x))) exp(i (b Y + c t(y))) exp(i c r(x, y)) and keep the last
 // factor to first order, 1 + i c r; the dropped terms are at most theta^2 / 2 in
 // relative terms, theta = max |c| max |r|.  Below this bound that is <= 2^-20
@@ -443,7 +443,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         p->r_scale = r_max > 0.0 ? (float)std::ldexp(1.0, std::min(100, (int)std::floor(std::log2(1.0 / r_max)))) : 1.0f;
         // (the separable degridder stages visibility indices in 31 bits)
         const bool fits = (int64_t)n_bl * n_t * n_chan < 0x7FFFFFFFll;
-        p->stats.separable = (L == 32 && p->sep_theta <= kSepThetaMax && fits) ? 1 : 0;
+        p->stats.separable = (separable_size(L) && p->sep_theta <= kSepThetaMax && fits) ? 1 : 0;
         p->stats.sep_phase = p->sep_theta;
     }
 
@@ -678,12 +678,15 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
 // the default kernel choice with the FP32 transform, direct phasors and the
 // plain adder.  The degridder takes them when most visibilities of the launch
 // lie in subgrids of at least 512 (as the default per-call choice does).
+// the fused composite kernels: the direct tensor-core ones at L = 32, the separable ones at
+// L = 32 and 24 where the plan is separable (the process-default kernel choice only)
+static bool fused_size(const idg_plan *p) { return p->L == 32 || (p->L == 24 && p->stats.separable); }
 static bool fused_grid(const idg_plan *p) {
-    return p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+    return fused_size(p) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
            p->opts.adder_mode == IDG_ADDER_ATOMIC && p->kernel_variant(IDG_KERNEL_GRIDDER) == 0;
 }
 static bool fused_degrid(const idg_plan *p, const SubgridSet &set) {
-    if (!(p->L == 32 && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+    if (!(fused_size(p) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
           p->kernel_variant(IDG_KERNEL_DEGRIDDER) == 0))
         return false;
     int64_t small = 0, all = 0;

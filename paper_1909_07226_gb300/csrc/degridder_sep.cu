@@ -58,8 +58,6 @@ namespace {
 using namespace dev;
 using namespace tc;
 
-constexpr int SL = 32;
-constexpr int SPIX = SL * SL;
 constexpr int NPW = 8, NCW = 8;                 // producer and consumer warps
 constexpr int NP = NPW * 32, NC = NCW * 32;
 constexpr int MMA_WARP = NPW + NCW;
@@ -68,41 +66,62 @@ constexpr int NT = NP + NC + 64;
 constexpr int TV = 64;                          // visibilities per tile (rows 2 k + re/im)
 constexpr int AST = 2;                          // A stages (gated by the MMAs)
 constexpr int EST = 4;                          // Ey*, coefficient stages and accumulators (gated by the consumers)
-constexpr int KT = 4;                           // K steps of 16 (8 x, re/im) over the 32 x
 constexpr int T4K = 128 * 32;                   // 128 rows x 16 K FP16
-// B (fixed per subgrid), each [KT][128 rows (q, y)]: Q0 hi, Q0 lo, Q1 hi
-constexpr int B0H_OFF = 0, B0L_OFF = B0H_OFF + KT * T4K, B1H_OFF = B0L_OFF + KT * T4K;
-constexpr int A_OFF = B1H_OFF + KT * T4K;       // A: [AST][m = 0 hi, m = 0 lo, m = 1 hi][KT][128 rows]
-constexpr int A_STAGE = 3 * KT * T4K;
-constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [2][16 y pairs][TV] float4 (written and read by the consumers)
-constexpr int EY_STAGE = SL * TV * 8;
-constexpr int CF_OFF = EY_OFF + 2 * EY_STAGE;   // coefficients: [EST][TV] float4 (a, b, c, index)
-constexpr int PART_OFF = CF_OFF + EST * TV * 16;  // consumer exchange: [2 tiles][re, im][h][4][TV] float
-constexpr int SEPD_SMEM = PART_OFF + 2 * 2 * 2 * 4 * TV * 4;
-constexpr int FFT_P = SL + 1;
-// the subgrid's A-terms (A_p, A_q: [2][L^2] 2 x 2 complex, 64 KB), fetched by bulk copies at the
-// start of the prologue beside the transform planes (A stages and Ey* table are free until the tiles)
-constexpr int AT_OFF = A_OFF + 4 * SL * FFT_P * 8;
-constexpr uint32_t AT_BYTES = SPIX * 32;       // one station
-constexpr uint32_t IDESC_N128 = idesc_m128(128);
-static_assert(4 * SL * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
-static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
+constexpr int CF_BYTES = EST * TV * 16;         // coefficients: [EST][TV] float4 (a, b, c, index)
+constexpr int PART_BYTES = 2 * 2 * 2 * 4 * TV * 4;   // consumer exchange: [2 tiles][re, im][h][4][TV] float
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
-static_assert(128 % MMA_WARP == 0, "B tasks spread evenly over the warps before the MMA warp");
-static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
-static_assert(SL == 32, "one grid row per lane of warp 0");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
+
+// Layout for subgrid size L (32 or 24)
+template <int L>
+struct SepD {
+    static constexpr int SL = L, SPIX = L * L;
+    static constexpr int KT = L / 8;                // K steps of 16 (8 x, re/im) over the L x
+    // B (fixed per subgrid), each [KT][4 L rows (q, y), padded to 128]: Q0 hi, Q0 lo, Q1 hi
+    static constexpr int B0H_OFF = 0, B0L_OFF = B0H_OFF + KT * T4K, B1H_OFF = B0L_OFF + KT * T4K;
+    static constexpr int A_OFF = B1H_OFF + KT * T4K;   // A: [AST][m = 0 hi, m = 0 lo, m = 1 hi][KT][128 rows]
+    static constexpr int A_STAGE = 3 * KT * T4K;
+    static constexpr int EY_OFF = A_OFF + AST * A_STAGE;   // Ey*: [2][L / 2 y pairs][TV] float4 (consumers)
+    static constexpr int EY_STAGE = L * TV * 8;
+    static constexpr int CF_OFF = EY_OFF + 2 * EY_STAGE;
+    static constexpr int PART_OFF = CF_OFF + CF_BYTES;
+    static constexpr int SMEM = PART_OFF + PART_BYTES;
+    static constexpr int FFT_P = L + 1;
+    // the subgrid's A-terms (A_p, A_q: [2][L^2] 2 x 2 complex), fetched by bulk copies at the
+    // start of the prologue beside the transform planes (A stages and Ey* table are free until
+    // the tiles)
+    static constexpr int AT_OFF = A_OFF + 4 * L * FFT_P * 8;
+    static constexpr uint32_t AT_BYTES = SPIX * 32;       // one station
+    static constexpr uint32_t IDESC_N = idesc_m128(4 * L);
+    // B tasks of the prologue: (q, y block of 8, x chunk of 4), one core matrix each
+    static constexpr int YB = L / 8, XC = L / 4, NTASK = 4 * YB * XC;
+    static constexpr int NWT = (NTASK + MMA_WARP - 1) / MMA_WARP;
+    static constexpr int EYP = L * TV / NC / 2;     // Ey* pairs per consumer thread
+    static_assert(L == 32 || L == 24, "subgrid sizes of the separable kernels");
+    static_assert(4 * L * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
+    static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
+    static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
+    static_assert(L <= 32, "one grid row per lane of warp 0");
+    static_assert(4 * L <= 128 && (4 * L) % 16 == 0, "B rows (q, y) in one MMA");
+    static_assert(L * TV % (2 * NC) == 0 && (L / 2) % 4 == 0, "Ey* pairs spread evenly over the consumers");
+    static_assert(L % 8 == 0 && 4 * NPW >= L, "x columns over the producer warps");
+};
 
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 2, %0;" :: "n"(NC) : "memory"); }
 
 // Visibilities of subgrid d of geometry g from its image src[L][L][4], or with
 // FUSED from the grid src[layer][N][N][4]: split and transformed in shared memory
 // first (Algorithm 2: split from the master grid, "IFFT", image-domain kernel, sum).
-template <bool FUSED>
+template <int L, bool FUSED>
 __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevSubgrid d,
                                                    const float4 *__restrict__ src, const uint8_t *__restrict__ flags,
                                                    const float4 *__restrict__ aterms, const float *__restrict__ taper,
                                                    float4 *__restrict__ vis_out) {
+    using C = SepD<L>;
+    constexpr int SL = C::SL, SPIX = C::SPIX, KT = C::KT, B0H_OFF = C::B0H_OFF, B0L_OFF = C::B0L_OFF;
+    constexpr int B1H_OFF = C::B1H_OFF, A_OFF = C::A_OFF, A_STAGE = C::A_STAGE, EY_OFF = C::EY_OFF;
+    constexpr int CF_OFF = C::CF_OFF, PART_OFF = C::PART_OFF, FFT_P = C::FFT_P, AT_OFF = C::AT_OFF;
+    constexpr uint32_t AT_BYTES = C::AT_BYTES;
     extern __shared__ __align__(1024) uint8_t smem[];
     float2 *s_fft = (float2 *)(smem + A_OFF);       // [4][L][L + 1] during the prologue
     float4 *s_coef = (float4 *)(smem + CF_OFF);
@@ -144,7 +163,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             if (aterms) mbar_expect_tx(smem_u32(&s_atbar), 2 * AT_BYTES);
         }
         __syncwarp();
-        if (FUSED) {
+        if (FUSED && lane < SL) {
             const float4 *gsrc = src + (size_t)d.layer * g.N * g.N * 2;
             bulk_g2s(smem_u32(smem + B0H_OFF + lane * SL * 32), gsrc + 2 * ((size_t)(d.r0 + lane) * g.N + d.q0),
                      SL * 32, smem_u32(&s_gbar));
@@ -194,13 +213,15 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     float tw_pre[NPIX];
 #pragma unroll
     for (int i = 0; i < NPIX; ++i) tw_pre[i] = tid + i * NT < SPIX ? taper[tid + i * NT] : 0.0f;
-    constexpr int NWT = 128 / MMA_WARP;
+    constexpr int NWT = C::NWT;
     float rr_pre[NWT];
 #pragma unroll
     for (int i = 0; i < NWT; ++i) {
         const int wt = warp + MMA_WARP * i;
-        rr_pre[i] = warp < MMA_WARP ? g.sep[2 * SL + (8 * ((wt >> 3) & 3) + (lane >> 2)) * SL + 4 * (wt & 7) + (lane & 3)]
-                                    : 0.0f;
+        const int yb = (wt / C::XC) % C::YB, xc = wt % C::XC;
+        rr_pre[i] = warp < MMA_WARP && wt < C::NTASK
+                        ? g.sep[2 * SL + (8 * yb + (lane >> 2)) * SL + 4 * xc + (lane & 3)]
+                        : 0.0f;
     }
     __syncthreads();      // the copies' barriers are initialised
 
@@ -220,7 +241,10 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             s_fft[(3 * SL + i) * FFT_P + j] = make_float2(sg * b.z, sg * b.w);
         }
         __syncthreads();
-        fft2_planar_pairs32<+1>(s_fft, tid);
+        if constexpr (SL == 32)
+            fft2_planar_pairs32<+1>(s_fft, tid);
+        else
+            fft2_planar<SL, +1>(s_fft, tid, NT);
     }
     if (aterms) {
         bool late = false;
@@ -232,7 +256,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     for (int ip = 0; ip < NPIX; ++ip) {
         const int pix = tid + ip * NT;
         if (pix >= SPIX) break;
-        const int y = pix >> 5, x = pix & (SL - 1);
+        const int y = pix / SL, x = pix % SL;
         M22 P;
         if (FUSED) {      // (-1)^(x+y) / L^2 of the transform
             const float sg = ((x + y) & 1) ? -1.0f / SPIX : 1.0f / SPIX;
@@ -272,21 +296,22 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
     if (m > 0.0f) frexpf(m, &e2);
     const float scale = ldexpf(1.0f, 10 - e2);
     const float inv_scale = ldexpf(1.0f, e2 - 10);
-    // B: Q0 = scale P (hi and lo), Q1 = scale r P / sigma (hi), rows 32 q + y; one core matrix
+    // B: Q0 = scale P (hi and lo), Q1 = scale r P / sigma (hi), rows L q + y; one core matrix
     // (8 rows y, 4 x) per warp store: warp-task wt = (q, y block, x chunk of 4)
     if (warp < MMA_WARP) {
         const float rs = scale / g.c_scale;
 #pragma unroll
         for (int i = 0; i < NWT; ++i) {
             const int wt = warp + MMA_WARP * i;
-            const int q = wt >> 5, yb = (wt >> 3) & 3, xc = wt & 7;
+            if (wt >= C::NTASK) break;
+            const int q = wt / (C::YB * C::XC), yb = (wt / C::XC) % C::YB, xc = wt % C::XC;
             const int y = 8 * yb + (lane >> 2), x = 4 * xc + (lane & 3);
             const float2 p = s_fft[(q * SL + y) * FFT_P + x];
             const float rr = rr_pre[i] * rs;
             uint32_t h0, l0;
             split_e(p.x * scale, p.y * scale, h0, l0);
             const uint32_t h1 = pack_f16x2(p.x * rr, p.y * rr);
-            const uint32_t off = (uint32_t)(4 * q + yb) * kSBO + (uint32_t)(xc & 1) * kLBO + (uint32_t)(lane >> 2) * 16 +
+            const uint32_t off = (uint32_t)(C::YB * q + yb) * kSBO + (uint32_t)(xc & 1) * kLBO + (uint32_t)(lane >> 2) * 16 +
                                  (uint32_t)(lane & 3) * 4;
             const int kk = xc >> 1;
             *(uint32_t *)(smem + B0H_OFF + kk * T4K + off) = h0;
@@ -312,11 +337,11 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
                 for (int kk = 0; kk < KT; ++kk) {
                     const uint64_t da = da0 + (uint64_t)((s * A_STAGE + kk * T4K) >> 4);     // m = 0 hi
                     const uint64_t db = db0 + (uint64_t)((kk * T4K) >> 4);                  // Q0 hi
-                    mma_ss_i(dt, da, db, IDESC_N128, kk > 0 ? 1u : 0u);
-                    mma_ss_i(dt, da, db + (uint64_t)((KT * T4K) >> 4), IDESC_N128, 1u);        // Q0 lo
-                    mma_ss_i(dt, da + (uint64_t)((KT * T4K) >> 4), db, IDESC_N128, 1u);        // m = 0 lo
+                    mma_ss_i(dt, da, db, C::IDESC_N, kk > 0 ? 1u : 0u);
+                    mma_ss_i(dt, da, db + (uint64_t)((KT * T4K) >> 4), C::IDESC_N, 1u);        // Q0 lo
+                    mma_ss_i(dt, da + (uint64_t)((KT * T4K) >> 4), db, C::IDESC_N, 1u);        // m = 0 lo
                     mma_ss_i(dt, da + (uint64_t)((2 * KT * T4K) >> 4), db + (uint64_t)((2 * KT * T4K) >> 4),
-                             IDESC_N128, 1u);                                                // m = 1 hi x Q1 hi
+                             C::IDESC_N, 1u);                                                // m = 1 hi x Q1 hi
                 }
                 commit(smem_u32(&s_aempty[s]));
                 commit(smem_u32(&s_dfull[e]));
@@ -331,7 +356,8 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         // A rows are (re/im, k): row k = (Re E, -Im E), row 64 + k = (Im E, Re E).  Lane = 4 k_lo + x_lo:
         // warp w owns x = 4 w + x_lo (K step w / 2, chunk w % 2) and writes visibilities 8 kg + k_lo
         const int klo = lane >> 2, xlo = lane & 3, x = 4 * warp + xlo;
-        const float Xv = (float)(x - SL / 2), sx = g.sep[x], csig = g.c_scale;
+        const bool x_ok = SL == 32 || 4 * warp < SL;    // warps past the last x only keep the protocol
+        const float Xv = (float)(x - SL / 2), sx = g.sep[x_ok ? x : 0], csig = g.c_scale;
         const uint32_t a_off = (uint32_t)(warp >> 1) * T4K + (uint32_t)(warp & 1) * kLBO + (uint32_t)klo * 16 +
                                (uint32_t)xlo * 4;
         for (int t = 0; t < n_tiles; ++t) {
@@ -342,6 +368,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             uint8_t *As = smem + A_OFF + s * A_STAGE;
 #pragma unroll 2
             for (int kg = 0; kg < TV / 8; ++kg) {
+                if (!x_ok) break;
                 const float4 c = cf[8 * kg + klo];
                 float sn, cs;
                 __sincosf(fmaf(c.z, sx, c.x * Xv), &sn, &cs);
@@ -407,7 +434,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         // Ey* entries: visibility ke = ctid % TV, rows y = 2 p, 2 p + 1 of the pairs p = ctid / TV + 4 j
         // (ctid = consumer thread index); entry (p, k) = (cs_2p, cs_2p+1, -sn_2p, -sn_2p+1)
         const int ctid = tid - NP, ke = ctid & (TV - 1), p0 = ctid >> 6;
-        constexpr int EYP = SL * TV / NC / 2;     // pairs per thread
+        constexpr int EYP = C::EYP;               // pairs per thread
         float tys[2 * EYP];
 #pragma unroll
         for (int j = 0; j < EYP; ++j) {
@@ -418,7 +445,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             const int s = t & 1, e = t & 3;
             wait_or_fail(smem_u32(&s_eyfull[e]), (uint32_t)((t >> 2) & 1), failed);
             // Ey*_k(y) = exp(-i (b_k Y + c_k t(y))) of the tile (entry y TV + k), while its MMAs run
-            float4 *eyw = s_ey + s * (SL / 2 * TV);
+            float4 *eyw = s_ey + s * (SL / 2 * TV);     // [L / 2 pairs][TV]
             {
                 const float4 c = s_coef[e * TV + ke];
 #pragma unroll
@@ -439,11 +466,11 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
 #pragma unroll
             for (int q2 = 0; q2 < 2; ++q2) accp[q2][0] = accp[q2][1] = 0ull;
 #pragma unroll 1
-            for (int yc = 0; yc < 4; ++yc) {         // rows y in [8 yc, 8 yc + 8)
+            for (int yc = 0; yc < SL / 8; ++yc) {    // rows y in [8 yc, 8 yc + 8)
                 uint32_t r[2][8];
 #pragma unroll
                 for (int qp = 0; qp < 2; ++qp)       // columns 32 (2 h + q') + y
-                    tmem_ld8_nowait(lane_base + 128u * (uint32_t)e + (uint32_t)(64 * h + 32 * qp + 8 * yc), r[qp]);
+                    tmem_ld8_nowait(lane_base + 128u * (uint32_t)e + (uint32_t)(SL * (2 * h + qp) + 8 * yc), r[qp]);
                 ulonglong2 ep[4];
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) ep[pp] = ey[(4 * yc + pp) * TV + kl];
@@ -506,29 +533,45 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
 }
 
 // one CTA per subgrid of one plan (plan index idx[b] or first + b; image b of sub)
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 degridder_sep_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ sub,
                      const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                      const float *__restrict__ taper, float4 *__restrict__ vis_out) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    degridder_sep_body<false>(g, g.sub[sid], sub + (size_t)blockIdx.x * SPIX * 2, flags, aterms, taper, vis_out);
+    degridder_sep_body<L, false>(g, g.sub[sid], sub + (size_t)blockIdx.x * L * L * 2, flags, aterms, taper, vis_out);
 }
 
 // fused: one CTA per subgrid, read from the grid
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 degridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
                            const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                            const float *__restrict__ taper, float4 *__restrict__ vis_out) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    degridder_sep_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
+    degridder_sep_body<L, true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
 }
 
 // fused, one CTA per work item (job, subgrid) of a batch: split from the job's grid
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 degridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
     const int2 it = items[blockIdx.x];
     const JobDev &J = jobs[it.x];
-    degridder_sep_body<true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
+    degridder_sep_body<L, true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
+}
+
+template <int L>
+idg_status launch_sepd_set(bool fused, const Geometry &g, const SubgridSet &set, const void *src, const uint8_t *flags,
+                           const void *aterms, const float *taper, void *vis_out, cudaStream_t s) {
+    auto kern = fused ? degridder_sep_fused_kernel<L> : degridder_sep_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SepD<L>::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "separable degridder smem attribute");
+    kern<<<(unsigned)set.count, NT, SepD<L>::SMEM, s>>>(g, set.idx, set.first, (const float4 *)src, flags,
+                                                       (const float4 *)aterms, taper, (float4 *)vis_out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? IDG_OK
+                            : cuda_fail(e, fused ? "separable fused degridder launch" : "separable degridder launch");
 }
 
 }  // namespace
@@ -536,14 +579,22 @@ degridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restri
 cudaError_t prepare_sep_batch_kernels() {
     cudaError_t e = prepare_gridder_sep_batch();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(degridder_sep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
+        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SepD<32>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SepD<24>::SMEM);
     return e;
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_degridder_sep_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
+idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
-    degridder_sep_batch_kernel<<<(unsigned)count, NT, SEPD_SMEM, (cudaStream_t)stream>>>(jobs, items);
+    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24");
+    if (L == 32)
+        degridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepD<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
+    else
+        degridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepD<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "separable batch degridder launch");
     return IDG_OK;
@@ -551,31 +602,20 @@ idg_status launch_degridder_sep_batch(const JobDev *jobs, const int2 *items, int
 
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {
-    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 and a separable plan");
+    if (!separable_size(g.L) || !g.separable)
+        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(degridder_sep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
-    if (e != cudaSuccess) return cuda_fail(e, "separable degridder smem attribute");
-    degridder_sep_kernel<<<(unsigned)set.count, NT, SEPD_SMEM, s>>>(g, set.idx, set.first, (const float4 *)sub, flags,
-                                                                    (const float4 *)aterms, taper, (float4 *)vis_out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable degridder launch");
-    return IDG_OK;
+    return g.L == 32 ? launch_sepd_set<32>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream)
+                     : launch_sepd_set<24>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
 }
 
 idg_status launch_degridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
                                       const void *aterms, const float *taper, void *vis_out, void *stream) {
-    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 and a separable plan");
+    if (!separable_size(g.L) || !g.separable)
+        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(degridder_sep_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEPD_SMEM);
-    if (e != cudaSuccess) return cuda_fail(e, "separable degridder smem attribute");
-    degridder_sep_fused_kernel<<<(unsigned)set.count, NT, SEPD_SMEM, s>>>(g, set.idx, set.first, (const float4 *)grid,
-                                                                          flags, (const float4 *)aterms, taper,
-                                                                          (float4 *)vis_out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable fused degridder launch");
-    return IDG_OK;
+    return g.L == 32 ? launch_sepd_set<32>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream)
+                     : launch_sepd_set<24>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
 }
 
 idg_status read_sepd_error(int *code) {

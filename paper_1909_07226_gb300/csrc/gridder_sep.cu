@@ -72,8 +72,6 @@ namespace {
 using namespace dev;
 using namespace tc;
 
-constexpr int SL = 32;
-constexpr int SPIX = SL * SL;
 constexpr int NPW = 16;                        // producer warps
 constexpr int NP = NPW * 32;                   // producer threads
 constexpr int NT = NP + 32;                    // + the MMA warp
@@ -82,40 +80,60 @@ constexpr int GB = VB / 8;                     // groups per batch
 constexpr int FOLD = 64;                       // groups per accumulation period
 constexpr int SG = 8;                          // groups of 8 visibilities per stage
 constexpr int STAGES = 2;
-constexpr int B_GROUP = 192 * 32;              // B of one group: 192 rows x 16 K FP16 (hi 128 rows, then lo 64)
-constexpr int B_STAGE = SG * B_GROUP;
-// coefficients as two float pairs, [2][VB] (b, c) for the Ey side, then [2][VB] (a, c) for
-// the Ex side: the shared-memory pipe is close to its limit in the main loop and its cost
-// is the bytes each thread reads (a float4 where two floats are used costs twice)
-constexpr int COEF_OFF = STAGES * B_STAGE;
-constexpr int VIS_OFF = COEF_OFF + 2 * VB * 16;   // [2][VB][4] float2 (scaled V)
-constexpr int FOLD_OFF = VIS_OFF + 2 * VB * 32;   // [32][NP] float: folded sums of each producer
-constexpr int SEP_SMEM = FOLD_OFF + 32 * NP * 4;
-constexpr int FFT_P = SL + 1;
-// the subgrid's A-terms after the main loop: [2 stations][L^2] 2 x 2 complex, beside the
-// transform planes, over the stage and coefficient buffers
-constexpr int AT_OFF = 4 * SL * FFT_P * 8;
-constexpr uint32_t AT_BYTES = SPIX * 32;
-constexpr uint32_t A_COL = 192;                 // accumulator 0..191, then the A stages
-constexpr uint32_t IDESC_N192 = idesc_m128(192), IDESC_N64 = idesc_m128(64);
-static_assert(4 * SL * FFT_P * 8 <= FOLD_OFF, "transform planes fit over the stage buffers");
-static_assert(SEP_SMEM + 1024 <= 227 * 1024, "dynamic and static shared memory of one CTA");
-static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= VIS_OFF, "A-terms over the stage and coefficient buffers");
-static_assert(A_COL + 16 * SG * STAGES <= 512, "tensor memory");
 static_assert(FOLD / SG >= STAGES, "a period spans at least STAGES stages");
 static_assert((STAGES & (STAGES - 1)) == 0, "STAGES is a power of two");
 static_assert(FOLD % SG == 0 && GB % SG == 0, "periods and batches are whole stages");
+
+// Layout for subgrid size L (32 or 24).  A has 128 rows: lane quarter yq holds pixel rows
+// y = (L / 4) yq + ylo for ylo < L / 4 at lanes 8 q + ylo (at L = 24 lanes with ylo = 6, 7
+// carry zeros).  B has 6 L rows per group: (m = 0, re), (m = 0, im), (m = 1, re),
+// (m = 1, im), then the lo parts of m = 0 re and im, L rows each.
+template <int L>
+struct SepG {
+    static constexpr int SL = L, SPIX = L * L, YQ = L / 4;
+    static constexpr int B_GROUP = 6 * L * 32;   // B of one group: 6 L rows x 16 K FP16
+    static constexpr int B_STAGE = SG * B_GROUP;
+    // coefficients as two float pairs, [2][VB] (b, c) for the Ey side, then [2][VB] (a, c)
+    // for the Ex side: the shared-memory pipe is close to its limit in the main loop and its
+    // cost is the bytes each thread reads (a float4 where two floats are used costs twice)
+    static constexpr int COEF_OFF = STAGES * B_STAGE;
+    static constexpr int VIS_OFF = COEF_OFF + 2 * VB * 16;   // [2][VB][4] float2 (scaled V)
+    static constexpr int FOLD_OFF = VIS_OFF + 2 * VB * 32;   // [32][NP] float: folded sums of each producer
+    static constexpr int SMEM = FOLD_OFF + 32 * NP * 4;
+    static constexpr int FFT_P = L + 1;
+    // the subgrid's A-terms after the main loop: [2 stations][L^2] 2 x 2 complex, beside the
+    // transform planes, over the stage and coefficient buffers
+    static constexpr int AT_OFF = 4 * L * FFT_P * 8;
+    static constexpr uint32_t AT_BYTES = SPIX * 32;
+    // accumulator: main (m, re/im, x) at 0 .. 4 L, correction (m = 0) at 4 L .. 6 L; then the
+    // A stages
+    static constexpr uint32_t A_COL = 6 * L;
+    static constexpr uint32_t IDESC_NB = idesc_m128(6 * L), IDESC_NC = idesc_m128(2 * L);
+    static constexpr int NSL = L / 8;             // 16-column slices of the m = 0 block (fold)
+    static constexpr int XS = L / 4;              // x values per producer in the epilogue
+    static_assert(L == 32 || L == 24, "subgrid sizes of the separable kernels");
+    static_assert(4 * L * FFT_P * 8 <= FOLD_OFF, "transform planes fit over the stage buffers");
+    static_assert(SMEM + 1024 <= 227 * 1024, "dynamic and static shared memory of one CTA");
+    static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= VIS_OFF, "A-terms over the stage and coefficient buffers");
+    static_assert(A_COL % 16 == 0 && A_COL + 16 * SG * STAGES <= 512, "tensor memory");
+    static_assert(NSL <= NPW / 4, "one fold slice per warp of a lane quarter");
+};
 
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" :: "n"(NP) : "memory"); }
 
 // One subgrid d of geometry g (taper and A-terms applied): into o[L][L][4], or with
 // FUSED transformed in shared memory and added into the grid o[layer][N][N][4]
 // (Algorithm 1: direct sum, image-domain kernel, "FFT", add to the master grid).
-template <bool FUSED>
+template <int L, bool FUSED>
 __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSubgrid d,
                                                  const float4 *__restrict__ vis, const uint8_t *__restrict__ flags,
                                                  const float4 *__restrict__ aterms, const float *__restrict__ taper,
                                                  float4 *__restrict__ o) {
+    using C = SepG<L>;
+    constexpr int SL = C::SL, SPIX = C::SPIX, YQ = C::YQ, B_GROUP = C::B_GROUP, B_STAGE = C::B_STAGE;
+    constexpr int COEF_OFF = C::COEF_OFF, VIS_OFF = C::VIS_OFF, FOLD_OFF = C::FOLD_OFF, FFT_P = C::FFT_P;
+    constexpr int AT_OFF = C::AT_OFF, XS = C::XS;
+    constexpr uint32_t AT_BYTES = C::AT_BYTES, A_COL = C::A_COL;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sB = smem;
     float2 *s_cb = (float2 *)(smem + COEF_OFF);          // [2][VB] (b, c)
@@ -184,9 +202,10 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
 #pragma unroll
                 for (int i = 0; i < SG; ++i) {
                     if (i < ng) {
-                        mma_ta_i(tmem, ats + 16u * i, dbs + (uint64_t)((i * B_GROUP) >> 4), IDESC_N192,
+                        mma_ta_i(tmem, ats + 16u * i, dbs + (uint64_t)((i * B_GROUP) >> 4), C::IDESC_NB,
                                  (first && i == 0) ? 0u : 1u);
-                        mma_ta_i(tmem + 128u, ats + 16u * i + 8u, dbs + (uint64_t)((i * B_GROUP) >> 4), IDESC_N64, 1u);
+                        mma_ta_i(tmem + 4u * SL, ats + 16u * i + 8u, dbs + (uint64_t)((i * B_GROUP) >> 4), C::IDESC_NC,
+                                 1u);
                     }
                 }
                 if (last) commit(smem_u32(&s_foldbar));
@@ -210,18 +229,22 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         failed = __shfl_sync(0xffffffffu, failed, 0);
         load_taper();
     } else {
-        // A rows: r = 32 yq + lane holds polarisation qa = lane / 8 of pixel row y = 8 yq + lane % 8
+        // A rows: r = 32 yq + lane holds polarisation qa = lane / 8 of pixel row y = YQ yq + lane % 8
+        // (rows with lane % 8 >= YQ are zero)
         const int qa = lane >> 3, ylo = lane & 7;
+        const bool row_ok = YQ == 8 || ylo < YQ;
+        const int yrow = YQ * yq + (row_ok ? ylo : 0);
         const int ga = warp >> 2;                   // group of the stage whose A entries this warp writes
         const uint32_t lane_base = tmem + ((uint32_t)(32 * yq) << 16);
         // Ey of row y for visibilities 2 qa and 2 qa + 1 of the group: computed here, shared by shuffles
-        const float Yv = (float)(8 * yq + ylo - SL / 2);
-        const float ty = g.sep[SL + 8 * yq + ylo];
+        const float Yv = (float)(yrow - SL / 2);
+        const float ty = g.sep[SL + yrow];
         // B entries: x = 8 (warp & 3) + lane % 8, visibility j = 4 jh + lane / 8 of group i, where
         // (i, jh) = (combo / 2, combo % 2) for combo = 2 (warp / 4) + t, t = 0, 1
         const int xb = 8 * (warp & 3) + (lane & 7), jl = lane >> 3;
+        const bool x_ok = SL == 32 || xb < SL;      // the same for the whole warp (L is a multiple of 8)
         const float Xv = (float)(xb - SL / 2);
-        const float sx = g.sep[xb];
+        const float sx = g.sep[x_ok ? xb : 0];
         const float csig = g.c_scale;
         const uint16_t m1h = 0xBC00u;      // FP16 -1
 
@@ -284,11 +307,18 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // this thread's row, columns 16 sl .. of the m = 0 block (main + correction) and of m = 1;
             // the accumulator is released right after the loads
+            constexpr bool all_fold = C::NSL == NPW / 4;
+            if (!all_fold && sl >= C::NSL) {      // no slice of the m = 0 block for this warp
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&s_folded));
+                return;
+            }
             uint32_t r[16], rc[16], r1[16];
             const uint32_t base = lane_base + 16u * (uint32_t)sl;
             tmem_ld16(base, r);
-            tmem_ld16(base + 128u, rc);
-            tmem_ld16(base + 64u, r1);
+            tmem_ld16(base + 4u * SL, rc);
+            tmem_ld16(base + 2u * SL, r1);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_folded));
@@ -358,6 +388,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                         const float sn = __shfl_sync(0xffffffffu, (j & 1) ? es[1] : es[0], src);
                         const float2 v = vb[(kb + j) * 4 + qa];
                         split_e_m(fmaf(v.x, cs, -v.y * sn), fmaf(v.x, sn, v.y * cs), m1h, e[j], e[8 + j]);
+                        if (!row_ok) e[j] = e[8 + j] = 0u;
                     }
                     tmem_st16(lane_base + A_COL + 16u * SG * (uint32_t)s + 16u * (uint32_t)(ga + 4 * gg), e);
                 }
@@ -366,6 +397,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                 uint8_t *Bs = sB + s * B_STAGE;
 #pragma unroll
                 for (int gg = 0; gg < SG / 4; ++gg) {
+                    if (!x_ok) break;
                     // visibilities j0 = 2 jl and j0 + 1 of group i = warp / 4 + 4 gg sit in adjacent K
                     // slots of each row: one 8-byte store per row
                     const int i = (warp >> 2) + 4 * gg, j0 = 2 * jl;
@@ -390,10 +422,10 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
                     }
                     uint8_t *Bg = Bs + i * B_GROUP + (uint32_t)(xb >> 3) * kSBO + (uint32_t)(jl >> 1) * kLBO +
                                   (uint32_t)(xb & 7) * 16 + (uint32_t)(jl & 1) * 8;
-                    // row blocks of 32 (4 kSBO): m = 0 re, m = 0 im, m = 1 re, m = 1 im, then the lo
-                    // parts of m = 0 re and im (rows 128 + x, 160 + x)
+                    // row blocks of L (L / 8 kSBO): m = 0 re, m = 0 im, m = 1 re, m = 1 im, then the lo
+                    // parts of m = 0 re and im (rows 4 L + x, 5 L + x)
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) *(uint2 *)(Bg + 4 * q * kSBO) = make_uint2(w[q][0], w[q][1]);
+                    for (int q = 0; q < 6; ++q) *(uint2 *)(Bg + (SL / 8) * q * kSBO) = make_uint2(w[q][0], w[q][1]);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -409,35 +441,34 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         }
         // the epilogue's global reads first: taper, and r(x, y) of this thread's x range
         load_taper();
-        const int x0 = 16 * (sl & 1) + 8 * (sl >> 1);
-        const int y = 8 * yq + ylo;
-        float rr_pre[8];
+        const int x0 = XS * sl;                     // this thread's x range in the epilogue
+        float rr_pre[XS];
 #pragma unroll
-        for (int xi = 0; xi < 8; ++xi) rr_pre[xi] = g.sep[2 * SL + y * SL + x0 + xi];
+        for (int xi = 0; xi < XS; ++xi) rr_pre[xi] = g.sep[2 * SL + yrow * SL + x0 + xi];
         while (next_fold < n_batches) {
             fold(next_fold);
             ++next_fold;
         }
         if (failed && lane == 0) atomicExch(&g_sep_error, 1);
         producers_sync();      // every producer is past the stage and batch buffers and has folded
-        if (!failed) {
-            // I = S0 + i r S1 / sigma into the polarisation planes.  Column slice sl holds the
-            // re (sl < 2) or im (sl >= 2) part of x in [16 (sl & 1), + 16); the thread with
-            // slice sl takes 8 of those x, reading the re and im parts of both slices.
-            const int tre = tid & ~256, tim = tid | 256;     // threads holding re and im of this row and x range
+        if (!failed && row_ok) {
+            // I = S0 + i r S1 / sigma into the polarisation planes.  Column C of the m = 0 block
+            // (re: C = x, im: C = L + x) was folded by the thread of slice C / 16 of this row,
+            // warp 4 (C / 16) + yq, as its entry C % 16.
             const float rs = 1.0f / csig;
 #pragma unroll
-            for (int xi = 0; xi < 8; ++xi) {
-                const int x = x0 + xi, c = x & 15;
+            for (int xi = 0; xi < XS; ++xi) {
+                const int x = x0 + xi, cre = x, cim = SL + x;
+                const int tre = (4 * (cre >> 4) + yq) * 32 + lane, tim = (4 * (cim >> 4) + yq) * 32 + lane;
                 float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f;
                 if (n_batches) {
-                    s0r = s_fold[c * NP + tre];
-                    s0i = s_fold[c * NP + tim];
-                    s1r = s_fold[(16 + c) * NP + tre];
-                    s1i = s_fold[(16 + c) * NP + tim];
+                    s0r = s_fold[(cre & 15) * NP + tre];
+                    s0i = s_fold[(cim & 15) * NP + tim];
+                    s1r = s_fold[(16 + (cre & 15)) * NP + tre];
+                    s1i = s_fold[(16 + (cim & 15)) * NP + tim];
                 }
                 const float rr = rr_pre[xi] * rs;
-                s_fft[(qa * SL + y) * FFT_P + x] = make_float2(fmaf(-rr, s1i, s0r), fmaf(rr, s1r, s0i));
+                s_fft[(qa * SL + yrow) * FFT_P + x] = make_float2(fmaf(-rr, s1i, s0r), fmaf(rr, s1r, s0i));
             }
         }
     }
@@ -453,7 +484,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         for (int ip = 0; ip < NPIX; ++ip) {
             const int pix = tid + ip * NT;
             if (pix >= SPIX) break;
-            const int y = pix >> 5, x = pix & (SL - 1);
+            const int y = pix / SL, x = pix % SL;
             M22 P;
 #pragma unroll
             for (int c = 0; c < 4; ++c) P.m[c] = s_fft[(c * SL + y) * FFT_P + x];
@@ -475,11 +506,14 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         }
         if (FUSED) {
             __syncthreads();
-            fft2_planar_pairs32<-1>(s_fft, tid);
+            if constexpr (SL == 32)
+                fft2_planar_pairs32<-1>(s_fft, tid);
+            else
+                fft2_planar<SL, -1>(s_fft, tid, NT);
             const float inv = 1.0f / (float)SPIX;
             float4 *dst = o + (size_t)d.layer * g.N * g.N * 2;
             for (int pix = tid; pix < SPIX; pix += NT) {
-                const int i = pix >> 5, j = pix & (SL - 1);
+                const int i = pix / SL, j = pix % SL;
                 const float sg = ((i + j) & 1) ? -inv : inv;
                 const float2 p0 = s_fft[(0 * SL + i) * FFT_P + j], p1 = s_fft[(1 * SL + i) * FFT_P + j];
                 const float2 p2 = s_fft[(2 * SL + i) * FFT_P + j], p3 = s_fft[(3 * SL + i) * FFT_P + j];
@@ -498,41 +532,67 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
 }
 
 // one CTA per subgrid of one plan (plan index idx[b] or first + b): subgrid images
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 gridder_sep_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                    const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                    const float *__restrict__ taper, float4 *__restrict__ out) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    gridder_sep_body<false>(g, g.sub[sid], vis, flags, aterms, taper, out + (size_t)blockIdx.x * SPIX * 2);
+    gridder_sep_body<L, false>(g, g.sub[sid], vis, flags, aterms, taper, out + (size_t)blockIdx.x * L * L * 2);
 }
 
 // fused: one CTA per subgrid, transformed and added into the grid
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 gridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                          const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                          const float *__restrict__ taper, float4 *__restrict__ grid) {
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
-    gridder_sep_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
+    gridder_sep_body<L, true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
 }
 
 // fused, one CTA per work item (job, subgrid) of a batch: added into the job's grid
+template <int L>
 __global__ void __launch_bounds__(NT, 1)
 gridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
     const int2 it = items[blockIdx.x];
     const JobDev &J = jobs[it.x];
-    gridder_sep_body<true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
+    gridder_sep_body<L, true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
+}
+
+template <int L>
+idg_status launch_sep_set(bool fused, const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                          const void *aterms, const float *taper, void *out, cudaStream_t s) {
+    auto kern = fused ? gridder_sep_fused_kernel<L> : gridder_sep_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SepG<L>::SMEM);
+    if (e != cudaSuccess) return cuda_fail(e, "separable gridder smem attribute");
+    kern<<<(unsigned)set.count, NT, SepG<L>::SMEM, s>>>(g, set.idx, set.first, (const float4 *)vis, flags,
+                                                       (const float4 *)aterms, taper, (float4 *)out);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, fused ? "separable fused gridder launch" : "separable gridder launch");
 }
 
 }  // namespace
 
+bool separable_size(int L) { return L == 32 || L == 24; }
+
 cudaError_t prepare_gridder_sep_batch() {
-    return cudaFuncSetAttribute(gridder_sep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEP_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(gridder_sep_batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SepG<32>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SepG<24>::SMEM);
+    return e;
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_gridder_sep_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
+idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
-    gridder_sep_batch_kernel<<<(unsigned)count, NT, SEP_SMEM, (cudaStream_t)stream>>>(jobs, items);
+    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24");
+    if (L == 32)
+        gridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepG<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
+    else
+        gridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepG<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "separable batch gridder launch");
     return IDG_OK;
@@ -540,31 +600,20 @@ idg_status launch_gridder_sep_batch(const JobDev *jobs, const int2 *items, int64
 
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {
-    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 and a separable plan");
+    if (!separable_size(g.L) || !g.separable)
+        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(gridder_sep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEP_SMEM);
-    if (e != cudaSuccess) return cuda_fail(e, "separable gridder smem attribute");
-    gridder_sep_kernel<<<(unsigned)set.count, NT, SEP_SMEM, s>>>(g, set.idx, set.first, (const float4 *)vis, flags,
-                                                                 (const float4 *)aterms, taper, (float4 *)out);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable gridder launch");
-    return IDG_OK;
+    return g.L == 32 ? launch_sep_set<32>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream)
+                     : launch_sep_set<24>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
 }
 
 idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                                     const void *aterms, const float *taper, void *grid, void *stream) {
-    if (g.L != SL || !g.separable) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 and a separable plan");
+    if (!separable_size(g.L) || !g.separable)
+        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaFuncSetAttribute(gridder_sep_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SEP_SMEM);
-    if (e != cudaSuccess) return cuda_fail(e, "separable gridder smem attribute");
-    gridder_sep_fused_kernel<<<(unsigned)set.count, NT, SEP_SMEM, s>>>(g, set.idx, set.first, (const float4 *)vis,
-                                                                       flags, (const float4 *)aterms, taper,
-                                                                       (float4 *)grid);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable fused gridder launch");
-    return IDG_OK;
+    return g.L == 32 ? launch_sep_set<32>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream)
+                     : launch_sep_set<24>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
 }
 
 idg_status read_sep_error(int *code) {

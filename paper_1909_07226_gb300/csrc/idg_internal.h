@@ -190,14 +190,16 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
 
 // tensor-core gridder (L = 32; FP16 hi/lo split products, FP32 accumulation in
 // tensor memory) and the device error word of the bounded waits
-// separable tensor-core gridder (L = 32, g.separable): subgrid images, or fused
+// subgrid sizes the separable tensor-core kernels are built for (32 and 24)
+bool separable_size(int L);
+// separable tensor-core gridder (L = 32 or 24, g.separable): subgrid images, or fused
 // with the transform and the adder into grid
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream);
 idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status read_sep_error(int *code);
-// separable tensor-core degridder (L = 32, g.separable): from subgrid images, or
+// separable tensor-core degridder (L = 32 or 24, g.separable): from subgrid images, or
 // fused with the splitter and the inverse transform from grid
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream);
@@ -225,9 +227,10 @@ idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, 
 struct JobDev;
 idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-// the separable kernels over work items of jobs whose plans are separable
-idg_status launch_gridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-idg_status launch_degridder_sep_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+// the separable kernels over work items of jobs (subgrid size L) whose plans are separable
+idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
+idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count,
+                                      void *stream);
 
 // calibration (calibration.cu): residuals and cost over the visibilities of a subgrid
 // set (res holds the model visibilities on entry), and the A-term gradient from the
