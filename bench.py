@@ -54,11 +54,19 @@ ISSUE_PER_VISPIX_TC = 9
 # Kernels without a capture of their current code report no traffic.
 FUSED_VARIANT = "tcgen05_tmemA_ws_nt288_fused"
 SEP_VARIANT = "tcgen05_separable_fused"
-# Tensor-core work of the separable kernels (kind::f16, M = 128, K = 16 per MMA, 2 FLOP
-# per multiply-add): the gridder issues N = 192 + 64 per group of 8 visibilities, the
-# degridder 4 K steps of 4 x N = 128 per tile of 64 visibilities.
-SEP_GRID_FLOP_PER_GROUP = 2 * 128 * 16 * (192 + 64)
-SEP_DEGRID_FLOP_PER_TILE = 4 * 2 * 128 * 16 * (4 * 128)
+# Tensor-core work of the separable kernels at subgrid size L (kind::f16, M = 128, K = 16
+# per MMA, 2 FLOP per multiply-add): the gridder issues N = 6 L + 2 L per group of 8
+# visibilities (192 + 64 at L = 32), the degridder L / 8 K steps of 4 x N = 4 L per tile
+# of 64 visibilities.
+
+
+def sep_grid_flop_per_group(L):
+    return 2 * 128 * 16 * (6 * L + 2 * L)
+
+
+def sep_degrid_flop_per_tile(L):
+    return (L // 8) * 4 * 2 * 128 * 16 * (4 * L)
+
 # Half of those products are the FP16 hi/lo split that keeps FP32 accuracy: the
 # gridder's N = 256 columns are A_hi x [B_hi (128) | B0_lo (64)] and A_lo x B0_hi (64);
 # the degridder's four N = 128 products per K step are hi x hi of the m = 0 and the
@@ -490,8 +498,8 @@ def run_gb300(args, world, rank, local):
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
     bf16_src = "measured burst" if "bf16_tflops" in peaks else "fallback"
     kp = plan.export()[:, 9].astype(np.int64)                 # K_p per subgrid (descriptor field 9)
-    sep_flop = {"gridder": float(((kp + 7) // 8).sum()) * SEP_GRID_FLOP_PER_GROUP,
-                "degridder": float(((kp + 63) // 64).sum()) * SEP_DEGRID_FLOP_PER_TILE}
+    sep_flop = {"gridder": float(((kp + 7) // 8).sum()) * sep_grid_flop_per_group(wl.subgrid_size),
+                "degridder": float(((kp + 63) // 64).sum()) * sep_degrid_flop_per_tile(wl.subgrid_size)}
     kernels = {}
     for k, d in prof.items():
         if d["launches"] == 0:
@@ -540,8 +548,8 @@ def run_gb300(args, world, rank, local):
         roof["useful_basis"] = kernels[dom]["useful_basis"]
     if "achieved_vispix" in kernels[dom]:
         roof["achieved_vispix"] = kernels[dom]["achieved_vispix"]
-        roof["flop_basis"] = ("MMA FLOP issued: gridder 2*128*16*(192+64) per group of 8 visibilities, degridder "
-                              "4*2*128*16*(4*128) per tile of 64 (FP16 hi/lo split products included)")
+        roof["flop_basis"] = ("MMA FLOP issued: gridder 2*128*16*8L per group of 8 visibilities, degridder "
+                              "(L/8)*4*2*128*16*4L per tile of 64 (FP16 hi/lo split products included)")
     gpu_launches = int(sum(d["launches"] for d in prof.values()))
 
     # image-side steps, outside the grid + degrid step: the whole grid to the image and
@@ -868,9 +876,24 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
     info = batch.info()
     classes = {}
     for w, p in zip(jobs, plans):
-        c = classes.setdefault(f"L{w.subgrid_size}", {"jobs": 0, "vis": 0})
+        c = classes.setdefault(f"L{w.subgrid_size}", {"jobs": 0, "vis": 0, "separable_jobs": 0})
         c["jobs"] += 1
         c["vis"] += int(w.n_vis)
+        c["separable_jobs"] += int(p.stats.separable)
+    # per class: the plain per-job form of that class's jobs alone (grid + degrid)
+    for name, c in classes.items():
+        sel = [(p, b) for w, p, b in zip(jobs, plans, bufs) if f"L{w.subgrid_size}" == name]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for p, b in sel:
+            b["grid"].zero_()
+            idg.grid(p, b["vis"], b["flags"], None, b["taper"], b["grid"], stream)
+            idg.degrid(p, b["grid"], b["flags"], None, b["taper"], b["vis_out"], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c["plain_ms"] = e0.elapsed_time(e1)
+        c["plain_mvis_per_s"] = c["vis"] / c["plain_ms"] / 1e3
     batch.destroy()
     return {"n_vis": int(n_vis), "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
             "plain_mvis_per_s": n_vis / ms_plain / 1e3, "batched_mvis_per_s": n_vis / ms_batch / 1e3,
