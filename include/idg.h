@@ -111,9 +111,13 @@ typedef struct {
     int32_t device;           /* CUDA device holding the plan's metadata          */
     int32_t separable;        /* 1: the separable tensor-core kernels apply (L = 32
                                  or 24, and sep_phase <= 1.38e-3), see idg_grid   */
-    double sep_phase;         /* max |2 pi (w - w0)| * max |r(x, y)| in radians, r the
+    double sep_phase;         /* max |2 pi (w - w_s)| * max |r(x, y)| in radians, r the
                                  part of n' = sqrt(1 - l^2 - m^2) - 1 that is not
-                                 n'(l, 0) + n'(0, m)                              */
+                                 n'(l, 0) + n'(0, m); w_s is the subgrid's w offset
+                                 w0 when that meets the bound, else the middle of
+                                 each subgrid's own w range (the separable kernels
+                                 then apply exp(+-2 pi i (w_s - w0) n') to the
+                                 subgrid image)                                    */
 } idg_plan_stats;
 
 /* Number of int32 fields per exported subgrid descriptor, and their order. */

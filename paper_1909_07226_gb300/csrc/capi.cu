@@ -415,27 +415,39 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     p->any_dropped = pr.n_dropped > 0;
 
     // bound on the phase of the separable remainder: max |c_k| max |r(x, y)| with
-    // c_k = 2 pi (w_k - w0) and r = n'(x, y) - n'(x, L/2) - n'(L/2, y); per
-    // subgrid the ends of its channel range bound the linear dependence on f
+    // c_k = 2 pi (w_k - w_s) and r = n'(x, y) - n'(x, L/2) - n'(L/2, y); per
+    // subgrid the ends of its channel range bound the linear dependence on f.  w_s
+    // is the subgrid's w offset w0 when that meets the bound; otherwise the middle of
+    // each subgrid's own w range, and the separable kernels apply the rest,
+    // exp(+-2 pi i (w_s - w0) n'(x, y)), to the subgrid image
     {
         auto n1 = [&](int x, int y) {
             const double l = ((double)x - 0.5 * L) * p->S / L;
             const double m = ((double)y - 0.5 * L) * p->S / L;
             return std::sqrt(1.0 - l * l - m * m) - 1.0;
         };
-        double r_max = 0.0, dw_max = 0.0;
+        double r_max = 0.0, dw0_max = 0.0, dws_max = 0.0;
         for (int y = 0; y < L; ++y)
             for (int x = 0; x < L; ++x) r_max = std::max(r_max, std::fabs(n1(x, y) - n1(x, L / 2) - n1(L / 2, y)));
+        p->w_mid.assign((size_t)n_sub, 0.0);
         for (int64_t s = 0; s < n_sub; ++s) {
             const int32_t *d = &p->desc[s * kDescFields];
             const double w0 = w_step > 0.0 ? (double)(d[IDG_DESC_LAYER] + pr.k_min) * w_step : 0.0;
             const int c0 = d[IDG_DESC_C0], c1 = d[IDG_DESC_C0] + d[IDG_DESC_NC] - 1;
+            double lo = 0.0, hi = 0.0;
             for (int t = d[IDG_DESC_T0]; t < d[IDG_DESC_T0] + d[IDG_DESC_NT]; ++t) {
                 const double w = uvw_m[((size_t)d[IDG_DESC_BASELINE] * n_t + t) * 3 + 2];
-                dw_max = std::max(dw_max, std::max(std::fabs(w * freqs_hz[c0] / kSpeedOfLight - w0),
-                                                   std::fabs(w * freqs_hz[c1] / kSpeedOfLight - w0)));
+                const double wa = w * freqs_hz[c0] / kSpeedOfLight, wb = w * freqs_hz[c1] / kSpeedOfLight;
+                if (t == d[IDG_DESC_T0]) lo = hi = wa;
+                lo = std::min(lo, std::min(wa, wb));
+                hi = std::max(hi, std::max(wa, wb));
             }
+            dw0_max = std::max(dw0_max, std::max(std::fabs(lo - w0), std::fabs(hi - w0)));
+            dws_max = std::max(dws_max, 0.5 * (hi - lo));
+            p->w_mid[s] = 0.5 * (lo + hi);
         }
+        p->sep_mid = 6.283185307179586476925286766559 * dw0_max * r_max > kSepThetaMax;
+        const double dw_max = p->sep_mid ? dws_max : dw0_max;
         const double c_max = 6.283185307179586476925286766559 * dw_max;
         p->sep_theta = c_max * r_max;
         p->c_scale = 1.0f;
@@ -477,6 +489,9 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         split_pair(g.u0 * k_uv, g.a0h, g.a0l);
         split_pair(g.v0 * k_uv, g.b0h, g.b0l);
         split_pair(g.w0 * kTwoPi, g.c0h, g.c0l);
+        const double ws = p->sep_mid ? p->w_mid[s] : g.w0;
+        split_pair(ws * kTwoPi, g.csh, g.csl);
+        g.dws = (float)(2.0 * (ws - g.w0));
     }
     std::vector<int32_t> span_order;
     // device work order: most visibilities first (longest-processing-time first

@@ -268,6 +268,13 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
         } else {
             P = load_m22(src + 2 * pix);
         }
+        if (d.dws != 0.0f) {      // the sums use w_s: the rest of the w offset, exp(-i 2 pi (w_s - w0) n')
+            float sn, cs;
+            sincospif(d.dws * g.nprime[pix], &sn, &cs);     // (dws in half turns: exact reduction)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                P.m[q] = make_float2(P.m[q].x * cs + P.m[q].y * sn, P.m[q].y * cs - P.m[q].x * sn);
+        }
         if (aterms) {
             const float4 *at = (const float4 *)(smem + AT_OFF);
             const M22 Ap = load_m22(at + 2 * pix);
@@ -406,7 +413,7 @@ __device__ __forceinline__ void degridder_sep_body(const Geometry &g, const DevS
             if (r.in) {
                 cf.x = pair_coef(r.uv.x, r.uv.y, r.sc.x, r.sc.y, d.a0h, d.a0l);
                 cf.y = pair_coef(r.uv.z, r.uv.w, r.sc.x, r.sc.y, d.b0h, d.b0l);
-                cf.z = pair_coef(r.w.x, r.w.y, r.sc.z, r.sc.w, d.c0h, d.c0l);
+                cf.z = pair_coef(r.w.x, r.w.y, r.sc.z, r.sc.w, d.csh, d.csl);
                 cf.w = __uint_as_float(r.vi | (r.flag ? 0x80000000u : 0u));
             }
             return cf;

@@ -279,7 +279,7 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             if (pin) {
                 cf_next.x = pair_coef(puv.x, puv.y, pws.x, pws.y, d.a0h, d.a0l);
                 cf_next.y = pair_coef(puv.z, puv.w, pws.x, pws.y, d.b0h, d.b0l);
-                cf_next.z = pair_coef(pw.x, pw.y, pws.z, pws.w, d.c0h, d.c0l);
+                cf_next.z = pair_coef(pw.x, pw.y, pws.z, pws.w, d.csh, d.csl);
             }
         };
         // coefficients and raw V of the batch; the batch's largest |component| into s_red[bb]
@@ -488,6 +488,13 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             M22 P;
 #pragma unroll
             for (int c = 0; c < 4; ++c) P.m[c] = s_fft[(c * SL + y) * FFT_P + x];
+            if (d.dws != 0.0f) {      // the sums used w_s: the rest of the w offset, exp(i 2 pi (w_s - w0) n')
+                float sn, cs;
+                sincospif(d.dws * g.nprime[pix], &sn, &cs);     // (dws in half turns: exact reduction)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    P.m[c] = make_float2(P.m[c].x * cs - P.m[c].y * sn, P.m[c].x * sn + P.m[c].y * cs);
+            }
             if (aterms) {
                 const float4 *at = (const float4 *)(smem + AT_OFF);
                 const M22 Ap = load_m22(at + 2 * pix);

@@ -13,15 +13,19 @@ namespace idg {
 constexpr double kSpeedOfLight = 299792458.0;   // m/s
 constexpr int kDescFields = IDG_DESC_FIELDS;
 
-// Work description of one subgrid on the device (96 B, 16-B aligned).
+// Work description of one subgrid on the device (112 B, 16-B aligned).
 struct alignas(16) DevSubgrid {
     int32_t bl, slot, t0, nt, c0, nc, q0, r0, layer, kp, st_p, st_q;
     double u0, v0, w0;     // centre of the subgrid in wavelengths (Sect. 3.3)
     // the phase offsets of the centre as float pairs (hi + lo = the FP64 value to
     // about 2^-48): u0 k_uv, v0 k_uv and 2 pi w0
     float a0h, a0l, b0h, b0l, c0h, c0l;
+    // the separable kernels' w offset w_s (w0, or the middle of the subgrid's w range
+    // when the plan needs it to meet the remainder bound): 2 pi w_s as a float pair, and
+    // 2 (w_s - w0), the phase in half turns per unit of n' they apply to the subgrid image
+    float csh, csl, dws;
 };
-static_assert(sizeof(DevSubgrid) == 96, "DevSubgrid layout");
+static_assert(sizeof(DevSubgrid) == 112, "DevSubgrid layout");
 
 // Geometry and pointers the kernels read; passed by value to every launch.
 struct Geometry {
@@ -92,6 +96,8 @@ struct idg_plan {
     float *d_scale_f2 = nullptr;
     float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
     double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
+    bool sep_mid = false;                  // the separable kernels take w_s = the middle of each subgrid's w range
+    std::vector<double> w_mid;             // [n_sub] middle of each subgrid's w range (wavelengths)
     float c_scale = 1.0f;
     float r_scale = 1.0f;
     bool any_dropped = false;
