@@ -61,17 +61,21 @@ def test_remainder_is_fourth_order_in_the_direction_cosines():
 
 
 def _theta_definition(wl):
+    # max |2 pi (w - w_s)| max |r|: w_s = the subgrid's w offset w0 when that gives a
+    # phase within the bound, else the middle of each subgrid's own w range
     op = O.plan(wl)
     L, S = wl.subgrid_size, wl.grid_size * wl.cell_size
     r_max = np.abs(_split(L, S)[3]).max()
     c = 299792458.0
-    dw = 0.0
+    dw0 = dws = 0.0
     for row in op.desc:
         bl, t0, nt, c0, nc = row[O.D_BL], row[O.D_T0], row[O.D_NT], row[O.D_C0], row[O.D_NC]
         w0 = (row[O.D_LAYER] + op.k_min) * wl.w_step if wl.w_step > 0 else 0.0
         w = wl.uvw_m[bl, t0:t0 + nt, 2][:, None] * wl.freqs_hz[None, c0:c0 + nc] / c
-        dw = max(dw, np.abs(w - w0).max())
-    return 2 * np.pi * dw * r_max
+        dw0 = max(dw0, np.abs(w - w0).max())
+        dws = max(dws, 0.5 * (w.max() - w.min()))
+    theta0 = 2 * np.pi * dw0 * r_max
+    return theta0 if theta0 <= 1.38e-3 else 2 * np.pi * dws * r_max
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12),
