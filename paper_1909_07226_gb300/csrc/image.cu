@@ -154,7 +154,7 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
     for (int k = 0; k < R; ++k) x[k] = y[k];
 }
 
-__host__ __device__ __forceinline__ int radix_of(int len) { return len >= 16 ? 16 : len; }
+__host__ __device__ constexpr int radix_of(int len) { return len >= 16 ? 16 : len; }
 
 // Shared-memory layout of a CTA's lines: position-major, the NL lines of a position
 // adjacent, so that a thread's polarisations sit together and the threads of a warp
@@ -232,6 +232,71 @@ __device__ __forceinline__ void fft_dif_lines(float2 *buf, int n, const float2 *
     }
 }
 
+// The same transform with the length n a compile-time constant (the 4096-point rows
+// and 64-point columns of the 4096 x 4096 grid): all index arithmetic folds to shifts,
+// and where it holds (no padding, or every step of radix 16: steps h = 1, 16, 256) the
+// slots of a butterfly's points are slot(base) + j ps with a constant ps, so a point
+// costs one add instead of the slot arithmetic.
+template <int N, bool PAD>
+__host__ __device__ constexpr bool slots_linear() {
+    if (!PAD) return true;
+    for (int len = N; len > 1; len /= 16)
+        if (radix_of(len) != 16) return false;
+    return true;
+}
+
+template <int R, int NL, bool PAD, int N, int LEN>
+__device__ __forceinline__ void dif_step_ct(float2 *buf, const float2 *tws, int sign) {
+    constexpr int H = LEN / R, GPL = N / R;
+    constexpr int PS = PAD ? H + H / 16 + H / 256 : H;      // slot stride of a butterfly's points
+    for (int t = threadIdx.x; t < NL * GPL; t += blockDim.x) {
+        const int line = t % NL, g = t / NL;
+        const int b = g / H, i = g % H;
+        const int base = b * LEN + i;
+        float2 v[R];
+        if constexpr (slots_linear<N, PAD>()) {
+            const int s0 = slot<PAD>(base) * NL + line;
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = buf[s0 + j * PS * NL];
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = buf[slot<PAD>(base + j * H) * NL + line];
+        }
+        if (sign > 0)
+            dft_reg<R, 1>(v);
+        else
+            dft_reg<R, -1>(v);
+        if constexpr (slots_linear<N, PAD>()) {
+            const int s0 = slot<PAD>(base) * NL + line;
+#pragma unroll
+            for (int k = 0; k < R; ++k) buf[s0 + k * PS * NL] = k ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                buf[slot<PAD>(base + k * H) * NL + line] = k ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
+        }
+    }
+}
+
+template <int NL, bool PAD, int N, int LEN>
+__device__ __forceinline__ void dif_steps_ct(float2 *buf, const float2 *tws, int sign) {
+    if constexpr (LEN > 1) {
+        constexpr int R = LEN >= 16 ? 16 : LEN;
+        dif_step_ct<R, NL, PAD, N, LEN>(buf, tws, sign);
+        __syncthreads();
+        dif_steps_ct<NL, PAD, N, LEN / R>(buf, tws + (R - 1) * (LEN / R), sign);
+    }
+}
+
+// the n-point transform of the NL lines: compile-time n when NC > 0, else n at run time
+template <int NL, bool PAD, int NC>
+__device__ __forceinline__ void fft_lines(float2 *buf, int n, const float2 *tw, int sign) {
+    if constexpr (NC > 0)
+        dif_steps_ct<NL, PAD, NC, NC>(buf, tw, sign);
+    else
+        fft_dif_lines<NL, PAD>(buf, n, tw, sign);
+}
+
 // position of frequency f in the digit-reversed output of fft_dif_lines
 __device__ __forceinline__ int dif_pos(int f, int n) {
     int pos = 0;
@@ -248,7 +313,7 @@ __device__ __forceinline__ int dif_pos(int f, int n) {
 // (half of each 32-byte pixel; the other CTA of the row reads the other half of the
 // same sectors); in -> out, pre on the load.  Two CTAs fit an SM, so one CTA's loads
 // and stores overlap the other's transform.
-template <int SIGN>
+template <int SIGN, int NC>
 __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *__restrict__ in,
                                                                  float4 *__restrict__ out, int N, PixOp pre,
                                                                  const float2 *__restrict__ tw) {
@@ -264,15 +329,23 @@ __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *_
         buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
     }
     __syncthreads();
-    fft_dif_lines<2, true>(buf, N, tw, SIGN);
+    fft_lines<2, true, NC>(buf, N, tw, SIGN);
     float4 *orow = out + (size_t)y * N * 2 + hp;
-    for (int x = threadIdx.x; x < N; x += kRowThreads) orow[2 * x] = buf4[slot<true>(dif_pos(x, N))];
+    for (int x = threadIdx.x; x < N; x += kRowThreads) orow[2 * x] = buf4[slot<true>(dif_pos(x, NC ? NC : N))];
 }
+
+// N1 of split_n at compile time (N = N1 N2, N1 >= N2, both powers of two)
+__host__ __device__ constexpr int split_n_ct(int N) {
+    int logN = 0;
+    while ((1 << logN) < N) ++logN;
+    return 1 << ((logN + 1) / 2);
+}
+static_assert(split_n_ct(4096) == 64, "4096 = 64 x 64");
 
 // column pass A (four-step, N = N1 N2): CTA (y2, column block) transforms over y1 the
 // rows y1 N2 + y2 of kColBlock columns (4 kColBlock lines of N1 points), multiplies
 // output k1 by exp(SIGN 2 pi i y2 k1 / N) and writes it to row k1 N2 + y2 (in place)
-template <int SIGN>
+template <int SIGN, int NC>
 __global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__restrict__ img, int N, int N1, int N2) {
     extern __shared__ float4 img_smem4[];
     constexpr int NL = 4 * kColBlock;
@@ -295,10 +368,11 @@ __global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__res
         buf4[(y1 * NL + 4 * c) / 2 + 1] = p[1];
     }
     __syncthreads();
-    fft_dif_lines<NL, false>(buf, N1, tw, SIGN);
+    constexpr int NS = NC ? split_n_ct(NC) : 0;       // N1 = N2 at the compile-time sizes
+    fft_lines<NL, false, NS>(buf, N1, tw, SIGN);
     for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
         const int k1 = t / kColBlock, c = t % kColBlock;
-        const int q = (dif_pos(k1, N1) * NL + 4 * c) / 2;
+        const int q = (dif_pos(k1, NS ? NS : N1) * NL + 4 * c) / 2;
         const float2 w = w4[k1];
         const float4 a = buf4[q], b = buf4[q + 1];
         const float2 p0 = cmulf(make_float2(a.x, a.y), w), p1 = cmulf(make_float2(a.z, a.w), w);
@@ -312,7 +386,7 @@ __global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__res
 // column pass B: CTA (k1, column block) transforms over y2 the contiguous rows k1 N2 + y2
 // and writes frequency k = k1 + N1 k2 to row k of out, times post(x, k) (added with
 // accumulate)
-template <int SIGN>
+template <int SIGN, int NC>
 __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 *__restrict__ img,
                                                                    float4 *__restrict__ out, int N, int N1, int N2,
                                                                    PixOp post) {
@@ -331,10 +405,11 @@ __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 
         buf4[(y2 * NL + 4 * c) / 2 + 1] = p[1];
     }
     __syncthreads();
-    fft_dif_lines<NL, false>(buf, N2, tw, SIGN);
+    constexpr int NS = NC ? split_n_ct(NC) : 0;
+    fft_lines<NL, false, NS>(buf, N2, tw, SIGN);
     for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
         const int k2 = t / kColBlock, c = t % kColBlock;
-        const int q = (dif_pos(k2, N2) * NL + 4 * c) / 2;
+        const int q = (dif_pos(k2, NS ? NS : N2) * NL + 4 * c) / 2;
         const int y = k1 + N1 * k2, x = c0 + c;
         const float2 f = pix_factor(post, x, y, N);
         const float4 a = buf4[q], b = buf4[q + 1];
@@ -350,6 +425,17 @@ __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 
         o[0] = v0;
         o[1] = v1;
     }
+}
+
+template <int NC>
+cudaError_t set_image_smem(int rs, int ca, int cb) {
+    cudaError_t e = cudaFuncSetAttribute(image_rows_kernel<+1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_rows_kernel<-1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<+1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<-1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<+1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<-1, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+    return e;
 }
 
 void split_n(int N, int &N1, int &N2) {
@@ -370,9 +456,15 @@ cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, float2 *tw, i
     split_n(N, N1, N2);
     const int nb = N / kColBlock;
     step_twiddles_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N, SIGN);
-    image_rows_kernel<SIGN><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);          // along x
-    image_cols_a_kernel<SIGN><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);          // y1
-    image_cols_b_kernel<SIGN><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);  // y2
+    if (N == 4096) {           // the compile-time form of the LOFAR-sized grid
+        image_rows_kernel<SIGN, 4096><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);          // along x
+        image_cols_a_kernel<SIGN, 4096><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);          // y1
+        image_cols_b_kernel<SIGN, 4096><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);  // y2
+    } else {
+        image_rows_kernel<SIGN, 0><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);
+        image_cols_a_kernel<SIGN, 0><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);
+        image_cols_b_kernel<SIGN, 0><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);
+    }
     return cudaGetLastError();
 }
 
@@ -463,12 +555,8 @@ idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, 
         int N1, N2;
         split_n(N, N1, N2);
         const int rs = (int)rows_smem(N), ca = (int)cols_smem(N1), cb = (int)cols_smem(N2);
-        e = cudaFuncSetAttribute(image_rows_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_rows_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rs);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_a_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ca);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<+1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(image_cols_b_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cb);
+        e = set_image_smem<0>(rs, ca, cb);
+        if (e == cudaSuccess && N == 4096) e = set_image_smem<4096>(rs, ca, cb);
         if (e != cudaSuccess) return cuda_fail(e, "image transform shared-memory attribute");
     }
     if (h_window) {
