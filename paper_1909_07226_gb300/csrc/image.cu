@@ -269,11 +269,12 @@ __device__ __forceinline__ void dif_step_ct(float2 *buf, const float2 *tws, int 
         if constexpr (slots_linear<N, PAD>()) {
             const int s0 = slot<PAD>(base) * NL + line;
 #pragma unroll
-            for (int k = 0; k < R; ++k) buf[s0 + k * PS * NL] = k ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
+            for (int k = 0; k < R; ++k)      // (the last step, H = 1, has unit twiddles)
+                buf[s0 + k * PS * NL] = (k && H > 1) ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
         } else {
 #pragma unroll
             for (int k = 0; k < R; ++k)
-                buf[slot<PAD>(base + k * H) * NL + line] = k ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
+                buf[slot<PAD>(base + k * H) * NL + line] = (k && H > 1) ? cmulf(v[k], tws[(k - 1) * H + i]) : v[k];
         }
     }
 }
