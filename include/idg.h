@@ -113,7 +113,9 @@ typedef struct {
                                  or 24, and sep_phase <= 1.38e-3), see idg_grid   */
     double sep_phase;         /* max |2 pi (w - w_s)| * max |r(x, y)| in radians, r the
                                  part of n' = sqrt(1 - l^2 - m^2) - 1 that is not
-                                 n'(l, 0) + n'(0, m); w_s is the subgrid's w offset
+                                 n'(l, m0) + n'(m0, m) - n'(m0, m0), for the pixel
+                                 row m0 that makes max |r| smallest; w_s is the
+                                 subgrid's w offset
                                  w0 when that meets the bound, else the middle of
                                  each subgrid's own w range (the separable kernels
                                  then apply exp(+-2 pi i (w_s - w0) n') to the

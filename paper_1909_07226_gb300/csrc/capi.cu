@@ -415,7 +415,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     p->any_dropped = pr.n_dropped > 0;
 
     // bound on the phase of the separable remainder: max |c_k| max |r(x, y)| with
-    // c_k = 2 pi (w_k - w_s) and r = n'(x, y) - n'(x, L/2) - n'(L/2, y); per
+    // c_k = 2 pi (w_k - w_s) and r = n'(x, y) - n'(x, j0) - n'(j0, y) + n'(j0, j0); per
     // subgrid the ends of its channel range bound the linear dependence on f.  w_s
     // is the subgrid's w offset w0 when that meets the bound; otherwise the middle of
     // each subgrid's own w range, and the separable kernels apply the rest,
@@ -426,9 +426,20 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
             const double m = ((double)y - 0.5 * L) * p->S / L;
             return std::sqrt(1.0 - l * l - m * m) - 1.0;
         };
+        // the reference row and column j0 of the split: r is about -(l^2 - l0^2)(m^2 - l0^2) / 4,
+        // smallest in the largest |r| near l0^2 = half the largest l^2 (3 to 4 times smaller than
+        // through the centre); the best j0 on the diagonal (n' is symmetric in l and m)
         double r_max = 0.0, dw0_max = 0.0, dws_max = 0.0;
-        for (int y = 0; y < L; ++y)
-            for (int x = 0; x < L; ++x) r_max = std::max(r_max, std::fabs(n1(x, y) - n1(x, L / 2) - n1(L / 2, y)));
+        p->sep_j0 = L / 2;
+        for (int j = 0; j < L; ++j) {
+            double rm = 0.0;
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) rm = std::max(rm, std::fabs(n1(x, y) - n1(x, j) - n1(j, y) + n1(j, j)));
+            if (j == 0 || rm < r_max) {
+                r_max = rm;
+                p->sep_j0 = j;
+            }
+        }
         p->w_mid.assign((size_t)n_sub, 0.0);
         for (int64_t s = 0; s < n_sub; ++s) {
             const int32_t *d = &p->desc[s * kDescFields];
@@ -551,22 +562,24 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         split_pair(scale[c] * k_uv, scale_f2[4 * c], scale_f2[4 * c + 1]);
         split_pair(scale[c] * kTwoPi, scale_f2[4 * c + 2], scale_f2[4 * c + 3]);
     }
-    // n' table, then the separable split n' = s(x) + t(y) + r(x, y) with s and t
-    // the row and column through the centre pixel (l = 0 at X = 0, m = 0 at Y = 0)
+    // n' table, then the separable split n' = s(x) + t(y) + r(x, y) with s(x) = n'(x, j0)
+    // and t(y) = n'(j0, y) - n'(j0, j0), j0 the plan's reference row and column
     std::vector<float> nprime((size_t)2 * L * L + 2 * L);
     auto n1 = [&](int x, int y) {
         const double l = ((double)x - 0.5 * L) * p->S / L;
         const double m = ((double)y - 0.5 * L) * p->S / L;
         return std::sqrt(1.0 - l * l - m * m) - 1.0;
     };
+    const int j0 = p->sep_j0;
     for (int y = 0; y < L; ++y)
         for (int x = 0; x < L; ++x) {
             nprime[(size_t)y * L + x] = (float)n1(x, y);
-            nprime[(size_t)L * L + 2 * L + (size_t)y * L + x] = (float)(n1(x, y) - n1(x, L / 2) - n1(L / 2, y));
+            nprime[(size_t)L * L + 2 * L + (size_t)y * L + x] =
+                (float)(n1(x, y) - n1(x, j0) - n1(j0, y) + n1(j0, j0));
         }
     for (int i = 0; i < L; ++i) {
-        nprime[(size_t)L * L + i] = (float)n1(i, L / 2);
-        nprime[(size_t)L * L + L + i] = (float)n1(L / 2, i);
+        nprime[(size_t)L * L + i] = (float)n1(i, j0);
+        nprime[(size_t)L * L + L + i] = (float)(n1(j0, i) - n1(j0, j0));
     }
 
     // the default taper (calls with a NULL taper): c[y][x] = a_y a_x with a the PSWF

@@ -1,10 +1,11 @@
-// Separable gridder on the tensor cores (tcgen05), L = 32.
+// Separable gridder on the tensor cores (tcgen05), L = 32 and 24.
 //
 // The subgrid image of Eq. (ShiftedDirectImaging) is
 //   I_q(x, y) = sum_k V_kq exp(i (a_k X + b_k Y + c_k n'(x, y))),
-// with X = x - L/2, Y = y - L/2 and c_k = 2 pi (w_k - w0).  Splitting
-// n'(x, y) = s(x) + t(y) + r(x, y), s and t the row and column through the
-// centre pixel, the phasor factors into
+// with X = x - L/2, Y = y - L/2 and c_k = 2 pi (w_k - w_s) (w_s the subgrid's w
+// offset, see the epilogue).  Splitting n'(x, y) = s(x) + t(y) + r(x, y), s and t
+// a row and a column of n' (the plan's reference row and column j0: s(x) =
+// n'(x, j0), t(y) = n'(j0, y) - n'(j0, j0)), the phasor factors into
 //   Ex_k(x) = exp(i (a_k X + c_k s(x))),  Ey_k(y) = exp(i (b_k Y + c_k t(y))),
 // times exp(i c_k r(x, y)).  The remainder r is fourth order in (l, m); where
 // theta = max |c_k| max |r| is small (the plan checks theta <= 1.38e-3, so that

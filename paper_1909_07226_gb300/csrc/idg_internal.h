@@ -46,8 +46,9 @@ struct Geometry {
     double ds;                 // channel scale step (f_{c+1} - f_c)/c for uniformly spaced channels
     int recurrence;            // 1: phasors by channel recurrence (IDG_PHASOR_RECURRENCE)
     int anchor;                // channels per recurrence run (re-anchor interval)
-    // separable split n'(x, y) = s(x) + t(y) + r(x, y): s(x) = n'(x, Y = 0),
-    // t(y) = n'(X = 0, y), r the remainder; sep = [s[L] | t[L] | r[L][L]] (FP64
+    // separable split n'(x, y) = s(x) + t(y) + r(x, y): s(x) = n'(x, j0),
+    // t(y) = n'(j0, y) - n'(j0, j0) (j0 the reference row and column that makes
+    // max |r| smallest), r the remainder; sep = [s[L] | t[L] | r[L][L]] (FP64
     // differences rounded to FP32)
     const float *sep;
     int separable;             // 1: max |c_k| max |r| is small enough for the first-order w remainder
@@ -97,6 +98,7 @@ struct idg_plan {
     float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
     double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
     bool sep_mid = false;                  // the separable kernels take w_s = the middle of each subgrid's w range
+    int sep_j0 = 0;                        // reference row and column of the separable split
     std::vector<double> w_mid;             // [n_sub] middle of each subgrid's w range (wavelengths)
     float c_scale = 1.0f;
     float r_scale = 1.0f;

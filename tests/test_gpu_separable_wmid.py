@@ -17,11 +17,11 @@ C = 299792458.0
 SEP_THETA_MAX = 1.38e-3        # the plan's bound on the remainder phase
 
 CASES = {
-    "L24": dict(seed=84, n_st=6, n_t=96, n_chan=8, L=24, N=256, max_t=96, n_slots=3, flag_p=0.1,
+    "L24": dict(seed=84, n_st=6, n_t=96, n_chan=8, L=24, N=384, max_t=96, n_slots=3, flag_p=0.1,
                 diameter_m=1500.0, df=0.5e6),
-    "L24_long": dict(seed=84, n_st=6, n_t=256, n_chan=8, L=24, N=256, max_t=128, n_slots=3, flag_p=0.1,
+    "L24_long": dict(seed=84, n_st=6, n_t=256, n_chan=8, L=24, N=384, max_t=128, n_slots=3, flag_p=0.1,
                      diameter_m=1500.0, df=0.25e6, dt=5.0),
-    "L32": dict(seed=88, n_st=6, n_t=256, n_chan=8, L=32, N=256, max_t=128, n_slots=3, flag_p=0.1,
+    "L32": dict(seed=88, n_st=6, n_t=256, n_chan=8, L=32, N=320, max_t=128, n_slots=3, flag_p=0.1,
                 diameter_m=1500.0, df=0.25e6, dt=5.0),
 }
 
@@ -42,7 +42,9 @@ def theta_with_w0(wl, p):
         l, m = (x - 0.5 * L) * S / L, (y - 0.5 * L) * S / L
         return np.sqrt(1.0 - l * l - m * m) - 1.0
 
-    r = max(abs(n1(x, y) - n1(x, L / 2) - n1(L / 2, y)) for y in range(L) for x in range(L))
+    # the split through the reference row and column j0 that makes max |r| smallest
+    r = min(max(abs(n1(x, y) - n1(x, j) - n1(j, y) + n1(j, j)) for y in range(L) for x in range(L))
+            for j in range(L))
     dw = 0.0
     for d in p.export():
         w = wl.uvw_m[d[O.D_BL], d[O.D_T0]:d[O.D_T0] + d[O.D_NT], 2]

@@ -71,9 +71,9 @@ CASES = {
     # K_p = 2048 as in the LOFAR configuration: 8 folds of the hh | hl accumulators
     "long_kp": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6),
     "wide_channels": lambda: small32(aterms="identity", n_chan=16, diameter_m=30000.0, df=4e6),
-    # wide field with the separable remainder phase just under its bound (1.35e-3 rad)
-    "wide_field_near_bound": lambda: small32(N=256, cell=1e-3, diameter_m=300.0),
-    # wide field far over the bound (6.2e-2 rad): the separable choice falls back to the direct kernel
+    # wide field with the separable remainder phase just under its bound (1.34e-3 rad)
+    "wide_field_near_bound": lambda: small32(N=256, cell=1.2e-3, diameter_m=500.0),
+    # wide field far over the bound (1.4e-2 rad): the separable choice falls back to the direct kernel
     "wide_field_direct": lambda: small32(N=512, cell=1e-3, diameter_m=800.0),
 }
 

@@ -6,7 +6,8 @@ n'(x, y) = s(x) + t(y) + r(x, y).  These tests check, in FP64 numpy and
 independently of the library's code, (1) that the factorisation is exact up to
 the dropped remainder and that the dropped part obeys the theta^2 / 2 bound the
 plan relies on, and (2) that the plan's reported theta equals its definition:
-max over planned visibilities of |2 pi (w - w0)| times max |r|.
+max over planned visibilities of |2 pi (w - w_s)| times max |r|, with the split
+through the reference row and column j0 that makes max |r| smallest.
 """
 import numpy as np
 import pytest
@@ -23,12 +24,32 @@ def _nprime(L, S):
     return np.sqrt(1.0 - ll * ll - mm * mm) - 1.0
 
 
-def _split(L, S):
+def _split(L, S, j0=None):
+    # n' = s(x) + t(y) + r(x, y) through reference row and column j0 (default: the centre)
+    j0 = L // 2 if j0 is None else j0
     n1 = _nprime(L, S)
-    s = n1[L // 2, :]                      # row through the centre: n'(x, Y = 0)
-    t = n1[:, L // 2]                      # column: n'(X = 0, y)
+    s = n1[j0, :]                          # row j0: n'(x, j0)
+    t = n1[:, j0] - n1[j0, j0]             # column j0, less the shared corner
     r = n1 - s[None, :] - t[:, None]
     return n1, s, t, r
+
+
+def _best_j0(L, S):
+    return min(range(L), key=lambda j: np.abs(_split(L, S, j)[3]).max())
+
+
+def test_split_reference_off_centre_shrinks_the_remainder():
+    # r is about -(l^2 - l0^2)(m^2 - m0^2) / 4: a reference where l0^2 is half the largest
+    # l^2 takes max |r| 3 to 4 times below the split through the centre, and the split
+    # stays exact
+    for L, S in ((32, 0.2), (24, 0.2), (32, 0.5)):
+        j0 = _best_j0(L, S)
+        n1, s, t, r = _split(L, S, j0)
+        np.testing.assert_allclose(s[None, :] + t[:, None] + r, n1, rtol=0, atol=1e-15)
+        ratio = np.abs(_split(L, S)[3]).max() / np.abs(r).max()
+        assert 3.0 < ratio < 4.5, (L, S, ratio)
+        l0 = (j0 - L / 2) * S / L
+        assert abs(l0 * l0 - 0.5 * (0.5 * S) ** 2) < 0.25 * (0.5 * S) ** 2
 
 
 @pytest.mark.parametrize("S,c_max", [(0.04096, 2080.0), (0.128, 700.0), (0.5, 20.0)])
@@ -65,7 +86,7 @@ def _theta_definition(wl):
     # phase within the bound, else the middle of each subgrid's own w range
     op = O.plan(wl)
     L, S = wl.subgrid_size, wl.grid_size * wl.cell_size
-    r_max = np.abs(_split(L, S)[3]).max()
+    r_max = np.abs(_split(L, S, _best_j0(L, S))[3]).max()
     c = 299792458.0
     dw0 = dws = 0.0
     for row in op.desc:
