@@ -48,7 +48,7 @@ ISSUE_PER_VISPIX_TC = 9
 # separable) on the LOFAR-like slice, one launch of all 3206 subgrids, 4.731e9
 # visibility-pixels: gridder 178.3 + 5.7 MB (visibilities and coordinates in; the
 # atomically updated grid lines are still dirty in L2 when the launch ends), degridder
-# 31.0 + 92.9 MB
+# 31.1 + 92.4 MB
 # (grid lines and coordinates in, model visibilities out).  The traffic is
 # proportional to the work, so it scales to a full launch by the units processed.
 # Kernels without a capture of their current code report no traffic.
@@ -76,7 +76,7 @@ SEP_USEFUL_SHARE = 0.5
 DTYPE_SEP = "f32 (fp16 hi/lo split tensor-core products, fp32 accumulate)"
 KERNEL_TRAFFIC = {
     "gridder": {SEP_VARIANT: (178.3e6 + 5.7e6) / 4.731e9},
-    "degridder": {SEP_VARIANT: (31.0e6 + 92.9e6) / 4.731e9},
+    "degridder": {SEP_VARIANT: (31.1e6 + 92.4e6) / 4.731e9},
 }
 
 
