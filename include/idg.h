@@ -109,8 +109,8 @@ typedef struct {
     int32_t grid_size;        /* N                                                */
     int32_t n_bl, n_t, n_chan, n_stations, n_slots;
     int32_t device;           /* CUDA device holding the plan's metadata          */
-    int32_t separable;        /* 1: the separable tensor-core kernels apply (L = 32
-                                 or 24, and sep_phase <= 1.38e-3), see idg_grid   */
+    int32_t separable;        /* 1: the separable tensor-core kernels apply (L = 32,
+                                 24 or 16, and sep_phase <= 1.38e-3), see idg_grid */
     double sep_phase;         /* max |2 pi (w - w_s)| * max |r(x, y)| in radians, r the
                                  part of n' = sqrt(1 - l^2 - m^2) - 1 that is not
                                  n'(l, m0) + n'(m0, m) - n'(m0, m0), for the pixel
@@ -193,8 +193,8 @@ void idg_plan_destroy(idg_plan *plan);
  * the FP64 definition to FP32 rounding, not bit for bit across runs.
  * Device scratch of at most 512 MiB is taken from the stream-ordered allocator
  * (plus one grid-sized compensation buffer with IDG_ADDER_COMPENSATED).
- * At L = 32, and at L = 24 when the plan is separable, with the default kernel
- * choice, IDG_FFT_FP32, IDG_PHASOR_SINCOS and IDG_ADDER_ATOMIC the whole call is
+ * At L = 32, and at L = 24 and 16 when the plan is separable, with the default
+ * kernel choice, IDG_FFT_FP32, IDG_PHASOR_SINCOS and IDG_ADDER_ATOMIC the whole call is
  * one fused tensor-core launch (image-domain sum, taper and A-terms, transform
  * and adder per subgrid in one CTA) and takes no subgrid scratch.
  */
@@ -207,8 +207,8 @@ idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_fl
  * d_vis_out  device complex64 [n_bl][n_t][n_chan][4], OVERWRITTEN: flagged and
  *            dropped visibilities are set to 0.
  * Other arguments as for idg_grid.
- * At L = 32, and at L = 24 when the plan is separable, with the default kernel
- * choice, IDG_FFT_FP32 and IDG_PHASOR_SINCOS, when at least half the
+ * At L = 32, and at L = 24 and 16 when the plan is separable, with the default
+ * kernel choice, IDG_FFT_FP32 and IDG_PHASOR_SINCOS, when at least half the
  * visibilities lie in subgrids of 512 or more, the call
  * is one fused tensor-core launch (splitter, transform, A-terms and taper, and
  * the visibility sums per subgrid in one CTA) without subgrid scratch.
@@ -413,7 +413,7 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
  *                     into vis_out (overwritten; flagged and dropped -> 0)
  * For L = 32 the default batch variant ("tcgen05_fused", IDG_KERNEL_BATCH_*),
- * and for L = 24 the jobs whose plans are separable, instead run the fused
+ * and for L = 24 and 16 the jobs whose plans are separable, instead run the fused
  * tensor-core gridder (degridder) with one CTA per work
  * item, the sums on the tensor cores and the transform and adder (splitter) in
  * the same CTA; a class whose visibilities lie mostly in subgrids of fewer
@@ -530,7 +530,7 @@ idg_status idg_autotune(const idg_plan *plan, const void *d_vis, const uint8_t *
 
 /*
  * Device error words.  The tensor-core kernels (the L = 32 gridder and
- * degridder, the separable ones at L = 32 and 24, variants named "tcgen05_...",
+ * degridder, the separable ones at L = 32, 24 and 16, variants named "tcgen05_...",
  * and the IDG_FFT_TC_SPLIT transform)
  * wait on shared-memory barriers for their matrix operations and bulk copies;
  * every wait has an iteration limit, after which the kernel records an error

@@ -707,8 +707,8 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
 // plain adder.  The degridder takes them when most visibilities of the launch
 // lie in subgrids of at least 512 (as the default per-call choice does).
 // the fused composite kernels: the direct tensor-core ones at L = 32, the separable ones at
-// L = 32 and 24 where the plan is separable (the process-default kernel choice only)
-static bool fused_size(const idg_plan *p) { return p->L == 32 || (p->L == 24 && p->stats.separable); }
+// L = 32, 24 and 16 where the plan is separable (the process-default kernel choice only)
+static bool fused_size(const idg_plan *p) { return p->L == 32 || (separable_size(p->L) && p->stats.separable); }
 static bool fused_grid(const idg_plan *p) {
     return fused_size(p) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
            p->opts.adder_mode == IDG_ADDER_ATOMIC && p->kernel_variant(IDG_KERNEL_GRIDDER) == 0;

@@ -1,4 +1,4 @@
-// Separable degridder on the tensor cores (tcgen05), L = 32.
+// Separable degridder on the tensor cores (tcgen05), L = 32, 24 and 16.
 //
 // The visibilities of Algorithm 2 from the corrected subgrid image P_q(x, y)
 // (taper and A_p P A_q^H applied) are
@@ -72,7 +72,7 @@ constexpr int PART_BYTES = 2 * 2 * 2 * 4 * TV * 4;   // consumer exchange: [2 ti
 static_assert(AST == 2 && EST == 4, "stage arithmetic below");
 static_assert(EST * 128 <= 512, "accumulators in tensor memory");
 
-// Layout for subgrid size L (32 or 24)
+// Layout for subgrid size L (32, 24 or 16)
 template <int L>
 struct SepD {
     static constexpr int SL = L, SPIX = L * L;
@@ -97,7 +97,7 @@ struct SepD {
     static constexpr int YB = L / 8, XC = L / 4, NTASK = 4 * YB * XC;
     static constexpr int NWT = (NTASK + MMA_WARP - 1) / MMA_WARP;
     static constexpr int EYP = L * TV / NC / 2;     // Ey* pairs per consumer thread
-    static_assert(L == 32 || L == 24, "subgrid sizes of the separable kernels");
+    static_assert(L == 32 || L == 24 || L == 16, "subgrid sizes of the separable kernels");
     static_assert(4 * L * FFT_P * 8 <= AST * A_STAGE, "transform planes fit over the A stages");
     static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= CF_OFF, "A-terms before the coefficient stages");
     static_assert(3 * KT * T4K >= SPIX * 32, "the subgrid's grid rows fit in the B area");
@@ -591,17 +591,22 @@ cudaError_t prepare_sep_batch_kernels() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(degridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepD<24>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SepD<16>::SMEM);
     return e;
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
 idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
-    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24");
+    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32, 24 or 16");
     if (L == 32)
         degridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepD<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else
+    else if (L == 24)
         degridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepD<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
+    else
+        degridder_sep_batch_kernel<16><<<(unsigned)count, NT, SepD<16>::SMEM, (cudaStream_t)stream>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "separable batch degridder launch");
     return IDG_OK;
@@ -610,19 +615,25 @@ idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const int2 *ite
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {
     if (!separable_size(g.L) || !g.separable)
-        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24 and a separable plan");
+        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32, 24 or 16 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    return g.L == 32 ? launch_sepd_set<32>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream)
-                     : launch_sepd_set<24>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    switch (g.L) {
+    case 32: return launch_sepd_set<32>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    case 24: return launch_sepd_set<24>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    default: return launch_sepd_set<16>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    }
 }
 
 idg_status launch_degridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
                                       const void *aterms, const float *taper, void *vis_out, void *stream) {
     if (!separable_size(g.L) || !g.separable)
-        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32 or 24 and a separable plan");
+        return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32, 24 or 16 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    return g.L == 32 ? launch_sepd_set<32>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream)
-                     : launch_sepd_set<24>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    switch (g.L) {
+    case 32: return launch_sepd_set<32>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    case 24: return launch_sepd_set<24>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    default: return launch_sepd_set<16>(true, g, set, grid, flags, aterms, taper, vis_out, (cudaStream_t)stream);
+    }
 }
 
 idg_status read_sepd_error(int *code) {

@@ -1,4 +1,4 @@
-// Separable gridder on the tensor cores (tcgen05), L = 32 and 24.
+// Separable gridder on the tensor cores (tcgen05), L = 32, 24 and 16.
 //
 // The subgrid image of Eq. (ShiftedDirectImaging) is
 //   I_q(x, y) = sum_k V_kq exp(i (a_k X + b_k Y + c_k n'(x, y))),
@@ -85,9 +85,9 @@ static_assert(FOLD / SG >= STAGES, "a period spans at least STAGES stages");
 static_assert((STAGES & (STAGES - 1)) == 0, "STAGES is a power of two");
 static_assert(FOLD % SG == 0 && GB % SG == 0, "periods and batches are whole stages");
 
-// Layout for subgrid size L (32 or 24).  A has 128 rows: lane quarter yq holds pixel rows
-// y = (L / 4) yq + ylo for ylo < L / 4 at lanes 8 q + ylo (at L = 24 lanes with ylo = 6, 7
-// carry zeros).  B has 6 L rows per group: (m = 0, re), (m = 0, im), (m = 1, re),
+// Layout for subgrid size L (32, 24 or 16).  A has 128 rows: lane quarter yq holds pixel
+// rows y = (L / 4) yq + ylo for ylo < L / 4 at lanes 8 q + ylo (lanes with ylo >= L / 4
+// carry zeros: ylo = 6, 7 at L = 24, ylo >= 4 at L = 16).  B has 6 L rows per group: (m = 0, re), (m = 0, im), (m = 1, re),
 // (m = 1, im), then the lo parts of m = 0 re and im, L rows each.
 template <int L>
 struct SepG {
@@ -112,7 +112,7 @@ struct SepG {
     static constexpr uint32_t IDESC_NB = idesc_m128(6 * L), IDESC_NC = idesc_m128(2 * L);
     static constexpr int NSL = L / 8;             // 16-column slices of the m = 0 block (fold)
     static constexpr int XS = L / 4;              // x values per producer in the epilogue
-    static_assert(L == 32 || L == 24, "subgrid sizes of the separable kernels");
+    static_assert(L == 32 || L == 24 || L == 16, "subgrid sizes of the separable kernels");
     static_assert(4 * L * FFT_P * 8 <= FOLD_OFF, "transform planes fit over the stage buffers");
     static_assert(SMEM + 1024 <= 227 * 1024, "dynamic and static shared memory of one CTA");
     static_assert(AT_OFF % 16 == 0 && AT_OFF + 2 * (int)AT_BYTES <= VIS_OFF, "A-terms over the stage and coefficient buffers");
@@ -582,7 +582,7 @@ idg_status launch_sep_set(bool fused, const Geometry &g, const SubgridSet &set, 
 
 }  // namespace
 
-bool separable_size(int L) { return L == 32 || L == 24; }
+bool separable_size(int L) { return L == 32 || L == 24 || L == 16; }
 
 cudaError_t prepare_gridder_sep_batch() {
     cudaError_t e = cudaFuncSetAttribute(gridder_sep_batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -590,17 +590,22 @@ cudaError_t prepare_gridder_sep_batch() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepG<24>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gridder_sep_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SepG<16>::SMEM);
     return e;
 }
 
 // (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
 idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
     if (count <= 0) return IDG_OK;
-    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24");
+    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32, 24 or 16");
     if (L == 32)
         gridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepG<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else
+    else if (L == 24)
         gridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepG<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
+    else
+        gridder_sep_batch_kernel<16><<<(unsigned)count, NT, SepG<16>::SMEM, (cudaStream_t)stream>>>(jobs, items);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "separable batch gridder launch");
     return IDG_OK;
@@ -609,19 +614,25 @@ idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const int2 *items
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {
     if (!separable_size(g.L) || !g.separable)
-        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24 and a separable plan");
+        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32, 24 or 16 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    return g.L == 32 ? launch_sep_set<32>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream)
-                     : launch_sep_set<24>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
+    switch (g.L) {
+    case 32: return launch_sep_set<32>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
+    case 24: return launch_sep_set<24>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
+    default: return launch_sep_set<16>(false, g, set, vis, flags, aterms, taper, out, (cudaStream_t)stream);
+    }
 }
 
 idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                                     const void *aterms, const float *taper, void *grid, void *stream) {
     if (!separable_size(g.L) || !g.separable)
-        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32 or 24 and a separable plan");
+        return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32, 24 or 16 and a separable plan");
     if (set.count <= 0) return IDG_OK;
-    return g.L == 32 ? launch_sep_set<32>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream)
-                     : launch_sep_set<24>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+    switch (g.L) {
+    case 32: return launch_sep_set<32>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+    case 24: return launch_sep_set<24>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+    default: return launch_sep_set<16>(true, g, set, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+    }
 }
 
 idg_status read_sep_error(int *code) {

@@ -1,7 +1,8 @@
-"""GPU parity of the separable tensor-core kernels at L = 24 (the plans of the
-small, narrow-field workloads below pass the remainder bound, so the composite
-calls run the fused separable gridder and degridder), against the FP64 oracle
-on the same seeded inputs: relative RMS <= 1e-5 (tests.gpu_util.parity).
+"""GPU parity of the separable tensor-core kernels at L = 24 and 16 (the plans of
+the small, narrow-field workloads below pass the remainder bound, so the
+composite calls run the fused separable gridder and degridder), against the
+FP64 oracle on the same seeded inputs: relative RMS <= 1e-5
+(tests.gpu_util.parity).
 
 Cases: subgrids of up to 1024 visibilities (two staged batches and two
 accumulation periods of the gridder), W-layers, no A-terms, flags, and
@@ -35,6 +36,12 @@ CASES = {
                       diameter_m=2500.0, df=0.25e6, aterms="identity"),
     "short_kp": dict(seed=83, n_st=6, n_t=48, n_chan=4, L=24, N=128, max_t=8, n_slots=2, flag_p=0.1,
                      diameter_m=2500.0, df=0.25e6),
+    "L16_long_kp": dict(seed=91, n_st=5, n_t=128, n_chan=16, L=16, N=128, max_t=128, n_slots=2, flag_p=0.1,
+                        diameter_m=1200.0, df=0.25e6),
+    "L16_w_layers": dict(seed=92, n_st=5, n_t=96, n_chan=8, L=16, N=128, max_t=96, n_slots=1, flag_p=0.05,
+                         diameter_m=1200.0, df=0.25e6, w_step=20.0),
+    "L16_short_kp": dict(seed=93, n_st=6, n_t=48, n_chan=4, L=16, N=128, max_t=8, n_slots=2, flag_p=0.1,
+                         diameter_m=1200.0, df=0.25e6),
 }
 
 
@@ -71,11 +78,11 @@ def test_separable_l24_grid_and_degrid(case):
         assert degrid_launches == {"degridder": 1}
     else:
         assert "splitter" in degrid_launches and "fft" in degrid_launches
-    if case == "long_kp":
+    if case in ("long_kp", "L16_long_kp"):
         assert degrid_launches == {"degridder": 1}
     # (no_aterms: the workload's A-terms are the identity, which the oracle applies)
-    parity(g.cpu().numpy(), O.grid(wl, op), f"separable L=24 grid {case}")
-    parity(v.cpu().numpy(), O.degrid(wl, op, G), f"separable L=24 degrid {case}")
+    parity(g.cpu().numpy(), O.grid(wl, op), f"separable grid {case}")
+    parity(v.cpu().numpy(), O.degrid(wl, op, G), f"separable degrid {case}")
 
 
 def test_separable_l24_accumulates_and_flags_zero():
