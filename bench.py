@@ -876,10 +876,15 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
     info = batch.info()
     classes = {}
     for w, p in zip(jobs, plans):
-        c = classes.setdefault(f"L{w.subgrid_size}", {"jobs": 0, "vis": 0, "separable_jobs": 0})
+        c = classes.setdefault(f"L{w.subgrid_size}", {"jobs": 0, "vis": 0, "separable_jobs": 0,
+                                                      "separable_vis_fraction": 0.0})
         c["jobs"] += 1
         c["vis"] += int(w.n_vis)
         c["separable_jobs"] += int(p.stats.separable)
+        # visibilities (planned) in subgrids that the separable kernels take
+        c["separable_vis_fraction"] += p.stats.n_vis_sep
+    for c in classes.values():
+        c["separable_vis_fraction"] /= max(1, c["vis"])
     # per class: the plain per-job form of that class's jobs alone (grid + degrid)
     for name, c in classes.items():
         sel = [(p, b) for w, p, b in zip(jobs, plans, bufs) if f"L{w.subgrid_size}" == name]

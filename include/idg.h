@@ -109,17 +109,21 @@ typedef struct {
     int32_t grid_size;        /* N                                                */
     int32_t n_bl, n_t, n_chan, n_stations, n_slots;
     int32_t device;           /* CUDA device holding the plan's metadata          */
-    int32_t separable;        /* 1: the separable tensor-core kernels apply (L = 32,
-                                 24 or 16, and sep_phase <= 1.38e-3), see idg_grid */
-    double sep_phase;         /* max |2 pi (w - w_s)| * max |r(x, y)| in radians, r the
-                                 part of n' = sqrt(1 - l^2 - m^2) - 1 that is not
-                                 n'(l, m0) + n'(m0, m) - n'(m0, m0), for the pixel
-                                 row m0 that makes max |r| smallest; w_s is the
-                                 subgrid's w offset
-                                 w0 when that meets the bound, else the middle of
-                                 each subgrid's own w range (the separable kernels
-                                 then apply exp(+-2 pi i (w_s - w0) n') to the
-                                 subgrid image)                                    */
+    int32_t separable;        /* 1: every subgrid meets the remainder bound and the
+                                 separable tensor-core kernels take the whole plan
+                                 (L = 32, 24 or 16), see idg_grid                  */
+    double sep_phase;         /* max over subgrids of |2 pi (w - w_s)| * max |r(x, y)|
+                                 in radians, r the part of n' = sqrt(1 - l^2 - m^2) - 1
+                                 that is not n'(l, m0) + n'(m0, m) - n'(m0, m0), for
+                                 the pixel row m0 that makes max |r| smallest; w_s is
+                                 the subgrid's w offset w0 when that meets the bound
+                                 (1.38e-3), else the middle of the subgrid's own w
+                                 range (the separable kernels then apply
+                                 exp(+-2 pi i (w_s - w0) n') to the subgrid image)  */
+    int64_t n_sep_subgrids;   /* subgrids whose phase with their w_s meets the bound:
+                                 the separable kernels take these, the direct kernels
+                                 the rest (0 when L is not 32, 24 or 16)           */
+    int64_t n_vis_sep;        /* sum of K_p over those subgrids                    */
 } idg_plan_stats;
 
 /* Number of int32 fields per exported subgrid descriptor, and their order. */
@@ -196,7 +200,11 @@ void idg_plan_destroy(idg_plan *plan);
  * At L = 32, and at L = 24 and 16 when the plan is separable, with the default
  * kernel choice, IDG_FFT_FP32, IDG_PHASOR_SINCOS and IDG_ADDER_ATOMIC the whole call is
  * one fused tensor-core launch (image-domain sum, taper and A-terms, transform
- * and adder per subgrid in one CTA) and takes no subgrid scratch.
+ * and adder per subgrid in one CTA) and takes no subgrid scratch.  A plan with
+ * only some subgrids within the remainder bound (0 < n_sep_subgrids < n_subgrids)
+ * grids those in one separable launch and the rest with the direct kernels (at
+ * L = 32 a second fused launch; at 24 and 16 gridder, transform and adder
+ * through the scratch).
  */
 idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
                     const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);
@@ -211,7 +219,9 @@ idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_fl
  * kernel choice, IDG_FFT_FP32 and IDG_PHASOR_SINCOS, when at least half the
  * visibilities lie in subgrids of 512 or more, the call
  * is one fused tensor-core launch (splitter, transform, A-terms and taper, and
- * the visibility sums per subgrid in one CTA) without subgrid scratch.
+ * the visibility sums per subgrid in one CTA) without subgrid scratch.  A plan
+ * with only some subgrids within the remainder bound degrids those and the
+ * rest in separate launches, each by the same rules.
  */
 idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d_flags,
                       const void *d_aterms, const float *d_taper, void *d_vis_out,
@@ -413,7 +423,8 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
  *                     into vis_out (overwritten; flagged and dropped -> 0)
  * For L = 32 the default batch variant ("tcgen05_fused", IDG_KERNEL_BATCH_*),
- * and for L = 24 and 16 the jobs whose plans are separable, instead run the fused
+ * and for L = 24 and 16 the subgrids within the separable remainder bound (the
+ * work list of each L is split into those and the rest), instead run the fused
  * tensor-core gridder (degridder) with one CTA per work
  * item, the sums on the tensor cores and the transform and adder (splitter) in
  * the same CTA; a class whose visibilities lie mostly in subgrids of fewer

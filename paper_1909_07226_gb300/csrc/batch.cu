@@ -339,7 +339,7 @@ using namespace idg;
 struct idg_batch {
     struct Class {
         int L;
-        bool sep = false;              // L = 32 or 24 jobs whose plans take the separable kernels
+        bool sep = false;              // subgrids within the remainder bound (L = 32, 24, 16): the separable kernels
         int64_t n_items;
         double vispix;                 // sum of K_p L^2 of its items
         int2 *d_items = nullptr;
@@ -504,22 +504,24 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         b->n_vis += p->stats.n_vis_planned;
         if (p->any_dropped && bufs[j].vis_out)
             b->zero_on_degrid.push_back({bufs[j].vis_out, (size_t)p->n_bl * p->n_t * p->n_chan * 32});
-        size_t c = 0;
-        const bool sep = separable_size(p->L) && p->stats.separable;
-        while (c < b->classes.size() && (b->classes[c].L != p->L || b->classes[c].sep != sep)) ++c;
-        if (c == b->classes.size()) {
-            idg_batch::Class cl;
-            cl.L = p->L;
-            cl.sep = sep;
-            cl.n_items = 0;
-            cl.vispix = 0.0;
-            shapes_for(p->L, &cl.grid, &cl.degrid);
-            // L = 24 has tensor-core kernels only in the separable form
-            if (sep && p->L != 32) cl.grid = cl.degrid = kTcShape;
-            b->classes.push_back(cl);
-            per_class.emplace_back();
-        }
+        // one class per (L, separable): a plan's subgrids within the remainder bound go to
+        // the separable kernels, the others to the direct ones
         for (int64_t s = 0; s < p->stats.n_subgrids; ++s) {
+            const bool sep = separable_size(p->L) && p->sep_sub[s];
+            size_t c = 0;
+            while (c < b->classes.size() && (b->classes[c].L != p->L || b->classes[c].sep != sep)) ++c;
+            if (c == b->classes.size()) {
+                idg_batch::Class cl;
+                cl.L = p->L;
+                cl.sep = sep;
+                cl.n_items = 0;
+                cl.vispix = 0.0;
+                shapes_for(p->L, &cl.grid, &cl.degrid);
+                // L = 24 and 16 have tensor-core kernels only in the separable form
+                if (sep && p->L != 32) cl.grid = cl.degrid = kTcShape;
+                b->classes.push_back(cl);
+                per_class.emplace_back();
+            }
             per_class[c].push_back(make_int2(j, (int)s));
             b->classes[c].vispix += (double)p->kp_plan[s] * p->L * p->L;
         }
@@ -535,11 +537,6 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         auto &cl = b->classes[c];
         cl.n_items = (int64_t)items.size();
         if (cl.n_items > 2147483647) st = fail(IDG_ERR_INVALID_ARG, "too many subgrids in one batch class");
-        if (st == IDG_OK && cl.n_items > 0) {
-            e = cudaMalloc(&cl.d_items, sizeof(int2) * items.size());
-            if (e == cudaSuccess) e = cudaMemcpy(cl.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) st = cuda_fail(e, "batch work list");
-        }
         // the tensor-core path pays a fixed cost per subgrid: classes whose
         // visibilities sit mostly in subgrids of fewer than 512 take the fused kernels
         int64_t small = 0, all = 0;
@@ -559,6 +556,16 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
                     }
             }
             if (ks.tc) need_tc = true;
+        }
+        // one CTA per item in launch order (both directions on the tensor cores): keep a job's
+        // items together, most visibilities first within it, so that the CTAs in flight add
+        // into (split from) the same grid and share its lines in L2
+        if (cl.grid.tc && cl.degrid.tc)
+            std::stable_sort(items.begin(), items.end(), [](const int2 &x, const int2 &y) { return x.x < y.x; });
+        if (st == IDG_OK && cl.n_items > 0) {
+            e = cudaMalloc(&cl.d_items, sizeof(int2) * items.size());
+            if (e == cudaSuccess) e = cudaMemcpy(cl.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "batch work list");
         }
         // persistent grid: resident CTAs per SM x SMs, never more than the items
         for (int k = 0; k < 2 && st == IDG_OK; ++k) {

@@ -416,10 +416,11 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
 
     // bound on the phase of the separable remainder: max |c_k| max |r(x, y)| with
     // c_k = 2 pi (w_k - w_s) and r = n'(x, y) - n'(x, j0) - n'(j0, y) + n'(j0, j0); per
-    // subgrid the ends of its channel range bound the linear dependence on f.  w_s
-    // is the subgrid's w offset w0 when that meets the bound; otherwise the middle of
-    // each subgrid's own w range, and the separable kernels apply the rest,
-    // exp(+-2 pi i (w_s - w0) n'(x, y)), to the subgrid image
+    // subgrid the ends of its channel range bound the linear dependence on f.  Each
+    // subgrid takes w_s = its w offset w0 when that meets the bound, else the middle
+    // of its own w range (the separable kernels apply the rest, exp(+-2 pi i (w_s - w0)
+    // n'(x, y)), to the subgrid image); the subgrids that meet the bound with it go to
+    // the separable kernels, the others to the direct ones
     {
         auto n1 = [&](int x, int y) {
             const double l = ((double)x - 0.5 * L) * p->S / L;
@@ -429,7 +430,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         // the reference row and column j0 of the split: r is about -(l^2 - l0^2)(m^2 - l0^2) / 4,
         // smallest in the largest |r| near l0^2 = half the largest l^2 (3 to 4 times smaller than
         // through the centre); the best j0 on the diagonal (n' is symmetric in l and m)
-        double r_max = 0.0, dw0_max = 0.0, dws_max = 0.0;
+        double r_max = 0.0;
         p->sep_j0 = L / 2;
         for (int j = 0; j < L; ++j) {
             double rm = 0.0;
@@ -440,7 +441,13 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
                 p->sep_j0 = j;
             }
         }
-        p->w_mid.assign((size_t)n_sub, 0.0);
+        // (the separable degridder stages visibility indices in 31 bits)
+        const bool fits = (int64_t)n_bl * n_t * n_chan < 0x7FFFFFFFll;
+        const bool sized = separable_size(L) && fits;
+        p->w_sep.assign((size_t)n_sub, 0.0);
+        p->sep_sub.assign((size_t)n_sub, 0);
+        double theta = 0.0, c_max = 0.0;
+        int64_t n_sep = 0, kp_sep = 0;
         for (int64_t s = 0; s < n_sub; ++s) {
             const int32_t *d = &p->desc[s * kDescFields];
             const double w0 = w_step > 0.0 ? (double)(d[IDG_DESC_LAYER] + pr.k_min) * w_step : 0.0;
@@ -453,21 +460,26 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
                 lo = std::min(lo, std::min(wa, wb));
                 hi = std::max(hi, std::max(wa, wb));
             }
-            dw0_max = std::max(dw0_max, std::max(std::fabs(lo - w0), std::fabs(hi - w0)));
-            dws_max = std::max(dws_max, 0.5 * (hi - lo));
-            p->w_mid[s] = 0.5 * (lo + hi);
+            const double cw0 = kTwoPi * std::max(std::fabs(lo - w0), std::fabs(hi - w0));
+            const bool mid = cw0 * r_max > kSepThetaMax;
+            const double cs = mid ? kTwoPi * 0.5 * (hi - lo) : cw0;
+            p->w_sep[s] = mid ? 0.5 * (lo + hi) : w0;
+            theta = std::max(theta, cs * r_max);
+            if (sized && cs * r_max <= kSepThetaMax) {
+                p->sep_sub[s] = 1;
+                c_max = std::max(c_max, cs);
+                ++n_sep;
+                kp_sep += d[IDG_DESC_KP];
+            }
         }
-        p->sep_mid = 6.283185307179586476925286766559 * dw0_max * r_max > kSepThetaMax;
-        const double dw_max = p->sep_mid ? dws_max : dw0_max;
-        const double c_max = 6.283185307179586476925286766559 * dw_max;
-        p->sep_theta = c_max * r_max;
+        p->sep_theta = theta;
         p->c_scale = 1.0f;
         if (c_max > 1.0) p->c_scale = (float)std::ldexp(1.0, -(int)std::ceil(std::log2(c_max)));
         p->r_scale = r_max > 0.0 ? (float)std::ldexp(1.0, std::min(100, (int)std::floor(std::log2(1.0 / r_max)))) : 1.0f;
-        // (the separable degridder stages visibility indices in 31 bits)
-        const bool fits = (int64_t)n_bl * n_t * n_chan < 0x7FFFFFFFll;
-        p->stats.separable = (separable_size(L) && p->sep_theta <= kSepThetaMax && fits) ? 1 : 0;
+        p->stats.separable = (sized && n_sep == n_sub) ? 1 : 0;
         p->stats.sep_phase = p->sep_theta;
+        p->stats.n_sep_subgrids = n_sep;
+        p->stats.n_vis_sep = kp_sep;
     }
 
     // device metadata; without any CUDA device the plan stays host-only
@@ -500,23 +512,31 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         split_pair(g.u0 * k_uv, g.a0h, g.a0l);
         split_pair(g.v0 * k_uv, g.b0h, g.b0l);
         split_pair(g.w0 * kTwoPi, g.c0h, g.c0l);
-        const double ws = p->sep_mid ? p->w_mid[s] : g.w0;
+        const double ws = p->w_sep[s];
         split_pair(ws * kTwoPi, g.csh, g.csl);
         g.dws = (float)(2.0 * (ws - g.w0));
     }
     std::vector<int32_t> span_order;
-    // device work order: most visibilities first (longest-processing-time first
-    // for the block scheduler), ties in plan order
+    // device work order: the separable subgrids, then the others (one launch each),
+    // each part with most visibilities first (longest-processing-time first for the
+    // block scheduler), ties in plan order
+    const auto work_first = [&](int32_t a, int32_t b) {
+        if (p->sep_sub[a] != p->sep_sub[b]) return p->sep_sub[a] > p->sep_sub[b];
+        return hsub[a].kp > hsub[b].kp;
+    };
     std::vector<int32_t> order((size_t)std::max<int64_t>(n_sub, 1));
     std::iota(order.begin(), order.begin() + n_sub, 0);
-    std::stable_sort(order.begin(), order.begin() + n_sub,
-                     [&](int32_t a, int32_t b) { return hsub[a].kp > hsub[b].kp; });
+    std::stable_sort(order.begin(), order.begin() + n_sub, work_first);
     p->order.assign(order.begin(), order.begin() + n_sub);
     p->kp_prefix_order.assign((size_t)n_sub + 1, 0);
     p->kp_order.assign((size_t)n_sub, 0);
+    p->sep_prefix_order.assign((size_t)n_sub + 1, 0);
+    p->sep_prefix_plan.assign((size_t)n_sub + 1, 0);
     for (int64_t s = 0; s < n_sub; ++s) {
         p->kp_order[s] = hsub[order[s]].kp;
         p->kp_prefix_order[s + 1] = p->kp_prefix_order[s] + p->kp_order[s];
+        p->sep_prefix_order[s + 1] = p->sep_prefix_order[s] + p->sep_sub[order[s]];
+        p->sep_prefix_plan[s + 1] = p->sep_prefix_plan[s] + p->sep_sub[s];
     }
     // spans of whole baselines for the host-buffer calls (about 256 MB of
     // visibilities each, at least 4; the first and last cut to a quarter so the
@@ -545,13 +565,14 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         std::vector<int32_t> so((size_t)std::max<int64_t>(n_sub, 1));
         std::iota(so.begin(), so.begin() + n_sub, 0);
         for (size_t k = 0; k + 1 < p->span_first.size(); ++k)
-            std::stable_sort(so.begin() + p->span_first[k], so.begin() + p->span_first[k + 1],
-                             [&](int32_t a, int32_t b) { return hsub[a].kp > hsub[b].kp; });
+            std::stable_sort(so.begin() + p->span_first[k], so.begin() + p->span_first[k + 1], work_first);
         p->kp_span_order.assign((size_t)n_sub, 0);
         p->kp_prefix_span.assign((size_t)n_sub + 1, 0);
+        p->sep_prefix_span.assign((size_t)n_sub + 1, 0);
         for (int64_t s = 0; s < n_sub; ++s) {
             p->kp_span_order[s] = hsub[so[s]].kp;
             p->kp_prefix_span[s + 1] = p->kp_prefix_span[s] + p->kp_span_order[s];
+            p->sep_prefix_span[s + 1] = p->sep_prefix_span[s] + p->sep_sub[so[s]];
         }
         span_order.swap(so);
     }
@@ -707,14 +728,15 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
 // plain adder.  The degridder takes them when most visibilities of the launch
 // lie in subgrids of at least 512 (as the default per-call choice does).
 // the fused composite kernels: the direct tensor-core ones at L = 32, the separable ones at
-// L = 32, 24 and 16 where the plan is separable (the process-default kernel choice only)
-static bool fused_size(const idg_plan *p) { return p->L == 32 || (separable_size(p->L) && p->stats.separable); }
-static bool fused_grid(const idg_plan *p) {
-    return fused_size(p) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+// L = 32, 24 and 16 for subgrids that meet the remainder bound (the process-default kernel
+// choice only); sep: the launch's subgrids take the separable kernels
+static bool fused_size(const idg_plan *p, bool sep) { return p->L == 32 || (separable_size(p->L) && sep); }
+static bool fused_grid(const idg_plan *p, bool sep) {
+    return fused_size(p, sep) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
            p->opts.adder_mode == IDG_ADDER_ATOMIC && p->kernel_variant(IDG_KERNEL_GRIDDER) == 0;
 }
-static bool fused_degrid(const idg_plan *p, const SubgridSet &set) {
-    if (!(fused_size(p) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
+static bool fused_degrid(const idg_plan *p, const SubgridSet &set, bool sep) {
+    if (!(fused_size(p, sep) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
           p->kernel_variant(IDG_KERNEL_DEGRIDDER) == 0))
         return false;
     int64_t small = 0, all = 0;
@@ -725,13 +747,46 @@ static bool fused_degrid(const idg_plan *p, const SubgridSet &set) {
     return 2 * small <= all;
 }
 
-// Grid the subgrids at positions [first, first + count) of the order o, in
-// pieces of at most `chunk` subgrids that pass through the subgrid scratch
-// (gridder -> transform -> adder), or in one fused launch (no scratch).
-static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
+// Number of leading positions of [first, first + count) of order o that take the
+// separable kernels: the separable subgrids when they come first in the range (the
+// work order and every span list them first), else 0 and the direct kernels take
+// the whole range (they serve every subgrid).
+static int64_t sep_head(const idg_plan *p, Order o, int64_t first, int64_t count) {
+    if (p->stats.separable) return count;
+    const auto &pre = o == Order::Work ? p->sep_prefix_order : o == Order::Plan ? p->sep_prefix_plan : p->sep_prefix_span;
+    if (pre.empty()) return 0;
+    const int64_t ns = pre[first + count] - pre[first];
+    return pre[first + ns] - pre[first] == ns ? ns : 0;
+}
+
+// the composite calls need the subgrid scratch for a part that runs unfused
+static bool grid_needs_scratch(const idg_plan *p, Order o, int64_t first, int64_t count) {
+    const int64_t ns = sep_head(p, o, first, count);
+    return p->opts.adder_mode == IDG_ADDER_COMPENSATED || (ns > 0 && !fused_grid(p, true)) ||
+           (ns < count && !fused_grid(p, false));
+}
+static bool degrid_needs_scratch(const idg_plan *p, Order o, int64_t first, int64_t count) {
+    const int64_t ns = sep_head(p, o, first, count);
+    return (ns > 0 && !fused_degrid(p, order_of(p, o, first, ns), true)) ||
+           (ns < count && !fused_degrid(p, order_of(p, o, first + ns, count - ns), false));
+}
+// the same over every span of the host-buffer calls
+static bool spans_need_scratch(const idg_plan *p, bool grid) {
+    const auto &sf = p->span_first;
+    for (size_t k = 0; k + 1 < sf.size(); ++k)
+        if (sf[k + 1] > sf[k] && (grid ? grid_needs_scratch(p, Order::Span, sf[k], sf[k + 1] - sf[k])
+                                       : degrid_needs_scratch(p, Order::Span, sf[k], sf[k + 1] - sf[k])))
+            return true;
+    return false;
+}
+
+// Grid the subgrids at positions [first, first + count) of the order o, all of one
+// kind (g.separable), in pieces of at most `chunk` subgrids that pass through the
+// subgrid scratch (gridder -> transform -> adder), or in one fused launch (no scratch).
+static idg_status grid_part(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                             void *scratch, int64_t chunk, const void *vis, const uint8_t *flags, const void *aterms,
                             const float *taper, void *grid, void *cbuf, cudaStream_t s) {
-    if (!cbuf && fused_grid(p)) {
+    if (!cbuf && fused_grid(p, g.separable != 0)) {
         ProfileScope ps(IDG_KERNEL_GRIDDER, s, vispix(p, first, count, o));
         const SubgridSet set = order_of(p, o, first, count);
         return g.separable ? launch_gridder_sep_fused(g, set, vis, flags, aterms, taper, grid, s)
@@ -757,13 +812,13 @@ static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64
     return st;
 }
 
-// Degrid the subgrids [first, first + count) (splitter -> transform -> degridder),
-// or in one fused launch.
-static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
+// Degrid the subgrids [first, first + count), all of one kind (splitter -> transform
+// -> degridder), or in one fused launch.
+static idg_status degrid_part(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
                               void *scratch, int64_t chunk, const void *grid, const uint8_t *flags, const void *aterms,
                               const float *taper, void *vis_out, cudaStream_t s) {
     const SubgridSet all = order_of(p, o, first, count);
-    if (fused_degrid(p, all)) {
+    if (fused_degrid(p, all, g.separable != 0)) {
         ProfileScope ps(IDG_KERNEL_DEGRIDDER, s, vispix(p, first, count, o));
         return g.separable ? launch_degridder_sep_fused(g, all, grid, flags, aterms, taper, vis_out, s)
                            : launch_degridder_tcw_fused(g, all, grid, flags, aterms, taper, vis_out, s);
@@ -788,6 +843,42 @@ static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int
     return st;
 }
 
+// A range of positions: its separable head by the separable kernels, the rest by the
+// direct ones (g: the plan's geometry).
+static idg_status grid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
+                            void *scratch, int64_t chunk, const void *vis, const uint8_t *flags, const void *aterms,
+                            const float *taper, void *grid, void *cbuf, cudaStream_t s) {
+    const int64_t ns = sep_head(p, o, first, count);
+    Geometry gp = g;
+    idg_status st = IDG_OK;
+    if (ns > 0) {
+        gp.separable = 1;
+        st = grid_part(p, gp, o, first, ns, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
+    }
+    if (st == IDG_OK && ns < count) {
+        gp.separable = 0;
+        st = grid_part(p, gp, o, first + ns, count - ns, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
+    }
+    return st;
+}
+
+static idg_status degrid_span(const idg_plan *p, const Geometry &g, Order o, int64_t first, int64_t count,
+                              void *scratch, int64_t chunk, const void *grid, const uint8_t *flags, const void *aterms,
+                              const float *taper, void *vis_out, cudaStream_t s) {
+    const int64_t ns = sep_head(p, o, first, count);
+    Geometry gp = g;
+    idg_status st = IDG_OK;
+    if (ns > 0) {
+        gp.separable = 1;
+        st = degrid_part(p, gp, o, first, ns, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
+    }
+    if (st == IDG_OK && ns < count) {
+        gp.separable = 0;
+        st = degrid_part(p, gp, o, first + ns, count - ns, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
+    }
+    return st;
+}
+
 // The composite calls over the positions [first, first + count) of order o
 // (the whole plan in work order for idg_grid / idg_degrid, a plan-order range
 // for the range calls).
@@ -798,8 +889,9 @@ static idg_status grid_call(const idg_plan *p, Order o, int64_t first, int64_t c
     idg_status st = IDG_OK;
     const int64_t chunk = std::min(chunk_subgrids(p), count);
     const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
-    void *scratch = nullptr;     // the subgrid scratch, unless one fused launch takes the call
-    if (comp || !fused_grid(p)) st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
+    void *scratch = nullptr;     // the subgrid scratch, unless fused launches take the call
+    if (grid_needs_scratch(p, o, first, count))
+        st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
     const Geometry g = p->geometry();
     const size_t grid_f4 = (size_t)p->stats.n_w_layers * p->N * p->N * 2;
@@ -828,7 +920,7 @@ static idg_status degrid_call(const idg_plan *p, Order o, int64_t first, int64_t
     idg_status st = IDG_OK;
     const int64_t chunk = std::min(chunk_subgrids(p), count);
     void *scratch = nullptr;
-    if (!fused_degrid(p, order_of(p, o, first, count)))
+    if (degrid_needs_scratch(p, o, first, count))
         st = scratch_alloc(p->device, (size_t)chunk * p->L * p->L * 32, s, &scratch);
     if (st != IDG_OK) return st;
     st = degrid_span(p, p->geometry(), o, first, count, scratch, chunk, grid, flags, aterms, taper, vis_out, s);
@@ -1022,7 +1114,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     CopyJoin join(s, cs);
     const bool comp = p->opts.adder_mode == IDG_ADDER_COMPENSATED;
     const size_t sizes[6] = {nvis * 32, h_flags ? nvis : 0, at_bytes, h_taper ? (size_t)p->L * p->L * 4 : 0, grid_bytes,
-                             comp || !fused_grid(p) ? (size_t)chunk * p->L * p->L * 32 : 0};
+                             spans_need_scratch(p, true) ? (size_t)chunk * p->L * p->L * 32 : 0};
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
     const size_t grid_f4 = grid_bytes / 16;

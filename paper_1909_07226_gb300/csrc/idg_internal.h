@@ -21,7 +21,7 @@ struct alignas(16) DevSubgrid {
     // about 2^-48): u0 k_uv, v0 k_uv and 2 pi w0
     float a0h, a0l, b0h, b0l, c0h, c0l;
     // the separable kernels' w offset w_s (w0, or the middle of the subgrid's w range
-    // when the plan needs it to meet the remainder bound): 2 pi w_s as a float pair, and
+    // when it needs that to meet the remainder bound): 2 pi w_s as a float pair, and
     // 2 (w_s - w0), the phase in half turns per unit of n' they apply to the subgrid image
     float csh, csl, dws;
 };
@@ -51,8 +51,11 @@ struct Geometry {
     // max |r| smallest), r the remainder; sep = [s[L] | t[L] | r[L][L]] (FP64
     // differences rounded to FP32)
     const float *sep;
-    int separable;             // 1: max |c_k| max |r| is small enough for the first-order w remainder
-    float c_scale;             // power of two with max |c_k| c_scale <= 1 (c_k = 2 pi (w - w0))
+    // 1: the launch's subgrids meet the bound max |c_k| max |r| of the first-order w
+    // remainder (the plan's own value: every subgrid does; the composite calls set it
+    // per launch for the separable part of a plan)
+    int separable;
+    float c_scale;             // power of two with max |c_k| c_scale <= 1 over the separable subgrids (c_k = 2 pi (w - w_s))
     float r_scale;             // power of two with max |r(x, y)| r_scale <= 1
 };
 
@@ -97,9 +100,14 @@ struct idg_plan {
     float *d_scale_f2 = nullptr;
     float *d_nprime = nullptr;             // [L][L] n', then the separable tables [2 L + L^2]
     double sep_theta = 0.0;                // max |c_k| max |r(x, y)|: phase of the separable remainder
-    bool sep_mid = false;                  // the separable kernels take w_s = the middle of each subgrid's w range
     int sep_j0 = 0;                        // reference row and column of the separable split
-    std::vector<double> w_mid;             // [n_sub] middle of each subgrid's w range (wavelengths)
+    // per subgrid (plan order): the separable kernels' w offset w_s (wavelengths), and
+    // 1 where the remainder phase with it meets the bound (the separable kernels take it)
+    std::vector<double> w_sep;
+    std::vector<uint8_t> sep_sub;
+    // [n + 1] number of separable subgrids before each position of the work, plan and
+    // span orders (the work order and each span list the separable subgrids first)
+    std::vector<int64_t> sep_prefix_order, sep_prefix_plan, sep_prefix_span;
     float c_scale = 1.0f;
     float r_scale = 1.0f;
     bool any_dropped = false;
@@ -107,11 +115,13 @@ struct idg_plan {
     std::vector<int64_t> kp_prefix_plan;    // [n_sub + 1], sum of K_p in plan order
     std::vector<int64_t> kp_prefix_order;   // [n_sub + 1], sum of K_p in device work order
     std::vector<int32_t> kp_plan;           // [n_sub] K_p in plan order
-    std::vector<int32_t> kp_order;          // [n_sub] K_p in device work order (non-increasing)
+    std::vector<int32_t> kp_order;          // [n_sub] K_p in device work order (separable subgrids
+                                            // first, each part non-increasing)
     std::vector<int32_t> order;             // [n_sub] plan index of each work-order slot (host copy)
     // spans of whole baselines for the host-buffer calls: span k holds plan indices
     // [span_first[k], span_first[k + 1]) and baselines [span_bl[k], span_bl[k + 1]);
-    // span_order lists each span's subgrids by K_p descending (positions as in plan order)
+    // span_order lists each span's separable subgrids, then the others, each part by K_p
+    // descending (positions as in plan order)
     std::vector<int64_t> span_first;
     std::vector<int32_t> span_bl;
     int32_t *d_span_order = nullptr;
@@ -198,16 +208,16 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
 
 // tensor-core gridder (L = 32; FP16 hi/lo split products, FP32 accumulation in
 // tensor memory) and the device error word of the bounded waits
-// subgrid sizes the separable tensor-core kernels are built for (32 and 24)
+// subgrid sizes the separable tensor-core kernels are built for (32, 24 and 16)
 bool separable_size(int L);
-// separable tensor-core gridder (L = 32 or 24, g.separable): subgrid images, or fused
+// separable tensor-core gridder (L = 32, 24 or 16, g.separable): subgrid images, or fused
 // with the transform and the adder into grid
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream);
 idg_status launch_gridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status read_sep_error(int *code);
-// separable tensor-core degridder (L = 32 or 24, g.separable): from subgrid images, or
+// separable tensor-core degridder (L = 32, 24 or 16, g.separable): from subgrid images, or
 // fused with the splitter and the inverse transform from grid
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream);
@@ -235,7 +245,7 @@ idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, 
 struct JobDev;
 idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-// the separable kernels over work items of jobs (subgrid size L) whose plans are separable
+// the separable kernels over work items (subgrid size L) whose subgrids meet the bound
 idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
 idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count,
                                       void *stream);

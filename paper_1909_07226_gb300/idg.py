@@ -64,7 +64,8 @@ class PlanStats(ctypes.Structure):
                 ("subgrid_size", ctypes.c_int32), ("grid_size", ctypes.c_int32),
                 ("n_bl", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_chan", ctypes.c_int32),
                 ("n_stations", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("separable", ctypes.c_int32), ("sep_phase", ctypes.c_double)]
+                ("separable", ctypes.c_int32), ("sep_phase", ctypes.c_double),
+                ("n_sep_subgrids", ctypes.c_int64), ("n_vis_sep", ctypes.c_int64)]
 
 
 _lib = None

@@ -82,26 +82,32 @@ def test_remainder_is_fourth_order_in_the_direction_cosines():
 
 
 def _theta_definition(wl):
-    # max |2 pi (w - w_s)| max |r|: w_s = the subgrid's w offset w0 when that gives a
-    # phase within the bound, else the middle of each subgrid's own w range
+    # per subgrid: |2 pi (w - w_s)| max |r| with w_s = the subgrid's w offset w0 when
+    # that gives a phase within the bound, else the middle of the subgrid's own w range;
+    # the plan's phase is the largest, and the subgrids within the bound (with their
+    # K_p) are the ones the separable kernels take
     op = O.plan(wl)
     L, S = wl.subgrid_size, wl.grid_size * wl.cell_size
     r_max = np.abs(_split(L, S, _best_j0(L, S))[3]).max()
     c = 299792458.0
-    dw0 = dws = 0.0
+    theta, n_sep, kp_sep = 0.0, 0, 0
     for row in op.desc:
         bl, t0, nt, c0, nc = row[O.D_BL], row[O.D_T0], row[O.D_NT], row[O.D_C0], row[O.D_NC]
         w0 = (row[O.D_LAYER] + op.k_min) * wl.w_step if wl.w_step > 0 else 0.0
         w = wl.uvw_m[bl, t0:t0 + nt, 2][:, None] * wl.freqs_hz[None, c0:c0 + nc] / c
-        dw0 = max(dw0, np.abs(w - w0).max())
-        dws = max(dws, 0.5 * (w.max() - w.min()))
-    theta0 = 2 * np.pi * dw0 * r_max
-    return theta0 if theta0 <= 1.38e-3 else 2 * np.pi * dws * r_max
+        th = 2 * np.pi * np.abs(w - w0).max() * r_max
+        if th > 1.38e-3:
+            th = 2 * np.pi * 0.5 * (w.max() - w.min()) * r_max
+        theta = max(theta, th)
+        if th <= 1.38e-3:
+            n_sep += 1
+            kp_sep += int(row[O.D_KP])
+    return theta, n_sep, kp_sep
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(w_step=20.0, diameter_m=20000.0, n_t=24, max_t=12),
                                 dict(N=256, cell=5e-4, diameter_m=800.0), dict(N=256, cell=1e-3, diameter_m=300.0),
-                                dict(N=512, cell=1e-3, diameter_m=800.0)])
+                                dict(N=512, cell=1e-3, diameter_m=800.0), dict(N=512, cell=8e-4, diameter_m=800.0)])
 def test_plan_reports_the_remainder_phase(kw):
     from paper_1909_07226_gb300 import idg
     args = dict(seed=1032, n_st=5, n_t=48, n_chan=5, L=32, N=128, max_t=48, n_slots=1, flag_p=0.1,
@@ -109,9 +115,23 @@ def test_plan_reports_the_remainder_phase(kw):
     args.update(kw)
     wl = syn.make_small(**args)
     p = idg.plan_from_workload(wl)
-    want = _theta_definition(wl)
+    want, n_sep, kp_sep = _theta_definition(wl)
     assert p.stats.sep_phase == pytest.approx(want, rel=1e-9, abs=1e-15)
     assert p.stats.separable == (1 if want <= 1.38e-3 else 0)
+    assert (p.stats.n_sep_subgrids, p.stats.n_vis_sep) == (n_sep, kp_sep)
+    assert p.stats.separable == (1 if n_sep == p.n_subgrids else 0)
+
+
+def test_mixed_plan_splits_its_subgrids():
+    # a wide field where only the subgrids of small w spread meet the bound: some, not
+    # all, go to the separable kernels
+    from paper_1909_07226_gb300 import idg
+    wl = syn.make_small(seed=1032, n_st=5, n_t=48, n_chan=5, L=32, N=512, max_t=48, n_slots=1, flag_p=0.1,
+                        diameter_m=800.0, cell=8e-4)
+    p = idg.plan_from_workload(wl)
+    _, n_sep, kp_sep = _theta_definition(wl)
+    assert 0 < n_sep < p.n_subgrids
+    assert p.stats.separable == 0 and p.stats.n_sep_subgrids == n_sep and 0 < p.stats.n_vis_sep < p.stats.n_vis_planned
 
 
 def _fma32(a, b, c):
