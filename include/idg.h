@@ -124,6 +124,15 @@ typedef struct {
                                  the separable kernels take these, the direct kernels
                                  the rest (0 when L is not 32, 24 or 16)           */
     int64_t n_vis_sep;        /* sum of K_p over those subgrids                    */
+    int64_t n_split_subgrids; /* subgrids outside the bound that the composite calls
+                                 take in pieces: kt x kc blocks of their timesteps and
+                                 channels, each within the bound with its own w_s, at
+                                 the subgrid's position (the sums are linear in the
+                                 visibilities, so the pieces add up to the subgrid);
+                                 split where the direct kernels' extra cost per
+                                 visibility outweighs a piece's fixed cost        */
+    int64_t n_pieces;         /* number of those pieces                           */
+    int64_t n_vis_split;      /* sum of K_p over the split subgrids                */
 } idg_plan_stats;
 
 /* Number of int32 fields per exported subgrid descriptor, and their order. */
@@ -202,9 +211,11 @@ void idg_plan_destroy(idg_plan *plan);
  * one fused tensor-core launch (image-domain sum, taper and A-terms, transform
  * and adder per subgrid in one CTA) and takes no subgrid scratch.  A plan with
  * only some subgrids within the remainder bound (0 < n_sep_subgrids < n_subgrids)
- * grids those in one separable launch and the rest with the direct kernels (at
- * L = 32 a second fused launch; at 24 and 16 gridder, transform and adder
- * through the scratch).
+ * grids those, and the pieces of the subgrids it splits (n_split_subgrids), in
+ * one separable launch, and the rest with the direct kernels (at L = 32 a second
+ * fused launch; at 24 and 16 gridder, transform and adder through the scratch).
+ * Without the fused separable launch (other modes or kernel choices) the
+ * subgrids are not split: the separable ones go first, the others direct.
  */
 idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_flags,
                     const void *d_aterms, const float *d_taper, void *d_grid, idg_stream stream);
@@ -220,7 +231,8 @@ idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_fl
  * visibilities lie in subgrids of 512 or more, the call
  * is one fused tensor-core launch (splitter, transform, A-terms and taper, and
  * the visibility sums per subgrid in one CTA) without subgrid scratch.  A plan
- * with only some subgrids within the remainder bound degrids those and the
+ * with only some subgrids within the remainder bound degrids those (with the
+ * pieces of the subgrids it splits, when the separable part runs fused) and the
  * rest in separate launches, each by the same rules.
  */
 idg_status idg_degrid(const idg_plan *plan, const void *d_grid, const uint8_t *d_flags,

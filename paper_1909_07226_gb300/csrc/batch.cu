@@ -504,10 +504,13 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         b->n_vis += p->stats.n_vis_planned;
         if (p->any_dropped && bufs[j].vis_out)
             b->zero_on_degrid.push_back({bufs[j].vis_out, (size_t)p->n_bl * p->n_t * p->n_chan * 32});
-        // one class per (L, separable): a plan's subgrids within the remainder bound go to
-        // the separable kernels, the others to the direct ones
-        for (int64_t s = 0; s < p->stats.n_subgrids; ++s) {
-            const bool sep = separable_size(p->L) && p->sep_sub[s];
+        // one class per (L, separable): a plan's subgrids within the remainder bound and the
+        // pieces of the subgrids it splits go to the separable kernels, the others to the
+        // direct ones (entries s index the plan's device table: pieces at n_subgrids ..)
+        const int64_t n_sub = p->stats.n_subgrids, n_ent = n_sub + (int64_t)p->pieces.size();
+        for (int64_t s = 0; s < n_ent; ++s) {
+            if (s < n_sub && p->split_sub[s]) continue;
+            const bool sep = separable_size(p->L) && (s >= n_sub || p->sep_sub[s]);
             size_t c = 0;
             while (c < b->classes.size() && (b->classes[c].L != p->L || b->classes[c].sep != sep)) ++c;
             if (c == b->classes.size()) {
@@ -523,7 +526,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
                 per_class.emplace_back();
             }
             per_class[c].push_back(make_int2(j, (int)s));
-            b->classes[c].vispix += (double)p->kp_plan[s] * p->L * p->L;
+            b->classes[c].vispix += (double)p->kp_all[s] * p->L * p->L;
         }
     }
     idg_status st = IDG_OK;
@@ -532,7 +535,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         auto &items = per_class[c];
         // cost order: most visibilities first, ties by job and subgrid
         std::stable_sort(items.begin(), items.end(), [&](const int2 &x, const int2 &y) {
-            return plans[x.x]->kp_plan[x.y] > plans[y.x]->kp_plan[y.y];
+            return plans[x.x]->kp_all[x.y] > plans[y.x]->kp_all[y.y];
         });
         auto &cl = b->classes[c];
         cl.n_items = (int64_t)items.size();
@@ -541,7 +544,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         // visibilities sit mostly in subgrids of fewer than 512 take the fused kernels
         int64_t small = 0, all = 0;
         for (const int2 &it : items) {
-            const int64_t kp = plans[it.x]->kp_plan[it.y];
+            const int64_t kp = plans[it.x]->kp_all[it.y];
             all += kp;
             if (kp < 512) small += kp;
         }

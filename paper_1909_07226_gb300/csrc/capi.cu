@@ -165,6 +165,70 @@ __global__ void split_uvw_kernel(const double *__restrict__ uvw, float4 *__restr
 // (9.5e-7), the order of the rounding of the FP16 split sums themselves.
 constexpr double kSepThetaMax = 1.38e-3;
 
+// Pieces of subgrid s (outside the remainder bound with any single w_s): the
+// smallest grid of kt x kc equal blocks of its timesteps and channels (kt kc pieces,
+// most even cut first) whose blocks each meet the bound with w_s = the middle of the
+// block's own w range.  A piece costs the separable kernels' fixed cost per subgrid
+// (transform, A-terms, adder: about F_L visibilities' worth) and saves the direct
+// kernels' extra cost per visibility, so a subgrid of K_p visibilities is split only
+// into at most (rho_L - 1) K_p / F_L pieces, rho_L the measured ratio of the direct to
+// the separable kernels' time per visibility (L = 32: 3.8, 24: 2.7; at L = 16 the direct
+// kernels come within 20 % and pieces measured slower, so 1: none) and
+// F_L = 200 (L / 32)^2 visibilities.
+static void split_pieces(idg_plan *p, int64_t s, double r_max, const double *uvw, const double *freqs_hz,
+                         double *c_max) {
+    const int32_t *d = &p->desc[s * kDescFields];
+    const int t0 = d[IDG_DESC_T0], nt = d[IDG_DESC_NT], c0 = d[IDG_DESC_C0], nc = d[IDG_DESC_NC];
+    const int64_t kp = d[IDG_DESC_KP];
+    const double rho = p->L == 32 ? 3.8 : p->L == 24 ? 2.7 : 1.0;
+    const double F = 200.0 * (p->L / 32.0) * (p->L / 32.0);
+    const int64_t max_pieces = std::min<int64_t>((int64_t)((rho - 1.0) * (double)kp / F), (int64_t)nt * nc);
+    // w range (wavelengths) of the block [ta, tb) x [ca, cb): w_t f is linear in f, so the
+    // channel ends bound it
+    auto range = [&](int ta, int tb, int ca, int cb, double *lo, double *hi) {
+        const double fa = freqs_hz[ca] / kSpeedOfLight, fb = freqs_hz[cb - 1] / kSpeedOfLight;
+        for (int t = ta; t < tb; ++t) {
+            const double w = uvw[((size_t)d[IDG_DESC_BASELINE] * p->n_t + t) * 3 + 2];
+            const double a = std::min(w * fa, w * fb), b = std::max(w * fa, w * fb);
+            if (t == ta) *lo = a, *hi = b;
+            *lo = std::min(*lo, a);
+            *hi = std::max(*hi, b);
+        }
+    };
+    auto meets = [&](double lo, double hi) { return kTwoPi * 0.5 * (hi - lo) * r_max <= kSepThetaMax; };
+    for (int64_t prod = 2; prod <= max_pieces; ++prod)
+        for (int kt = 1; kt <= nt && kt <= prod; ++kt) {
+            if (prod % kt) continue;
+            const int64_t kc = prod / kt;
+            if (kc > nc) continue;
+            bool ok = true;
+            for (int i = 0; i < kt && ok; ++i)
+                for (int j = 0; j < kc && ok; ++j) {
+                    double lo, hi;
+                    range(t0 + (int)((int64_t)i * nt / kt), t0 + (int)((int64_t)(i + 1) * nt / kt),
+                          c0 + (int)((int64_t)j * nc / kc), c0 + (int)((int64_t)(j + 1) * nc / kc), &lo, &hi);
+                    ok = meets(lo, hi);
+                }
+            if (!ok) continue;
+            for (int i = 0; i < kt; ++i)
+                for (int j = 0; j < kc; ++j) {
+                    idg_plan::Piece pc;
+                    pc.parent = (int32_t)s;
+                    pc.t0 = t0 + (int)((int64_t)i * nt / kt);
+                    pc.nt = t0 + (int)((int64_t)(i + 1) * nt / kt) - pc.t0;
+                    pc.c0 = c0 + (int)((int64_t)j * nc / kc);
+                    pc.nc = c0 + (int)((int64_t)(j + 1) * nc / kc) - pc.c0;
+                    double lo, hi;
+                    range(pc.t0, pc.t0 + pc.nt, pc.c0, pc.c0 + pc.nc, &lo, &hi);
+                    pc.ws = 0.5 * (lo + hi);
+                    *c_max = std::max(*c_max, kTwoPi * 0.5 * (hi - lo));
+                    p->pieces.push_back(pc);
+                }
+            p->split_sub[s] = 1;
+            return;
+        }
+}
+
 idg::Geometry idg_plan::geometry() const {
     Geometry g;
     g.L = L;
@@ -296,6 +360,8 @@ void idg_plan_destroy(idg_plan *p) {
     cudaFree(p->d_sub);
     cudaFree(p->d_order);
     cudaFree(p->d_span_order);
+    cudaFree(p->d_fused_order);
+    cudaFree(p->d_fused_span);
     cudaFree(p->d_uvw);
     cudaFree(p->d_scale);
     cudaFree(p->d_uvw_f2);
@@ -446,6 +512,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         const bool sized = separable_size(L) && fits;
         p->w_sep.assign((size_t)n_sub, 0.0);
         p->sep_sub.assign((size_t)n_sub, 0);
+        p->split_sub.assign((size_t)n_sub, 0);
+        p->pieces.clear();
         double theta = 0.0, c_max = 0.0;
         int64_t n_sep = 0, kp_sep = 0;
         for (int64_t s = 0; s < n_sub; ++s) {
@@ -470,6 +538,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
                 c_max = std::max(c_max, cs);
                 ++n_sep;
                 kp_sep += d[IDG_DESC_KP];
+            } else if (sized) {
+                split_pieces(p, s, r_max, uvw_m, freqs_hz, &c_max);
             }
         }
         p->sep_theta = theta;
@@ -480,6 +550,14 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         p->stats.sep_phase = p->sep_theta;
         p->stats.n_sep_subgrids = n_sep;
         p->stats.n_vis_sep = kp_sep;
+        p->stats.n_pieces = (int64_t)p->pieces.size();
+        p->stats.n_split_subgrids = 0;
+        p->stats.n_vis_split = 0;
+        for (int64_t s = 0; s < n_sub; ++s)
+            if (p->split_sub[s]) {
+                ++p->stats.n_split_subgrids;
+                p->stats.n_vis_split += p->desc[s * kDescFields + IDG_DESC_KP];
+            }
     }
 
     // device metadata; without any CUDA device the plan stays host-only
@@ -516,6 +594,18 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         split_pair(ws * kTwoPi, g.csh, g.csl);
         g.dws = (float)(2.0 * (ws - g.w0));
     }
+    const int64_t n_pc = (int64_t)p->pieces.size();
+    if (n_pc > 0) hsub.resize((size_t)(n_sub + n_pc));
+    for (int64_t i = 0; i < n_pc; ++i) {
+        const idg_plan::Piece &pc = p->pieces[i];
+        DevSubgrid &g = hsub[n_sub + i];
+        g = hsub[pc.parent];
+        g.t0 = pc.t0; g.nt = pc.nt; g.c0 = pc.c0; g.nc = pc.nc; g.kp = pc.nt * pc.nc;
+        split_pair(pc.ws * kTwoPi, g.csh, g.csl);
+        g.dws = (float)(2.0 * (pc.ws - g.w0));
+    }
+    p->kp_all.assign((size_t)(n_sub + n_pc), 0);
+    for (int64_t s = 0; s < n_sub + n_pc; ++s) p->kp_all[s] = hsub[s].kp;
     std::vector<int32_t> span_order;
     // device work order: the separable subgrids, then the others (one launch each),
     // each part with most visibilities first (longest-processing-time first for the
@@ -576,6 +666,50 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         }
         span_order.swap(so);
     }
+    // the composite calls' lists when some subgrids go in pieces: d_sub entries of the
+    // separable subgrids and the pieces first, then the direct subgrids left, each part by
+    // K_p descending; for the whole plan and per span
+    std::vector<int32_t> fused_order, fused_span;
+    if (n_pc > 0) {
+        std::vector<int64_t> piece_first((size_t)n_sub + 1, 0);
+        for (const auto &pc : p->pieces) ++piece_first[pc.parent + 1];
+        for (int64_t s = 0; s < n_sub; ++s) piece_first[s + 1] += piece_first[s];
+        auto sep_kind = [&](int32_t e) { return e >= n_sub || p->sep_sub[e]; };
+        auto fused_first = [&](int32_t a, int32_t b) {
+            if (sep_kind(a) != sep_kind(b)) return sep_kind(a);
+            return hsub[a].kp > hsub[b].kp;
+        };
+        // entries of plan subgrids [a, b): each subgrid itself, or its pieces
+        auto entries = [&](int64_t a, int64_t b, std::vector<int32_t> &out) {
+            for (int64_t s = a; s < b; ++s) {
+                if (!p->split_sub[s]) out.push_back((int32_t)s);
+                for (int64_t i = piece_first[s]; i < piece_first[s + 1]; ++i) out.push_back((int32_t)(n_sub + i));
+            }
+        };
+        entries(0, n_sub, fused_order);
+        std::stable_sort(fused_order.begin(), fused_order.end(), fused_first);
+        p->fspan_first.assign(1, 0);
+        for (size_t k = 0; k + 1 < p->span_first.size(); ++k) {
+            const size_t a = fused_span.size();
+            entries(p->span_first[k], p->span_first[k + 1], fused_span);
+            std::stable_sort(fused_span.begin() + a, fused_span.end(), fused_first);
+            p->fspan_first.push_back((int64_t)fused_span.size());
+        }
+        auto lists = [&](const std::vector<int32_t> &ord, std::vector<int32_t> &kp, std::vector<int64_t> &kpre,
+                         std::vector<int64_t> &spre) {
+            const size_t n = ord.size();
+            kp.assign(n, 0);
+            kpre.assign(n + 1, 0);
+            spre.assign(n + 1, 0);
+            for (size_t i = 0; i < n; ++i) {
+                kp[i] = hsub[ord[i]].kp;
+                kpre[i + 1] = kpre[i] + kp[i];
+                spre[i + 1] = spre[i] + (sep_kind(ord[i]) ? 1 : 0);
+            }
+        };
+        lists(fused_order, p->kp_fused_order, p->kp_prefix_fused, p->sep_prefix_fused);
+        lists(fused_span, p->kp_fused_span, p->kp_prefix_fspan, p->sep_prefix_fspan);
+    }
     std::vector<double> scale(n_chan);
     std::vector<float> scale_f2((size_t)4 * n_chan);
     for (int c = 0; c < n_chan; ++c) {
@@ -624,6 +758,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
         {(void **)&p->d_order, order.data(), sizeof(int32_t) * order.size(), "work order"},
         {(void **)&p->d_span_order, span_order.data(), sizeof(int32_t) * span_order.size(), "span order"},
+        {(void **)&p->d_fused_order, fused_order.data(), sizeof(int32_t) * fused_order.size(), "piece work order"},
+        {(void **)&p->d_fused_span, fused_span.data(), sizeof(int32_t) * fused_span.size(), "piece span order"},
         {(void **)&p->d_uvw, uvw_m, sizeof(double) * n_uvw, "uvw"},
         {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
         {(void **)&p->d_scale_f2, scale_f2.data(), sizeof(float) * scale_f2.size(), "channel scale pairs"},
@@ -701,17 +837,33 @@ static SubgridSet span_set(const idg_plan *p, int64_t first, int64_t count) {
     return SubgridSet{p->d_span_order + first, 0, count, p->kp_span_order.data() + first};
 }
 
-// positions of a launch: in the work order, in plan order, or in the span order
-enum class Order { Work, Plan, Span };
+// positions of a launch: in the work order, in plan order, in the span order, or in the
+// composite calls' lists with pieces (whole plan or per span)
+enum class Order { Work, Plan, Span, Fused, FusedSpan };
 
 static SubgridSet order_of(const idg_plan *p, Order o, int64_t first, int64_t count) {
-    return o == Order::Work ? order_set(p, first, count)
-                            : o == Order::Plan ? plan_set(p, first, count) : span_set(p, first, count);
+    switch (o) {
+    case Order::Work: return order_set(p, first, count);
+    case Order::Plan: return plan_set(p, first, count);
+    case Order::Span: return span_set(p, first, count);
+    case Order::Fused: return SubgridSet{p->d_fused_order + first, 0, count, p->kp_fused_order.data() + first};
+    default: return SubgridSet{p->d_fused_span + first, 0, count, p->kp_fused_span.data() + first};
+    }
+}
+
+static const std::vector<int64_t> &kp_prefix(const idg_plan *p, Order o) {
+    switch (o) {
+    case Order::Work: return p->kp_prefix_order;
+    case Order::Plan: return p->kp_prefix_plan;
+    case Order::Span: return p->kp_prefix_span;
+    case Order::Fused: return p->kp_prefix_fused;
+    default: return p->kp_prefix_fspan;
+    }
 }
 
 // algorithmic work of a launch over positions [first, first + count)
 static double vispix(const idg_plan *p, int64_t first, int64_t count, Order o) {
-    const auto &pre = o == Order::Work ? p->kp_prefix_order : o == Order::Plan ? p->kp_prefix_plan : p->kp_prefix_span;
+    const auto &pre = kp_prefix(p, o);
     return (double)(pre[first + count] - pre[first]) * p->L * p->L;
 }
 static double pixels(const idg_plan *p, int64_t count) { return (double)count * p->L * p->L; }
@@ -753,7 +905,11 @@ static bool fused_degrid(const idg_plan *p, const SubgridSet &set, bool sep) {
 // the whole range (they serve every subgrid).
 static int64_t sep_head(const idg_plan *p, Order o, int64_t first, int64_t count) {
     if (p->stats.separable) return count;
-    const auto &pre = o == Order::Work ? p->sep_prefix_order : o == Order::Plan ? p->sep_prefix_plan : p->sep_prefix_span;
+    const auto &pre = o == Order::Work    ? p->sep_prefix_order
+                      : o == Order::Plan  ? p->sep_prefix_plan
+                      : o == Order::Span  ? p->sep_prefix_span
+                      : o == Order::Fused ? p->sep_prefix_fused
+                                          : p->sep_prefix_fspan;
     if (pre.empty()) return 0;
     const int64_t ns = pre[first + count] - pre[first];
     return pre[first + ns] - pre[first] == ns ? ns : 0;
@@ -770,12 +926,32 @@ static bool degrid_needs_scratch(const idg_plan *p, Order o, int64_t first, int6
     return (ns > 0 && !fused_degrid(p, order_of(p, o, first, ns), true)) ||
            (ns < count && !fused_degrid(p, order_of(p, o, first + ns, count - ns), false));
 }
+// Whole-plan composite calls and the host-buffer calls' spans run over the lists with
+// pieces when the plan has pieces and the separable kernels take them fused; else over
+// the plan's subgrids (work order, span order).
+static bool use_pieces(const idg_plan *p, bool grid) {
+    if (p->pieces.empty()) return false;
+    if (grid) return fused_grid(p, true);
+    return fused_degrid(p, order_of(p, Order::Fused, 0, p->sep_prefix_fused.back()), true);
+}
+struct Lists {
+    Order whole, span;
+    int64_t n;                              // entries of the whole-plan list
+    const std::vector<int64_t> *span_first; // span k at [(*span_first)[k], (*span_first)[k + 1])
+};
+static Lists lists_for(const idg_plan *p, bool grid) {
+    if (use_pieces(p, grid))
+        return Lists{Order::Fused, Order::FusedSpan, (int64_t)p->kp_fused_order.size(), &p->fspan_first};
+    return Lists{Order::Work, Order::Span, p->stats.n_subgrids, &p->span_first};
+}
+
 // the same over every span of the host-buffer calls
 static bool spans_need_scratch(const idg_plan *p, bool grid) {
-    const auto &sf = p->span_first;
+    const Lists ls = lists_for(p, grid);
+    const auto &sf = *ls.span_first;
     for (size_t k = 0; k + 1 < sf.size(); ++k)
-        if (sf[k + 1] > sf[k] && (grid ? grid_needs_scratch(p, Order::Span, sf[k], sf[k + 1] - sf[k])
-                                       : degrid_needs_scratch(p, Order::Span, sf[k], sf[k + 1] - sf[k])))
+        if (sf[k + 1] > sf[k] && (grid ? grid_needs_scratch(p, ls.span, sf[k], sf[k + 1] - sf[k])
+                                       : degrid_needs_scratch(p, ls.span, sf[k], sf[k + 1] - sf[k])))
             return true;
     return false;
 }
@@ -991,7 +1167,8 @@ idg_status idg_grid(const idg_plan *p, const void *vis, const uint8_t *flags, co
     idg_status st = check_call(p, vis, "d_vis", grid, "d_grid");
     if (st != IDG_OK) return st;
     if (!(taper = p->taper_or_default(taper))) return no_default_taper();
-    return grid_call(p, Order::Work, 0, p->stats.n_subgrids, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
+    const Lists ls = lists_for(p, true);
+    return grid_call(p, ls.whole, 0, ls.n, vis, flags, aterms, taper, grid, (cudaStream_t)stream);
 }
 
 idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags, const void *aterms,
@@ -1005,7 +1182,8 @@ idg_status idg_degrid(const idg_plan *p, const void *grid, const uint8_t *flags,
         cudaError_t e = cudaMemsetAsync(vis_out, 0, (size_t)p->n_bl * p->n_t * p->n_chan * 32, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(vis_out)");
     }
-    return degrid_call(p, Order::Work, 0, n, grid, flags, aterms, taper, vis_out, s);
+    const Lists ls = lists_for(p, false);
+    return degrid_call(p, ls.whole, 0, ls.n, grid, flags, aterms, taper, vis_out, s);
 }
 
 idg_status idg_grid_range(const idg_plan *p, int64_t first, int64_t count, const void *vis, const uint8_t *flags,
@@ -1131,7 +1309,8 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     if (e != cudaSuccess) return cuda_fail(e, "grid_host setup");
     if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
     if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
-    const auto &sf = p->span_first;
+    const Lists ls = lists_for(p, true);
+    const auto &sf = *ls.span_first;
     const auto &sb = p->span_bl;
     const Geometry g = p->geometry();
     for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
@@ -1144,7 +1323,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
             e = cudaStreamWaitEvent(s, e_up, 0);
         if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
         if (st == IDG_OK && sf[k + 1] > sf[k])
-            st = grid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
+            st = grid_span(p, g, ls.span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
                            (const uint8_t *)b.ptr[1], b.ptr[2], h_taper ? (const float *)b.ptr[3] : p->d_taper, b.ptr[4],
                            b.ptr[6], s);
     }
@@ -1197,12 +1376,13 @@ idg_status idg_degrid_host(const idg_plan *p, const void *h_grid, const uint8_t 
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_in, 0);
     if (e == cudaSuccess && p->any_dropped) e = cudaMemsetAsync(b.ptr[4], 0, nvis * 32, s);
     if (e != cudaSuccess) return cuda_fail(e, "degrid_host inputs");
-    const auto &sf = p->span_first;
+    const Lists ls = lists_for(p, false);
+    const auto &sf = *ls.span_first;
     const auto &sb = p->span_bl;
     const Geometry g = p->geometry();
     for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
         if (sf[k + 1] > sf[k])
-            st = degrid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
+            st = degrid_span(p, g, ls.span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
                              (const uint8_t *)b.ptr[1], b.ptr[2], h_taper ? (const float *)b.ptr[3] : p->d_taper,
                              b.ptr[4], s);
         cudaEvent_t e_done;
@@ -1278,7 +1458,8 @@ idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void
     if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
     if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
     if ((st = h2d(b.ptr[1], h_flags, sizes[1], cs, "copy of flags")) != IDG_OK) return st;
-    const auto &sf = p->span_first;
+    const Lists lg = lists_for(p, true), ld = lists_for(p, false);
+    const auto &sf = p->span_first;                // spans of baselines (the same k in every list)
     const auto &sb = p->span_bl;
     const Geometry g = p->geometry();
     // gridding, span by span behind the visibility copies
@@ -1290,7 +1471,8 @@ idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void
             e = cudaStreamWaitEvent(s, e_up, 0);
         if (st == IDG_OK && e != cudaSuccess) st = cuda_fail(e, "ordering the copy and compute streams");
         if (st == IDG_OK && sf[k + 1] > sf[k])
-            st = grid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b.ptr[0],
+            st = grid_span(p, g, lg.span, (*lg.span_first)[k], (*lg.span_first)[k + 1] - (*lg.span_first)[k],
+                           b.ptr[5], chunk, b.ptr[0],
                            (const uint8_t *)b.ptr[1], b.ptr[2], taper, b.ptr[4], b.ptr[6], s);
     }
     // the model grid lands while the gridding runs
@@ -1306,7 +1488,8 @@ idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void
     // degridding, span by span ahead of the visibility copies back
     for (size_t k = 0; k + 1 < sf.size() && st == IDG_OK; ++k) {
         if (sf[k + 1] > sf[k])
-            st = degrid_span(p, g, Order::Span, sf[k], sf[k + 1] - sf[k], b.ptr[5], chunk, b2.ptr[0],
+            st = degrid_span(p, g, ld.span, (*ld.span_first)[k], (*ld.span_first)[k + 1] - (*ld.span_first)[k],
+                             b.ptr[5], chunk, b2.ptr[0],
                              (const uint8_t *)b.ptr[1], b.ptr[2], taper, b2.ptr[1], s);
         cudaEvent_t e_done;
         if (st == IDG_OK && (e = ev.add(&e_done)) == cudaSuccess && (e = cudaEventRecord(e_done, s)) == cudaSuccess)

@@ -108,6 +108,25 @@ struct idg_plan {
     // [n + 1] number of separable subgrids before each position of the work, plan and
     // span orders (the work order and each span list the separable subgrids first)
     std::vector<int64_t> sep_prefix_order, sep_prefix_plan, sep_prefix_span;
+    // pieces: the composite calls may take a subgrid outside the bound as kt x kc blocks of
+    // its timesteps and channels, each within the bound with its own w_s, at the subgrid's
+    // position with its taper and A-terms (the sums are linear in the visibilities, so the
+    // pieces add up to the subgrid).  Their descriptors follow the plan's in d_sub.
+    struct Piece {
+        int32_t parent, t0, nt, c0, nc;
+        double ws;
+    };
+    std::vector<Piece> pieces;
+    std::vector<uint8_t> split_sub;        // [n_sub] 1: the composite calls take it in pieces
+    std::vector<int32_t> kp_all;           // [n_sub + pieces] K_p of every d_sub entry
+    // the composite calls' lists of d_sub entries when the plan has pieces: the separable
+    // subgrids and the pieces, then the direct subgrids left (each part by K_p descending);
+    // the same per span, span k at [fspan_first[k], fspan_first[k + 1])
+    int32_t *d_fused_order = nullptr;
+    int32_t *d_fused_span = nullptr;
+    std::vector<int32_t> kp_fused_order, kp_fused_span;
+    std::vector<int64_t> kp_prefix_fused, kp_prefix_fspan, sep_prefix_fused, sep_prefix_fspan;
+    std::vector<int64_t> fspan_first;
     float c_scale = 1.0f;
     float r_scale = 1.0f;
     bool any_dropped = false;

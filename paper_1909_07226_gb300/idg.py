@@ -65,7 +65,8 @@ class PlanStats(ctypes.Structure):
                 ("n_bl", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_chan", ctypes.c_int32),
                 ("n_stations", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("separable", ctypes.c_int32), ("sep_phase", ctypes.c_double),
-                ("n_sep_subgrids", ctypes.c_int64), ("n_vis_sep", ctypes.c_int64)]
+                ("n_sep_subgrids", ctypes.c_int64), ("n_vis_sep", ctypes.c_int64),
+                ("n_split_subgrids", ctypes.c_int64), ("n_pieces", ctypes.c_int64), ("n_vis_split", ctypes.c_int64)]
 
 
 _lib = None

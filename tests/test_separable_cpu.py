@@ -122,6 +122,64 @@ def test_plan_reports_the_remainder_phase(kw):
     assert p.stats.separable == (1 if n_sep == p.n_subgrids else 0)
 
 
+def _pieces_definition(wl):
+    # subgrids outside the bound: the smallest kt x kc grid of equal blocks of their
+    # timesteps and channels (floor cuts) whose blocks each meet the bound with the
+    # block's own middle w, if it has at most (rho_L - 1) K_p / F_L blocks
+    op = O.plan(wl)
+    L, S = wl.subgrid_size, wl.grid_size * wl.cell_size
+    r_max = np.abs(_split(L, S, _best_j0(L, S))[3]).max()
+    rho = {32: 3.8, 24: 2.7, 16: 1.0}[L]
+    F = 200.0 * (L / 32.0) ** 2
+    c = 299792458.0
+    n_split = n_pieces = kp_split = 0
+    for row in op.desc:
+        bl, t0, nt, c0, nc, kp = (int(row[i]) for i in (O.D_BL, O.D_T0, O.D_NT, O.D_C0, O.D_NC, O.D_KP))
+        w0 = (row[O.D_LAYER] + op.k_min) * wl.w_step if wl.w_step > 0 else 0.0
+        w = wl.uvw_m[bl, t0:t0 + nt, 2][:, None] * wl.freqs_hz[None, c0:c0 + nc] / c
+        th = 2 * np.pi * np.abs(w - w0).max() * r_max
+        if th > 1.38e-3:
+            th = 2 * np.pi * 0.5 * (w.max() - w.min()) * r_max
+        if th <= 1.38e-3:
+            continue
+        max_pieces = min(int((rho - 1.0) * kp / F), nt * nc)
+        found = 0
+        for prod in range(2, max_pieces + 1):
+            for kt in range(1, min(nt, prod) + 1):
+                kc = prod // kt
+                if prod % kt or kc > nc:
+                    continue
+                blocks = [w[i * nt // kt:(i + 1) * nt // kt, j * nc // kc:(j + 1) * nc // kc]
+                          for i in range(kt) for j in range(kc)]
+                if all(2 * np.pi * 0.5 * (b.max() - b.min()) * r_max <= 1.38e-3 for b in blocks):
+                    found = prod
+                    break
+            if found:
+                break
+        if found:
+            n_split += 1
+            n_pieces += found
+            kp_split += kp
+    return n_split, n_pieces, kp_split
+
+
+@pytest.mark.parametrize("kw", [dict(N=512, cell=8e-4, diameter_m=800.0), dict(N=512, cell=8e-4, diameter_m=300.0),
+                                dict(L=24, N=384, cell=8e-4, diameter_m=800.0, n_t=96, max_t=96, n_chan=12),
+                                dict(L=16, N=256, cell=1.2e-3, diameter_m=800.0, n_t=96, max_t=96, n_chan=12),
+                                dict(w_step=5.0, N=512, cell=8e-4, diameter_m=800.0)])
+def test_plan_splits_subgrids_outside_the_bound_into_pieces(kw):
+    from paper_1909_07226_gb300 import idg
+    args = dict(seed=1032, n_st=5, n_t=48, n_chan=5, L=32, N=128, max_t=48, n_slots=1, flag_p=0.1,
+                diameter_m=3000.0, df=0.25e6)
+    args.update(kw)
+    wl = syn.make_small(**args)
+    p = idg.plan_from_workload(wl)
+    s = p.stats
+    assert (s.n_split_subgrids, s.n_pieces, s.n_vis_split) == _pieces_definition(wl)
+    assert s.n_sep_subgrids + s.n_split_subgrids <= p.n_subgrids
+    assert s.n_vis_sep + s.n_vis_split <= s.n_vis_planned
+
+
 def test_mixed_plan_splits_its_subgrids():
     # a wide field where only the subgrids of small w spread meet the bound: some, not
     # all, go to the separable kernels
