@@ -900,7 +900,7 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
         c["plain_ms"] = e0.elapsed_time(e1)
         c["plain_mvis_per_s"] = c["vis"] / c["plain_ms"] / 1e3
     batch.destroy()
-    return {"n_vis": int(n_vis), "subgrids": info["n_items"], "persistent_launches_per_direction": info["n_launches"],
+    return {"n_vis": int(n_vis), "work_items": info["n_items"], "work_classes": info["n_launches"],
             "plain_mvis_per_s": n_vis / ms_plain / 1e3, "batched_mvis_per_s": n_vis / ms_batch / 1e3,
             "plain_ms": ms_plain, "batched_ms": ms_batch, "batched_over_plain": ms_plain / ms_batch,
             "classes": classes, "plan_seconds": plan_s, "autotune_trial_ms": trials}
@@ -909,8 +909,10 @@ def batched_compare(idg, syn, torch, dev, n_jobs, steps, warmup, seed=None):
 def run_batched(args, world, rank, local):
     """The uneven batch (config B): the same jobs gridded and degridded
     (a) one after another with idg_grid / idg_degrid (plain per-job form) and
-    (b) as one batch: one persistent launch per subgrid size, subgrids kept in
-    shared memory, the launch sequence replayed from a CUDA graph."""
+    (b) as one batch: per subgrid size a separable and a direct work class, each
+    one persistent launch or one tensor-core launch per job (programmatic
+    dependent launches), subgrids kept in shared memory, the launch sequence
+    replayed from a CUDA graph."""
     import torch
     from paper_1909_07226_gb300 import build as lib_build
     from paper_1909_07226_gb300 import idg
@@ -933,7 +935,7 @@ def run_batched(args, world, rank, local):
         "config": {"workload": f"Batched uneven: {args.jobs} snapshot jobs, U{{12..64}} stations, U{{64..1024}} t, "
                                f"U{{4..32}} ch of 0.2 MHz in 100-200 MHz, 0-20% flags, L in {{16,24,32}}, "
                                f"N in {{1024,2048,4096}}", "jobs": args.jobs, "n_vis": r["n_vis"],
-                   "subgrids": r["subgrids"], "persistent_launches_per_direction": r["persistent_launches_per_direction"],
+                   "work_items": r["work_items"], "work_classes": r["work_classes"],
                    "graph": True, "l2": "inputs larger than L2, no flush"},
         "plain_per_job": {"value": r["plain_mvis_per_s"], "unit": "MVis/s", "ms_per_step": r["plain_ms"]},
         "batched_over_plain": r["batched_over_plain"], "classes": r["classes"],

@@ -425,22 +425,25 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
 
 /*
  * Batched form: many independent jobs processed together.  A batch binds each
- * job's plan to its device buffers at creation.  All subgrids of all jobs with
- * the same subgrid size L form one work list ordered by cost (K_p, largest
- * first) and run in ONE persistent launch per L (a few CTAs per SM pulling
- * work items from a device counter).  Each work item is the whole per-subgrid
- * pipeline in one CTA, the subgrid staying in shared memory:
+ * job's plan to its device buffers at creation.  The work items (job, subgrid)
+ * of all jobs with the same subgrid size L form work classes: the subgrids
+ * within the separable remainder bound with the pieces of those the plans
+ * split (L = 32, 24, 16), and the other subgrids.  Each work item is the whole
+ * per-subgrid pipeline in one CTA, the subgrid staying in shared memory:
  *   idg_batch_grid    direct sum, taper and A_p^H . A_q, FFT, add into grid
  *                     (accumulated, as idg_grid)
  *   idg_batch_degrid  split from grid, IFFT, taper and A_p . A_q^H, degrid sum
  *                     into vis_out (overwritten; flagged and dropped -> 0)
- * For L = 32 the default batch variant ("tcgen05_fused", IDG_KERNEL_BATCH_*),
- * and for L = 24 and 16 the subgrids within the separable remainder bound (the
- * work list of each L is split into those and the rest), instead run the fused
- * tensor-core gridder (degridder) with one CTA per work
- * item, the sums on the tensor cores and the transform and adder (splitter) in
- * the same CTA; a class whose visibilities lie mostly in subgrids of fewer
- * than 512 takes the persistent kernel.  No device scratch is used.  With
+ * A class runs either the fused tensor-core kernels (the separable ones, and at
+ * L = 32 the direct ones with the default batch variant "tcgen05_fused",
+ * IDG_KERNEL_BATCH_*): one launch per job with one CTA per item, most
+ * visibilities first, each launch allowed to begin while the previous one
+ * ends (programmatic dependent launch: the jobs' outputs are disjoint, or
+ * summed by atomic adds); or ONE persistent launch over the class's items
+ * ordered by cost (K_p, largest first), a few CTAs per SM pulling items from a
+ * device counter: the packed-FP32 kernels, for the direct subgrids at L = 24,
+ * 16 and 8 and for any class whose visibilities lie mostly in subgrids of
+ * fewer than 512.  No device scratch is used.  With
  * IDG_BATCH_GRAPH the first call of each direction captures its launch
  * sequence into a CUDA graph, and later calls replay it (the buffers are fixed
  * by the batch, so the graph stays valid).
@@ -453,8 +456,8 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  *   flags    or NULL;  aterms  or NULL (identity);  taper  or NULL (the plan's
  *            default taper, as in idg_grid)
  *   grid     gridding output (accumulated) / degridding input
- * idg_batch_info returns the planned visibilities, work items and launches per
- * direction (1 per class).
+ * idg_batch_info returns the planned visibilities, the work items and the
+ * number of work classes (n_launches).
  */
 typedef struct idg_batch idg_batch;
 typedef struct {

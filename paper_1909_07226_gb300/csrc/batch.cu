@@ -343,6 +343,11 @@ struct idg_batch {
         int64_t n_items;
         double vispix;                 // sum of K_p L^2 of its items
         int2 *d_items = nullptr;
+        // the tensor-core kernels: one launch per job over its entries d_idx[run_first[r] ..
+        // run_first[r + 1]) (job run_job[r]), most visibilities first within the job
+        int32_t *d_idx = nullptr;
+        std::vector<int64_t> run_first;
+        std::vector<int> run_job;
         KernelShape grid, degrid;
         int grid_blocks = 0, degrid_blocks = 0;
     };
@@ -351,6 +356,7 @@ struct idg_batch {
     int flags = 0;
     int64_t n_vis = 0;                 // visibilities of all jobs (planned)
     JobDev *d_jobs = nullptr;
+    std::vector<JobDev> host_jobs;     // the same on the host: the tensor-core launches' arguments
     int *d_counters = nullptr;         // one per class
     std::vector<Class> classes;
     std::vector<std::pair<void *, size_t>> zero_on_degrid;   // vis_out of jobs with dropped samples
@@ -371,13 +377,25 @@ static idg_status batch_enqueue(idg_batch *b, bool degrid, cudaStream_t s) {
         if (cl.n_items == 0) continue;
         const KernelShape &ks = degrid ? cl.degrid : cl.grid;
         if (ks.tc) {
+            // one launch per job, its geometry as kernel arguments; every launch after the
+            // first may begin while the one before finishes (the jobs' outputs are disjoint
+            // or summed by atomic adds)
             ProfileScope ps(degrid ? IDG_KERNEL_BATCH_DEGRID : IDG_KERNEL_BATCH_GRID, s, cl.vispix);
-            const idg_status st =
-                cl.sep ? (degrid ? launch_degridder_sep_batch(cl.L, b->d_jobs, cl.d_items, cl.n_items, s)
-                                 : launch_gridder_sep_batch(cl.L, b->d_jobs, cl.d_items, cl.n_items, s))
-                       : (degrid ? launch_degridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s)
-                                 : launch_gridder_tcw_batch(b->d_jobs, cl.d_items, cl.n_items, s));
-            if (st != IDG_OK) return st;
+            for (size_t r = 0; r + 1 < cl.run_first.size(); ++r) {
+                const JobDev &J = b->host_jobs[cl.run_job[r]];
+                const SubgridSet set{cl.d_idx + cl.run_first[r], 0, cl.run_first[r + 1] - cl.run_first[r], nullptr};
+                const bool pdl = r > 0;
+                const idg_status st =
+                    cl.sep ? (degrid ? launch_degridder_sep_job(J.g, set, J.grid, J.flags, J.aterms, J.taper,
+                                                                J.vis_out, s, pdl)
+                                     : launch_gridder_sep_job(J.g, set, J.vis, J.flags, J.aterms, J.taper, J.grid, s,
+                                                              pdl))
+                           : (degrid ? launch_degridder_tcw_job(J.g, set, J.grid, J.flags, J.aterms, J.taper,
+                                                                J.vis_out, s, pdl)
+                                     : launch_gridder_tcw_job(J.g, set, J.vis, J.flags, J.aterms, J.taper, J.grid, s,
+                                                              pdl));
+                if (st != IDG_OK) return st;
+            }
             continue;
         }
         const int blocks = degrid ? cl.degrid_blocks : cl.grid_blocks;
@@ -453,7 +471,10 @@ void idg_batch_destroy(idg_batch *b) {
     if (b->graph_grid) cudaGraphExecDestroy(b->graph_grid);
     if (b->graph_degrid) cudaGraphExecDestroy(b->graph_degrid);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-    for (auto &c : b->classes) cudaFree(c.d_items);
+    for (auto &c : b->classes) {
+        cudaFree(c.d_items);
+        cudaFree(c.d_idx);
+    }
     cudaFree(b->d_jobs);
     cudaFree(b->d_counters);
     if (prev >= 0) cudaSetDevice(prev);
@@ -560,15 +581,27 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
             }
             if (ks.tc) need_tc = true;
         }
-        // one CTA per item in launch order (both directions on the tensor cores): keep a job's
-        // items together, most visibilities first within it, so that the CTAs in flight add
-        // into (split from) the same grid and share its lines in L2
-        if (cl.grid.tc && cl.degrid.tc)
-            std::stable_sort(items.begin(), items.end(), [](const int2 &x, const int2 &y) { return x.x < y.x; });
         if (st == IDG_OK && cl.n_items > 0) {
             e = cudaMalloc(&cl.d_items, sizeof(int2) * items.size());
             if (e == cudaSuccess) e = cudaMemcpy(cl.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = cuda_fail(e, "batch work list");
+        }
+        // the tensor-core launches: the items grouped by job, most visibilities first in each
+        if (st == IDG_OK && cl.n_items > 0 && (cl.grid.tc || cl.degrid.tc)) {
+            std::vector<int2> by_job(items);
+            std::stable_sort(by_job.begin(), by_job.end(), [](const int2 &x, const int2 &y) { return x.x < y.x; });
+            std::vector<int32_t> idx(by_job.size());
+            for (size_t i = 0; i < by_job.size(); ++i) {
+                idx[i] = by_job[i].y;
+                if (i == 0 || by_job[i].x != by_job[i - 1].x) {
+                    cl.run_first.push_back((int64_t)i);
+                    cl.run_job.push_back(by_job[i].x);
+                }
+            }
+            cl.run_first.push_back((int64_t)idx.size());
+            e = cudaMalloc(&cl.d_idx, sizeof(int32_t) * idx.size());
+            if (e == cudaSuccess) e = cudaMemcpy(cl.d_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "batch tensor-core work list");
         }
         // persistent grid: resident CTAs per SM x SMs, never more than the items
         for (int k = 0; k < 2 && st == IDG_OK; ++k) {
@@ -590,6 +623,7 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         if (e != cudaSuccess) st = cuda_fail(e, "batch tensor-core kernel attributes");
     }
     if (st == IDG_OK) {
+        b->host_jobs = hj;
         e = cudaMalloc(&b->d_jobs, sizeof(JobDev) * hj.size());
         if (e == cudaSuccess) e = cudaMemcpy(b->d_jobs, hj.data(), sizeof(JobDev) * hj.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * std::max<size_t>(1, b->classes.size()));
@@ -685,7 +719,7 @@ idg_status idg_batch_info(const idg_batch *b, int64_t *n_vis, int64_t *n_items, 
     for (auto &c : b->classes) {
         items += c.n_items;
         if (c.n_items == 0) continue;
-        launches += 1;      // one launch per class and direction
+        launches += 1;      // work classes: one persistent launch, or one tensor-core launch per job
     }
     if (n_vis) *n_vis = b->n_vis;
     if (n_items) *n_items = items;

@@ -555,17 +555,9 @@ __global__ void __launch_bounds__(NT, 1)
 degridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
                            const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                            const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     degridder_sep_body<L, true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
-}
-
-// fused, one CTA per work item (job, subgrid) of a batch: split from the job's grid
-template <int L>
-__global__ void __launch_bounds__(NT, 1)
-degridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
-    const int2 it = items[blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    degridder_sep_body<L, true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
 }
 
 template <int L>
@@ -586,31 +578,17 @@ idg_status launch_sepd_set(bool fused, const Geometry &g, const SubgridSet &set,
 cudaError_t prepare_sep_batch_kernels() {
     cudaError_t e = prepare_gridder_sep_batch();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(degridder_sep_fused_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepD<32>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(degridder_sep_fused_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepD<24>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(degridder_sep_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(degridder_sep_fused_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepD<16>::SMEM);
     return e;
 }
 
-// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
-    if (count <= 0) return IDG_OK;
-    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32, 24 or 16");
-    if (L == 32)
-        degridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepD<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else if (L == 24)
-        degridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepD<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else
-        degridder_sep_batch_kernel<16><<<(unsigned)count, NT, SepD<16>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable batch degridder launch");
-    return IDG_OK;
-}
 
 idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {
@@ -622,6 +600,25 @@ idg_status launch_degridder_sep(const Geometry &g, const SubgridSet &set, const 
     case 24: return launch_sepd_set<24>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
     default: return launch_sepd_set<16>(false, g, set, sub, flags, aterms, taper, vis_out, (cudaStream_t)stream);
     }
+}
+
+// a batch's launch of the fused kernel over one job's items (the shared-memory attribute
+// is set by prepare_tcw_batch_kernels, outside graph capture); pdl: see launch_pdl
+idg_status launch_degridder_sep_job(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *vis_out, void *stream, bool pdl) {
+    if (set.count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned n = (unsigned)set.count;
+    const float4 *gr = (const float4 *)grid, *at = (const float4 *)aterms;
+    float4 *o = (float4 *)vis_out;
+    cudaError_t e;
+    switch (g.L) {
+    case 32: e = launch_pdl(degridder_sep_fused_kernel<32>, n, NT, SepD<32>::SMEM, s, pdl, g, set.idx, set.first, gr, flags, at, taper, o); break;
+    case 24: e = launch_pdl(degridder_sep_fused_kernel<24>, n, NT, SepD<24>::SMEM, s, pdl, g, set.idx, set.first, gr, flags, at, taper, o); break;
+    case 16: e = launch_pdl(degridder_sep_fused_kernel<16>, n, NT, SepD<16>::SMEM, s, pdl, g, set.idx, set.first, gr, flags, at, taper, o); break;
+    default: return fail(IDG_ERR_UNSUPPORTED, "the separable degridder needs L = 32, 24 or 16");
+    }
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, "separable degridder job launch");
 }
 
 idg_status launch_degridder_sep_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,

@@ -341,16 +341,9 @@ __global__ void __launch_bounds__(DNT, 2)
 degridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ grid,
                            const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                            const float *__restrict__ taper, float4 *__restrict__ vis_out) {
+    allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     degridder_tcw_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
-}
-
-// fused, one CTA per work item (job, subgrid) of a batch: split from the job's grid
-__global__ void __launch_bounds__(DNT, 2)
-degridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
-    const int2 it = items[blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    degridder_tcw_body<true>(J.g, J.g.sub[it.y], J.grid, J.flags, J.aterms, J.taper, J.vis_out);
 }
 
 }  // namespace
@@ -374,19 +367,22 @@ cudaError_t prepare_tcw_batch_kernels() {
     cudaError_t e = prepare_gridder_tcw_batch();
     if (e == cudaSuccess) e = prepare_sep_batch_kernels();
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(degridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM);
+        e = cudaFuncSetAttribute(degridder_tcw_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, D_SMEM);
     return e;
 }
 
-// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_degridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
-    if (count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    degridder_tcw_batch_kernel<<<(unsigned)count, DNT, D_SMEM, s>>>(jobs, items);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch degridder launch");
-    return IDG_OK;
+// a batch's launch of the fused kernel over one job's items (the shared-memory attribute
+// is set by prepare_tcw_batch_kernels, outside graph capture); pdl: see launch_pdl
+idg_status launch_degridder_tcw_job(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *vis_out, void *stream, bool pdl) {
+    if (g.L != DL) return fail(IDG_ERR_UNSUPPORTED, "the tensor-core degridder is built for L = 32");
+    if (set.count <= 0) return IDG_OK;
+    const cudaError_t e = launch_pdl(degridder_tcw_fused_kernel, (unsigned)set.count, DNT, D_SMEM, (cudaStream_t)stream,
+                                     pdl, g, set.idx, set.first, (const float4 *)grid, flags, (const float4 *)aterms,
+                                     taper, (float4 *)vis_out);
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, "tensor-core degridder job launch");
 }
+
 
 idg_status launch_degridder_tcw(const Geometry &g, const SubgridSet &set, const void *sub, const uint8_t *flags,
                                 const void *aterms, const float *taper, void *vis_out, void *stream) {

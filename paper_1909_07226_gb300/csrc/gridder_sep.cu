@@ -555,17 +555,9 @@ __global__ void __launch_bounds__(NT, 1)
 gridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                          const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                          const float *__restrict__ taper, float4 *__restrict__ grid) {
+    allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     gridder_sep_body<L, true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
-}
-
-// fused, one CTA per work item (job, subgrid) of a batch: added into the job's grid
-template <int L>
-__global__ void __launch_bounds__(NT, 1)
-gridder_sep_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
-    const int2 it = items[blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    gridder_sep_body<L, true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
 }
 
 template <int L>
@@ -585,30 +577,34 @@ idg_status launch_sep_set(bool fused, const Geometry &g, const SubgridSet &set, 
 bool separable_size(int L) { return L == 32 || L == 24 || L == 16; }
 
 cudaError_t prepare_gridder_sep_batch() {
-    cudaError_t e = cudaFuncSetAttribute(gridder_sep_batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gridder_sep_fused_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SepG<32>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gridder_sep_batch_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(gridder_sep_fused_kernel<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepG<24>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gridder_sep_batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(gridder_sep_fused_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  SepG<16>::SMEM);
     return e;
 }
 
-// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
-    if (count <= 0) return IDG_OK;
-    if (!separable_size(L)) return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32, 24 or 16");
-    if (L == 32)
-        gridder_sep_batch_kernel<32><<<(unsigned)count, NT, SepG<32>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else if (L == 24)
-        gridder_sep_batch_kernel<24><<<(unsigned)count, NT, SepG<24>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    else
-        gridder_sep_batch_kernel<16><<<(unsigned)count, NT, SepG<16>::SMEM, (cudaStream_t)stream>>>(jobs, items);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "separable batch gridder launch");
-    return IDG_OK;
+// a batch's launch of the fused kernel over one job's items (the shared-memory attribute
+// is set by prepare_tcw_batch_kernels, outside graph capture); pdl: see launch_pdl
+idg_status launch_gridder_sep_job(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                  const void *aterms, const float *taper, void *grid, void *stream, bool pdl) {
+    if (set.count <= 0) return IDG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned n = (unsigned)set.count;
+    const float4 *v = (const float4 *)vis, *at = (const float4 *)aterms;
+    float4 *o = (float4 *)grid;
+    cudaError_t e;
+    switch (g.L) {
+    case 32: e = launch_pdl(gridder_sep_fused_kernel<32>, n, NT, SepG<32>::SMEM, s, pdl, g, set.idx, set.first, v, flags, at, taper, o); break;
+    case 24: e = launch_pdl(gridder_sep_fused_kernel<24>, n, NT, SepG<24>::SMEM, s, pdl, g, set.idx, set.first, v, flags, at, taper, o); break;
+    case 16: e = launch_pdl(gridder_sep_fused_kernel<16>, n, NT, SepG<16>::SMEM, s, pdl, g, set.idx, set.first, v, flags, at, taper, o); break;
+    default: return fail(IDG_ERR_UNSUPPORTED, "the separable gridder needs L = 32, 24 or 16");
+    }
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, "separable gridder job launch");
 }
 
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,

@@ -357,16 +357,9 @@ __global__ void __launch_bounds__(WS_NT, 2)
 gridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t first, const float4 *__restrict__ vis,
                          const uint8_t *__restrict__ flags, const float4 *__restrict__ aterms,
                          const float *__restrict__ taper, float4 *__restrict__ grid) {
+    allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     gridder_tcw_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
-}
-
-// fused, one CTA per work item (job, subgrid) of a batch: added into the job's grid
-__global__ void __launch_bounds__(WS_NT, 2)
-gridder_tcw_batch_kernel(const JobDev *__restrict__ jobs, const int2 *__restrict__ items) {
-    const int2 it = items[blockIdx.x];
-    const JobDev &J = jobs[it.x];
-    gridder_tcw_body<true>(J.g, J.g.sub[it.y], J.vis, J.flags, J.aterms, J.taper, J.grid);
 }
 
 }  // namespace
@@ -387,18 +380,21 @@ idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, co
 }
 
 cudaError_t prepare_gridder_tcw_batch() {
-    return cudaFuncSetAttribute(gridder_tcw_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
+    return cudaFuncSetAttribute(gridder_tcw_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WS_SMEM);
 }
 
-// (the shared-memory attribute is set by prepare_tcw_batch_kernels, outside graph capture)
-idg_status launch_gridder_tcw_batch(const JobDev *jobs, const int2 *items, int64_t count, void *stream) {
-    if (count <= 0) return IDG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    gridder_tcw_batch_kernel<<<(unsigned)count, WS_NT, WS_SMEM, s>>>(jobs, items);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "tensor-core batch gridder launch");
-    return IDG_OK;
+// a batch's launch of the fused kernel over one job's items (the shared-memory attribute
+// is set by prepare_tcw_batch_kernels, outside graph capture); pdl: see launch_pdl
+idg_status launch_gridder_tcw_job(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                  const void *aterms, const float *taper, void *grid, void *stream, bool pdl) {
+    if (g.L != TC_L) return fail(IDG_ERR_UNSUPPORTED, "the tensor-core gridder is built for L = 32");
+    if (set.count <= 0) return IDG_OK;
+    const cudaError_t e = launch_pdl(gridder_tcw_fused_kernel, (unsigned)set.count, WS_NT, WS_SMEM, (cudaStream_t)stream,
+                                     pdl, g, set.idx, set.first, (const float4 *)vis, flags, (const float4 *)aterms,
+                                     taper, (float4 *)grid);
+    return e == cudaSuccess ? IDG_OK : cuda_fail(e, "tensor-core gridder job launch");
 }
+
 
 idg_status launch_gridder_tcw(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
                               const void *aterms, const float *taper, void *out, void *stream) {

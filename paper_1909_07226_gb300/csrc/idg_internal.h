@@ -258,16 +258,16 @@ idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, co
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
                                       const void *aterms, const float *taper, void *vis_out, void *stream);
-// the fused kernels over the (job, subgrid) work items items[0 .. count) of a
-// batch (jobs: device job table, see batch_jobs.cuh): each item added into
-// (split from) its job's grid
-struct JobDev;
-idg_status launch_gridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-idg_status launch_degridder_tcw_batch(const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-// the separable kernels over work items (subgrid size L) whose subgrids meet the bound
-idg_status launch_gridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count, void *stream);
-idg_status launch_degridder_sep_batch(int L, const JobDev *jobs, const struct int2 *items, int64_t count,
-                                      void *stream);
+// the fused kernels of one job of a batch (the plan's geometry, a set of its d_sub entries),
+// as a programmatic dependent launch when pdl (see tc_common.cuh)
+idg_status launch_gridder_sep_job(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                  const void *aterms, const float *taper, void *grid, void *stream, bool pdl);
+idg_status launch_degridder_sep_job(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *vis_out, void *stream, bool pdl);
+idg_status launch_gridder_tcw_job(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,
+                                  const void *aterms, const float *taper, void *grid, void *stream, bool pdl);
+idg_status launch_degridder_tcw_job(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
+                                    const void *aterms, const float *taper, void *vis_out, void *stream, bool pdl);
 
 // calibration (calibration.cu): residuals and cost over the visibilities of a subgrid
 // set (res holds the model visibilities on entry), and the A-term gradient from the

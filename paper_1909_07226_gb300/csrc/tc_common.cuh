@@ -173,5 +173,30 @@ __device__ __forceinline__ void split_e_m(float x, float y, uint16_t m1, uint32_
         "}" : "=r"(hi), "=r"(lo) : "f"(x), "f"(y), "h"(m1));
 }
 
+// Programmatic dependent launch.  A kernel that calls allow_dependents() lets the next
+// kernel of its stream, when that one was launched with launch_pdl(..., pdl = true), begin
+// once every CTA of this kernel has made the call (here at CTA entry: the next kernel's
+// CTAs fill the SMs this kernel's last wave leaves).  Only for a next kernel that reads
+// nothing this kernel writes (the batches' per-job launches: other jobs' grids and
+// visibilities, or the same grid by atomic adds).  Without the attribute the call has
+// no effect.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Exp, typename... Act>
+cudaError_t launch_pdl(void (*fn)(Exp...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
+                       Act &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, fn, static_cast<Act &&>(args)...);
+}
+
 }  // namespace tc
 }  // namespace idg
