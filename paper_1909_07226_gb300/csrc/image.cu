@@ -57,10 +57,20 @@ struct PixOp {
     float w0_2pi;        // 2 pi w0 of the layer (image side)
     float sign;          // +1 gridding side (exp(+i ...)), -1 degridding side
     float S;             // image size in direction cosines
-    const float2 *cbar;  // [N] effective window at zero shift (complex), or null; conjugated if sign < 0
+    // [N] reciprocal of the effective window at zero shift, 1 / cbar (gridding side) or
+    // 1 / conj cbar (degridding side), complex; or null
+    const float2 *icbar;
 };
 
+// the factor with the window's reciprocal values cx = icbar[x], cy = icbar[y] given
+__device__ __forceinline__ float2 pix_factor_w(const PixOp &op, int x, int y, int N, float2 cx, float2 cy);
+
 __device__ __forceinline__ float2 pix_factor(const PixOp &op, int x, int y, int N) {
+    if (op.mode == 1 && op.icbar) return pix_factor_w(op, x, y, N, op.icbar[x], op.icbar[y]);
+    return pix_factor_w(op, x, y, N, make_float2(1.0f, 0.0f), make_float2(1.0f, 0.0f));
+}
+
+__device__ __forceinline__ float2 pix_factor_w(const PixOp &op, int x, int y, int N, float2 cx, float2 cy) {
     if (op.mode == 2) return make_float2(1.0f, 0.0f);
     const float sg = ((x + y) & 1) ? -1.0f : 1.0f;
     if (op.mode == 0) return make_float2(sg, 0.0f);
@@ -74,13 +84,10 @@ __device__ __forceinline__ float2 pix_factor(const PixOp &op, int x, int y, int 
         re = sg * c;
         im = sg * s;
     }
-    if (op.cbar) {
+    if (op.icbar) {
         // divide by cbar(x) cbar(y) (gridding side) or by its conjugate (degridding side)
-        const float2 cx = op.cbar[x], cy = op.cbar[y];
-        float pr = cx.x * cy.x - cx.y * cy.y, pi = cx.x * cy.y + cx.y * cy.x;
-        if (op.sign < 0.0f) pi = -pi;
-        const float inv = 1.0f / (pr * pr + pi * pi);
-        const float nr = (re * pr + im * pi) * inv, ni = (im * pr - re * pi) * inv;
+        const float pr = cx.x * cy.x - cx.y * cy.y, pi = cx.x * cy.y + cx.y * cy.x;
+        const float nr = re * pr - im * pi, ni = re * pi + im * pr;
         re = nr;
         im = ni;
     }
@@ -289,6 +296,94 @@ __device__ __forceinline__ void dif_steps_ct(float2 *buf, const float2 *tws, int
     }
 }
 
+// The compile-time N-point transform (radix 16 only, N = 16^3) with the step twiddles
+// formed in registers: T[m] = exp(SIGN 2 pi i m / N) for m < N / 16 (shared memory), a
+// butterfly of the step over sub-transforms of length LEN takes w = T[i N / LEN] =
+// exp(SIGN 2 pi i i / LEN) and multiplies output k by w^k, the powers by a product tree
+// of depth at most 4 (w^2, w^4, w^8 by squaring, the rest as products of two of them):
+// 14 complex products instead of 15 table reads, which kept the row pass waiting on L2
+// (the full step table, 30 KB at N = 4096, does not stay in the L1 beside three CTAs'
+// shared memory).
+template <int SIGN, int NL, bool PAD, int N, int LEN>
+__device__ __forceinline__ void dif_step_pow(float2 *buf, const float2 *T) {
+    constexpr int R = 16, H = LEN / R, GPL = N / R;
+    constexpr int PS = PAD ? H + H / 16 + H / 256 : H;
+    static_assert(slots_linear<N, PAD>(), "radix 16 throughout");
+    for (int t = threadIdx.x; t < NL * GPL; t += blockDim.x) {
+        const int line = t % NL, g = t / NL;
+        const int b = g / H, i = g % H;
+        const int s0 = slot<PAD>(b * LEN + i) * NL + line;
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = buf[s0 + j * PS * NL];
+        dft_reg<R, SIGN>(v);
+        buf[s0] = v[0];
+        if constexpr (H > 1) {
+            float2 w[R];
+            w[1] = T[i * (N / LEN)];
+            w[2] = cmulf(w[1], w[1]);
+            w[3] = cmulf(w[2], w[1]);
+            w[4] = cmulf(w[2], w[2]);
+            w[5] = cmulf(w[4], w[1]);
+            w[6] = cmulf(w[4], w[2]);
+            w[7] = cmulf(w[4], w[3]);
+            w[8] = cmulf(w[4], w[4]);
+#pragma unroll
+            for (int k = 9; k < R; ++k) w[k] = cmulf(w[8], w[k - 8]);
+#pragma unroll
+            for (int k = 1; k < R; ++k) buf[s0 + k * PS * NL] = cmulf(v[k], w[k]);
+        } else {
+#pragma unroll
+            for (int k = 1; k < R; ++k) buf[s0 + k * PS * NL] = v[k];
+        }
+    }
+}
+
+// The first step (LEN = N) of the same transform with its points read straight from the
+// row in global memory: line `line` of position x is polarisation 2 hp + line of pixel x
+// of `row` (the image's 32-byte pixels), times the input factor of pixel (x, y).  This
+// skips one shared-memory store and load of the whole row.
+template <int SIGN, bool PAD, int N>
+__device__ __forceinline__ void dif_step_pow_first(float2 *buf, const float2 *T, const float2 *row, int hp, int y,
+                                                   const PixOp &pre) {
+    constexpr int R = 16, NL = 2, H = N / R, GPL = N / R;
+    constexpr int PS = PAD ? H + H / 16 + H / 256 : H;
+    for (int t = threadIdx.x; t < NL * GPL; t += blockDim.x) {
+        const int line = t % NL, i = t / NL;
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int x = i + j * H;
+            v[j] = cmulf(row[4 * x + 2 * hp + line], pix_factor(pre, x, y, N));
+        }
+        dft_reg<R, SIGN>(v);
+        const int s0 = slot<PAD>(i) * NL + line;
+        buf[s0] = v[0];
+        float2 w[R];
+        w[1] = T[i];
+        w[2] = cmulf(w[1], w[1]);
+        w[3] = cmulf(w[2], w[1]);
+        w[4] = cmulf(w[2], w[2]);
+        w[5] = cmulf(w[4], w[1]);
+        w[6] = cmulf(w[4], w[2]);
+        w[7] = cmulf(w[4], w[3]);
+        w[8] = cmulf(w[4], w[4]);
+#pragma unroll
+        for (int k = 9; k < R; ++k) w[k] = cmulf(w[8], w[k - 8]);
+#pragma unroll
+        for (int k = 1; k < R; ++k) buf[s0 + k * PS * NL] = cmulf(v[k], w[k]);
+    }
+}
+
+template <int SIGN, int NL, bool PAD, int N, int LEN>
+__device__ __forceinline__ void dif_steps_pow(float2 *buf, const float2 *T) {
+    if constexpr (LEN > 1) {
+        dif_step_pow<SIGN, NL, PAD, N, LEN>(buf, T);
+        __syncthreads();
+        dif_steps_pow<SIGN, NL, PAD, N, LEN / 16>(buf, T);
+    }
+}
+
 // the n-point transform of the NL lines: compile-time n when NC > 0, else n at run time
 template <int NL, bool PAD, int NC>
 __device__ __forceinline__ void fft_lines(float2 *buf, int n, const float2 *tw, int sign) {
@@ -323,14 +418,42 @@ __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *_
     float2 *buf = (float2 *)img_smem4;
     const int y = blockIdx.x >> 1, hp = blockIdx.x & 1;
     const float4 *row = in + (size_t)y * N * 2 + hp;
-    for (int x = threadIdx.x; x < N; x += kRowThreads) {
-        const float4 a = row[2 * x];
-        const float2 f = pix_factor(pre, x, y, N);
-        const float2 p0 = cmulf(make_float2(a.x, a.y), f), p1 = cmulf(make_float2(a.z, a.w), f);
-        buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
+    constexpr bool POW = NC == 4096;                 // 16^3: the power-twiddle form
+    float2 *T = buf + 2 * padded_len(NC ? NC : 32);  // [N / 16] exp(SIGN 2 pi i m / N)
+    if constexpr (POW) {
+        for (int m = threadIdx.x; m < NC / 16; m += kRowThreads) {
+            float sn, cs;
+            sincospif((float)SIGN * 2.0f * (float)m / (float)NC, &sn, &cs);
+            T[m] = make_float2(cs, sn);
+        }
+        // the checkerboard only (the gridding side's uv grid): the first step reads the row
+        // itself.  Only instantiated for SIGN > 0: in the image-to-grid kernel a second load
+        // path cost its window-factor loads 8 % (measured).
+        if (SIGN > 0 && pre.mode == 0) {
+            __syncthreads();
+            dif_step_pow_first<SIGN, true, 4096>(buf, T, (const float2 *)(in + (size_t)y * N * 2), hp, y, pre);
+            __syncthreads();
+            dif_steps_pow<SIGN, 2, true, 4096, 256>(buf, T);
+        } else {                 // (with the window's reciprocal: once per pixel, on the load)
+            for (int x = threadIdx.x; x < N; x += kRowThreads) {
+                const float4 a = row[2 * x];
+                const float2 f = pix_factor(pre, x, y, N);
+                const float2 p0 = cmulf(make_float2(a.x, a.y), f), p1 = cmulf(make_float2(a.z, a.w), f);
+                buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
+            }
+            __syncthreads();
+            dif_steps_pow<SIGN, 2, true, 4096, 4096>(buf, T);
+        }
+    } else {
+        for (int x = threadIdx.x; x < N; x += kRowThreads) {
+            const float4 a = row[2 * x];
+            const float2 f = pix_factor(pre, x, y, N);
+            const float2 p0 = cmulf(make_float2(a.x, a.y), f), p1 = cmulf(make_float2(a.z, a.w), f);
+            buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
+        }
+        __syncthreads();
+        fft_lines<2, true, NC>(buf, N, tw, SIGN);
     }
-    __syncthreads();
-    fft_lines<2, true, NC>(buf, N, tw, SIGN);
     float4 *orow = out + (size_t)y * N * 2 + hp;
     for (int x = threadIdx.x; x < N; x += kRowThreads) orow[2 * x] = buf4[slot<true>(dif_pos(x, NC ? NC : N))];
 }
@@ -398,6 +521,13 @@ __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 
     float2 *tw = buf + NL * N2;
     const int nb = N / kColBlock;
     const int k1 = blockIdx.x / nb, c0 = (blockIdx.x % nb) * kColBlock;
+    // the window's reciprocal at this CTA's columns and output rows (k1 + N1 k2)
+    float2 *icx = tw + N2, *icy = icx + kColBlock;
+    const bool win = post.mode == 1 && post.icbar;
+    if (win) {
+        for (int t = threadIdx.x; t < kColBlock + N2; t += kColThreads)
+            icx[t] = t < kColBlock ? post.icbar[c0 + t] : post.icbar[k1 + N1 * (t - kColBlock)];
+    }
     step_twiddles(tw, N2, SIGN, threadIdx.x, blockDim.x);
     for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
         const int y2 = t / kColBlock, c = t % kColBlock;
@@ -412,7 +542,7 @@ __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 
         const int k2 = t / kColBlock, c = t % kColBlock;
         const int q = (dif_pos(k2, NS ? NS : N2) * NL + 4 * c) / 2;
         const int y = k1 + N1 * k2, x = c0 + c;
-        const float2 f = pix_factor(post, x, y, N);
+        const float2 f = win ? pix_factor_w(post, x, y, N, icx[c], icy[k2]) : pix_factor(post, x, y, N);
         const float4 a = buf4[q], b = buf4[q + 1];
         const float2 q0 = cmulf(make_float2(a.x, a.y), f), q1 = cmulf(make_float2(a.z, a.w), f);
         const float2 q2 = cmulf(make_float2(b.x, b.y), f), q3 = cmulf(make_float2(b.z, b.w), f);
@@ -446,8 +576,8 @@ void split_n(int N, int &N1, int &N2) {
     N2 = N / N1;
 }
 
-size_t rows_smem(int N) { return (size_t)(2 * padded_len(N)) * sizeof(float2); }
-size_t cols_smem(int n) { return (size_t)(4 * kColBlock * n + 2 * n) * sizeof(float2); }
+size_t rows_smem(int N) { return (size_t)(2 * padded_len(N) + N / 16) * sizeof(float2); }
+size_t cols_smem(int n) { return (size_t)(4 * kColBlock * n + 3 * n + kColBlock) * sizeof(float2); }
 
 // in -> out: pre on the way in, the 2D transform of sign SIGN, post on the way out
 template <int SIGN>
@@ -456,12 +586,12 @@ cudaError_t transform2d(const float4 *in, float4 *out, float4 *s1, float2 *tw, i
     int N1, N2;
     split_n(N, N1, N2);
     const int nb = N / kColBlock;
-    step_twiddles_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N, SIGN);
-    if (N == 4096) {           // the compile-time form of the LOFAR-sized grid
+    if (N == 4096) {           // the compile-time form of the LOFAR-sized grid (its own twiddles)
         image_rows_kernel<SIGN, 4096><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);          // along x
         image_cols_a_kernel<SIGN, 4096><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);          // y1
         image_cols_b_kernel<SIGN, 4096><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);  // y2
     } else {
+        step_twiddles_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N, SIGN);
         image_rows_kernel<SIGN, 0><<<2 * N, kRowThreads, rows_smem(N), s>>>(in, s1, N, pre, tw);
         image_cols_a_kernel<SIGN, 0><<<N2 * nb, kColThreads, cols_smem(N1), s>>>(s1, N, N1, N2);
         image_cols_b_kernel<SIGN, 0><<<N1 * nb, kColThreads, cols_smem(N2), s>>>(s1, out, N, N1, N2, post);
@@ -532,7 +662,7 @@ std::vector<float> effective_window(const double *a, int L, int N) {
 
 struct ImageBufs {
     cudaStream_t s;
-    void *s1 = nullptr, *cbar = nullptr, *tw = nullptr;
+    void *s1 = nullptr, *cbar = nullptr, *tw = nullptr;     // cbar: the reciprocal window
     explicit ImageBufs(cudaStream_t st) : s(st) {}
     ~ImageBufs() {
         if (s1) cudaFreeAsync(s1, s);
@@ -541,7 +671,7 @@ struct ImageBufs {
     }
 };
 
-idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, const double *h_window,
+idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, const double *h_window, int sign,
                        cudaStream_t s, ImageBufs &bufs, int &logN) {
     if (!p || !a_ptr || !b_ptr) return fail(IDG_ERR_INVALID_ARG, "plan, input and output are required");
     const int N = p->N;
@@ -572,10 +702,19 @@ idg_status image_setup(const idg_plan *p, const void *a_ptr, const void *b_ptr, 
         for (int x = 0; x < N; ++x)
             if (!(std::hypot(cb[2 * x], cb[2 * x + 1]) > 1e-30))
                 return fail(IDG_ERR_INVALID_ARG, "the effective window vanishes on the image");
+        // the kernels multiply by 1 / cbar (gridding side) or 1 / conj cbar (degridding side),
+        // formed here in FP64 and rounded once
+        std::vector<float> icb(2 * (size_t)N);
+        for (int x = 0; x < N; ++x) {
+            const double re = cb[2 * x], im = sign > 0 ? cb[2 * x + 1] : -(double)cb[2 * x + 1];
+            const double d = re * re + im * im;
+            icb[2 * x] = (float)(re / d);
+            icb[2 * x + 1] = (float)(-im / d);
+        }
         st = scratch_alloc(dev, sizeof(float) * 2 * N, s, &bufs.cbar);
         if (st != IDG_OK) return st;
         // (a copy from pageable memory returns once the source has been staged)
-        e = cudaMemcpyAsync(bufs.cbar, cb.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(bufs.cbar, icb.data(), sizeof(float) * 2 * N, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "effective window upload");
     }
     return IDG_OK;
@@ -593,7 +732,7 @@ idg_status idg_image_from_grid(const idg_plan *p, const void *d_grid, const doub
     cudaStream_t s = (cudaStream_t)stream;
     ImageBufs bufs(s);
     int logN = 0;
-    idg_status st = image_setup(p, d_grid, d_image, h_window, s, bufs, logN);
+    idg_status st = image_setup(p, d_grid, d_image, h_window, +1, s, bufs, logN);
     if (st != IDG_OK) return st;
     const int N = p->N;
     for (int k = 0; k < p->stats.n_w_layers; ++k) {
@@ -612,7 +751,7 @@ idg_status idg_grid_from_image(const idg_plan *p, const void *d_image, const dou
     cudaStream_t s = (cudaStream_t)stream;
     ImageBufs bufs(s);
     int logN = 0;
-    idg_status st = image_setup(p, d_image, d_grid, h_window, s, bufs, logN);
+    idg_status st = image_setup(p, d_image, d_grid, h_window, -1, s, bufs, logN);
     if (st != IDG_OK) return st;
     const int N = p->N;
     for (int k = 0; k < p->stats.n_w_layers; ++k) {
