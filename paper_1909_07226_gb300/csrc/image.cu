@@ -466,6 +466,40 @@ __host__ __device__ constexpr int split_n_ct(int N) {
 }
 static_assert(split_n_ct(4096) == 64, "4096 = 64 x 64");
 
+// The 64-point transforms of the column passes at N = 4096 (N1 = N2 = 64) straight from
+// global memory to global memory: line l of a CTA is polarisation l % 4 of column
+// c0 + l / 4, so the 32 lines of a warp are 256 contiguous bytes of an image row.  The
+// first step (radix 16, H = 4) reads its 16 points (positions i + 4 j) from the rows
+// src_row(i + 4 j), the second (radix 4, H = 1) leaves frequency f = b + 16 k at
+// position 4 b + k and hands it to out(f, line, value): one shared-memory exchange
+// between the steps instead of a load, two steps and a store through shared memory.
+// tw: the step twiddles of the 64-point transform (step_twiddles).
+template <int SIGN, typename SrcRow, typename Out>
+__device__ __forceinline__ void cols64(float2 *buf, const float2 *tw, SrcRow src_row, Out out) {
+    constexpr int NL = 4 * kColBlock, H = 4;
+    static_assert(NL * H == kColThreads, "one first-step butterfly per thread");
+    {
+        const int line = threadIdx.x % NL, i = threadIdx.x / NL;
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = src_row(i + H * j)[line];
+        dft_reg<16, SIGN>(v);
+        buf[i * NL + line] = v[0];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) buf[(i + H * k) * NL + line] = cmulf(v[k], tw[(k - 1) * H + i]);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NL * 16; t += kColThreads) {
+        const int line = t % NL, b = t / NL;
+        float2 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = buf[(4 * b + k) * NL + line];
+        dft_reg<4, SIGN>(v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out(b + 16 * k, line, v[k]);
+    }
+}
+
 // column pass A (four-step, N = N1 N2): CTA (y2, column block) transforms over y1 the
 // rows y1 N2 + y2 of kColBlock columns (4 kColBlock lines of N1 points), multiplies
 // output k1 by exp(SIGN 2 pi i y2 k1 / N) and writes it to row k1 N2 + y2 (in place)
@@ -484,6 +518,16 @@ __global__ void __launch_bounds__(kColThreads) image_cols_a_kernel(float4 *__res
         float s, co;
         sincospif((float)SIGN * 2.0f * (float)((y2 * k1) & (N - 1)) / (float)N, &s, &co);
         w4[k1] = make_float2(co, s);
+    }
+    if constexpr (NC == 4096) {
+        __syncthreads();                            // the twiddles
+        float2 *img2 = (float2 *)img;
+        cols64<SIGN>(buf, tw,
+                     [&](int y1) { return img2 + ((size_t)(y1 * 64 + y2) * 4096 + c0) * 4; },
+                     [&](int k1, int line, float2 v) {
+                         img2[((size_t)(k1 * 64 + y2) * 4096 + c0) * 4 + line] = cmulf(v, w4[k1]);
+                     });
+        return;
     }
     for (int t = threadIdx.x; t < N1 * kColBlock; t += kColThreads) {
         const int y1 = t / kColBlock, c = t % kColBlock;
@@ -529,6 +573,26 @@ __global__ void __launch_bounds__(kColThreads) image_cols_b_kernel(const float4 
             icx[t] = t < kColBlock ? post.icbar[c0 + t] : post.icbar[k1 + N1 * (t - kColBlock)];
     }
     step_twiddles(tw, N2, SIGN, threadIdx.x, blockDim.x);
+    if constexpr (NC == 4096) {
+        __syncthreads();                            // the twiddles and window values
+        const float2 *img2 = (const float2 *)img;
+        float2 *out2 = (float2 *)out;
+        cols64<SIGN>(buf, tw,
+                     [&](int y2) { return img2 + ((size_t)(k1 * 64 + y2) * 4096 + c0) * 4; },
+                     [&](int k2, int line, float2 v) {
+                         const int y = k1 + 64 * k2, c = line >> 2, x = c0 + c;
+                         const float2 f = win ? pix_factor_w(post, x, y, 4096, icx[c], icy[k2])
+                                              : pix_factor(post, x, y, 4096);
+                         float2 r = cmulf(v, f);
+                         float2 *o = out2 + ((size_t)y * 4096 + c0) * 4 + line;
+                         if (post.accumulate) {
+                             const float2 u = *o;
+                             r = make_float2(r.x + u.x, r.y + u.y);
+                         }
+                         *o = r;
+                     });
+        return;
+    }
     for (int t = threadIdx.x; t < N2 * kColBlock; t += kColThreads) {
         const int y2 = t / kColBlock, c = t % kColBlock;
         const float4 *p = img + ((size_t)(k1 * N2 + y2) * N + c0 + c) * 2;
