@@ -375,6 +375,29 @@ __device__ __forceinline__ void dif_step_pow_first(float2 *buf, const float2 *T,
     }
 }
 
+// The last step (LEN = 16, unit twiddles) of the 4096-point row transform with its outputs
+// written straight to the row in natural order: butterfly b leaves frequency
+// f = 256 k + 16 (b % 16) + b / 16 at output k, so the butterflies are taken with b / 16
+// fastest across the lanes (16 consecutive pixels per warp and k) and their shared-memory
+// reads stay free of bank conflicts (slot stride 273).  orow: polarisation 2 hp + line of
+// pixel x at orow[4 x + 2 hp + line].
+template <int SIGN>
+__device__ __forceinline__ void dif_step_pow_last_store(const float2 *buf, float2 *orow, int hp) {
+    constexpr int R = 16, NL = 2, N = 4096;
+    for (int t = threadIdx.x; t < NL * (N / R); t += blockDim.x) {
+        const int line = t % NL, q = t / NL;
+        const int b = (q % 16) * 16 + q / 16;
+        const int s0 = slot<true>(16 * b) * NL + line;
+        float2 v[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) v[j] = buf[s0 + j * NL];
+        dft_reg<R, SIGN>(v);
+        const int f0 = 16 * (b % 16) + b / 16;
+#pragma unroll
+        for (int k = 0; k < R; ++k) orow[4 * (256 * k + f0) + 2 * hp + line] = v[k];
+    }
+}
+
 template <int SIGN, int NL, bool PAD, int N, int LEN>
 __device__ __forceinline__ void dif_steps_pow(float2 *buf, const float2 *T) {
     if constexpr (LEN > 1) {
@@ -432,8 +455,6 @@ __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *_
         if (SIGN > 0 && pre.mode == 0) {
             __syncthreads();
             dif_step_pow_first<SIGN, true, 4096>(buf, T, (const float2 *)(in + (size_t)y * N * 2), hp, y, pre);
-            __syncthreads();
-            dif_steps_pow<SIGN, 2, true, 4096, 256>(buf, T);
         } else {                 // (with the window's reciprocal: once per pixel, on the load)
             for (int x = threadIdx.x; x < N; x += kRowThreads) {
                 const float4 a = row[2 * x];
@@ -442,8 +463,13 @@ __global__ void __launch_bounds__(kRowThreads) image_rows_kernel(const float4 *_
                 buf4[slot<true>(x)] = make_float4(p0.x, p0.y, p1.x, p1.y);
             }
             __syncthreads();
-            dif_steps_pow<SIGN, 2, true, 4096, 4096>(buf, T);
+            dif_step_pow<SIGN, 2, true, 4096, 4096>(buf, T);
         }
+        __syncthreads();
+        dif_step_pow<SIGN, 2, true, 4096, 256>(buf, T);
+        __syncthreads();
+        dif_step_pow_last_store<SIGN>(buf, (float2 *)(out + (size_t)y * N * 2), hp);
+        return;
     } else {
         for (int x = threadIdx.x; x < N; x += kRowThreads) {
             const float4 a = row[2 * x];
