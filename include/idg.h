@@ -228,7 +228,8 @@ idg_status idg_grid(const idg_plan *plan, const void *d_vis, const uint8_t *d_fl
  * Other arguments as for idg_grid.
  * At L = 32, and at L = 24 and 16 when the plan is separable, with the default
  * kernel choice, IDG_FFT_FP32 and IDG_PHASOR_SINCOS, when at least half the
- * visibilities lie in subgrids of 512 or more, the call
+ * visibilities lie in subgrids of 64 or more (separable kernels; 512 for the
+ * direct tensor-core degridder), the call
  * is one fused tensor-core launch (splitter, transform, A-terms and taper, and
  * the visibility sums per subgrid in one CTA) without subgrid scratch.  A plan
  * with only some subgrids within the remainder bound degrids those (with the
@@ -443,7 +444,7 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  * ordered by cost (K_p, largest first), a few CTAs per SM pulling items from a
  * device counter: the packed-FP32 kernels, for the direct subgrids at L = 24,
  * 16 and 8 and for any class whose visibilities lie mostly in subgrids of
- * fewer than 512.  No device scratch is used.  With
+ * fewer than 64 (separable classes) or 512 (direct).  No device scratch is used.  With
  * IDG_BATCH_GRAPH the first call of each direction captures its launch
  * sequence into a CUDA graph, and later calls replay it (the buffers are fixed
  * by the batch, so the graph stays valid).

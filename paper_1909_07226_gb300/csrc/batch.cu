@@ -561,13 +561,15 @@ idg_status idg_batch_create(const idg_plan *const *plans, const idg_job_buffers 
         auto &cl = b->classes[c];
         cl.n_items = (int64_t)items.size();
         if (cl.n_items > 2147483647) st = fail(IDG_ERR_INVALID_ARG, "too many subgrids in one batch class");
-        // the tensor-core path pays a fixed cost per subgrid: classes whose
-        // visibilities sit mostly in subgrids of fewer than 512 take the fused kernels
+        // the tensor-core path pays a fixed cost per subgrid: classes whose visibilities
+        // sit mostly in subgrids of fewer than kTcwFusedKpMin (direct) or kSepFusedKpMin
+        // (separable) visibilities take the persistent kernels
+        const int64_t kmin = cl.sep ? kSepFusedKpMin : kTcwFusedKpMin;
         int64_t small = 0, all = 0;
         for (const int2 &it : items) {
             const int64_t kp = plans[it.x]->kp_all[it.y];
             all += kp;
-            if (kp < 512) small += kp;
+            if (kp < kmin) small += kp;
         }
         for (int k = 0; k < 2; ++k) {
             KernelShape &ks = k ? cl.degrid : cl.grid;

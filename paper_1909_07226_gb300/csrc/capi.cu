@@ -878,7 +878,8 @@ static idg_status check_range(const idg_plan *p, int64_t first, int64_t count) {
 // (2) for a subgrid in one CTA, with the transform in shared memory; they serve
 // the default kernel choice with the FP32 transform, direct phasors and the
 // plain adder.  The degridder takes them when most visibilities of the launch
-// lie in subgrids of at least 512 (as the default per-call choice does).
+// lie in subgrids of at least kTcwFusedKpMin (direct) or kSepFusedKpMin
+// (separable), as the default per-call choice does.
 // the fused composite kernels: the direct tensor-core ones at L = 32, the separable ones at
 // L = 32, 24 and 16 for subgrids that meet the remainder bound (the process-default kernel
 // choice only); sep: the launch's subgrids take the separable kernels
@@ -891,10 +892,11 @@ static bool fused_degrid(const idg_plan *p, const SubgridSet &set, bool sep) {
     if (!(fused_size(p, sep) && p->opts.fft_mode == IDG_FFT_FP32 && p->opts.precision_mode == IDG_PHASOR_SINCOS &&
           p->kernel_variant(IDG_KERNEL_DEGRIDDER) == 0))
         return false;
+    const int32_t kmin = sep ? kSepFusedKpMin : kTcwFusedKpMin;
     int64_t small = 0, all = 0;
     for (int64_t i = 0; i < set.count; ++i) {
         all += set.kp_host[i];
-        if (set.kp_host[i] < 512) small += set.kp_host[i];
+        if (set.kp_host[i] < kmin) small += set.kp_host[i];
     }
     return 2 * small <= all;
 }

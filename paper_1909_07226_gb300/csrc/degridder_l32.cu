@@ -44,7 +44,7 @@ idg_status launch_sep_auto(const Geometry &g, const SubgridSet &set, const void 
     int64_t small = 0, all = 0;
     for (int64_t i = 0; i < set.count; ++i) {
         all += set.kp_host[i];
-        if (set.kp_host[i] < 512) small += set.kp_host[i];
+        if (set.kp_host[i] < kSepFusedKpMin) small += set.kp_host[i];
     }
     if (2 * small > all) return degrid_f2_launch_static<32, 4, 128, 3>(g, set, sub, flags, aterms, taper, vis_out, s);
     return launch_degridder_sep(g, set, sub, flags, aterms, taper, vis_out, (void *)s);

@@ -229,6 +229,14 @@ idg_status launch_degridder_rec(const Geometry &g, const SubgridSet &set, const 
 // tensor memory) and the device error word of the bounded waits
 // subgrid sizes the separable tensor-core kernels are built for (32, 24 and 16)
 bool separable_size(int L);
+// The fused (and one-CTA-per-subgrid) degridders pay a fixed prologue per subgrid, so a
+// launch takes them only when at least half its visibilities lie in subgrids of at least
+// this many: 512 for the direct tensor-core degridder; for the separable one, whose
+// per-visibility cost is lower, 64 (on the precision workload's subgrids of 256 the fused
+// separable degridder took 29.4 ms against 63.1 ms for splitter, transform and the
+// packed-FP32 degridder).
+constexpr int32_t kTcwFusedKpMin = 512;
+constexpr int32_t kSepFusedKpMin = 64;
 // separable tensor-core gridder (L = 32, 24 or 16, g.separable): subgrid images, or fused
 // with the transform and the adder into grid
 idg_status launch_gridder_sep(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,

@@ -1,7 +1,9 @@
 """Batched form: several jobs with different subgrid and grid sizes gridded and
-degridded together (one persistent launch per subgrid size, subgrids kept in
-shared memory), each job checked against the FP64 oracle; the same with the
-launch sequence captured in a CUDA graph and replayed."""
+degridded together (per subgrid size one work class, or two when some subgrids
+take the separable kernels and others the direct ones: one persistent launch,
+or tensor-core launches per job; subgrids kept in shared memory), each job
+checked against the FP64 oracle; the same with the launch sequence captured in
+a CUDA graph and replayed."""
 import numpy as np
 import pytest
 
@@ -48,7 +50,7 @@ def test_batch_grid_and_degrid_match_the_oracle(graph):
                          vis_out=torch.full(w.vis.shape, 5.0 + 5.0j, dtype=torch.complex64, device="cuda")))
     b = idg.Batch(plans, jobs, graph=graph)
     info = b.info()
-    # one fused launch per subgrid size (the L = 32 job has only small subgrids)
+    # one work class per subgrid size
     assert info["n_launches"] == 4 and info["n_items"] == sum(p.n_subgrids for p in plans)
     for rep in range(2):                 # second pass replays the captured graph
         for j in jobs:

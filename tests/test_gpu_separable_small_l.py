@@ -7,7 +7,7 @@ FP64 oracle on the same seeded inputs: relative RMS <= 1e-5
 Cases: subgrids of up to 1024 visibilities (two staged batches and two
 accumulation periods of the gridder), W-layers, no A-terms, flags, and
 subgrids of at most 32 visibilities.  Where most visibilities lie in subgrids
-of fewer than 512, the degridder takes the unfused splitter, transform and
+of fewer than 64, the degridder takes the unfused splitter, transform and
 packed kernel, as at L = 32."""
 import numpy as np
 import pytest
@@ -72,9 +72,9 @@ def test_separable_l24_grid_and_degrid(case):
         idg.profile_enable(False)
     idg.device_errors()
     assert grid_launches == {"gridder": 1}          # one fused separable launch
-    # the degridder fuses when at least half the visibilities lie in subgrids of 512 or more
+    # the degridder fuses when at least half the visibilities lie in subgrids of 64 or more
     kp = p.export()[:, O.D_KP]
-    if 2 * kp[kp < 512].sum() <= kp.sum():
+    if 2 * kp[kp < 64].sum() <= kp.sum():
         assert degrid_launches == {"degridder": 1}
     else:
         assert "splitter" in degrid_launches and "fft" in degrid_launches

@@ -298,7 +298,8 @@ def test_tc_degridder_lofar_slice_sampled(tcd_selected):
 # transform, direct phasors, plain adder) a composite call grids each subgrid
 # in one CTA (gridder, transform and adder) and degrids it in one CTA
 # (splitter, transform and degridder) when most of its visibilities lie in
-# subgrids of K_p >= 512.  The launch counters show which path ran.
+# subgrids of K_p >= 64 (separable plans; 512 for the direct kernels).  The
+# launch counters show which path ran.
 
 def _no_aterms(wl):
     wl.aterms = None
@@ -314,9 +315,11 @@ FUSED_CASES = {
     # two A-term slots and two w layers, K_p 8 .. 768: fused degridder, ragged groups
     "long_kp_slots_layers": lambda: small32(n_t=192, n_chan=8, max_t=96, n_st=4, df=0.25e6, n_slots=2,
                                             w_step=100.0, diameter_m=2000.0),
-    # many small subgrids (K_p <= 160): fused gridder, separate degridding stages
+    # many small subgrids (K_p <= 160, half of the visibilities in subgrids of 64 or more)
     "short_kp_w_layers": lambda: small32(n_t=128, n_chan=16, max_t=128, n_st=4, df=0.25e6, w_step=20.0,
                                          diameter_m=20000.0),
+    # subgrids of at most 32 visibilities: fused gridder, separate degridding stages
+    "tiny_kp": lambda: small32(n_t=64, n_chan=8, max_t=4, n_st=4),
     "points_flags_aterms": CASES["points_flags_aterms"],
     "huge_magnitudes": CASES["huge_magnitudes"],
 }
@@ -328,7 +331,8 @@ def _launches(prof):
 
 def _kp_mostly_long(p):
     kp = p.export()[:, O.D_KP]
-    return 2 * kp[kp < 512].sum() <= kp.sum()
+    kmin = 64 if p.stats.separable else 512
+    return 2 * kp[kp < kmin].sum() <= kp.sum()
 
 
 @pytest.mark.parametrize("case", sorted(FUSED_CASES))
