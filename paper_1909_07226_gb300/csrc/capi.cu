@@ -767,17 +767,37 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_taper, taper_def.data(), sizeof(float) * taper_def.size(), "default taper"},
         {(void **)&p->d_ones, ones.data(), sizeof(float) * ones.size(), "unit taper"},
     };
+    // The uploads and the pair kernel run on a private non-blocking stream that only this
+    // call waits for: plans are made on host threads while other threads run (and record
+    // graphs of) their own work, and a device-wide synchronisation would wait on those
+    // streams and invalidate a graph capture in progress.
+    cudaStream_t ps = nullptr;
+    e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        idg_plan_destroy(p);
+        return cuda_fail(e, "plan upload stream");
+    }
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    } guard{ps};
     for (auto &u : ups) {
         if (u.bytes == 0) continue;
         e = cudaMalloc(u.dst, u.bytes);
         if (e != cudaSuccess) {
             idg_status st = cuda_fail(e, (std::string("cudaMalloc(") + u.what + ")").c_str());
+            cudaStreamSynchronize(ps);
             idg_plan_destroy(p);
             return st;
         }
-        e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+        // (from pageable memory: the call returns once the source has been staged)
+        e = cudaMemcpyAsync(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, ps);
         if (e != cudaSuccess) {
-            idg_status st = cuda_fail(e, (std::string("cudaMemcpy(") + u.what + ")").c_str());
+            idg_status st = cuda_fail(e, (std::string("cudaMemcpyAsync(") + u.what + ")").c_str());
+            cudaStreamSynchronize(ps);
             idg_plan_destroy(p);
             return st;
         }
@@ -786,12 +806,13 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         const size_t n_bt = (size_t)n_bl * n_t;
         e = cudaMalloc((void **)&p->d_uvw_f2, sizeof(float) * 8 * std::max<size_t>(n_bt, 1));
         if (e == cudaSuccess && n_bt > 0) {
-            split_uvw_kernel<<<(unsigned)((n_bt + 255) / 256), 256>>>(p->d_uvw, (float4 *)p->d_uvw_f2, n_bt);
+            split_uvw_kernel<<<(unsigned)((n_bt + 255) / 256), 256, 0, ps>>>(p->d_uvw, (float4 *)p->d_uvw_f2, n_bt);
             e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
         if (e != cudaSuccess) {
             idg_status st = cuda_fail(e, "uvw pairs");
+            cudaStreamSynchronize(ps);
             idg_plan_destroy(p);
             return st;
         }
