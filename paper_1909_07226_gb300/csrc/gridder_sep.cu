@@ -151,6 +151,32 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
     const int total_groups = (d.kp + 7) / 8;
     const int n_batches = (d.kp + VB - 1) / VB;     // = accumulation periods (FOLD = GB)
 
+    // staging (producers): visibility tid of batch b, loaded into registers one batch ahead;
+    // the first batch's loads go out before the set-up below, so their latency overlaps it
+    float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, puv = pa, pws = pa;
+    float2 pw = make_float2(0.f, 0.f);
+    bool pin = false, pflag = false;
+    const float4 *uvw2 = (const float4 *)g.uvw_f2;
+    const float4 *sc2 = (const float4 *)g.scale_f2;
+    auto load_batch = [&](int b) {
+        const int k = b * VB + tid;
+        pin = k < d.kp;
+        pflag = false;
+        if (pin) {
+            int t, c;
+            const size_t vi = vis_index(g, d, k, t, c);
+            const size_t bt = (size_t)d.bl * g.n_t + t;
+            puv = uvw2[2 * bt];
+            const float4 w4 = uvw2[2 * bt + 1];
+            pw = make_float2(w4.x, w4.y);
+            pws = sc2[c];
+            pflag = flags && flags[vi];
+            pa = vis[2 * vi];          // loaded whatever the flag: the load does not wait for it
+            pb = vis[2 * vi + 1];
+        }
+    };
+    if (!mma_warp) load_batch(0);
+
     if (mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(&s_tmem)), "n"(512));
@@ -249,29 +275,6 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
         const float csig = g.c_scale;
         const uint16_t m1h = 0xBC00u;      // FP16 -1
 
-        // staging: visibility tid of batch b, loaded into registers one batch ahead
-        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa, puv = pa, pws = pa;
-        float2 pw = make_float2(0.f, 0.f);
-        bool pin = false, pflag = false;
-        const float4 *uvw2 = (const float4 *)g.uvw_f2;
-        const float4 *sc2 = (const float4 *)g.scale_f2;
-        auto load_batch = [&](int b) {
-            const int k = b * VB + tid;
-            pin = k < d.kp;
-            pflag = false;
-            if (pin) {
-                int t, c;
-                const size_t vi = vis_index(g, d, k, t, c);
-                const size_t bt = (size_t)d.bl * g.n_t + t;
-                puv = uvw2[2 * bt];
-                const float4 w4 = uvw2[2 * bt + 1];
-                pw = make_float2(w4.x, w4.y);
-                pws = sc2[c];
-                pflag = flags && flags[vi];
-                pa = vis[2 * vi];          // loaded whatever the flag: the load does not wait for it
-                pb = vis[2 * vi + 1];
-            }
-        };
         // phase coefficients of the staged visibility: u (f/c) k_uv - u0 k_uv and so on, from
         // float pairs with error-free products and sums, rounded once to FP32
         float4 cf_next = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -338,7 +341,6 @@ __device__ __forceinline__ void gridder_sep_body(const Geometry &g, const DevSub
             }
         };
 
-        load_batch(0);
         form_coef();
         store_batch(0);
         producers_sync();
