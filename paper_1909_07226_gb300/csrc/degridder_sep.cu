@@ -558,6 +558,7 @@ degridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t 
     allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     degridder_sep_body<L, true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
+    complete_after_primary();
 }
 
 template <int L>

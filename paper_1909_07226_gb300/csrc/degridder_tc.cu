@@ -344,6 +344,7 @@ degridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t 
     allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     degridder_tcw_body<true>(g, g.sub[sid], grid, flags, aterms, taper, vis_out);
+    complete_after_primary();
 }
 
 }  // namespace

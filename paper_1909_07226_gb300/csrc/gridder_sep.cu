@@ -560,6 +560,7 @@ gridder_sep_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t fi
     allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     gridder_sep_body<L, true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
+    complete_after_primary();
 }
 
 template <int L>

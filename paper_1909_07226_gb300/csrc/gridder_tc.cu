@@ -360,6 +360,7 @@ gridder_tcw_fused_kernel(Geometry g, const int32_t *__restrict__ idx, int64_t fi
     allow_dependents();
     const int sid = idx ? idx[blockIdx.x] : (int)(first + blockIdx.x);
     gridder_tcw_body<true>(g, g.sub[sid], vis, flags, aterms, taper, grid);
+    complete_after_primary();
 }
 
 }  // namespace

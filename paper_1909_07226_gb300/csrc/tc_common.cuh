@@ -181,6 +181,10 @@ __device__ __forceinline__ void split_e_m(float x, float y, uint16_t m1, uint32_
 // visibilities, or the same grid by atomic adds).  Without the attribute the call has
 // no effect.
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// At the end of such a kernel: as a dependent launch, the CTA exits only once the kernel
+// before it has completed, so that kernels complete in stream order (work after the last
+// one then also follows every earlier one).  No effect on an ordinary launch.
+__device__ __forceinline__ void complete_after_primary() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... Exp, typename... Act>
 cudaError_t launch_pdl(void (*fn)(Exp...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
