@@ -440,7 +440,8 @@ idg_status idg_degrid_subgrids(const idg_plan *plan, int64_t first, int64_t coun
  * IDG_KERNEL_BATCH_*): one launch per job with one CTA per item, most
  * visibilities first, each launch allowed to begin while the previous one
  * ends (programmatic dependent launch: the jobs' outputs are disjoint, or
- * summed by atomic adds); or ONE persistent launch over the class's items
+ * summed by atomic adds; the kernels still complete in stream order); or ONE
+ * persistent launch over the class's items
  * ordered by cost (K_p, largest first), a few CTAs per SM pulling items from a
  * device counter: the packed-FP32 kernels, for the direct subgrids at L = 24,
  * 16 and 8 and for any class whose visibilities lie mostly in subgrids of
