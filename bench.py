@@ -75,8 +75,8 @@ def sep_degrid_flop_per_tile(L):
 SEP_USEFUL_SHARE = 0.5
 DTYPE_SEP = "f32 (fp16 hi/lo split tensor-core products, fp32 accumulate)"
 KERNEL_TRAFFIC = {
-    "gridder": {SEP_VARIANT: (178.4e6 + 5.4e6) / 4.731e9},
-    "degridder": {SEP_VARIANT: (31.2e6 + 91.9e6) / 4.731e9},
+    "gridder": {SEP_VARIANT: (178.5e6 + 5.6e6) / 4.731e9},
+    "degridder": {SEP_VARIANT: (31.2e6 + 92.4e6) / 4.731e9},
 }
 
 
