@@ -609,10 +609,13 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
     std::vector<int32_t> span_order;
     // device work order: the separable subgrids, then the others (one launch each),
     // each part with most visibilities first (longest-processing-time first for the
-    // block scheduler), ties in plan order
+    // block scheduler), ties by A-term slot, then in plan order: the CTAs in flight then
+    // share their slot's A-terms in L2 (a plan with A-terms every few timesteps has more
+    // of them than L2 holds, and plan order is baseline-major)
     const auto work_first = [&](int32_t a, int32_t b) {
         if (p->sep_sub[a] != p->sep_sub[b]) return p->sep_sub[a] > p->sep_sub[b];
-        return hsub[a].kp > hsub[b].kp;
+        if (hsub[a].kp != hsub[b].kp) return hsub[a].kp > hsub[b].kp;
+        return hsub[a].slot < hsub[b].slot;
     };
     std::vector<int32_t> order((size_t)std::max<int64_t>(n_sub, 1));
     std::iota(order.begin(), order.begin() + n_sub, 0);
@@ -677,7 +680,8 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         auto sep_kind = [&](int32_t e) { return e >= n_sub || p->sep_sub[e]; };
         auto fused_first = [&](int32_t a, int32_t b) {
             if (sep_kind(a) != sep_kind(b)) return sep_kind(a);
-            return hsub[a].kp > hsub[b].kp;
+            if (hsub[a].kp != hsub[b].kp) return hsub[a].kp > hsub[b].kp;
+            return hsub[a].slot < hsub[b].slot;
         };
         // entries of plan subgrids [a, b): each subgrid itself, or its pieces
         auto entries = [&](int64_t a, int64_t b, std::vector<int32_t> &out) {
