@@ -630,9 +630,9 @@ class JobBuffers(ctypes.Structure):
 
 
 class Batch:
-    """idg_batch: jobs (plan + device tensors) gridded/degridded together in one
-    persistent launch per subgrid size.  Keeps references to the plans and
-    tensors so they outlive the batch."""
+    """idg_batch: jobs (plan + device tensors) gridded/degridded together in work
+    classes per subgrid size (one persistent launch, or tensor-core launches per
+    job).  Keeps references to the plans and tensors so they outlive the batch."""
 
     def __init__(self, plans, jobs, graph: bool = False):
         import torch

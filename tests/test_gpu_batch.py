@@ -179,3 +179,28 @@ def test_batch_autotune_keeps_results():
     torch.cuda.synchronize()
     for i, (w, op, j) in enumerate(zip(wls, ops, jobs)):
         parity(j["grid"].cpu().numpy(), O.grid(w, op), f"batch grid job {i} after autotune")
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_jobs_adding_into_one_grid(graph):
+    # three separable L = 32 jobs of one grid size gridded into the same grid by one batch:
+    # their per-job launches may overlap (programmatic dependent launches) and add into
+    # the grid together; the result is the sum of the three oracle grids
+    import torch
+    wls = [syn.make_small(seed=410 + i, n_st=5, n_t=96, n_chan=8, L=32, N=256, max_t=96, n_slots=1, flag_p=0.05,
+                          diameter_m=2500.0 + 500.0 * i) for i in range(3)]
+    plans = [idg.plan_from_workload(w) for w in wls]
+    assert all(p.stats.separable == 1 for p in plans)
+    grid = torch.zeros((1, 256, 256, 4), dtype=torch.complex64, device="cuda")
+    jobs = []
+    for w in wls:
+        d = workload_to_device(w)
+        jobs.append(dict(vis=d["vis"], flags=d["flags"], aterms=d["aterms"], taper=d["taper"], grid=grid,
+                         vis_out=None))
+    b = idg.Batch(plans, jobs, graph=graph)
+    for rep in range(2):
+        grid.zero_()
+        b.grid()
+        idg.device_errors()
+        ref = sum(O.grid(w, O.plan(w)) for w in wls)
+        parity(grid.cpu().numpy(), ref, f"three jobs into one grid, pass {rep}")
