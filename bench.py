@@ -725,6 +725,7 @@ def precision_errors(idg, syn, torch, dev, stream, n_t=32):
     forms = {"direct_sincos": dict(),
              "channel_recurrence": dict(precision_mode=idg.PHASOR_RECURRENCE),
              "compensated_adder": dict(adder_mode=idg.ADDER_COMPENSATED),
+             "sorted_adder": dict(adder_mode=idg.ADDER_SORTED),
              "tc_split_transform": dict(fft_mode=idg.FFT_TC_SPLIT)}
     sl = syn.make_lofar(with_vis=True, n_t=n_t, slot_len=16, name="precision")
     op = O.plan(sl)
@@ -1012,7 +1013,8 @@ def run_precision(args, world, rank, local):
              "channel_recurrence+compensated_adder": dict(precision_mode=idg.PHASOR_RECURRENCE,
                                                           adder_mode=idg.ADDER_COMPENSATED),
              "direct_sincos+tc_split_transform": dict(precision_mode=idg.PHASOR_SINCOS,
-                                                      fft_mode=idg.FFT_TC_SPLIT)}
+                                                      fft_mode=idg.FFT_TC_SPLIT),
+             "direct_sincos+sorted_adder": dict(precision_mode=idg.PHASOR_SINCOS, adder_mode=idg.ADDER_SORTED)}
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     out = {}

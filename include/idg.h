@@ -94,9 +94,17 @@ enum { IDG_FFT_FP32 = 0,           /* FP32 FFT in shared memory                 
                                       per stage), FP32 accumulation; subgrid size 32
                                       only (IDG_ERR_UNSUPPORTED otherwise)          */
 enum { IDG_ADDER_ATOMIC = 0,       /* 16-byte vector atomic adds                    */
-       IDG_ADDER_COMPENSATED = 1 };/* atomics + exact TwoSum error into a compensation
+       IDG_ADDER_COMPENSATED = 1,  /* atomics + exact TwoSum error into a compensation
                                       grid folded in at the end (O(eps) instead of
                                       O(n eps) summation error; grid-sized scratch) */
+       IDG_ADDER_SORTED = 2 };     /* deterministic: the gridding runs in plan order, in
+                                      chunks of consecutive subgrids; one CTA per 32 x 32
+                                      grid tile sums the chunk's subgrids that overlap
+                                      it in plan order (plan-held tile lists) and adds
+                                      the sum with plain stores.  The grid is the same
+                                      bit for bit on every run (for a given plan and
+                                      device), with no atomics.  Batches add with
+                                      atomics whatever the plan's adder.            */
 
 typedef struct {
     int64_t n_subgrids;       /* P, number of blocks                              */
@@ -384,7 +392,7 @@ idg_status idg_grid_degrid_host(const idg_plan *plan, const void *h_vis, const v
  *     with a plan of no subgrids does only the lookup and serves as the
  *     warm-up.  The cached address stays valid while the device's context
  *     lives: calls after cudaDeviceReset are not supported.
- *   - Only the plain atomic adder runs here.  A plan created with
+ *   - The atomic and the sorted adder run here.  A plan created with
  *     IDG_ADDER_COMPENSATED needs a grid-sized compensation buffer and is
  *     refused with IDG_ERR_UNSUPPORTED before any work is enqueued.
  *   - All calls on one device share the array.  Calls whose work overlaps on

@@ -130,3 +130,90 @@ idg_status launch_fold_compensation(void *grid, const void *comp, size_t n_float
 }
 
 }  // namespace idg
+
+// Sorted (deterministic) adder, IDG_ADDER_SORTED.  The grid is cut into tiles of kTile x
+// kTile pixels per layer; the plan lists, for every tile that a subgrid overlaps, those
+// subgrids by plan index (ascending).  The subgrids come in chunks of consecutive plan
+// indices [first, first + count) (scratch slot = plan index - first).  One CTA owns a tile:
+// it finds the chunk's part of the tile's list by binary search, sums the parts of those
+// subgrid images that fall on the tile in that order, then adds the sum to the tile with
+// plain loads and stores.  No two CTAs write a pixel and the summation order is fixed, so
+// the grid is the same bit for bit from run to run.
+namespace idg {
+namespace {
+
+constexpr int kTileThreads = 256;
+constexpr int kTilePix = kTile * kTile / kTileThreads;     // pixels per thread
+
+__global__ void __launch_bounds__(kTileThreads)
+tile_adder_kernel(Geometry g, const int32_t *__restrict__ tile_ids, const int32_t *__restrict__ tile_first,
+                  const int32_t *__restrict__ tile_sub, int first, int count, const float4 *__restrict__ sub,
+                  float4 *__restrict__ grid) {
+    const int L = g.L, N = g.N, ntx = (N + kTile - 1) / kTile;
+    // the chunk's entries of this tile's list: [lo, hi) with first <= plan index < first + count
+    int lo = tile_first[blockIdx.x], hi = tile_first[blockIdx.x + 1];
+    {
+        int a = lo, b = hi;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (tile_sub[m] < first) a = m + 1;
+            else b = m;
+        }
+        lo = a;
+        b = hi;
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (tile_sub[m] < first + count) a = m + 1;
+            else b = m;
+        }
+        hi = a;
+    }
+    if (lo == hi) return;                 // (the same for every thread of the CTA)
+    const int tile = tile_ids[blockIdx.x];
+    const int layer = tile / (ntx * ntx), rem = tile - layer * ntx * ntx;
+    const int y0 = (rem / ntx) * kTile, x0 = (rem % ntx) * kTile;
+    float4 a[kTilePix][2];
+#pragma unroll
+    for (int m = 0; m < kTilePix; ++m) a[m][0] = a[m][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = lo; e < hi; ++e) {
+        const int s = tile_sub[e];
+        const int r0 = g.sub[s].r0, q0 = g.sub[s].q0;
+        const float4 *src = sub + (size_t)(s - first) * L * L * 2;
+#pragma unroll
+        for (int m = 0; m < kTilePix; ++m) {
+            const int p = threadIdx.x + m * kTileThreads;
+            const int i = y0 + p / kTile - r0, j = x0 + p % kTile - q0;
+            if (i >= 0 && i < L && j >= 0 && j < L) {
+                const float4 u = src[2 * (i * L + j)], v = src[2 * (i * L + j) + 1];
+                a[m][0] = make_float4(a[m][0].x + u.x, a[m][0].y + u.y, a[m][0].z + u.z, a[m][0].w + u.w);
+                a[m][1] = make_float4(a[m][1].x + v.x, a[m][1].y + v.y, a[m][1].z + v.z, a[m][1].w + v.w);
+            }
+        }
+    }
+    float4 *dst = grid + (size_t)layer * N * N * 2;
+#pragma unroll
+    for (int m = 0; m < kTilePix; ++m) {
+        const int p = threadIdx.x + m * kTileThreads;
+        const int y = y0 + p / kTile, x = x0 + p % kTile;
+        if (y >= N || x >= N) continue;
+        float4 *o = dst + 2 * ((size_t)y * N + x);
+        const float4 u = o[0], v = o[1];
+        o[0] = make_float4(u.x + a[m][0].x, u.y + a[m][0].y, u.z + a[m][0].z, u.w + a[m][0].w);
+        o[1] = make_float4(v.x + a[m][1].x, v.y + a[m][1].y, v.z + a[m][1].z, v.w + a[m][1].w);
+    }
+}
+
+}  // namespace
+
+idg_status launch_adder_sorted(const Geometry &g, const SubgridSet &set, const void *sub, void *grid,
+                               const SortedTiles &t, void *stream) {
+    if (set.count <= 0 || t.n_tiles == 0) return IDG_OK;
+    if (set.idx) return fail(IDG_ERR_INVALID_ARG, "the sorted adder takes consecutive plan indices");
+    tile_adder_kernel<<<(unsigned)t.n_tiles, kTileThreads, 0, (cudaStream_t)stream>>>(
+        g, t.tile_ids, t.tile_first, t.tile_sub, (int)set.first, (int)set.count, (const float4 *)sub, (float4 *)grid);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "sorted adder launch");
+    return IDG_OK;
+}
+
+}  // namespace idg

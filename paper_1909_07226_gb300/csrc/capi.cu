@@ -362,6 +362,9 @@ void idg_plan_destroy(idg_plan *p) {
     cudaFree(p->d_span_order);
     cudaFree(p->d_fused_order);
     cudaFree(p->d_fused_span);
+    cudaFree(p->d_tile_ids);
+    cudaFree(p->d_tile_first);
+    cudaFree(p->d_tile_sub);
     cudaFree(p->d_uvw);
     cudaFree(p->d_scale);
     cudaFree(p->d_uvw_f2);
@@ -403,7 +406,7 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         return fail(IDG_ERR_INVALID_ARG, "unknown fft_mode");
     if (o.fft_mode == IDG_FFT_TC_SPLIT && !dft_tc_supported(L))
         return fail(IDG_ERR_UNSUPPORTED, "the tensor-core subgrid transform is built for subgrid size 32");
-    if (o.adder_mode != IDG_ADDER_ATOMIC && o.adder_mode != IDG_ADDER_COMPENSATED)
+    if (o.adder_mode != IDG_ADDER_ATOMIC && o.adder_mode != IDG_ADDER_COMPENSATED && o.adder_mode != IDG_ADDER_SORTED)
         return fail(IDG_ERR_INVALID_ARG, "unknown adder_mode");
     if (aterm_offsets[0] != 0 || aterm_offsets[n_slots] != n_t)
         return fail(IDG_ERR_INVALID_ARG, "aterm_offsets must start at 0 and end at n_t");
@@ -757,6 +760,31 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
 
     const std::vector<float> ones((size_t)L * L, 1.0f);
 
+    // IDG_ADDER_SORTED: for every grid tile that subgrids overlap, those subgrids in plan order
+    std::vector<int32_t> tile_ids, tile_first, tile_sub;
+    if (o.adder_mode == IDG_ADDER_SORTED && n_sub > 0) {
+        const int ntx = (N + kTile - 1) / kTile;
+        const int64_t per_layer = (int64_t)ntx * ntx, n_tiles = per_layer * p->stats.n_w_layers;
+        std::vector<int32_t> count((size_t)n_tiles + 1, 0);
+        auto each_tile = [&](int64_t s, auto &&fn) {
+            const DevSubgrid &g = hsub[s];
+            for (int ty = g.r0 / kTile; ty <= (g.r0 + L - 1) / kTile; ++ty)
+                for (int tx = g.q0 / kTile; tx <= (g.q0 + L - 1) / kTile; ++tx) fn(g.layer * per_layer + ty * ntx + tx);
+        };
+        for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { ++count[t + 1]; });
+        for (int64_t t = 0; t < n_tiles; ++t) count[t + 1] += count[t];
+        std::vector<int32_t> entries((size_t)count[n_tiles]), fill(count.begin(), count.end() - 1);
+        for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { entries[fill[t]++] = (int32_t)s; });
+        for (int64_t t = 0; t < n_tiles; ++t)
+            if (count[t + 1] > count[t]) {
+                tile_ids.push_back((int32_t)t);
+                tile_first.push_back((int32_t)tile_sub.size());
+                tile_sub.insert(tile_sub.end(), entries.begin() + count[t], entries.begin() + count[t + 1]);
+            }
+        tile_first.push_back((int32_t)tile_sub.size());
+        p->n_tiles_sorted = (int64_t)tile_ids.size();
+    }
+
     struct Up { void **dst; const void *src; size_t bytes; const char *what; };
     Up ups[] = {
         {(void **)&p->d_sub, hsub.data(), sizeof(DevSubgrid) * hsub.size(), "subgrid descriptors"},
@@ -764,6 +792,9 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         {(void **)&p->d_span_order, span_order.data(), sizeof(int32_t) * span_order.size(), "span order"},
         {(void **)&p->d_fused_order, fused_order.data(), sizeof(int32_t) * fused_order.size(), "piece work order"},
         {(void **)&p->d_fused_span, fused_span.data(), sizeof(int32_t) * fused_span.size(), "piece span order"},
+        {(void **)&p->d_tile_ids, tile_ids.data(), sizeof(int32_t) * tile_ids.size(), "sorted adder tiles"},
+        {(void **)&p->d_tile_first, tile_first.data(), sizeof(int32_t) * tile_first.size(), "sorted adder tile lists"},
+        {(void **)&p->d_tile_sub, tile_sub.data(), sizeof(int32_t) * tile_sub.size(), "sorted adder tile subgrids"},
         {(void **)&p->d_uvw, uvw_m, sizeof(double) * n_uvw, "uvw"},
         {(void **)&p->d_scale, scale.data(), sizeof(double) * scale.size(), "channel scales"},
         {(void **)&p->d_scale_f2, scale_f2.data(), sizeof(float) * scale_f2.size(), "channel scale pairs"},
@@ -942,10 +973,20 @@ static int64_t sep_head(const idg_plan *p, Order o, int64_t first, int64_t count
     return pre[first + ns] - pre[first] == ns ? ns : 0;
 }
 
+// the adder's per-call device buffer: the compensation grid (IDG_ADDER_COMPENSATED); none
+// for the atomic and the sorted adder
+static size_t adder_buffer_bytes(const idg_plan *p) {
+    if (p->opts.adder_mode == IDG_ADDER_COMPENSATED) return (size_t)p->stats.n_w_layers * p->N * p->N * 32;
+    return 0;
+}
+static SortedTiles sorted_tiles(const idg_plan *p) {
+    return SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted};
+}
+
 // the composite calls need the subgrid scratch for a part that runs unfused
 static bool grid_needs_scratch(const idg_plan *p, Order o, int64_t first, int64_t count) {
     const int64_t ns = sep_head(p, o, first, count);
-    return p->opts.adder_mode == IDG_ADDER_COMPENSATED || (ns > 0 && !fused_grid(p, true)) ||
+    return p->opts.adder_mode != IDG_ADDER_ATOMIC || (ns > 0 && !fused_grid(p, true)) ||
            (ns < count && !fused_grid(p, false));
 }
 static bool degrid_needs_scratch(const idg_plan *p, Order o, int64_t first, int64_t count) {
@@ -967,6 +1008,9 @@ struct Lists {
     const std::vector<int64_t> *span_first; // span k at [(*span_first)[k], (*span_first)[k + 1])
 };
 static Lists lists_for(const idg_plan *p, bool grid) {
+    // the sorted adder takes its subgrids in chunks of consecutive plan indices
+    if (grid && p->opts.adder_mode == IDG_ADDER_SORTED)
+        return Lists{Order::Plan, Order::Plan, p->stats.n_subgrids, &p->span_first};
     if (use_pieces(p, grid))
         return Lists{Order::Fused, Order::FusedSpan, (int64_t)p->kp_fused_order.size(), &p->fspan_first};
     return Lists{Order::Work, Order::Span, p->stats.n_subgrids, &p->span_first};
@@ -1009,7 +1053,9 @@ static idg_status grid_part(const idg_plan *p, const Geometry &g, Order o, int64
         }
         if (st == IDG_OK) {
             ProfileScope ps(IDG_KERNEL_ADDER, s, 96.0 * pixels(p, cnt));
-            st = cbuf ? launch_adder_compensated(g, set, scratch, grid, cbuf, s) : launch_adder(g, set, scratch, grid, s);
+            st = p->opts.adder_mode == IDG_ADDER_SORTED ? launch_adder_sorted(g, set, scratch, grid, sorted_tiles(p), s)
+                 : cbuf                                 ? launch_adder_compensated(g, set, scratch, grid, cbuf, s)
+                                                        : launch_adder(g, set, scratch, grid, s);
         }
     }
     return st;
@@ -1098,17 +1144,18 @@ static idg_status grid_call(const idg_plan *p, Order o, int64_t first, int64_t c
     if (st != IDG_OK) return st;
     const Geometry g = p->geometry();
     const size_t grid_f4 = (size_t)p->stats.n_w_layers * p->N * p->N * 2;
-    void *cbuf = nullptr;
-    if (comp) {
-        st = scratch_alloc(p->device, grid_f4 * 16, s, &cbuf);
+    const size_t abytes = adder_buffer_bytes(p);
+    void *cbuf = nullptr;      // the compensation grid or the sorted adder's marks, zeroed
+    if (abytes) {
+        st = scratch_alloc(p->device, abytes, s, &cbuf);
         if (st == IDG_OK) {
-            cudaError_t e0 = cudaMemsetAsync(cbuf, 0, grid_f4 * 16, s);
-            if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(compensation)");
+            cudaError_t e0 = cudaMemsetAsync(cbuf, 0, abytes, s);
+            if (e0 != cudaSuccess) st = cuda_fail(e0, "cudaMemsetAsync(adder buffer)");
         }
     }
     if (st == IDG_OK) st = grid_span(p, g, o, first, count, scratch, chunk, vis, flags, aterms, taper, grid, cbuf, s);
-    if (comp && cbuf) {
-        if (st == IDG_OK) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
+    if (cbuf) {
+        if (st == IDG_OK && comp) st = launch_fold_compensation(grid, cbuf, grid_f4, s);
         cudaFreeAsync(cbuf, s);
     }
     cudaError_t e = scratch ? cudaFreeAsync(scratch, s) : cudaSuccess;
@@ -1323,7 +1370,8 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
     const size_t grid_f4 = grid_bytes / 16;
-    if (st == IDG_OK && comp) st = scratch_alloc(p->device, grid_f4 * 16, s, &b.ptr[6]);
+    const size_t abytes = adder_buffer_bytes(p);
+    if (st == IDG_OK && abytes) st = scratch_alloc(p->device, abytes, s, &b.ptr[6]);
     if (st != IDG_OK) return st;
     Events ev;
     cudaEvent_t e_alloc, e_end;
@@ -1332,7 +1380,7 @@ idg_status idg_grid_host(const idg_plan *p, const void *h_vis, const uint8_t *h_
     if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e_alloc, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
-    if (e == cudaSuccess && comp) e = cudaMemsetAsync(b.ptr[6], 0, grid_f4 * 16, s);
+    if (e == cudaSuccess && abytes) e = cudaMemsetAsync(b.ptr[6], 0, abytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "grid_host setup");
     if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;
     if ((st = h2d(b.ptr[3], h_taper, sizes[3], cs, "copy of taper")) != IDG_OK) return st;
@@ -1465,7 +1513,8 @@ idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void
     for (int k = 0; k < 6 && st == IDG_OK; ++k)
         if (sizes[k]) st = scratch_alloc(p->device, sizes[k], s, &b.ptr[k]);
     const size_t grid_f4 = grid_bytes / 16;
-    if (st == IDG_OK && comp) st = scratch_alloc(p->device, grid_f4 * 16, s, &b.ptr[6]);
+    const size_t abytes = adder_buffer_bytes(p);
+    if (st == IDG_OK && abytes) st = scratch_alloc(p->device, abytes, s, &b.ptr[6]);
     if (st == IDG_OK) st = scratch_alloc(p->device, grid_bytes, s, &b2.ptr[0]);       // model grid
     if (st == IDG_OK) st = scratch_alloc(p->device, nvis * 32, s, &b2.ptr[1]);        // model visibilities
     if (st != IDG_OK) return st;
@@ -1479,7 +1528,7 @@ idg_status idg_grid_degrid_host(const idg_plan *p, const void *h_vis, const void
     if (e == cudaSuccess) e = cudaEventRecord(e_alloc, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e_alloc, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.ptr[4], 0, grid_bytes, s);
-    if (e == cudaSuccess && comp) e = cudaMemsetAsync(b.ptr[6], 0, grid_f4 * 16, s);
+    if (e == cudaSuccess && abytes) e = cudaMemsetAsync(b.ptr[6], 0, abytes, s);
     if (e == cudaSuccess && p->any_dropped) e = cudaMemsetAsync(b2.ptr[1], 0, nvis * 32, s);
     if (e != cudaSuccess) return cuda_fail(e, "grid_degrid_host setup");
     if ((st = h2d(b.ptr[2], h_aterms, at_bytes, cs, "copy of A-terms")) != IDG_OK) return st;

@@ -127,6 +127,12 @@ struct idg_plan {
     std::vector<int32_t> kp_fused_order, kp_fused_span;
     std::vector<int64_t> kp_prefix_fused, kp_prefix_fspan, sep_prefix_fused, sep_prefix_fspan;
     std::vector<int64_t> fspan_first;
+    // IDG_ADDER_SORTED: the tiles of the grid that subgrids overlap, with those subgrids
+    // (plan indices, ascending); see SortedTiles
+    int32_t *d_tile_ids = nullptr;
+    int32_t *d_tile_first = nullptr;
+    int32_t *d_tile_sub = nullptr;
+    int64_t n_tiles_sorted = 0;
     float c_scale = 1.0f;
     float r_scale = 1.0f;
     bool any_dropped = false;
@@ -266,6 +272,21 @@ idg_status launch_gridder_tcw_fused(const Geometry &g, const SubgridSet &set, co
                                     const void *aterms, const float *taper, void *grid, void *stream);
 idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, const void *grid, const uint8_t *flags,
                                       const void *aterms, const float *taper, void *vis_out, void *stream);
+// the sorted (deterministic) adder's tiles: kTile x kTile grid pixels per layer; for each of
+// the n_tiles tiles that subgrids overlap, its id (layer (ntx ntx) + ty ntx + tx, ntx =
+// ceil(N / kTile)) and the plan indices of those subgrids, ascending, at
+// tile_sub[tile_first[k] .. tile_first[k + 1]) (device arrays)
+constexpr int kTile = 32;
+struct SortedTiles {
+    const int32_t *tile_ids;
+    const int32_t *tile_first;
+    const int32_t *tile_sub;
+    int64_t n_tiles;
+};
+// adds the images of the set's subgrids (consecutive plan indices: set.first + i in scratch
+// slot i) into the grid tile by tile in plan-index order
+idg_status launch_adder_sorted(const Geometry &g, const SubgridSet &set, const void *sub, void *grid,
+                               const SortedTiles &t, void *stream);
 // the fused kernels of one job of a batch (the plan's geometry, a set of its d_sub entries),
 // as a programmatic dependent launch when pdl (see tc_common.cuh)
 idg_status launch_gridder_sep_job(const Geometry &g, const SubgridSet &set, const void *vis, const uint8_t *flags,

@@ -21,9 +21,9 @@
 // device's context lives as long as the process: after cudaDeviceReset the
 // cached address is stale, and the call is not supported.
 //
-// Only the plain atomic adder can run here: the compensated adder needs a
-// grid-sized compensation buffer, which this call cannot allocate, so plans
-// with IDG_ADDER_COMPENSATED are refused.
+// The compensated adder needs a grid-sized compensation buffer, which this call
+// cannot allocate, so plans with IDG_ADDER_COMPENSATED are refused.  The sorted
+// adder (IDG_ADDER_SORTED) needs no buffer: its plans run in plan order.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -97,9 +97,15 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
     // FFT and the adder read it, so nothing in the scratch has to start at zero.
     cudaStream_t s = (cudaStream_t)stream;
     const Geometry g = p->geometry();
-    const SubgridSet all{p->d_order, 0, n, p->kp_order.data()};
+    // (the sorted adder takes the subgrids in plan order: slot i holds plan index i)
+    const bool sorted = p->opts.adder_mode == IDG_ADDER_SORTED;
+    const SubgridSet all = sorted ? SubgridSet{nullptr, 0, n, p->kp_plan.data()}
+                                  : SubgridSet{p->d_order, 0, n, p->kp_order.data()};
     st = launch_gridder(g, all, p->kernel_variant(IDG_KERNEL_GRIDDER), vis, flags, aterms, taper, scratch, s);
     if (st == IDG_OK) st = launch_subgrid_fft(p, n, -1, scratch, s);
-    if (st == IDG_OK) st = launch_adder(g, all, scratch, grid, s);
+    if (st == IDG_OK)
+        st = sorted ? launch_adder_sorted(g, all, scratch, grid,
+                                          SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted}, s)
+                    : launch_adder(g, all, scratch, grid, s);
     return st;
 }

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "IDG_OK", 1: "IDG_ERR_INVALID_ARG", 2: "IDG_ERR_NO_MEMORY", 3
 DESC_FIELDS = 10
 PHASOR_SINCOS, PHASOR_RECURRENCE = 0, 1
 FFT_FP32, FFT_TC_SPLIT = 0, 1
-ADDER_ATOMIC, ADDER_COMPENSATED = 0, 1
+ADDER_ATOMIC, ADDER_COMPENSATED, ADDER_SORTED = 0, 1, 2
 
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTED = [

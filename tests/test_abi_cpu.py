@@ -98,6 +98,7 @@ def _create(**over):
     (dict(max_timesteps_per_subgrid=0), "max_timesteps"),
     (dict(kernel_size=float("nan")), "kernel_size"),
     (dict(precision_mode=7), "precision_mode"),
+    (dict(adder_mode=3), "adder_mode"),
     (dict(aterm_offsets=np.array([0, 5, 5, 8], dtype=np.int32)), "increasing"),
     (dict(aterm_offsets=np.array([1, 8], dtype=np.int32)), "start at 0"),
     (dict(baselines=np.array([[0, 9]] * 6, dtype=np.int32)), "station"),
