@@ -775,11 +775,15 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         for (int64_t t = 0; t < n_tiles; ++t) count[t + 1] += count[t];
         std::vector<int32_t> entries((size_t)count[n_tiles]), fill(count.begin(), count.end() - 1);
         for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { entries[fill[t]++] = (int32_t)s; });
-        for (int64_t t = 0; t < n_tiles; ++t)
-            if (count[t + 1] > count[t]) {
+        // the tiles with short lists first, then those with long lists (one cluster each)
+        for (int heavy = 0; heavy < 2; ++heavy)
+            for (int64_t t = 0; t < n_tiles; ++t) {
+                const int32_t len = count[t + 1] - count[t];
+                if (len == 0 || (len > kHeavyEntries) != (heavy == 1)) continue;
                 tile_ids.push_back((int32_t)t);
                 tile_first.push_back((int32_t)tile_sub.size());
                 tile_sub.insert(tile_sub.end(), entries.begin() + count[t], entries.begin() + count[t + 1]);
+                p->n_heavy_sorted += heavy;
             }
         tile_first.push_back((int32_t)tile_sub.size());
         p->n_tiles_sorted = (int64_t)tile_ids.size();
@@ -980,7 +984,7 @@ static size_t adder_buffer_bytes(const idg_plan *p) {
     return 0;
 }
 static SortedTiles sorted_tiles(const idg_plan *p) {
-    return SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted};
+    return SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted, p->n_heavy_sorted};
 }
 
 // the composite calls need the subgrid scratch for a part that runs unfused

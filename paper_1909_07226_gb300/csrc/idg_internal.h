@@ -133,6 +133,7 @@ struct idg_plan {
     int32_t *d_tile_first = nullptr;
     int32_t *d_tile_sub = nullptr;
     int64_t n_tiles_sorted = 0;
+    int64_t n_heavy_sorted = 0;
     float c_scale = 1.0f;
     float r_scale = 1.0f;
     bool any_dropped = false;
@@ -275,13 +276,18 @@ idg_status launch_degridder_tcw_fused(const Geometry &g, const SubgridSet &set, 
 // the sorted (deterministic) adder's tiles: kTile x kTile grid pixels per layer; for each of
 // the n_tiles tiles that subgrids overlap, its id (layer (ntx ntx) + ty ntx + tx, ntx =
 // ceil(N / kTile)) and the plan indices of those subgrids, ascending, at
-// tile_sub[tile_first[k] .. tile_first[k + 1]) (device arrays)
+// tile_sub[tile_first[k] .. tile_first[k + 1]) (device arrays).  The rows of tiles whose
+// list is longer than kHeavyEntries come last (n_heavy of them); each takes a cluster of
+// kHeavyCluster CTAs
 constexpr int kTile = 32;
+constexpr int kHeavyEntries = 64;
+constexpr int kHeavyCluster = 8;
 struct SortedTiles {
     const int32_t *tile_ids;
     const int32_t *tile_first;
     const int32_t *tile_sub;
     int64_t n_tiles;
+    int64_t n_heavy;
 };
 // adds the images of the set's subgrids (consecutive plan indices: set.first + i in scratch
 // slot i) into the grid tile by tile in plan-index order

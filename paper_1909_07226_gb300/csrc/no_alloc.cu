@@ -105,7 +105,8 @@ extern "C" idg_status idg_grid_no_alloc(const idg_plan *p, const void *vis, cons
     if (st == IDG_OK) st = launch_subgrid_fft(p, n, -1, scratch, s);
     if (st == IDG_OK)
         st = sorted ? launch_adder_sorted(g, all, scratch, grid,
-                                          SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted}, s)
+                                          SortedTiles{p->d_tile_ids, p->d_tile_first, p->d_tile_sub, p->n_tiles_sorted,
+                                                      p->n_heavy_sorted}, s)
                     : launch_adder(g, all, scratch, grid, s);
     return st;
 }

@@ -1,9 +1,11 @@
 """GPU tests of the sorted (deterministic) adder, IDG_ADDER_SORTED: one CTA per 32 x 32
 grid tile sums the subgrids that overlap it in plan order and adds the sum with plain
-stores.  The grid matches the FP64 oracle (relative RMS <= 1e-5, tests.gpu_util.parity)
-and is the same bit for bit on repeated calls, through the device-buffer composite call
-(mixed plan: separable and direct parts), plan-order ranges, W-layers and the host-buffer
-call; idg_grid_no_alloc gives the same bits as idg_grid."""
+stores; a tile that more than 64 subgrids overlap takes a cluster of 8 CTAs, each summing
+a fixed segment of the tile's list, the partial sums added in rank order.  The grid
+matches the FP64 oracle (relative RMS <= 1e-5, tests.gpu_util.parity) and is the same bit
+for bit on repeated calls, through the device-buffer composite call (mixed plan:
+separable and direct parts), plan-order ranges, W-layers and the host-buffer call;
+idg_grid_no_alloc gives the same bits as idg_grid."""
 import numpy as np
 import pytest
 
@@ -23,6 +25,13 @@ CASES = {
     # a grid size that is not a multiple of the tile (partial tiles at the edges)
     "L16_ragged_tiles": dict(seed=95, n_st=6, n_t=48, n_chan=4, L=16, N=200, max_t=16, n_slots=1, flag_p=0.0,
                              diameter_m=1500.0),
+    # short baselines, short subgrids: 896 subgrids on a few central tiles, 12 (L = 16) and 17
+    # (L = 24, ragged edge) of them overlapped by more than 64 subgrids (up to 145 and 205),
+    # beside tiles with short lists
+    "L16_heavy_tiles": dict(seed=96, n_st=8, n_t=256, n_chan=4, L=16, N=256, max_t=8, n_slots=2, flag_p=0.05,
+                            diameter_m=300.0),
+    "L24_heavy_tiles_ragged": dict(seed=96, n_st=8, n_t=256, n_chan=4, L=24, N=200, max_t=8, n_slots=2,
+                                   flag_p=0.05, diameter_m=300.0),
 }
 
 
@@ -51,9 +60,12 @@ def test_sorted_adder_matches_the_oracle_bit_for_bit_on_repeats(case):
     parity(outs[0], O.grid(wl, op), f"sorted adder {case}")
 
 
-def test_sorted_adder_ranges_and_host_buffers():
+@pytest.mark.parametrize("case", ["L32_mixed", "L24_heavy_tiles_ragged"])
+def test_sorted_adder_ranges_and_host_buffers(case):
+    # (in the heavy-tile case the range boundary cuts the long lists: each range's part of
+    # a list is split over the cluster on its own)
     import torch
-    wl = syn.make_small(**CASES["L32_mixed"])
+    wl = syn.make_small(**CASES[case])
     p = idg.plan_from_workload(wl, adder_mode=idg.ADDER_SORTED)
     op = O.plan(wl)
     d = workload_to_device(wl)
@@ -62,17 +74,18 @@ def test_sorted_adder_ranges_and_host_buffers():
     idg.grid_range(p, 0, n // 2, d["vis"], d["flags"], d["aterms"], d["taper"], g)
     idg.grid_range(p, n // 2, n - n // 2, d["vis"], d["flags"], d["aterms"], d["taper"], g)
     idg.device_errors()
-    parity(g.cpu().numpy(), O.grid(wl, op), "sorted adder, two ranges")
+    parity(g.cpu().numpy(), O.grid(wl, op), f"sorted adder, two ranges {case}")
     gh = np.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=np.complex64)
     idg.grid_host(p, wl.vis.astype(np.complex64), wl.flags, wl.aterms.astype(np.complex64),
                   wl.taper.astype(np.float32), gh)
-    parity(gh, O.grid(wl, op), "sorted adder, host buffers")
+    parity(gh, O.grid(wl, op), f"sorted adder, host buffers {case}")
 
 
-def test_no_alloc_with_the_sorted_adder():
+@pytest.mark.parametrize("case", ["L16_ragged_tiles", "L16_heavy_tiles"])
+def test_no_alloc_with_the_sorted_adder(case):
     # the static scratch holds the whole plan in plan order: the same bits as idg_grid
     import torch
-    wl = syn.make_small(**CASES["L16_ragged_tiles"])
+    wl = syn.make_small(**CASES[case])
     p = idg.plan_from_workload(wl, adder_mode=idg.ADDER_SORTED)
     d = workload_to_device(wl)
     shape = (p.n_w_layers, wl.grid_size, wl.grid_size, 4)
@@ -83,4 +96,4 @@ def test_no_alloc_with_the_sorted_adder():
     idg.device_errors()
     a, b = g0.cpu().numpy(), g1.cpu().numpy()
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
-    parity(a, O.grid(wl, O.plan(wl)), "sorted adder, no allocation")
+    parity(a, O.grid(wl, O.plan(wl)), f"sorted adder, no allocation {case}")
