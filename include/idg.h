@@ -101,10 +101,13 @@ enum { IDG_ADDER_ATOMIC = 0,       /* 16-byte vector atomic adds                
                                       chunks of consecutive subgrids; one CTA per 32 x 32
                                       grid tile sums the chunk's subgrids that overlap
                                       it in plan order (plan-held tile lists) and adds
-                                      the sum with plain stores.  The grid is the same
-                                      bit for bit on every run (for a given plan and
-                                      device), with no atomics.  Batches add with
-                                      atomics whatever the plan's adder.            */
+                                      the sum with plain stores; a tile that more than
+                                      64 subgrids of the plan overlap takes a cluster of
+                                      8 CTAs, fixed segments of its list summed apart and
+                                      added in rank order.  The grid is the same bit for
+                                      bit on every run (for a given plan, device and
+                                      range boundaries), with no atomics.  Batches add
+                                      with atomics whatever the plan's adder.       */
 
 typedef struct {
     int64_t n_subgrids;       /* P, number of blocks                              */
