@@ -5,7 +5,8 @@ front, or a host framework whose allocator already holds all free device
 memory) use this entry point, whose subgrid scratch is a fixed 64 MiB array
 inside the library.  The test calls it through the C ABI twice in a row, on
 two different plans, and compares each result with idg_grid's on the same
-inputs within the parity tolerance of the other GPU tests.  It also checks
+inputs within the parity tolerance of the other GPU tests, and with the FP64
+oracle (the default and the recurrence + split tensor-core forms).  It also checks
 that an over-size plan is refused before any work is done and that a call
 leaves the free device memory unchanged.  This file is collected last, so a
 run that stops at the first failure has run every other test already.
@@ -51,14 +52,31 @@ def _reference_and_no_alloc(wl, **opt):
     return p, ref.cpu().numpy(), out.cpu().numpy()
 
 
+def _w_layer_workload():
+    return syn.make_small(seed=515, n_st=7, n_t=40, n_chan=6, L=32, N=256, max_t=10, n_slots=2, flag_p=0.1,
+                          w_step=20.0, diameter_m=15000.0)
+
+
+@pytest.mark.parametrize("form", ["default", "recurrence_tc_split"])
+@pytest.mark.parametrize("case", ["tiny", "L32_w_layers"])
+def test_no_alloc_matches_the_oracle(case, form):
+    # against the FP64 oracle itself (Alg. 1 end to end), not only against idg_grid
+    from oracle import oracle as O
+    wl = syn.make_tiny() if case == "tiny" else _w_layer_workload()
+    if form == "recurrence_tc_split" and wl.subgrid_size != 32:
+        pytest.skip("the split tensor-core transform is built for L = 32")
+    opt = {} if form == "default" else dict(precision_mode=idg.PHASOR_RECURRENCE, fft_mode=idg.FFT_TC_SPLIT)
+    _, _, out = _reference_and_no_alloc(wl, **opt)
+    parity(out, O.grid(wl, O.plan(wl)), f"no-alloc {case} {form} vs oracle")
+
+
 def test_no_alloc_matches_idg_grid_on_two_calls_in_a_row():
     # first call: the tiny workload (112 subgrids of 24 x 24)
     p1, ref1, out1 = _reference_and_no_alloc(syn.make_tiny())
     parity(out1, ref1, "no-alloc call 1 vs idg_grid")
     # second call: another plan with more subgrids, A-terms, flags, W-layers;
     # the scratch still holds call 1's subgrids and must not leak into it
-    wl2 = syn.make_small(seed=515, n_st=7, n_t=40, n_chan=6, L=32, N=256, max_t=10, n_slots=2, flag_p=0.1,
-                         w_step=20.0, diameter_m=15000.0)
+    wl2 = _w_layer_workload()
     p2, ref2, out2 = _reference_and_no_alloc(wl2)
     assert p2.n_subgrids > p1.n_subgrids and p2.n_w_layers > 1
     parity(out2, ref2, "no-alloc call 2 vs idg_grid")
