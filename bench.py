@@ -1076,6 +1076,17 @@ def run_precision(args, world, rank, local):
         ms = e0.elapsed_time(e1) / args.steps
         out[name]["mvis_per_s"] = wl.n_vis / ms / 1e3
         out[name]["ms_per_step"] = ms
+        # after the timed steps: one grid call under the library's per-kernel event profile
+        idg.profile_enable(True)
+        try:
+            idg.profile_read(reset=True)
+            grid.zero_()
+            idg.grid(p, vis, None, aterms, taper, grid, stream)
+            torch.cuda.synchronize()
+            out[name]["grid_stage_ms"] = {k: round(v["ms"], 3) for k, v in idg.profile_read(reset=True).items()
+                                          if v["launches"]}
+        finally:
+            idg.profile_enable(False)
         p.destroy()
     clocks = sampler.stop()
     best = max(out.values(), key=lambda r: r["mvis_per_s"])
