@@ -457,6 +457,10 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         return fail(IDG_ERR_NO_MEMORY, "host allocation in the planner failed");
     }
     const int64_t n_sub = (int64_t)(pr.desc.size() / kDescFields);
+    if (n_sub > INT32_MAX) {              // work orders, spans and tile lists hold int32 indices
+        delete p;
+        return fail(IDG_ERR_INVALID_ARG, "the plan has more subgrids than 32-bit subgrid indices hold");
+    }
     p->desc = std::move(pr.desc);
     memset(&p->stats, 0, sizeof p->stats);
     p->stats.n_subgrids = n_sub;
@@ -598,6 +602,10 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
         g.dws = (float)(2.0 * (ws - g.w0));
     }
     const int64_t n_pc = (int64_t)p->pieces.size();
+    if (n_sub + n_pc > INT32_MAX) {
+        delete p;
+        return fail(IDG_ERR_INVALID_ARG, "the plan's subgrids and pieces exceed 32-bit work indices");
+    }
     if (n_pc > 0) hsub.resize((size_t)(n_sub + n_pc));
     for (int64_t i = 0; i < n_pc; ++i) {
         const idg_plan::Piece &pc = p->pieces[i];
@@ -771,8 +779,14 @@ idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const in
             for (int ty = g.r0 / kTile; ty <= (g.r0 + L - 1) / kTile; ++ty)
                 for (int tx = g.q0 / kTile; tx <= (g.q0 + L - 1) / kTile; ++tx) fn(g.layer * per_layer + ty * ntx + tx);
         };
-        for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { ++count[t + 1]; });
-        for (int64_t t = 0; t < n_tiles; ++t) count[t + 1] += count[t];
+        std::vector<int64_t> total((size_t)n_tiles + 1, 0);
+        for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { ++total[t + 1]; });
+        for (int64_t t = 0; t < n_tiles; ++t) total[t + 1] += total[t];
+        if (total[n_tiles] > INT32_MAX) {
+            delete p;
+            return fail(IDG_ERR_INVALID_ARG, "the sorted adder's tile lists exceed 32-bit offsets");
+        }
+        for (int64_t t = 0; t <= n_tiles; ++t) count[t] = (int32_t)total[t];
         std::vector<int32_t> entries((size_t)count[n_tiles]), fill(count.begin(), count.end() - 1);
         for (int64_t s = 0; s < n_sub; ++s) each_tile(s, [&](int64_t t) { entries[fill[t]++] = (int32_t)s; });
         // the tiles with short lists first, then those with long lists (one cluster each)
