@@ -181,8 +181,9 @@ void idg_plan_options_default(idg_plan_options *opts);
  * w_step_lambda  >= 0, W-layer spacing in wavelengths (0: no W-layers)
  * opts           NULL for defaults
  * out            receives the plan (NULL on failure)
- * Errors: IDG_ERR_INVALID_ARG (message says which argument), IDG_ERR_NO_MEMORY,
- *         IDG_ERR_CUDA.
+ * Errors: IDG_ERR_INVALID_ARG (message says which argument, or that the plan's
+ *         subgrids, pieces or sorted-adder tile lists exceed 32-bit indices),
+ *         IDG_ERR_NO_MEMORY, IDG_ERR_CUDA.
  */
 idg_status idg_plan_create(const double *uvw_m, const double *freqs_hz, const int32_t *baselines,
                            const int32_t *aterm_offsets, int n_bl, int n_t, int n_chan,
