@@ -417,7 +417,9 @@ idg_status idg_grid_no_alloc(const idg_plan *plan, const void *d_vis, const uint
  * idg_grid_subgrids    direct sum + taper + A_p^H . A_q  (image domain)
  * idg_fft_subgrids     in-place centred transform, direction -1 (image -> uv,
  *                      Alg. 1) or +1 (uv -> image, Alg. 2), both scaled by L^-2
- * idg_add_subgrids     grid[layer][r0 + i][q0 + j] += subgrid[i][j]
+ * idg_add_subgrids     grid[layer][r0 + i][q0 + j] += subgrid[i][j] (atomic adds; the
+ *                      sorted tile adder for IDG_ADDER_SORTED plans, so the same bits
+ *                      on every call; compensated plans add with plain atomics here)
  * idg_split_subgrids   subgrid[i][j] = grid[layer][r0 + i][q0 + j]
  * idg_degrid_subgrids  taper + A_p . A_q^H, then the degridding sum, from image
  *                      domain subgrids; writes only the visibilities of these

@@ -1638,6 +1638,8 @@ idg_status idg_add_subgrids(const idg_plan *p, int64_t first, int64_t count, con
     if (st != IDG_OK) return st;
     if ((st = check_range(p, first, count)) != IDG_OK || count == 0) return st;
     ProfileScope ps(IDG_KERNEL_ADDER, stream, 96.0 * pixels(p, count));
+    if (p->opts.adder_mode == IDG_ADDER_SORTED)   // (a plan-order range is what the sorted adder takes)
+        return launch_adder_sorted(p->geometry(), plan_set(p, first, count), sub, grid, sorted_tiles(p), stream);
     return launch_adder(p->geometry(), plan_set(p, first, count), sub, grid, stream);
 }
 

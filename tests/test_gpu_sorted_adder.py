@@ -97,3 +97,24 @@ def test_no_alloc_with_the_sorted_adder(case):
     a, b = g0.cpu().numpy(), g1.cpu().numpy()
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
     parity(a, O.grid(wl, O.plan(wl)), f"sorted adder, no allocation {case}")
+
+
+def test_stage_add_of_a_sorted_plan():
+    # idg_add_subgrids of a sorted plan takes the tile adder: the same bits on every call,
+    # and the oracle's grid after the stage gridder and transform
+    import torch
+    wl = syn.make_small(**CASES["L24_heavy_tiles_ragged"])
+    p = idg.plan_from_workload(wl, adder_mode=idg.ADDER_SORTED)
+    d = workload_to_device(wl)
+    n, L = p.n_subgrids, wl.subgrid_size
+    sub = torch.zeros((n, L, L, 4), dtype=torch.complex64, device="cuda")
+    idg.grid_subgrids(p, 0, n, d["vis"], d["flags"], d["aterms"], d["taper"], sub)
+    idg.fft_subgrids(p, n, -1, sub)
+    outs = []
+    for _ in range(2):
+        g = torch.zeros((p.n_w_layers, wl.grid_size, wl.grid_size, 4), dtype=torch.complex64, device="cuda")
+        idg.add_subgrids(p, 0, n, sub, g)
+        outs.append(g.cpu().numpy())
+    idg.device_errors()
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+    parity(outs[0], O.grid(wl, O.plan(wl)), "sorted plan, stage calls")
