@@ -4,8 +4,8 @@ stores; a tile that more than 64 subgrids overlap takes a cluster of 8 CTAs, eac
 a fixed segment of the tile's list, the partial sums added in rank order.  The grid
 matches the FP64 oracle (relative RMS <= 1e-5, tests.gpu_util.parity) and is the same bit
 for bit on repeated calls, through the device-buffer composite call (mixed plan:
-separable and direct parts), plan-order ranges, W-layers and the host-buffer call;
-idg_grid_no_alloc gives the same bits as idg_grid."""
+separable and direct parts), plan-order ranges, W-layers, the host-buffer call and the
+stage add; idg_grid_no_alloc gives the same bits as idg_grid."""
 import numpy as np
 import pytest
 
