@@ -185,14 +185,15 @@ static void split_pieces(idg_plan *p, int64_t s, double r_max, const double *uvw
     const int64_t max_pieces = std::min<int64_t>((int64_t)((rho - 1.0) * (double)kp / F), (int64_t)nt * nc);
     // w range (wavelengths) of the block [ta, tb) x [ca, cb): w_t f is linear in f, so the
     // channel ends bound it
+    // (every block has at least one timestep and one channel: kt <= nt, kc <= nc)
     auto range = [&](int ta, int tb, int ca, int cb, double *lo, double *hi) {
         const double fa = freqs_hz[ca] / kSpeedOfLight, fb = freqs_hz[cb - 1] / kSpeedOfLight;
+        *lo = INFINITY;
+        *hi = -INFINITY;
         for (int t = ta; t < tb; ++t) {
             const double w = uvw[((size_t)d[IDG_DESC_BASELINE] * p->n_t + t) * 3 + 2];
-            const double a = std::min(w * fa, w * fb), b = std::max(w * fa, w * fb);
-            if (t == ta) *lo = a, *hi = b;
-            *lo = std::min(*lo, a);
-            *hi = std::max(*hi, b);
+            *lo = std::min(*lo, std::min(w * fa, w * fb));
+            *hi = std::max(*hi, std::max(w * fa, w * fb));
         }
     };
     auto meets = [&](double lo, double hi) { return kTwoPi * 0.5 * (hi - lo) * r_max <= kSepThetaMax; };
