@@ -187,3 +187,35 @@ def test_kernel_choice_is_per_plan(lib):
         idg.plan_set_kernel_variant(a, "gridder", n)
     with pytest.raises(idg.IDGError):
         idg.plan_set_kernel_variant(a, "adder", 0)
+
+
+def header_enums():
+    """Every enumerator of include/idg.h with its value (implicit ones counted on)."""
+    text = open(os.path.join(ROOT, "include", "idg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = (x.strip() for x in item.partition("="))
+            nxt = int(val) if val else nxt
+            values[name] = nxt
+            nxt += 1
+    return values
+
+
+def test_binding_constants_match_the_header():
+    e = header_enums()
+    for py in ("PHASOR_SINCOS", "PHASOR_RECURRENCE", "FFT_FP32", "FFT_TC_SPLIT", "ADDER_ATOMIC",
+               "ADDER_COMPENSATED", "ADDER_SORTED", "TAPER_PSWF", "TAPER_IDG_OPTIMAL", "BATCH_GRAPH"):
+        assert getattr(idg, py) == e["IDG_" + py], py
+    assert idg.STATUS_NAMES == {v: k for k, v in e.items() if k == "IDG_OK" or k.startswith("IDG_ERR_")}
+    kernels = sorted((v, k) for k, v in e.items() if k.startswith("IDG_KERNEL_") and k != "IDG_KERNEL_COUNT")
+    assert idg.KERNELS == [k[len("IDG_KERNEL_"):].lower() for _, k in kernels]
+    assert e["IDG_KERNEL_COUNT"] == len(idg.KERNELS)
+    desc = sorted((v, k) for k, v in e.items() if k.startswith("IDG_DESC_"))
+    assert [v for v, _ in desc] == list(range(idg.DESC_FIELDS))
+    assert [k for _, k in desc][:2] == ["IDG_DESC_BASELINE", "IDG_DESC_SLOT"]
