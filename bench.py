@@ -74,6 +74,8 @@ def sep_degrid_flop_per_tile(L):
 # contraction (hi x hi) is the other half.
 SEP_USEFUL_SHARE = 0.5
 DTYPE_SEP = "f32 (fp16 hi/lo split tensor-core products, fp32 accumulate)"
+DTYPE_MIXED = ("f32 (fp16 hi/lo split tensor-core products for subgrids within the separable bound and "
+               "pieces, packed fp32 for the rest; fp32 accumulate)")
 KERNEL_TRAFFIC = {
     "gridder": {SEP_VARIANT: (178.5e6 + 5.6e6) / 4.731e9},
     "degridder": {SEP_VARIANT: (31.2e6 + 92.4e6) / 4.731e9},
@@ -932,7 +934,7 @@ def run_batched(args, world, rank, local):
         "metric": "grid+degrid MVis/s (batched form vs plain per-job form)", "value": r["batched_mvis_per_s"],
         "unit": "MVis/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": r["batched_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": DTYPE_MIXED, "data": "synthetic",
         "config": {"workload": f"Batched uneven: {args.jobs} snapshot jobs, U{{12..64}} stations, U{{64..1024}} t, "
                                f"U{{4..32}} ch of 0.2 MHz in 100-200 MHz, 0-20% flags, L in {{16,24,32}}, "
                                f"N in {{1024,2048,4096}}", "jobs": args.jobs, "n_vis": r["n_vis"],
@@ -981,7 +983,7 @@ def run_serving(args, world, rank, local):
         "metric": "grid+degrid MVis/s and latency (serving form vs plain per-job FIFO)",
         "value": srv["grid_degrid_mvis_per_s"],
         "unit": "MVis/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * srv["makespan_s"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_MIXED, "data": "synthetic",
         "config": {"workload": f"Serving: Poisson arrivals, {args.jobs} requests from the batched "
                                f"distribution, kinds {list(kinds)} (uniform), 5 major cycles per cycle job, "
                                f"150 GB admission budget, 32 slots; rates {args.rate} and {4 * args.rate} jobs/s",
@@ -1054,9 +1056,12 @@ def run_precision(args, world, rank, local):
     sampler = ClockSampler(local)
     sampler.start()
     n_sub = None
+    direct_separable = False
     for name, kw in forms.items():
         p = idg.plan_from_workload(wl, **kw)
         n_sub = p.n_subgrids
+        if name == "direct_sincos":
+            direct_separable = bool(p.stats.separable)
 
         def step():
             grid.zero_()
@@ -1093,7 +1098,8 @@ def run_precision(args, world, rank, local):
     rec = {"metric": "grid+degrid MVis/s per precision form, with error vs the FP64 oracle",
            "value": out["direct_sincos"]["mvis_per_s"], "unit": "MVis/s", "n_gpus": 1, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": out["direct_sincos"]["ms_per_step"],
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": DTYPE_SEP if direct_separable else DTYPE_MIXED, "data": "synthetic",
            "config": {"workload": "Precision: LOFAR-like with A-terms every 16 timesteps (256 slots); accuracy on "
                                   "the first 256 timesteps against the FP64 oracle", "n_vis": int(wl.n_vis),
                       "n_subgrids": n_sub},
